@@ -1,0 +1,194 @@
+/*
+ * fe.h - C ABI of libfe, the GB300 (sm_103a) iPiano solver for the
+ * Fields-of-Experts despeckling model with the I-divergence data term.
+ *
+ * Problem (Chen et al., "A higher-order MRF based variational model for
+ * multiplicative noise reduction"; Eq. variant of Sec. II-B):
+ *
+ *     argmin_{u > 0}  H(u) = F(u) + G(u)
+ *     F(u) = sum_i theta_i sum_p log(1 + (k_i * u)_p^2)      (Eq. FOEmodel)
+ *     G(u) = (lambda / 2) sum_p (u_p^2 - 2 f_p^2 log u_p)    (Eq. dataterm2)
+ *
+ * solved by iPiano (Sec. II-C, Eq. fplusg and the update rule under it):
+ *
+ *     u^{n+1} = prox_{alpha_n G}(u^n - alpha_n grad F(u^n) + beta (u^n - u^{n-1}))
+ *     grad F(u) = sum_i theta_i K_i^T rho'(K_i u),  rho'(z) = 2z / (1 + z^2)
+ *     prox: u_p = (uhat_p + sqrt(uhat_p^2 + 4(1+tau l) tau l f_p^2)) / (2(1+tau l))
+ *
+ * Conventions that the paper leaves open (fixed here, identical to the FP64
+ * oracle used by the tests):
+ *   - k_i * u is a true 2-D convolution of the image extended by 3 pixels with
+ *     half-sample symmetric reflection (... c b a | a b c ...); K_i^T is the
+ *     exact transpose of that linear map (boundary fold included).
+ *   - alpha_n = 2 (1 - beta) / (L_n + 2 c2).  A trial is accepted iff
+ *       F(u^{n+1}) <= F(u^n) + <grad F(u^n), u^{n+1} - u^n> + L_n/2 |u^{n+1} - u^n|^2
+ *     else L_n <- eta L_n and the trial is redone (at most max_backtrack
+ *     times per iteration).  L is never decreased.  u^{-1} = u^0.
+ *   - Convergence: |H^{n+1} - H^n| / |H^{n+1}| < tol.
+ *
+ * Data layout: every image is a dense row-major float32 array, pitch = W.
+ * Pointers named "any" may be host (pageable or pinned) or device pointers of
+ * the current device; copies use cudaMemcpyDefault.  Device pointers must be
+ * 4-byte aligned.  The library keeps its own device state (iterates, gradient,
+ * f^2, per-tile partial sums) and frees it in fe_destroy.
+ *
+ * Errors: no call aborts or throws across the ABI.  Every call returns an
+ * fe_status; fe_last_error() gives a message for the last failure on a
+ * context.  Calls are stream-ordered on the stream given to fe_init; calls
+ * that return host values synchronise that stream.
+ *
+ * Threads: a context must not be used by two host threads at once.
+ */
+#ifndef FE_H
+#define FE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FE_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define FE_API __attribute__((visibility("default")))
+#else
+#define FE_API
+#endif
+
+typedef enum {
+    FE_OK = 0,
+    FE_EINVAL = 1,          /* bad argument (null, size < 8, f <= 0 or not finite, ...) */
+    FE_ENOMEM = 2,          /* device allocation failed */
+    FE_ECUDA = 3,           /* a CUDA runtime call failed */
+    FE_ENONFINITE = 4,      /* a trial produced a non-finite energy/step */
+    FE_EBACKTRACK = 5,      /* more than max_backtrack rejections in one iteration */
+    FE_ETIMEOUT = 6,        /* the device-side trial budget ran out */
+    FE_ENOTCONVERGED = 7,   /* fe_solve hit max_iter before the tolerance */
+    FE_EUNSUPPORTED = 8     /* option not available in this build */
+} fe_status;
+
+typedef enum {
+    FE_FP32 = 0,            /* filter bank in FP32 FFMA (parity-grade) */
+    FE_TF32 = 1,            /* filter bank on the tensor cores, TF32 operands */
+    FE_BF16 = 2             /* filter bank on the tensor cores, BF16 operands */
+} fe_precision;
+
+/* Solver parameters.  All pointers are HOST pointers, copied by fe_init. */
+typedef struct {
+    int nf;                 /* number of filters, 1..64 (48 in the paper) */
+    int ksize;              /* filter side; must be 7 */
+    const float *filters;   /* nf * 7 * 7, filter i at filters + 49 i, row-major k_i[a][b] */
+    const float *theta;     /* nf weights theta_i >= 0 (Eq. FOEmodel) */
+    double lambda;          /* data-term weight lambda > 0 (Eq. variant) */
+    double beta;            /* inertia, 0 <= beta < 1 */
+    double L0;              /* initial Lipschitz estimate L_{-1} > 0 */
+    double eta;             /* backtracking factor > 1 */
+    double c2;              /* step-size margin c2 >= 0 */
+    int max_backtrack;      /* rejections allowed per iteration, >= 0 */
+    int prec;               /* fe_precision */
+    int tile;               /* 0 = default tiling */
+} fe_params;
+
+/* Per-image solver state summary (host struct, filled by fe_get_info). */
+typedef struct {
+    long long n;            /* accepted iterations since fe_init */
+    long long trials;       /* trial evaluations (accepted + rejected) */
+    long long backtracks;   /* rejected trials in total */
+    double L;               /* current Lipschitz estimate L_n */
+    double alpha;           /* alpha_n for the current L_n */
+    double F, G, H;         /* energies at u^n */
+    double H_prev;          /* H at u^{n-1} */
+    double rel_change;      /* |H^n - H^{n-1}| / |H^n| of the last accepted step */
+    double last_gd;         /* <grad F(u^{n-1}), u^n - u^{n-1}> of the last accepted step */
+    double last_dd;         /* |u^n - u^{n-1}|^2 */
+    double last_dp;         /* <u^n - u^{n-1}, u^{n-1} - u^{n-2}> */
+    int status;             /* fe_status of this image */
+    int converged;          /* 1 once the tolerance of the last fe_solve was met */
+} fe_info;
+
+typedef struct fe_ctx fe_ctx;
+
+/* Default parameters: nf = 0 and filters = NULL (caller sets them),
+ * lambda 5, beta 0.8, L0 1, eta 2, c2 1e-6, max_backtrack 30, FP32. */
+FE_API void fe_default_params(fe_params *p);
+
+/* Create a context for nimg images of sizes H[j] x W[j] (each >= 8) with
+ * observations f[j] (any pointer, H[j]*W[j] floats, all > 0 and finite) and
+ * optional starting points u0[j] (any pointer, > 0; u0 == NULL or u0[j] ==
+ * NULL means u^0 = f).  Allocates the device state, computes grad F(u^0),
+ * F(u^0), G(u^0).  stream is a cudaStream_t (NULL = legacy default stream).
+ * Errors: FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_EUNSUPPORTED (*out is NULL). */
+FE_API fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg,
+                        const int *H, const int *W,
+                        const float *const *f, const float *const *u0, void *stream);
+
+/* Single-image form of fe_init_batch. */
+FE_API fe_status fe_init(fe_ctx **out, const fe_params *p, int H, int W,
+                  const float *f, const float *u0, void *stream);
+
+/* Restart every image from new observations (and optional starts) of the
+ * same sizes, without reallocating.  Same argument rules as fe_init_batch. */
+FE_API fe_status fe_reset(fe_ctx *ctx, const float *const *f, const float *const *u0);
+
+FE_API void fe_destroy(fe_ctx *ctx);
+
+/* Run n accepted iPiano iterations on every image that has no error
+ * (Sec. II-C update rule with the backtracking rule above).  The whole loop
+ * runs on the device: one fused trial kernel per trial, accept/reject decided
+ * on the device.  Asynchronous unless worst != NULL, in which case it
+ * synchronises and stores the first non-OK per-image status (or FE_OK). */
+FE_API fe_status fe_step(fe_ctx *ctx, int n, fe_status *worst);
+
+/* Iterate until |H^{n+1}-H^n|/|H^{n+1}| < rel_tol or max_iter accepted
+ * iterations (counted from this call) on every image.  Synchronises.
+ * Returns FE_OK if all images converged, FE_ENOTCONVERGED if some hit
+ * max_iter, else the first error status. */
+FE_API fe_status fe_solve(fe_ctx *ctx, int max_iter, double rel_tol);
+
+/* Summary of image img (synchronises). */
+FE_API fe_status fe_get_info(fe_ctx *ctx, int img, fe_info *out);
+
+/* Copy u^n of image img to out (any pointer, H*W floats). */
+FE_API fe_status fe_get_u(fe_ctx *ctx, int img, float *out);
+
+/* Energies of an arbitrary u (any pointer, H*W floats of image img's size,
+ * u > 0) against image img's f: E = F + G.  Any output pointer may be NULL.
+ * Synchronises. */
+FE_API fe_status fe_energy(fe_ctx *ctx, int img, const float *u, double *E, double *F, double *G);
+
+/* grad F(u) (Sec. II-C) for an arbitrary u (any pointer) into g (any pointer),
+ * both H*W floats of image img's size; F(u) into *F if F != NULL.
+ * Synchronises. */
+FE_API fe_status fe_gradient(fe_ctx *ctx, int img, const float *u, float *g, double *F);
+
+/* Checkpoint: copy u^n, u^{n-1}, grad F(u^n) (any pointers, H*W floats each;
+ * any may be NULL) and the scalar state of image img. */
+FE_API fe_status fe_get_state(fe_ctx *ctx, int img, float *u, float *u_prev, float *g, fe_info *info);
+
+/* Restore a checkpoint taken with fe_get_state (same sizes and params):
+ * continuing from it reproduces the uninterrupted run bit for bit. */
+FE_API fe_status fe_set_state(fe_ctx *ctx, int img, const float *u, const float *u_prev,
+                       const float *g, const fe_info *info);
+
+/* Number of images / size of image img. */
+FE_API int fe_num_images(const fe_ctx *ctx);
+FE_API fe_status fe_image_size(const fe_ctx *ctx, int img, int *H, int *W);
+
+/* Device kernel launches issued by this context since creation (trial,
+ * gradient, energy and bookkeeping kernels), for launch accounting. */
+FE_API long long fe_launch_count(const fe_ctx *ctx);
+
+/* Select how fe_step/fe_solve drive the device loop: 0 = host loop of
+ * kernel launches in chunks, 1 = one CUDA graph with a device-side while
+ * node (default when the driver supports it). */
+FE_API fe_status fe_set_loop_mode(fe_ctx *ctx, int mode);
+
+FE_API const char *fe_last_error(const fe_ctx *ctx);
+FE_API const char *fe_status_string(fe_status s);
+FE_API int fe_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FE_H */

@@ -103,6 +103,9 @@ def lib():
             L.orc_ipiano_step.argtypes = [_D, C.c_int, C.c_int, _D, _D, C.c_int, C.c_int,
                                           C.POINTER(OrcParams), _D, _D, C.c_double,
                                           _D, _D, _D]
+            L.orc_ipiano_fixed.restype = C.c_int
+            L.orc_ipiano_fixed.argtypes = [_D, C.c_int, C.c_int, _D, _D, C.c_int, C.c_int,
+                                           C.POINTER(OrcParams), _D, C.c_int, _D, _D, _D]
             L.orc_num_threads.restype = C.c_int
             L.orc_set_threads.argtypes = [C.c_int]
             _lib = L
@@ -274,6 +277,22 @@ def ipiano_step(f, filters, theta, prm: OrcParams, u, u_prev, L_in):
     st = lib().orc_ipiano_step(_p(f), H, W, _p(k), _p(th), nf, ks, C.byref(prm),
                                _p(u), _p(up), float(L_in), _p(u1), _p(rec), _p(Lout))
     return dict(u1=u1, rec=rec, L=float(Lout[0]), status=int(st))
+
+
+def ipiano_fixed(f, filters, theta, prm: OrcParams, Lseq, u, u_prev=None):
+    """Iterations with the prescribed L_k (no backtracking test).  Returns
+    dict with u, u_prev, rec (n x 9, rec[:, 5] = descent-test margin), status."""
+    f = _d(f)
+    k, th, nf, ks = _bank(filters, theta)
+    H, W = f.shape
+    Ls = _d(np.atleast_1d(Lseq))
+    n = Ls.size
+    u = _d(u).copy()
+    up = _d(u if u_prev is None else u_prev).copy()
+    rec = np.zeros((max(n, 1), ORC_REC))
+    st = lib().orc_ipiano_fixed(_p(f), H, W, _p(k), _p(th), nf, ks, C.byref(prm), _p(Ls), n,
+                                _p(u), _p(up), _p(rec))
+    return dict(u=u, u_prev=up, rec=rec[:n], status=int(st))
 
 
 def num_threads() -> int:

@@ -473,6 +473,61 @@ ORC_API int orc_ipiano_step(const double *f, int H, int W, const double *bank,
     return status;
 }
 
+/* iPiano with a prescribed sequence L_0..L_{n-1} and no backtracking test:
+ * alpha_k = 2(1-beta)/(L_k + 2 c2) and the Sec. II-C update.  Starts from
+ * (u_io, u_prev_io) = (u^0, u^{-1}) and returns (u^n, u^{n-1}) in them.
+ * rec (n x ORC_REC) as orc_ipiano, except rec[5] = the margin of the
+ * descent test F(u^k) + <g,D> + L_k/2 |D|^2 - F(u^{k+1}) (>= 0 means the
+ * backtracking rule would accept the step). */
+ORC_API int orc_ipiano_fixed(const double *f, int H, int W, const double *bank,
+                             const double *theta, int nf, int ks, const orc_params *p,
+                             const double *Lseq, int n, double *u_io, double *u_prev_io,
+                             double *rec)
+{
+    const long N = (long)H * W;
+    double *u = u_io, *up = u_prev_io;
+    double *u1 = (double *)malloc(sizeof(double) * N);
+    double *g = (double *)malloc(sizeof(double) * N);
+    int status = ORC_OK;
+    double F = orc_gradF(u, H, W, bank, theta, nf, ks, g);
+    for (int k = 0; k < n; ++k) {
+        const double L = Lseq[k], alpha = step_size(p, L);
+        double gd = 0.0, dd = 0.0, dp = 0.0;
+        for (long q = 0; q < N; ++q) {
+            const double uhat = u[q] - alpha * g[q] + p->beta * (u[q] - up[q]);
+            u1[q] = orc_prox(uhat, f[q], alpha, p->lambda);
+            const double d = u1[q] - u[q];
+            gd += g[q] * d;
+            dd += d * d;
+            dp += d * (u[q] - up[q]);
+        }
+        const double F1 = orc_gradF(u1, H, W, bank, theta, nf, ks, g);
+        const double G1 = orc_G(u1, f, N, p->lambda);
+        if (!isfinite(F1) || !isfinite(G1)) {
+            status = ORC_ENONFINITE;
+            break;
+        }
+        if (rec) {
+            double *r = rec + (size_t)k * ORC_REC;
+            r[0] = L;
+            r[1] = alpha;
+            r[2] = F1;
+            r[3] = G1;
+            r[4] = F1 + G1;
+            r[5] = F + gd + 0.5 * L * dd - F1;
+            r[6] = gd;
+            r[7] = dd;
+            r[8] = dp;
+        }
+        memcpy(up, u, sizeof(double) * N);
+        memcpy(u, u1, sizeof(double) * N);
+        F = F1;
+    }
+    free(u1);
+    free(g);
+    return status;
+}
+
 ORC_API int orc_num_threads(void)
 {
 #ifdef _OPENMP

@@ -1,0 +1,681 @@
+// Host side of the libfe C ABI (include/fe.h): contexts, device memory,
+// argument validation, and the device-driven iPiano loop.
+//
+// The loop over iterations never reads energies back to the host: every
+// launch of the trial kernel either performs one trial per active image
+// (accepted or rejected on the device) or exits at once for finished images.
+// Two drivers are provided: a host loop that launches trial kernels in chunks
+// and reads one integer (the active-image count) between chunks, and a CUDA
+// graph whose while-node re-launches the trial kernel until the kernel's
+// last CTA clears the condition.  Both are bounded by a device-side trial
+// budget, so neither can spin forever.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fe_internal.cuh"
+
+using namespace fe;
+
+struct fe_ctx {
+    int dev = 0;
+    cudaStream_t s = nullptr;
+    fe_params prm{};
+    std::vector<float> filt, theta;
+    int nimg = 0, ntiles = 0, nfp = 0;
+    std::vector<int> H, W;
+    std::vector<ImgDesc> himg;
+    std::vector<TileDesc> htile;
+    std::vector<void *> allocs;
+    ImgDesc *d_imgs = nullptr;
+    ImgState *d_st = nullptr;
+    TileDesc *d_tiles = nullptr;
+    double *d_part = nullptr;
+    unsigned *d_arr = nullptr;
+    LoopCtl *d_loop = nullptr;
+    float *d_wf = nullptr, *d_wa = nullptr, *d_th = nullptr;
+    double *d_res = nullptr;
+    int *d_flag = nullptr;
+    float *d_scratch = nullptr;  // 2 planes of the largest image (host-pointer staging)
+    size_t max_plane = 0;
+    KParams kp{};
+    long long host_launches = 0;
+    std::string err;
+    int loop_mode = 1;
+    bool graph_built = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+};
+
+namespace {
+
+fe_status set_err(fe_ctx *c, fe_status s, const char *fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+thread_local std::string g_init_err;
+
+#define FE_CUDA(c, call)                                                                   \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return set_err((c), FE_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                           __FILE__, __LINE__);                                            \
+    } while (0)
+
+__global__ void prep_kernel(const float *f, const float *u0, float *f2, float *ua, float *ub,
+                            size_t N, int *bad) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float fv = f[i];
+        const float f2v = fv * fv;
+        const float uv = u0 ? u0[i] : fv;
+        const bool ok = fv > 0.0f && isfinite(fv) && f2v > 0.0f && isfinite(f2v) && uv > 0.0f &&
+                        isfinite(uv);
+        f2[i] = f2v;
+        ua[i] = uv;
+        ub[i] = uv;
+        if (!ok) atomicOr(bad, 1);
+    }
+}
+
+__global__ void begin_kernel(ImgState *st, int nimg, long long n, double tol, LoopCtl *lc,
+                             long long budget) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int nact = 0;
+    for (int j = 0; j < nimg; ++j) {
+        if (st[j].status == FE_OK) {
+            st[j].done = 0;
+            st[j].converged = 0;
+            st[j].bt = 0;
+            st[j].target = st[j].n + n;
+            st[j].tol = tol;
+            ++nact;
+        } else {
+            st[j].done = 1;
+        }
+    }
+    lc->grid_arrivals = 0u;
+    lc->active = nact;
+    lc->budget = budget;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+fe_status dalloc(fe_ctx *c, T **p, size_t count) {
+    void *q = nullptr;
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(c, FE_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    c->allocs.push_back(q);
+    *p = static_cast<T *>(q);
+    return FE_OK;
+}
+
+fe_status validate_params(fe_ctx *c, const fe_params *p) {
+    if (!p) return set_err(c, FE_EINVAL, "params is NULL");
+    if (p->nf < 1 || p->nf > NFMAX) return set_err(c, FE_EINVAL, "nf=%d outside 1..%d", p->nf, NFMAX);
+    if (p->ksize != KS) return set_err(c, FE_EINVAL, "ksize=%d, only 7 is supported", p->ksize);
+    if (!p->filters || !p->theta) return set_err(c, FE_EINVAL, "filters or theta is NULL");
+    for (int i = 0; i < p->nf * KT; ++i)
+        if (!std::isfinite(p->filters[i])) return set_err(c, FE_EINVAL, "filter weight %d not finite", i);
+    for (int i = 0; i < p->nf; ++i)
+        if (!(p->theta[i] >= 0.0f) || !std::isfinite(p->theta[i]))
+            return set_err(c, FE_EINVAL, "theta[%d] must be finite and >= 0", i);
+    if (!(p->lambda > 0.0) || !std::isfinite(p->lambda)) return set_err(c, FE_EINVAL, "lambda must be > 0");
+    if (!(p->beta >= 0.0 && p->beta < 1.0)) return set_err(c, FE_EINVAL, "beta must be in [0,1)");
+    if (!(p->L0 > 0.0) || !std::isfinite(p->L0)) return set_err(c, FE_EINVAL, "L0 must be > 0");
+    if (!(p->eta > 1.0) || !std::isfinite(p->eta)) return set_err(c, FE_EINVAL, "eta must be > 1");
+    if (!(p->c2 >= 0.0) || !std::isfinite(p->c2)) return set_err(c, FE_EINVAL, "c2 must be >= 0");
+    if (p->max_backtrack < 0) return set_err(c, FE_EINVAL, "max_backtrack must be >= 0");
+    if (p->prec != FE_FP32 && p->prec != FE_TF32 && p->prec != FE_BF16)
+        return set_err(c, FE_EINVAL, "unknown precision %d", p->prec);
+    if (p->prec != FE_FP32) return set_err(c, FE_EUNSUPPORTED, "precision %d not built", p->prec);
+    if (p->tile != 0 && p->tile != fp32_tile())
+        return set_err(c, FE_EUNSUPPORTED, "tile %d not available (0 or %d)", p->tile, fp32_tile());
+    return FE_OK;
+}
+
+fe_status load_inputs(fe_ctx *c, const float *const *f, const float *const *u0) {
+    if (!f) return set_err(c, FE_EINVAL, "f is NULL");
+    FE_CUDA(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->s));
+    for (int j = 0; j < c->nimg; ++j) {
+        if (!f[j]) return set_err(c, FE_EINVAL, "f[%d] is NULL", j);
+        const size_t N = (size_t)c->H[j] * c->W[j];
+        ImgDesc &im = c->himg[j];
+        // stage f in u[1] and u0 in u[0]; the prep kernel squares f, checks
+        // positivity and writes u^0 into u[0] and u[2] (u^{-1} = u^0)
+        FE_CUDA(c, cudaMemcpyAsync(im.u[1], f[j], N * 4, cudaMemcpyDefault, c->s));
+        const bool has_u0 = u0 && u0[j];
+        if (has_u0) FE_CUDA(c, cudaMemcpyAsync(im.u[0], u0[j], N * 4, cudaMemcpyDefault, c->s));
+        const int blocks = (int)std::min<size_t>((N + 255) / 256, 4096);
+        prep_kernel<<<blocks, 256, 0, c->s>>>(im.u[1], has_u0 ? im.u[0] : nullptr, im.f2, im.u[0], im.u[2],
+                                              N, c->d_flag);
+        FE_CUDA(c, cudaGetLastError());
+        ++c->host_launches;
+    }
+    int bad = 0;
+    FE_CUDA(c, cudaMemcpyAsync(&bad, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    FE_CUDA(c, cudaStreamSynchronize(c->s));
+    if (bad) return set_err(c, FE_EINVAL, "f and u0 must be finite and > 0 (f^2 must not underflow)");
+    // fresh state, then grad F(u^0), F(u^0), G(u^0) on the device
+    std::vector<ImgState> hs(c->nimg);
+    for (auto &s : hs) {
+        std::memset(&s, 0, sizeof s);
+        s.L = c->prm.L0;
+        s.alpha = 2.0 * (1.0 - c->prm.beta) / (c->prm.L0 + 2.0 * c->prm.c2);
+        s.status = FE_OK;
+    }
+    FE_CUDA(c, cudaMemcpyAsync(c->d_st, hs.data(), sizeof(ImgState) * hs.size(), cudaMemcpyHostToDevice, c->s));
+    FE_CUDA(c, cudaMemsetAsync(c->d_arr, 0, sizeof(unsigned) * c->nimg, c->s));
+    KParams kp = c->kp;
+    kp.tile0 = 0;
+    FE_CUDA(c, fp32_launch(MODE_INIT, kp, c->ntiles, c->s));
+    ++c->host_launches;
+    FE_CUDA(c, cudaMemcpyAsync(hs.data(), c->d_st, sizeof(ImgState) * hs.size(), cudaMemcpyDeviceToHost, c->s));
+    FE_CUDA(c, cudaStreamSynchronize(c->s));
+    for (int j = 0; j < c->nimg; ++j)
+        if (hs[j].status != FE_OK) return set_err(c, (fe_status)hs[j].status, "image %d: non-finite energy at u^0", j);
+    return FE_OK;
+}
+
+fe_status build_graph(fe_ctx *c) {
+    if (c->graph_built) return FE_OK;
+    cudaGraph_t g = nullptr;
+    FE_CUDA(c, cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return set_err(c, FE_EUNSUPPORTED, "conditional graph nodes unavailable: %s", cudaGetErrorString(e));
+    }
+    // cudaGraphNodeParams has no default constructor in C++ (union member);
+    // build it zero-filled in raw storage
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+    std::memset(raw, 0, sizeof raw);
+    cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cn;
+    e = cudaGraphAddNode(&cn, g, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return set_err(c, FE_EUNSUPPORTED, "cudaGraphAddNode(while): %s", cudaGetErrorString(e));
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    KParams kp = c->kp;
+    kp.tile0 = 0;
+    kp.cond = (unsigned long long)h;
+    kp.use_cond = 1;
+    void *args[] = {&kp};
+    cudaKernelNodeParams knp;
+    std::memset(&knp, 0, sizeof knp);
+    knp.func = const_cast<void *>(fp32_trial_entry());
+    knp.gridDim = dim3(c->ntiles);
+    knp.blockDim = dim3(256);
+    knp.sharedMemBytes = (unsigned)fp32_smem_bytes();
+    knp.kernelParams = args;
+    cudaGraphNode_t kn;
+    e = cudaGraphAddKernelNode(&kn, body, nullptr, 0, &knp);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return set_err(c, FE_ECUDA, "cudaGraphAddKernelNode: %s", cudaGetErrorString(e));
+    }
+    cudaGraphExec_t ex;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return set_err(c, FE_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    }
+    c->graph = g;
+    c->gexec = ex;
+    c->graph_built = true;
+    return FE_OK;
+}
+
+// Run trial launches until no image is active (or the budget is spent).
+fe_status run_loop(fe_ctx *c, long long n_hint, long long budget, bool sync) {
+    if (c->loop_mode == 1) {
+        fe_status st = build_graph(c);
+        if (st == FE_OK) {
+            FE_CUDA(c, cudaGraphLaunch(c->gexec, c->s));
+            if (sync) FE_CUDA(c, cudaStreamSynchronize(c->s));
+            return FE_OK;
+        }
+        if (st != FE_EUNSUPPORTED) return st;
+        c->loop_mode = 0;  // fall back to the chunked host loop of the same kernel
+    }
+    KParams kp = c->kp;
+    kp.tile0 = 0;
+    long long launched = 0;
+    long long chunk = std::max<long long>(1, std::min<long long>(n_hint, 64));
+    for (;;) {
+        const long long todo = std::min(chunk, budget - launched);
+        for (long long k = 0; k < todo; ++k) FE_CUDA(c, fp32_launch(MODE_TRIAL, kp, c->ntiles, c->s));
+        launched += todo;
+        LoopCtl lc;
+        FE_CUDA(c, cudaMemcpyAsync(&lc, c->d_loop, sizeof lc, cudaMemcpyDeviceToHost, c->s));
+        FE_CUDA(c, cudaStreamSynchronize(c->s));
+        if (lc.active == 0 || launched >= budget) break;
+        chunk = 16;
+    }
+    return FE_OK;
+}
+
+fe_status fetch_states(fe_ctx *c, std::vector<ImgState> &hs) {
+    hs.resize(c->nimg);
+    FE_CUDA(c, cudaMemcpyAsync(hs.data(), c->d_st, sizeof(ImgState) * c->nimg, cudaMemcpyDeviceToHost, c->s));
+    FE_CUDA(c, cudaStreamSynchronize(c->s));
+    return FE_OK;
+}
+
+fe_status check_img(fe_ctx *c, int img) {
+    if (!c) return FE_EINVAL;
+    if (img < 0 || img >= c->nimg) return set_err(c, FE_EINVAL, "image index %d outside 0..%d", img, c->nimg - 1);
+    return FE_OK;
+}
+
+// Stage a caller pointer for reading by a kernel: device pointers are used
+// directly, host pointers are copied into scratch plane `slot`.
+fe_status stage_in(fe_ctx *c, const float *src, size_t N, int slot, const float **out) {
+    if (is_device_ptr(src)) {
+        *out = src;
+        return FE_OK;
+    }
+    float *dst = c->d_scratch + (size_t)slot * c->max_plane;
+    FE_CUDA(c, cudaMemcpyAsync(dst, src, N * 4, cudaMemcpyDefault, c->s));
+    *out = dst;
+    return FE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fe_abi_version(void) { return FE_ABI_VERSION; }
+
+const char *fe_status_string(fe_status s) {
+    switch (s) {
+        case FE_OK: return "ok";
+        case FE_EINVAL: return "invalid argument";
+        case FE_ENOMEM: return "out of device memory";
+        case FE_ECUDA: return "CUDA error";
+        case FE_ENONFINITE: return "non-finite value in a trial";
+        case FE_EBACKTRACK: return "backtracking limit reached";
+        case FE_ETIMEOUT: return "device trial budget exhausted";
+        case FE_ENOTCONVERGED: return "not converged within max_iter";
+        case FE_EUNSUPPORTED: return "unsupported option";
+    }
+    return "unknown status";
+}
+
+const char *fe_last_error(const fe_ctx *ctx) { return ctx ? ctx->err.c_str() : g_init_err.c_str(); }
+
+void fe_default_params(fe_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->ksize = KS;
+    p->lambda = 5.0;
+    p->beta = 0.8;
+    p->L0 = 1.0;
+    p->eta = 2.0;
+    p->c2 = 1e-6;
+    p->max_backtrack = 30;
+    p->prec = FE_FP32;
+    p->tile = 0;
+}
+
+void fe_destroy(fe_ctx *c) {
+    if (!c) return;
+    if (c->s) cudaStreamSynchronize(c->s);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    for (void *p : c->allocs) cudaFree(p);
+    delete c;
+}
+
+fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H, const int *W,
+                        const float *const *f, const float *const *u0, void *stream) {
+    g_init_err.clear();
+    if (!out) return FE_EINVAL;
+    *out = nullptr;
+    fe_ctx *c = new fe_ctx();
+    auto bail = [&](fe_status s) {
+        g_init_err = c->err;
+        fe_destroy(c);
+        return s;
+    };
+    fe_status st = validate_params(c, p);
+    if (st != FE_OK) return bail(st);
+    if (nimg < 1 || !H || !W || !f) return bail(set_err(c, FE_EINVAL, "need nimg >= 1 and non-NULL H, W, f"));
+    c->prm = *p;
+    c->nimg = nimg;
+    c->s = static_cast<cudaStream_t>(stream);
+    c->filt.assign(p->filters, p->filters + (size_t)p->nf * KT);
+    c->theta.assign(p->theta, p->theta + p->nf);
+    c->nfp = ((p->nf + 7) / 8) * 8;
+    const int T = fp32_tile();
+    size_t plane_total = 0;
+    for (int j = 0; j < nimg; ++j) {
+        if (H[j] < 8 || W[j] < 8 || H[j] > 65536 || W[j] > 65536)
+            return bail(set_err(c, FE_EINVAL, "image %d: size %dx%d outside 8..65536", j, H[j], W[j]));
+        c->H.push_back(H[j]);
+        c->W.push_back(W[j]);
+        const size_t N = (size_t)H[j] * W[j];
+        c->max_plane = std::max(c->max_plane, (N + 63) / 64 * 64);
+        plane_total += 6 * ((N + 63) / 64 * 64);
+        const int ty = (H[j] + T - 1) / T, tx = (W[j] + T - 1) / T;
+        ImgDesc d{};
+        d.H = H[j];
+        d.W = W[j];
+        d.tile_begin = (int)c->htile.size();
+        d.ntiles = ty * tx;
+        d.lambda = p->lambda;
+        for (int a = 0; a < ty; ++a)
+            for (int b = 0; b < tx; ++b) c->htile.push_back(TileDesc{j, a * T, b * T, 0});
+        c->himg.push_back(d);
+    }
+    if (c->htile.size() > (size_t)0x7fffffff) return bail(set_err(c, FE_EINVAL, "too many tiles"));
+    c->ntiles = (int)c->htile.size();
+    if (cudaGetDevice(&c->dev) != cudaSuccess) return bail(set_err(c, FE_ECUDA, "no CUDA device"));
+
+    if (cudaError_t e = fp32_prepare(); e != cudaSuccess)
+        return bail(set_err(c, FE_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e)));
+
+    float *planes = nullptr;
+    if ((st = dalloc(c, &planes, plane_total)) != FE_OK) return bail(st);
+    size_t off = 0;
+    for (int j = 0; j < nimg; ++j) {
+        const size_t N = (size_t)H[j] * W[j], P = (N + 63) / 64 * 64;
+        ImgDesc &d = c->himg[j];
+        for (int k = 0; k < 3; ++k) d.u[k] = planes + off + k * P;
+        for (int k = 0; k < 2; ++k) d.g[k] = planes + off + (3 + k) * P;
+        d.f2 = planes + off + 5 * P;
+        off += 6 * P;
+    }
+    if ((st = dalloc(c, &c->d_imgs, nimg)) != FE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_st, nimg)) != FE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_tiles, c->ntiles)) != FE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_part, (size_t)c->ntiles * NRED)) != FE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_arr, nimg)) != FE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_loop, 1)) != FE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_wf, (size_t)KT * NFMAX)) != FE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_wa, (size_t)NFMAX * KT_PAD)) != FE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_th, NFMAX)) != FE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_res, 2 * (size_t)nimg)) != FE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_flag, 4)) != FE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_scratch, 2 * c->max_plane)) != FE_OK) return bail(st);
+
+    // weight tables: forward = flipped taps (convolution as correlation),
+    // tap-major; adjoint = taps as stored, filter-major (correlation = K^T)
+    std::vector<float> wf((size_t)KT * NFMAX, 0.f), wa((size_t)NFMAX * KT_PAD, 0.f), th(NFMAX, 0.f);
+    for (int i = 0; i < p->nf; ++i) {
+        for (int t = 0; t < KT; ++t) {
+            wf[(size_t)t * NFMAX + i] = p->filters[(size_t)i * KT + (KT - 1 - t)];
+            wa[(size_t)i * KT_PAD + t] = p->filters[(size_t)i * KT + t];
+        }
+        th[i] = p->theta[i];
+    }
+    if (cudaMemcpy(c->d_wf, wf.data(), wf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_wa, wa.data(), wa.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_th, th.data(), th.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_imgs, c->himg.data(), sizeof(ImgDesc) * nimg, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_tiles, c->htile.data(), sizeof(TileDesc) * c->ntiles, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+        return bail(set_err(c, FE_ECUDA, "upload of descriptors failed: %s", cudaGetErrorString(cudaGetLastError())));
+
+    KParams &kp = c->kp;
+    std::memset(&kp, 0, sizeof kp);
+    kp.imgs = c->d_imgs;
+    kp.st = c->d_st;
+    kp.tiles = c->d_tiles;
+    kp.partials = c->d_part;
+    kp.img_arrivals = c->d_arr;
+    kp.loop = c->d_loop;
+    kp.wf = c->d_wf;
+    kp.wa = c->d_wa;
+    kp.theta = c->d_th;
+    kp.nfp = c->nfp;
+    kp.nimg = nimg;
+    kp.ntiles = c->ntiles;
+    kp.beta = p->beta;
+    kp.eta = p->eta;
+    kp.c2 = p->c2;
+    kp.max_bt = p->max_backtrack;
+    kp.results = c->d_res;
+
+    if (cudaMemset(c->d_loop, 0, sizeof(LoopCtl)) != cudaSuccess)
+        return bail(set_err(c, FE_ECUDA, "cudaMemset: %s", cudaGetErrorString(cudaGetLastError())));
+    if ((st = load_inputs(c, f, u0)) != FE_OK) return bail(st);
+    *out = c;
+    return FE_OK;
+}
+
+fe_status fe_init(fe_ctx **out, const fe_params *p, int H, int W, const float *f, const float *u0, void *stream) {
+    const float *fa[1] = {f};
+    const float *ua[1] = {u0};
+    return fe_init_batch(out, p, 1, &H, &W, fa, u0 ? ua : nullptr, stream);
+}
+
+fe_status fe_reset(fe_ctx *c, const float *const *f, const float *const *u0) {
+    if (!c) return FE_EINVAL;
+    return load_inputs(c, f, u0);
+}
+
+fe_status fe_set_loop_mode(fe_ctx *c, int mode) {
+    if (!c || (mode != 0 && mode != 1)) return FE_EINVAL;
+    c->loop_mode = mode;
+    return FE_OK;
+}
+
+fe_status fe_step(fe_ctx *c, int n, fe_status *worst) {
+    if (!c) return FE_EINVAL;
+    if (n < 0) return set_err(c, FE_EINVAL, "n must be >= 0");
+    if (n > 0) {
+        const long long budget = (long long)n * (c->prm.max_backtrack + 1) + 1;
+        begin_kernel<<<1, 32, 0, c->s>>>(c->d_st, c->nimg, n, 0.0, c->d_loop, budget);
+        FE_CUDA(c, cudaGetLastError());
+        ++c->host_launches;
+        fe_status st = run_loop(c, n, budget, worst != nullptr);
+        if (st != FE_OK) return st;
+    }
+    if (worst) {
+        std::vector<ImgState> hs;
+        fe_status st = fetch_states(c, hs);
+        if (st != FE_OK) return st;
+        *worst = FE_OK;
+        for (auto &s : hs)
+            if (s.status != FE_OK) {
+                *worst = (fe_status)s.status;
+                break;
+            }
+    }
+    return FE_OK;
+}
+
+fe_status fe_solve(fe_ctx *c, int max_iter, double rel_tol) {
+    if (!c) return FE_EINVAL;
+    if (max_iter < 0 || !(rel_tol >= 0.0)) return set_err(c, FE_EINVAL, "max_iter >= 0 and rel_tol >= 0 required");
+    const long long budget = (long long)max_iter * (c->prm.max_backtrack + 1) + 1;
+    begin_kernel<<<1, 32, 0, c->s>>>(c->d_st, c->nimg, max_iter, rel_tol, c->d_loop, budget);
+    FE_CUDA(c, cudaGetLastError());
+    ++c->host_launches;
+    fe_status st = run_loop(c, std::min(max_iter, 32), budget, true);
+    if (st != FE_OK) return st;
+    std::vector<ImgState> hs;
+    if ((st = fetch_states(c, hs)) != FE_OK) return st;
+    for (auto &s : hs)
+        if (s.status != FE_OK) return (fe_status)s.status;
+    for (auto &s : hs)
+        if (!s.converged) return FE_ENOTCONVERGED;
+    return FE_OK;
+}
+
+fe_status fe_get_info(fe_ctx *c, int img, fe_info *out) {
+    fe_status st = check_img(c, img);
+    if (st != FE_OK) return st;
+    if (!out) return set_err(c, FE_EINVAL, "out is NULL");
+    ImgState s;
+    FE_CUDA(c, cudaMemcpyAsync(&s, c->d_st + img, sizeof s, cudaMemcpyDeviceToHost, c->s));
+    FE_CUDA(c, cudaStreamSynchronize(c->s));
+    out->n = s.n;
+    out->trials = s.trials;
+    out->backtracks = s.backtracks;
+    out->L = s.L;
+    out->alpha = s.alpha;
+    out->F = s.F;
+    out->G = s.G;
+    out->H = s.H;
+    out->H_prev = s.H_prev;
+    out->rel_change = s.rel_change;
+    out->last_gd = s.last_gd;
+    out->last_dd = s.last_dd;
+    out->last_dp = s.last_dp;
+    out->status = s.status;
+    out->converged = s.converged;
+    return FE_OK;
+}
+
+fe_status fe_get_state(fe_ctx *c, int img, float *u, float *u_prev, float *g, fe_info *info) {
+    fe_status st = check_img(c, img);
+    if (st != FE_OK) return st;
+    ImgState s;
+    FE_CUDA(c, cudaMemcpyAsync(&s, c->d_st + img, sizeof s, cudaMemcpyDeviceToHost, c->s));
+    FE_CUDA(c, cudaStreamSynchronize(c->s));
+    const ImgDesc &d = c->himg[img];
+    const size_t N = (size_t)d.H * d.W;
+    if (u) FE_CUDA(c, cudaMemcpyAsync(u, d.u[s.cur], N * 4, cudaMemcpyDefault, c->s));
+    if (u_prev) FE_CUDA(c, cudaMemcpyAsync(u_prev, d.u[(s.cur + 2) % 3], N * 4, cudaMemcpyDefault, c->s));
+    if (g) FE_CUDA(c, cudaMemcpyAsync(g, d.g[s.gcur], N * 4, cudaMemcpyDefault, c->s));
+    FE_CUDA(c, cudaStreamSynchronize(c->s));
+    if (info) return fe_get_info(c, img, info);
+    return FE_OK;
+}
+
+fe_status fe_set_state(fe_ctx *c, int img, const float *u, const float *u_prev, const float *g, const fe_info *info) {
+    fe_status st = check_img(c, img);
+    if (st != FE_OK) return st;
+    if (!u || !u_prev || !g || !info) return set_err(c, FE_EINVAL, "u, u_prev, g and info are required");
+    ImgState s;
+    FE_CUDA(c, cudaMemcpyAsync(&s, c->d_st + img, sizeof s, cudaMemcpyDeviceToHost, c->s));
+    FE_CUDA(c, cudaStreamSynchronize(c->s));
+    const ImgDesc &d = c->himg[img];
+    const size_t N = (size_t)d.H * d.W;
+    FE_CUDA(c, cudaMemcpyAsync(d.u[s.cur], u, N * 4, cudaMemcpyDefault, c->s));
+    FE_CUDA(c, cudaMemcpyAsync(d.u[(s.cur + 2) % 3], u_prev, N * 4, cudaMemcpyDefault, c->s));
+    FE_CUDA(c, cudaMemcpyAsync(d.g[s.gcur], g, N * 4, cudaMemcpyDefault, c->s));
+    s.n = info->n;
+    s.trials = info->trials;
+    s.backtracks = info->backtracks;
+    s.L = info->L;
+    s.alpha = info->alpha;
+    s.F = info->F;
+    s.G = info->G;
+    s.H = info->H;
+    s.H_prev = info->H_prev;
+    s.rel_change = info->rel_change;
+    s.last_gd = info->last_gd;
+    s.last_dd = info->last_dd;
+    s.last_dp = info->last_dp;
+    s.status = info->status;
+    s.converged = info->converged;
+    s.bt = 0;
+    s.done = 0;
+    FE_CUDA(c, cudaMemcpyAsync(c->d_st + img, &s, sizeof s, cudaMemcpyHostToDevice, c->s));
+    FE_CUDA(c, cudaStreamSynchronize(c->s));
+    return FE_OK;
+}
+
+fe_status fe_get_u(fe_ctx *c, int img, float *out) { return fe_get_state(c, img, out, nullptr, nullptr, nullptr); }
+
+static fe_status ext_launch(fe_ctx *c, int mode, int img, const float *u, float *g, double *F, double *G) {
+    fe_status st = check_img(c, img);
+    if (st != FE_OK) return st;
+    if (!u) return set_err(c, FE_EINVAL, "u is NULL");
+    const ImgDesc &d = c->himg[img];
+    const size_t N = (size_t)d.H * d.W;
+    const float *ud;
+    if ((st = stage_in(c, u, N, 0, &ud)) != FE_OK) return st;
+    float *gd = nullptr;
+    const bool g_dev = g && is_device_ptr(g);
+    if (mode == MODE_GRAD_EXT) gd = g_dev ? g : c->d_scratch + c->max_plane;
+    // positivity of u is required by log u in G
+    FE_CUDA(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->s));
+    KParams kp = c->kp;
+    kp.tile0 = d.tile_begin;
+    kp.u_ext = ud;
+    kp.g_ext = gd;
+    FE_CUDA(c, fp32_launch(mode, kp, d.ntiles, c->s));
+    ++c->host_launches;
+    double res[2];
+    FE_CUDA(c, cudaMemcpyAsync(res, c->d_res + 2 * img, sizeof res, cudaMemcpyDeviceToHost, c->s));
+    if (mode == MODE_GRAD_EXT && g && !g_dev) FE_CUDA(c, cudaMemcpyAsync(g, gd, N * 4, cudaMemcpyDefault, c->s));
+    FE_CUDA(c, cudaStreamSynchronize(c->s));
+    if (F) *F = res[0];
+    if (G) *G = res[1];
+    return FE_OK;
+}
+
+fe_status fe_energy(fe_ctx *c, int img, const float *u, double *E, double *F, double *G) {
+    double f_ = 0, g_ = 0;
+    fe_status st = ext_launch(c, MODE_ENERGY_EXT, img, u, nullptr, &f_, &g_);
+    if (st != FE_OK) return st;
+    if (E) *E = f_ + g_;
+    if (F) *F = f_;
+    if (G) *G = g_;
+    return FE_OK;
+}
+
+fe_status fe_gradient(fe_ctx *c, int img, const float *u, float *g, double *F) {
+    if (c && !g) return set_err(c, FE_EINVAL, "g is NULL");
+    return ext_launch(c, MODE_GRAD_EXT, img, u, g, F, nullptr);
+}
+
+int fe_num_images(const fe_ctx *c) { return c ? c->nimg : 0; }
+
+fe_status fe_image_size(const fe_ctx *c, int img, int *H, int *W) {
+    if (!c || img < 0 || img >= c->nimg) return FE_EINVAL;
+    if (H) *H = c->H[img];
+    if (W) *W = c->W[img];
+    return FE_OK;
+}
+
+long long fe_launch_count(const fe_ctx *c) {
+    if (!c) return 0;
+    LoopCtl lc;
+    if (cudaMemcpyAsync(&lc, c->d_loop, sizeof lc, cudaMemcpyDeviceToHost, c->s) != cudaSuccess ||
+        cudaStreamSynchronize(c->s) != cudaSuccess)
+        return -1;
+    // trial kernels are counted on the device (host loop and graph alike),
+    // every other kernel on the host
+    return c->host_launches + lc.launches;
+}
+
+}  // extern "C"

@@ -1,0 +1,555 @@
+// Fused FP32 iPiano trial kernel for the FoE / I-divergence despeckling model.
+//
+// One CTA handles one TY x TX output tile of one image and does, in shared
+// memory, every step of one iPiano trial (Sec. II-C):
+//
+//   1. load u^n, u^{n-1}, g^n, f^2 on the tile + 6-pixel halo (symmetric
+//      reflection at the image border) and form the inertial forward step
+//      uhat = u^n - alpha g^n + beta (u^n - u^{n-1})             (update rule)
+//   2. closed-form prox of alpha G, pointwise, on tile + halo 6 (Sec. II-C):
+//      u = (uhat + sqrt(uhat^2 + 4(1+t l) t l f^2)) / (2 (1 + t l)), evaluated
+//      as 2 t l f^2 / (sqrt(D) - uhat) when uhat < 0 (no cancellation)
+//   3. forward filter bank z_i = k_i * u on tile + halo 3, 7x7 taps, FFMA
+//   4. r_i = theta_i rho'(z_i) = theta_i 2 z_i / (1 + z_i^2) (zero outside the
+//      image), and the energy term theta_i log(1 + z_i^2) on the tile
+//   5. adjoint bank g = sum_i K_i^T r_i on the tile (correlation with k_i),
+//      plus the transpose of the symmetric extension: values of K_i^T r on
+//      the 3-pixel frame outside the image are folded back onto the pixels
+//      they mirror
+//   6. per-tile FP64 partial sums of F(u^{n+1}), G(u^{n+1}), <g^n, D>, |D|^2,
+//      <D, u^n - u^{n-1}>; the last CTA of the image reduces them in a fixed
+//      order and applies the backtracking test (accept / L <- eta L).
+//
+// Filters are processed in groups of G = 8 so that the 8 response planes of
+// the tile + halo fit in shared memory; the adjoint accumulators stay in
+// registers across groups.
+//
+// Work split (256 threads, TY = TX = 64):
+//   forward: units of 1 column x 7 rows x 8 filters over the 70 x 70 halo
+//            region (700 units); a unit slides the 13-row column window over
+//            the 7 kernel columns, each weight vector is a broadcast LDS.128
+//   adjoint: units of 4 x 4 output pixels (256 units, one per thread); each
+//            window row is three LDS.128, each filter's 49 weights are held
+//            in registers while its 10 window rows stream through
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "fe_internal.cuh"
+
+namespace fe {
+namespace {
+
+constexpr int TY = 64, TX = 64, NT = 256, G = 8;
+constexpr int R6Y = TY + 12, R6X = TX + 12;  // u^{n+1} region (tile + 6)
+constexpr int R3Y = TY + 6, R3X = TX + 6;    // response region (tile + 3)
+constexpr int SU_LD = R6X;                   // 76
+constexpr int SR_LD = 72;                    // >= R3X, multiple of 4, covers 4*15 + 12
+constexpr int NWARP = NT / 32;
+constexpr int FWD_ROWS = 7;                               // rows per forward unit
+constexpr int FWD_UNITS = R3X * (R3Y / FWD_ROWS);         // 700
+constexpr int RING = 2 * 3 * R3X + 2 * 3 * TY;            // 804 frame positions
+constexpr int RING_PER_T = (RING + NT - 1) / NT;          // 4
+static_assert(R3Y % FWD_ROWS == 0, "forward units tile the halo rows");
+static_assert((TY / 4) * (TX / 4) == NT, "one 4x4 adjoint unit per thread");
+static_assert(SR_LD >= 4 * (TX / 4 - 1) + 12, "adjoint window loads stay in the row");
+static_assert(TY == TX, "ring layout assumes a square tile");
+
+constexpr size_t SM_U = (size_t)R6Y * SU_LD;
+constexpr size_t SM_R = (size_t)G * R3Y * SR_LD;
+constexpr size_t SM_WF = (size_t)KT * NFMAX;
+constexpr size_t SM_WA = (size_t)NFMAX * KT_PAD;
+constexpr size_t SM_TH = NFMAX;
+constexpr size_t SM_FLOATS = SM_U + SM_R + SM_WF + SM_WA + SM_TH;
+constexpr size_t SM_BYTES = SM_FLOATS * 4 + (size_t)NWARP * NRED * 8;
+static_assert(SM_FLOATS % 2 == 0, "double scratch alignment");
+static_assert(SM_BYTES <= 227 * 1024, "fits the opt-in shared memory of one CTA");
+
+// Symmetric (half-sample) reflection for j in [-6, n+6) when n >= 6; indices
+// further out only feed responses outside the image and are clamped.
+__device__ __forceinline__ int reflect(int j, int n) {
+    j = j < 0 ? -j - 1 : j;
+    j = j >= n ? 2 * n - 1 - j : j;
+    return min(max(j, 0), n - 1);
+}
+
+// Closed-form prox of t*G at uhat (Sec. II-C), tl = t * lambda.
+__device__ __forceinline__ float prox_g(float uhat, float f2, float tl) {
+    const float D = fmaf(uhat, uhat, 4.0f * (1.0f + tl) * tl * f2);
+    const float sD = sqrtf(D);
+    return uhat >= 0.0f ? (uhat + sD) / (2.0f * (1.0f + tl)) : (2.0f * tl * f2) / (sD - uhat);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Position p in [0, T+6) of the frame/tile grid along one axis -> image
+// coordinate j; returns whether that position belongs to this tile (main
+// rows inside the image, or frame rows whose mirror image lies in the tile).
+__device__ __forceinline__ bool axis_pos(int p, int t0, int T, int N, int &j) {
+    if (p < 3) {
+        j = p - 3;
+        return t0 == 0;
+    }
+    if (p < T + 3) {
+        j = t0 + p - 3;
+        return j < N;
+    }
+    j = N + (p - T - 3);
+    const int tgt = 2 * N - 1 - j;
+    return tgt >= t0 && tgt < t0 + T;
+}
+
+__device__ __forceinline__ void ring_to_pos(int idx, int &pr, int &pc) {
+    if (idx < 3 * R3X) {
+        pr = idx / R3X;
+        pc = idx % R3X;
+    } else if (idx < 6 * R3X) {
+        idx -= 3 * R3X;
+        pr = TY + 3 + idx / R3X;
+        pc = idx % R3X;
+    } else if (idx < 6 * R3X + 3 * TY) {
+        idx -= 6 * R3X;
+        pr = 3 + idx / 3;
+        pc = idx % 3;
+    } else {
+        idx -= 6 * R3X + 3 * TY;
+        pr = 3 + idx / 3;
+        pc = TX + 3 + idx % 3;
+    }
+}
+
+__device__ __forceinline__ int pos_to_ring(int pr, int pc) {
+    if (pr < 3) return pr * R3X + pc;
+    if (pr >= TY + 3) return 3 * R3X + (pr - TY - 3) * R3X + pc;
+    if (pc < 3) return 6 * R3X + (pr - 3) * 3 + pc;
+    return 6 * R3X + 3 * TY + (pr - 3) * 3 + (pc - TX - 3);
+}
+
+// Accept / reject of the backtracking rule for one image (one thread).
+__device__ void decide(const KParams &p, ImgState *st, const double *t, int mode) {
+    const double F1 = t[0], G1 = t[1], gd = t[2], dd = t[3], dp = t[4];
+    if (mode == MODE_INIT) {
+        st->F = F1;
+        st->G = G1;
+        st->H = F1 + G1;
+        st->H_prev = F1 + G1;
+        st->alpha = 2.0 * (1.0 - p.beta) / (st->L + 2.0 * p.c2);
+        if (!isfinite(F1) || !isfinite(G1)) {
+            st->status = FE_ENONFINITE;
+            st->done = 1;
+        }
+        return;
+    }
+    st->trials += 1;
+    if (!isfinite(F1) || !isfinite(G1) || !isfinite(gd) || !isfinite(dd)) {
+        st->status = FE_ENONFINITE;
+        st->done = 1;
+        return;
+    }
+    if (F1 <= st->F + gd + 0.5 * st->L * dd) {
+        const double H1 = F1 + G1;
+        st->rel_change = fabs(H1 - st->H) / fabs(H1);
+        st->H_prev = st->H;
+        st->F = F1;
+        st->G = G1;
+        st->H = H1;
+        st->last_gd = gd;
+        st->last_dd = dd;
+        st->last_dp = dp;
+        st->cur = (st->cur + 1) % 3;
+        st->gcur ^= 1;
+        st->n += 1;
+        st->bt = 0;
+        if (st->tol > 0.0 && st->rel_change < st->tol) {
+            st->converged = 1;
+            st->done = 1;
+        }
+    } else {
+        st->backtracks += 1;
+        if (st->bt >= p.max_bt) {
+            st->status = FE_EBACKTRACK;
+            st->done = 1;
+            return;
+        }
+        st->bt += 1;
+        st->L *= p.eta;
+        st->alpha = 2.0 * (1.0 - p.beta) / (st->L + 2.0 * p.c2);
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(NT, 1) fp32_tile_kernel(const KParams p) {
+    extern __shared__ __align__(16) float smem[];
+    float *sU = smem;
+    float *sR = sU + SM_U;
+    float *sWf = sR + SM_R;
+    float *sWa = sWf + SM_WF;
+    float *sTh = sWa + SM_WA;
+    double *sRed = reinterpret_cast<double *>(sTh + SM_TH);
+    __shared__ int sLast;
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int gtile = p.tile0 + (int)blockIdx.x;
+    const TileDesc td = p.tiles[gtile];
+    const int img = td.img;
+    const ImgDesc im = p.imgs[img];
+    ImgState *st = p.st + img;
+    const int H = im.H, W = im.W, y0 = td.y0, x0 = td.x0;
+
+    bool active = true;
+    int gcur_out = 0;
+    if (MODE == MODE_TRIAL) {
+        active = (st->done == 0) && (st->n < st->target);
+        gcur_out = st->gcur ^ 1;
+    }
+
+    if (active) {
+        // ---- filter bank into shared memory ------------------------------
+        for (int j = tid; j < KT * NFMAX / 4; j += NT)
+            reinterpret_cast<float4 *>(sWf)[j] = reinterpret_cast<const float4 *>(p.wf)[j];
+        for (int j = tid; j < NFMAX * KT_PAD / 4; j += NT)
+            reinterpret_cast<float4 *>(sWa)[j] = reinterpret_cast<const float4 *>(p.wa)[j];
+        if (tid < NFMAX) sTh[tid] = p.theta[tid];
+
+        // ---- 1+2: inertial step and prox on tile + 6 ---------------------
+        double accF = 0.0, accG = 0.0, accGD = 0.0, accDD = 0.0, accDP = 0.0;
+        {
+            int cur = 0, gcur = 0;
+            float a = 0.f, b = 0.f, tl = 0.f;
+            if (MODE == MODE_TRIAL) {
+                cur = st->cur;
+                gcur = st->gcur;
+                const double alpha = st->alpha;
+                a = (float)alpha;
+                b = (float)p.beta;
+                tl = (float)(alpha * im.lambda);
+            }
+            const float *uc = (MODE == MODE_TRIAL || MODE == MODE_INIT) ? im.u[cur] : p.u_ext;
+            const float *upv = im.u[(cur + 2) % 3];
+            const float *gc = im.g[gcur];
+            float *un = im.u[(cur + 1) % 3];
+            const float *f2p = im.f2;
+            for (int idx = tid; idx < R6Y * R6X; idx += NT) {
+                const int ry = idx / R6X, rx = idx - ry * R6X;
+                const int y = y0 - 6 + ry, x = x0 - 6 + rx;
+                const size_t off = (size_t)reflect(y, H) * W + reflect(x, W);
+                const bool inner = ry >= 6 && ry < 6 + TY && rx >= 6 && rx < 6 + TX && y < H && x < W;
+                float v;
+                if (MODE == MODE_TRIAL) {
+                    const float u0 = __ldg(uc + off), u_1 = __ldg(upv + off), g0 = __ldg(gc + off);
+                    const float f2 = __ldg(f2p + off);
+                    const float dprev = u0 - u_1;
+                    const float uhat = fmaf(-a, g0, fmaf(b, dprev, u0));
+                    v = prox_g(uhat, f2, tl);
+                    if (inner) {
+                        un[off] = v;
+                        const float d = v - u0;
+                        accGD += (double)(g0 * d);
+                        accDD += (double)(d * d);
+                        accDP += (double)(d * dprev);
+                        accG += (double)(v * v - 2.0f * f2 * logf(v));
+                    }
+                } else {
+                    v = __ldg(uc + off);
+                    if (inner) accG += (double)(v * v - 2.0f * __ldg(f2p + off) * logf(v));
+                }
+                sU[ry * SU_LD + rx] = v;
+            }
+        }
+
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+        float fr[RING_PER_T];
+#pragma unroll
+        for (int k = 0; k < RING_PER_T; ++k) fr[k] = 0.f;
+        const int aux = tid & 15, auy = tid >> 4;  // adjoint unit of this thread
+
+        for (int grp = 0; grp < p.nfp / G; ++grp) {
+            __syncthreads();  // sU / weights ready; previous group's sR reads done
+            // ---- 3+4: forward bank and potential on tile + 3 -------------
+            for (int unit = tid; unit < FWD_UNITS; unit += NT) {
+                const int c = unit % R3X, rb = unit / R3X;
+                float z[FWD_ROWS][G];
+#pragma unroll
+                for (int r = 0; r < FWD_ROWS; ++r)
+#pragma unroll
+                    for (int i = 0; i < G; ++i) z[r][i] = 0.f;
+                const float *ucol = sU + rb * FWD_ROWS * SU_LD + c;
+                const float *wcol = sWf + grp * G;
+#pragma unroll 1
+                for (int bb = 0; bb < KS; ++bb) {
+                    float v[FWD_ROWS + KS - 1];
+#pragma unroll
+                    for (int r = 0; r < FWD_ROWS + KS - 1; ++r) v[r] = ucol[r * SU_LD + bb];
+#pragma unroll
+                    for (int aa = 0; aa < KS; ++aa) {
+                        const float4 w0 = *reinterpret_cast<const float4 *>(wcol + (aa * KS + bb) * NFMAX);
+                        const float4 w1 = *reinterpret_cast<const float4 *>(wcol + (aa * KS + bb) * NFMAX + 4);
+                        const float w[G] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                        for (int r = 0; r < FWD_ROWS; ++r)
+#pragma unroll
+                            for (int i = 0; i < G; ++i) z[r][i] = fmaf(w[i], v[r + aa], z[r][i]);
+                    }
+                }
+                // epilogue: rho' into sR, rho into the energy partial
+                const int x = x0 - 3 + c;
+                const bool colin = x >= 0 && x < W, colint = c >= 3 && c < 3 + TX;
+                float fsum = 0.f;
+#pragma unroll
+                for (int r = 0; r < FWD_ROWS; ++r) {
+                    const int pr = rb * FWD_ROWS + r;
+                    const int y = y0 - 3 + pr;
+                    const bool inimg = colin && y >= 0 && y < H;
+                    const bool inner = inimg && colint && pr >= 3 && pr < 3 + TY;
+#pragma unroll
+                    for (int i = 0; i < G; ++i) {
+                        const float zz = z[r][i];
+                        const float q = fmaf(zz, zz, 1.0f);
+                        const float th = sTh[grp * G + i];
+                        if (MODE != MODE_ENERGY_EXT)
+                            sR[(i * R3Y + pr) * SR_LD + c] = inimg ? th * __fdividef(2.0f * zz, q) : 0.0f;
+                        if (inner) fsum = fmaf(th, __logf(q), fsum);
+                    }
+                }
+                accF += (double)fsum;
+            }
+            if (MODE == MODE_ENERGY_EXT) continue;
+            __syncthreads();  // sR complete
+
+            // ---- 5: adjoint bank on the tile (4x4 unit per thread) --------
+            for (int i = 0; i < G; ++i) {
+                const float *wrow = sWa + (grp * G + i) * KT_PAD;
+                float kw[KT_PAD];
+#pragma unroll
+                for (int j = 0; j < KT_PAD / 4; ++j) {
+                    const float4 t = reinterpret_cast<const float4 *>(wrow)[j];
+                    kw[4 * j] = t.x;
+                    kw[4 * j + 1] = t.y;
+                    kw[4 * j + 2] = t.z;
+                    kw[4 * j + 3] = t.w;
+                }
+                const float *Ri = sR + (size_t)i * R3Y * SR_LD + (4 * auy) * SR_LD + 4 * aux;
+#pragma unroll
+                for (int rr = 0; rr < 4 + KS - 1; ++rr) {
+                    const float4 a0 = *reinterpret_cast<const float4 *>(Ri + rr * SR_LD);
+                    const float4 a1 = *reinterpret_cast<const float4 *>(Ri + rr * SR_LD + 4);
+                    const float4 a2 = *reinterpret_cast<const float4 *>(Ri + rr * SR_LD + 8);
+                    const float v[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
+#pragma unroll
+                    for (int pp = 0; pp < 4; ++pp) {
+                        const int aa = rr - pp;
+                        if (aa < 0 || aa >= KS) continue;
+#pragma unroll
+                        for (int bb = 0; bb < KS; ++bb)
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) acc[pp][q] = fmaf(kw[aa * KS + bb], v[q + bb], acc[pp][q]);
+                    }
+                }
+            }
+            // ---- 5b: K^T r on the frame outside the image (border tiles) --
+            const bool border = y0 == 0 || x0 == 0 || y0 + TY > H - 3 || x0 + TX > W - 3;
+            if (border) {
+#pragma unroll
+                for (int k = 0; k < RING_PER_T; ++k) {
+                    const int idx = tid + k * NT;
+                    if (idx >= RING) break;
+                    int pr, pc, j, jx;
+                    ring_to_pos(idx, pr, pc);
+                    if (!axis_pos(pr, y0, TY, H, j) || !axis_pos(pc, x0, TX, W, jx)) continue;
+                    // s(j, jx) = sum_i sum_ab k_i[a][b] r_i(j - 3 + a, jx - 3 + b)
+                    float s = 0.f;
+                    for (int i = 0; i < G; ++i) {
+                        const float *wrow = sWa + (grp * G + i) * KT_PAD;
+                        const float *Ri = sR + (size_t)i * R3Y * SR_LD;
+                        for (int aa = 0; aa < KS; ++aa) {
+                            const int rrow = j - y0 + aa;  // response-region row
+                            const int yy = j - 3 + aa;     // image row
+                            if (rrow < 0 || rrow >= R3Y || yy < 0 || yy >= H) continue;
+                            for (int bb = 0; bb < KS; ++bb) {
+                                const int rcol = jx - x0 + bb;
+                                const int xx = jx - 3 + bb;
+                                if (rcol < 0 || rcol >= R3X || xx < 0 || xx >= W) continue;
+                                s = fmaf(wrow[aa * KS + bb], Ri[rrow * SR_LD + rcol], s);
+                            }
+                        }
+                    }
+                    fr[k] += s;
+                }
+            }
+        }
+
+        if (MODE != MODE_ENERGY_EXT) {
+            // ---- fold the frame back onto the pixels it mirrors ----------
+            __syncthreads();  // all sR reads done; reuse sR for the ring
+            const bool border = y0 == 0 || x0 == 0 || y0 + TY > H - 3 || x0 + TX > W - 3;
+            if (border) {
+#pragma unroll
+                for (int k = 0; k < RING_PER_T; ++k) {
+                    const int idx = tid + k * NT;
+                    if (idx < RING) sR[idx] = fr[k];
+                }
+                __syncthreads();
+            }
+            float *gout;
+            if (MODE == MODE_GRAD_EXT)
+                gout = p.g_ext;
+            else if (MODE == MODE_INIT)
+                gout = im.g[0];
+            else
+                gout = im.g[gcur_out];
+#pragma unroll
+            for (int pp = 0; pp < 4; ++pp) {
+                const int y = y0 + 4 * auy + pp;
+                if (y >= H) continue;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int x = x0 + 4 * aux + q;
+                    if (x >= W) continue;
+                    float gv = acc[pp][q];
+                    if (border && (y < 3 || y >= H - 3 || x < 3 || x >= W - 3)) {
+                        // frame positions that the symmetric extension maps onto (y, x)
+                        int py[3], px[3], ny = 1, nx = 1;
+                        py[0] = y - y0 + 3;
+                        px[0] = x - x0 + 3;
+                        if (y < 3) py[ny++] = 2 - y;                  // j = -y-1
+                        if (y >= H - 3) py[ny++] = TY + 2 + H - y;    // j = 2H-1-y
+                        if (x < 3) px[nx++] = 2 - x;
+                        if (x >= W - 3) px[nx++] = TX + 2 + W - x;
+                        for (int m = 0; m < ny; ++m)
+                            for (int n = 0; n < nx; ++n) {
+                                if (m == 0 && n == 0) continue;
+                                gv += sR[pos_to_ring(py[m], px[n])];
+                            }
+                    }
+                    gout[(size_t)y * W + x] = gv;
+                }
+            }
+        }
+
+        // ---- 6: per-tile FP64 partial sums -------------------------------
+        double vals[NRED] = {accF, accG, accGD, accDD, accDP};
+#pragma unroll
+        for (int k = 0; k < NRED; ++k) {
+            const double v = warp_sum(vals[k]);
+            if (lane == 0) sRed[warp * NRED + k] = v;
+        }
+        __syncthreads();
+        if (tid < NRED) {
+            double s = 0.0;
+            for (int w = 0; w < NWARP; ++w) s += sRed[w * NRED + tid];
+            p.partials[(size_t)gtile * NRED + tid] = s;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            const unsigned prev = atomicAdd(p.img_arrivals + img, 1u);
+            sLast = (prev == (unsigned)im.ntiles - 1u);
+        }
+        __syncthreads();
+        if (sLast) {
+            // the last CTA of this image: fixed-order reduction + decision
+            __threadfence();
+            double part[NRED];
+#pragma unroll
+            for (int k = 0; k < NRED; ++k) part[k] = 0.0;
+            for (int t = tid; t < im.ntiles; t += NT)
+#pragma unroll
+                for (int k = 0; k < NRED; ++k) part[k] += __ldcg(p.partials + (size_t)(im.tile_begin + t) * NRED + k);
+#pragma unroll
+            for (int k = 0; k < NRED; ++k) {
+                const double v = warp_sum(part[k]);
+                if (lane == 0) sRed[warp * NRED + k] = v;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double tot[NRED];
+                for (int k = 0; k < NRED; ++k) {
+                    double s = 0.0;
+                    for (int w = 0; w < NWARP; ++w) s += sRed[w * NRED + k];
+                    tot[k] = s;
+                }
+                tot[1] *= 0.5 * im.lambda;  // G = (lambda/2) sum_p (u^2 - 2 f^2 log u)
+                if (MODE == MODE_TRIAL || MODE == MODE_INIT) {
+                    decide(p, st, tot, MODE);
+                } else {
+                    p.results[2 * img] = tot[0];
+                    p.results[2 * img + 1] = tot[1];
+                }
+                p.img_arrivals[img] = 0u;
+                __threadfence();
+            }
+        }
+    }
+
+    // ---- loop control: the last CTA of the launch --------------------------
+    if (MODE == MODE_TRIAL) {
+        if (tid == 0) {
+            __threadfence();
+            const unsigned prev = atomicAdd(&p.loop->grid_arrivals, 1u);
+            if (prev == gridDim.x - 1u) {
+                __threadfence();
+                LoopCtl *lc = p.loop;
+                lc->grid_arrivals = 0u;
+                long long budget = lc->budget - 1;
+                int nact = 0;
+                for (int j = 0; j < p.nimg; ++j) {
+                    volatile ImgState *s = p.st + j;
+                    if (s->done == 0 && s->n < s->target) {
+                        if (budget <= 0) {
+                            s->status = FE_ETIMEOUT;
+                            s->done = 1;
+                        } else {
+                            ++nact;
+                        }
+                    }
+                }
+                lc->budget = budget;
+                lc->active = nact;
+                lc->launches += 1;
+                __threadfence();
+                if (p.use_cond) cudaGraphSetConditional(p.cond, nact > 0 ? 1u : 0u);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+size_t fp32_smem_bytes() { return SM_BYTES; }
+int fp32_tile() { return TY; }
+
+cudaError_t fp32_prepare() {
+    cudaError_t e;
+    e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_TRIAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_BYTES);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_INIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_BYTES);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_GRAD_EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_BYTES);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fp32_tile_kernel<MODE_ENERGY_EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_BYTES);
+}
+
+cudaError_t fp32_launch(int mode, const KParams &p, int ngrid, cudaStream_t s) {
+    const dim3 grid(ngrid), block(NT);
+    switch (mode) {
+        case MODE_TRIAL: fp32_tile_kernel<MODE_TRIAL><<<grid, block, SM_BYTES, s>>>(p); break;
+        case MODE_INIT: fp32_tile_kernel<MODE_INIT><<<grid, block, SM_BYTES, s>>>(p); break;
+        case MODE_GRAD_EXT: fp32_tile_kernel<MODE_GRAD_EXT><<<grid, block, SM_BYTES, s>>>(p); break;
+        case MODE_ENERGY_EXT: fp32_tile_kernel<MODE_ENERGY_EXT><<<grid, block, SM_BYTES, s>>>(p); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+const void *fp32_trial_entry() { return reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL>); }
+
+}  // namespace fe

@@ -1,0 +1,98 @@
+// Internal declarations of libfe shared by its translation units.
+//
+// Device data model (per image j of a context):
+//   u[0..2]  three rotating FP32 planes: u^n = u[cur], u^{n-1} = u[(cur+2)%3],
+//            the trial writes u^{n+1} into u[(cur+1)%3]
+//   g[0..1]  grad F(u^n) = g[gcur]; the trial writes grad F(u^{n+1}) into g[gcur^1]
+//   f2       f^2 (the data term and its prox only use f^2)
+// A rejected trial leaves cur/gcur untouched, so its outputs are simply
+// overwritten by the next trial.  All planes are row-major with pitch W.
+//
+// Each launch of a tile kernel covers every tile of every image; the last
+// block to finish an image reduces that image's per-tile partial sums in a
+// fixed order (deterministic) and takes the accept/reject decision of the
+// backtracking rule on the device; the last block of the grid updates the
+// device-side loop control (count of active images, trial budget, and the
+// while-condition of the CUDA graph when the loop runs as a graph).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fe.h"
+
+namespace fe {
+
+constexpr int NRED = 5;  // F(u1), G(u1), <g,D>, |D|^2, <D, u^n - u^{n-1}>
+constexpr int NFMAX = 64;
+constexpr int KS = 7;
+constexpr int KT = KS * KS;  // 49 taps
+constexpr int KT_PAD = 52;   // per-filter stride of the adjoint weight table
+
+enum Mode : int {
+    MODE_TRIAL = 0,       // one iPiano trial from u^n, u^{n-1}, g^n
+    MODE_INIT = 1,        // g = grad F(u[0]) into g[0]; F, G; initialise the state
+    MODE_GRAD_EXT = 2,    // g_ext = grad F(u_ext); F, G into results
+    MODE_ENERGY_EXT = 3,  // F(u_ext), G(u_ext) into results
+};
+
+struct ImgDesc {
+    int H, W;
+    int tile_begin, ntiles;
+    float *u[3];
+    float *g[2];
+    float *f2;
+    double lambda;
+};
+
+struct ImgState {
+    double F, G, H, H_prev;
+    double L, alpha;
+    double rel_change, last_gd, last_dd, last_dp;
+    double tol;
+    long long n, trials, backtracks, target;
+    int cur, gcur, bt, status, done, converged;
+};
+
+struct TileDesc {
+    int img, y0, x0, pad;
+};
+
+struct LoopCtl {
+    unsigned grid_arrivals;  // blocks arrived in the current launch
+    int active;              // images still iterating after the last launch
+    long long budget;        // trial launches left before FE_ETIMEOUT
+    long long launches;      // trial launches executed (for launch accounting)
+};
+
+struct KParams {
+    const ImgDesc *imgs;
+    ImgState *st;
+    const TileDesc *tiles;
+    double *partials;        // [ntiles][NRED]
+    unsigned *img_arrivals;  // [nimg]
+    LoopCtl *loop;
+    const float *wf;     // forward weights, flipped, tap-major: wf[t * NFMAX + i] = k_i[48 - t]
+    const float *wa;     // adjoint weights, filter-major: wa[i * KT_PAD + t] = k_i[t]
+    const float *theta;  // [NFMAX], zero beyond nf
+    int nfp;             // nf rounded up to the filter-group size
+    int nimg, ntiles;
+    double beta, eta, c2;
+    int max_bt;
+    int tile0;                  // first global tile of this launch (grid covers tile0 ..)
+    const float *u_ext;         // input of the EXT modes (one image per launch)
+    float *g_ext;               // gradient output of MODE_GRAD_EXT
+    double *results;            // [nimg][2]: F, G of the EXT modes
+    unsigned long long cond;    // cudaGraphConditionalHandle of the while node
+    int use_cond;
+};
+
+// FP32 fused tile kernel (fe_fp32.cu)
+size_t fp32_smem_bytes();
+int fp32_tile();
+cudaError_t fp32_prepare();  // opt in to the large shared-memory carve-out
+cudaError_t fp32_launch(int mode, const KParams &p, int grid, cudaStream_t s);
+const void *fp32_trial_entry();
+
+// Bookkeeping kernels (fe_api.cu)
+}  // namespace fe

@@ -167,3 +167,22 @@ def test_tolerance_stop(orc):
     H = np.concatenate([[out["F0"] + out["G0"]], out["rec"][:, 4]])
     rel = np.abs(np.diff(H)) / np.abs(H[1:])
     assert rel[-1] < 1e-6 and np.all(rel[:-1] >= 1e-6)
+
+
+def test_fixed_sequence_matches_backtracking_run(orc):
+    """Replaying the accepted L_n of a backtracking run with the prescribed-L
+    iteration reproduces the run, and every replayed margin is >= 0."""
+    k, th = _bank(6, seed=2)
+    _, f = _problem(14, 15, seed=8)
+    prm = orc.params(lam=0.05, beta=0.7, L0=1e-3, max_iter=25)
+    a = orc.ipiano(f, k, th, prm)
+    assert a["status"] == 0 and a["rec"][:, 5].sum() > 0
+    b = orc.ipiano_fixed(f, k, th, prm, a["rec"][:, 0], f)
+    np.testing.assert_allclose(b["u"], a["u"], rtol=1e-13)
+    np.testing.assert_allclose(b["rec"][:, 4], a["rec"][:, 4], rtol=1e-13)
+    assert np.all(b["rec"][:, 5] >= 0)
+    # a rejected candidate (L / eta at a backtracked iteration) has margin < 0
+    n = int(np.argmax(a["rec"][:, 5] > 0))
+    start = orc.ipiano_fixed(f, k, th, prm, a["rec"][:n, 0], f) if n else dict(u=f, u_prev=f)
+    c = orc.ipiano_fixed(f, k, th, prm, [a["rec"][n, 0] / 2.0], start["u"], start["u_prev"])
+    assert c["rec"][0, 5] < 0
