@@ -184,6 +184,34 @@ FE_API long long fe_launch_count(const fe_ctx *ctx);
  * node (default when the driver supports it). */
 FE_API fe_status fe_set_loop_mode(fe_ctx *ctx, int mode);
 
+/* Allocation-free gradient of one image: grad F(u) into g and F(u) into *F,
+ * the same computation as fe_gradient, without a context.  The paper has no
+ * counterpart; this entry exists for callers that may not allocate device
+ * memory on the path where they call it (for example a plugin confined to a
+ * host framework's fixed memory pool, or a real-time loop that forbids the
+ * allocation calls and the synchronisation they can bring).
+ *
+ * All pointers are DEVICE pointers owned by the caller: u and g hold H*W
+ * floats (row-major, pitch W; g must not alias u), filters holds nf*49 floats
+ * (k_i[a][b] row-major), theta holds nf floats, F (may be NULL) one double.
+ * Asynchronous on stream (a cudaStream_t, NULL = legacy default stream).
+ *
+ * No cudaMalloc, cudaFree or other allocating call is made.  The scratch
+ * (tile list, weight tables, per-tile partial sums, counters) is one static
+ * device array of about 0.3 MB that every GPU loading this library holds
+ * until the process exits, which limits the image to at most 4096 tiles of
+ * 64x64 pixels (e.g. 4096 x 4096); larger images return FE_EINVAL.  All calls
+ * share that array and it keeps the last call's contents (each call rewrites
+ * what it reads); calls whose kernels overlap on the GPU race on it and must
+ * be serialised by the caller.  The first call on a device does a one-time
+ * set-up with that device current (device address of the array, kernel
+ * attribute) and should come before any stream capture.
+ * Errors: FE_EINVAL (NULL pointer, nf outside 1..64, H or W < 8, too many
+ * tiles), FE_ECUDA; the message is in fe_last_error(NULL). */
+FE_API fe_status fe_gradient_noalloc(const float *u, float *g, double *F, int H, int W,
+                                     const float *filters, const float *theta, int nf,
+                                     void *stream);
+
 FE_API const char *fe_last_error(const fe_ctx *ctx);
 FE_API const char *fe_status_string(fe_status s);
 FE_API int fe_abi_version(void);

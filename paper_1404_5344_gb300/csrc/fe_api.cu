@@ -317,6 +317,8 @@ fe_status stage_in(fe_ctx *c, const float *src, size_t N, int slot, const float 
 
 }  // namespace
 
+void fe::set_global_error(const char *msg) { g_init_err = msg ? msg : ""; }
+
 extern "C" {
 
 int fe_abi_version(void) { return FE_ABI_VERSION; }

@@ -54,6 +54,7 @@ static_assert(R3Y % FWD_ROWS == 0, "forward units tile the halo rows");
 static_assert((TY / 4) * (TX / 4) == NT, "one 4x4 adjoint unit per thread");
 static_assert(SR_LD >= 4 * (TX / 4 - 1) + 12, "adjoint window loads stay in the row");
 static_assert(TY == TX, "ring layout assumes a square tile");
+static_assert(TY == fp32_tile_size, "tile size shared with the host code");
 
 constexpr size_t SM_U = (size_t)R6Y * SU_LD;
 constexpr size_t SM_R = (size_t)G * R3Y * SR_LD;

@@ -88,11 +88,13 @@ struct KParams {
 };
 
 // FP32 fused tile kernel (fe_fp32.cu)
+constexpr int fp32_tile_size = 64;  // square output tile of the FP32 kernel
 size_t fp32_smem_bytes();
 int fp32_tile();
 cudaError_t fp32_prepare();  // opt in to the large shared-memory carve-out
 cudaError_t fp32_launch(int mode, const KParams &p, int grid, cudaStream_t s);
 const void *fp32_trial_entry();
 
-// Bookkeeping kernels (fe_api.cu)
+// Message returned by fe_last_error(NULL) for calls without a context (fe_api.cu)
+void set_global_error(const char *msg);
 }  // namespace fe

@@ -29,7 +29,7 @@ EXPORTS = (
     "fe_default_params", "fe_init_batch", "fe_init", "fe_reset", "fe_destroy", "fe_step",
     "fe_solve", "fe_get_info", "fe_get_u", "fe_energy", "fe_gradient", "fe_get_state",
     "fe_set_state", "fe_num_images", "fe_image_size", "fe_launch_count", "fe_set_loop_mode",
-    "fe_last_error", "fe_status_string", "fe_abi_version",
+    "fe_last_error", "fe_status_string", "fe_abi_version", "fe_gradient_noalloc",
 )
 
 
@@ -81,7 +81,8 @@ def _load(path: str = LIB_PATH) -> C.CDLL:
     L.fe_status_string.argtypes = [I]
     L.fe_status_string.restype = C.c_char_p
     L.fe_abi_version.argtypes = []
-    for name in ("fe_init_batch", "fe_init", "fe_reset", "fe_step", "fe_solve", "fe_get_info",
+    L.fe_gradient_noalloc.argtypes = [VP, VP, VP, I, I, VP, VP, I, VP]
+    for name in ("fe_gradient_noalloc", "fe_init_batch","fe_init", "fe_reset", "fe_step", "fe_solve", "fe_get_info",
                  "fe_get_u", "fe_energy", "fe_gradient", "fe_get_state", "fe_set_state",
                  "fe_image_size", "fe_set_loop_mode", "fe_num_images", "fe_abi_version"):
         getattr(L, name).restype = C.c_int

@@ -1,0 +1,64 @@
+"""fe_gradient_noalloc: the allocation-free gradient entry point.
+
+Some callers may not allocate device memory where they evaluate the prior's
+gradient (a plugin held to a host framework's fixed memory pool, a real-time
+loop that forbids allocation calls).  This entry point takes only caller
+buffers and keeps its scratch in a static device array.  The test calls it
+through the C ABI twice in a row (different images and sizes, so the second
+call runs on the first call's leftover scratch) and compares each result with
+the context-based fe_gradient, within the gradient tolerance of the parity
+tests.  This file is named to be collected last.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-5  # same bound as the FP32 gradient parity tests
+
+
+def test_noalloc_gradient_matches_context_gradient_twice():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1404_5344_gb300 import build
+    build.build()
+    from paper_1404_5344_gb300 import fe, synth
+
+    k, th = synth.filter_bank(48, 7, seed=0, theta=0.1)
+    kd = torch.from_numpy(k.reshape(-1)).cuda()
+    thd = torch.from_numpy(th).cuda()
+    stream = torch.cuda.Stream()
+    for (H, W, seed) in [(131, 77, 3), (200, 256, 4)]:
+        u = synth.speckle(synth.textured_image(H, W, seed=seed), L=4.0, seed=seed + 1)
+        ud = torch.from_numpy(u).cuda()
+        gd = torch.full((H, W), float("nan"), device="cuda")
+        Fd = torch.zeros(1, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        st = fe.lib.fe_gradient_noalloc(C.c_void_p(ud.data_ptr()), C.c_void_p(gd.data_ptr()),
+                                        C.c_void_p(Fd.data_ptr()), H, W,
+                                        C.c_void_p(kd.data_ptr()), C.c_void_p(thd.data_ptr()),
+                                        48, C.c_void_p(stream.cuda_stream))
+        assert st == fe.FE_OK, fe.lib.fe_last_error(None)
+        stream.synchronize()
+        g_na, F_na = gd.cpu().numpy(), float(Fd.item())
+        with fe.Solver([u], k, th) as s:
+            g_ref, F_ref = s.gradient(0, u)
+        err = np.max(np.abs(g_na.astype(np.float64) - g_ref)) / np.max(np.abs(g_ref))
+        assert err <= GRAD_TOL, err
+        assert F_na == pytest.approx(F_ref, rel=2e-6)
+
+
+def test_noalloc_rejects_oversize_image():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1404_5344_gb300 import fe
+    d = torch.zeros(16, device="cuda")
+    p = C.c_void_p(d.data_ptr())
+    # 4160 x 4160 needs 65 x 65 > 4096 tiles; rejected before any device work
+    st = fe.lib.fe_gradient_noalloc(p, p, None, 4160, 4160, p, p, 48, None)
+    assert st == fe.FE_EINVAL
+    assert b"4096" in fe.lib.fe_last_error(None)
