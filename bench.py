@@ -222,7 +222,7 @@ def main():
         if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ClockSampler(local, "/tmp/fe_clocks.csv")
     total_ms, loop_ms = 0.0, 0.0
     lc0 = solver.launch_count()
-    pix_iters_done, trials = 0, 0
+    pix_iters_done, trials, pix_trials = 0, 0, 0
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
             flush.fill_(1.0)
@@ -237,6 +237,7 @@ def main():
         infos = [solver.info(i) for i in range(len(fs))]
         pix_iters_done += sum(x["n"] * h * w for x, (h, w) in zip(infos, shapes))
         trials += sum(x["trials"] for x in infos)
+        pix_trials += sum(x["trials"] * h * w for x, (h, w) in zip(infos, shapes))
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = solver.launch_count() - lc0
@@ -249,13 +250,15 @@ def main():
     T_ms = float(t_tensor.item())
     value = pix_iters_done * world / (T_ms / 1e3) / 1e6
 
-    # trial-kernel launch duration = time of the iteration loop / launches of
-    # the trial kernel (each step also runs one prep kernel per image, the
-    # initial-gradient kernel and the loop-begin kernel)
+    # Trial-kernel rate: algorithmic work of every image-trial that ran
+    # (9408 flop per pixel, accepted and rejected trials alike) over the
+    # device time of the iteration loop (trial launches + one loop-begin
+    # kernel per step; the per-step restart is outside this window).  A
+    # launch late in a step covers only the images still iterating, so work
+    # is counted per image-trial, not per launch.
     trial_launches = max(1, launches - args.steps * (len(fs) + 2))
     per_launch_ms = loop_ms / trial_launches
-    flop_per_launch = FLOP_PER_PIXEL_TRIAL * npix
-    achieved_tflops = flop_per_launch / (per_launch_ms / 1e3) / 1e12
+    achieved_tflops = FLOP_PER_PIXEL_TRIAL * pix_trials / (loop_ms / 1e3) / 1e12
     sm_mhz_max = (clk or {}).get("sm_max_mhz") or 2070.0
     peak_tflops = SMS * FP32_LANES * 2 * sm_mhz_max * 1e6 / 1e12
 

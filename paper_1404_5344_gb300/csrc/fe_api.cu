@@ -239,7 +239,7 @@ fe_status build_graph(fe_ctx *c) {
     std::memset(&knp, 0, sizeof knp);
     knp.func = const_cast<void *>(fp32_trial_entry());
     knp.gridDim = dim3(c->ntiles);
-    knp.blockDim = dim3(256);
+    knp.blockDim = dim3(fp32_threads());
     knp.sharedMemBytes = (unsigned)fp32_smem_bytes();
     knp.kernelParams = args;
     cudaGraphNode_t kn;

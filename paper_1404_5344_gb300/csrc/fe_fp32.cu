@@ -20,14 +20,16 @@
 //      <D, u^n - u^{n-1}>; the last CTA of the image reduces them in a fixed
 //      order and applies the backtracking test (accept / L <- eta L).
 //
-// Filters are processed in groups of G = 8 so that the 8 response planes of
+// Filters are processed in groups of G = 4 so that the 4 response planes of
 // the tile + halo fit in shared memory; the adjoint accumulators stay in
 // registers across groups.
 //
-// Work split (256 threads, TY = TX = 64):
-//   forward: units of 1 column x 7 rows x 8 filters over the 70 x 70 halo
-//            region (700 units); a unit slides the 13-row column window over
-//            the 7 kernel columns, each weight vector is a broadcast LDS.128
+// Work split (256 threads, two CTAs per SM so that one CTA's barrier waits
+// are covered by the other; TY = TX = 64, G = 4):
+//   forward: units of 1 column x 10 rows x 4 filters over the 70 x 70 halo
+//            region (490 units, two rounds); a unit slides its 16-row column
+//            window over the 7 kernel columns; weight vectors are uniform
+//            128-bit loads from the tap-major table in global memory (L1)
 //   adjoint: units of 4 x 4 output pixels (256 units, one per thread); each
 //            window row is three LDS.128, each filter's 49 weights are held
 //            in registers while its 10 window rows stream through
@@ -40,31 +42,33 @@
 namespace fe {
 namespace {
 
-constexpr int TY = 64, TX = 64, NT = 256, G = 8;
+constexpr int TY = 64, TX = 64, NT = 256, G = 4;
 constexpr int R6Y = TY + 12, R6X = TX + 12;  // u^{n+1} region (tile + 6)
 constexpr int R3Y = TY + 6, R3X = TX + 6;    // response region (tile + 3)
-constexpr int SU_LD = R6X;                   // 76
+constexpr int SU_LD = 87;  // >= R6X; 10*87 = 70 (mod 32): unit rows wrap without bank conflicts
 constexpr int SR_LD = 72;                    // >= R3X, multiple of 4, covers 4*15 + 12
 constexpr int NWARP = NT / 32;
-constexpr int FWD_ROWS = 7;                               // rows per forward unit
-constexpr int FWD_UNITS = R3X * (R3Y / FWD_ROWS);         // 700
-constexpr int RING = 2 * 3 * R3X + 2 * 3 * TY;            // 804 frame positions
-constexpr int RING_PER_T = (RING + NT - 1) / NT;          // 4
+constexpr int FWD_ROWS = 10;                       // rows per forward unit
+constexpr int FWD_WIN = FWD_ROWS + KS - 1;         // 16-row column window
+constexpr int FWD_UNITS = R3X * (R3Y / FWD_ROWS);  // 490
+constexpr int ADJ_UNITS = (TY / 4) * (TX / 4);     // 256
+constexpr int RING = 2 * 3 * R3X + 2 * 3 * TY;     // 804 frame positions
+constexpr int RING_PER_T = (RING + NT - 1) / NT;   // 4
 static_assert(R3Y % FWD_ROWS == 0, "forward units tile the halo rows");
-static_assert((TY / 4) * (TX / 4) == NT, "one 4x4 adjoint unit per thread");
+static_assert(NT == ADJ_UNITS, "one adjoint unit per thread");
 static_assert(SR_LD >= 4 * (TX / 4 - 1) + 12, "adjoint window loads stay in the row");
 static_assert(TY == TX, "ring layout assumes a square tile");
 static_assert(TY == fp32_tile_size, "tile size shared with the host code");
 
 constexpr size_t SM_U = (size_t)R6Y * SU_LD;
 constexpr size_t SM_R = (size_t)G * R3Y * SR_LD;
-constexpr size_t SM_WF = (size_t)KT * NFMAX;
-constexpr size_t SM_WA = (size_t)NFMAX * KT_PAD;
-constexpr size_t SM_TH = NFMAX;
-constexpr size_t SM_FLOATS = SM_U + SM_R + SM_WF + SM_WA + SM_TH;
+constexpr size_t SM_FLOATS = SM_U + SM_R;
 constexpr size_t SM_BYTES = SM_FLOATS * 4 + (size_t)NWARP * NRED * 8;
 static_assert(SM_FLOATS % 2 == 0, "double scratch alignment");
-static_assert(SM_BYTES <= 227 * 1024, "fits the opt-in shared memory of one CTA");
+static_assert(2 * (SM_BYTES + 1024) <= 228 * 1024, "two CTAs per SM");
+static_assert(RING <= SM_R, "the frame ring reuses sR");
+
+constexpr float LN2 = 0.69314718055994530942f;
 
 // Symmetric (half-sample) reflection for j in [-6, n+6) when n >= 6; indices
 // further out only feed responses outside the image and are clamped.
@@ -182,15 +186,73 @@ __device__ void decide(const KParams &p, ImgState *st, const double *t, int mode
     }
 }
 
+// Forward bank of one unit (1 column x FWD_ROWS rows x G filters of group
+// grp) and its epilogue: r_i into sR, theta_i log2(1 + z_i^2) summed over the
+// unit's tile pixels.  MASK: some pixel of the unit lies outside the image.
+template <int MODE, bool MASK>
+__device__ __forceinline__ float forward_unit(const float *__restrict__ sU, float *__restrict__ sR,
+                                              const float *__restrict__ wf, const float *__restrict__ theta,
+                                              int grp, int c, int rb, int y0, int x0, int H, int W) {
+    float z[FWD_ROWS][G];
+#pragma unroll
+    for (int r = 0; r < FWD_ROWS; ++r)
+#pragma unroll
+        for (int i = 0; i < G; ++i) z[r][i] = 0.f;
+    const float *ucol = sU + rb * FWD_ROWS * SU_LD + c;
+    const float *wcol = wf + grp * G;
+#pragma unroll 1
+    for (int bb = 0; bb < KS; ++bb) {
+        float v[FWD_WIN];
+#pragma unroll
+        for (int r = 0; r < FWD_WIN; ++r) v[r] = ucol[r * SU_LD + bb];
+#pragma unroll
+        for (int aa = 0; aa < KS; ++aa) {
+            const float4 w0 = __ldg(reinterpret_cast<const float4 *>(wcol + (aa * KS + bb) * NFMAX));
+            const float w[G] = {w0.x, w0.y, w0.z, w0.w};
+#pragma unroll
+            for (int r = 0; r < FWD_ROWS; ++r)
+#pragma unroll
+                for (int i = 0; i < G; ++i) z[r][i] = fmaf(w[i], v[r + aa], z[r][i]);
+        }
+    }
+    float th[G], th2[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+        th[i] = __ldg(theta + grp * G + i);
+        th2[i] = 2.0f * th[i];
+    }
+    const int x = x0 - 3 + c;
+    const bool colin = x >= 0 && x < W, colint = c >= 3 && c < 3 + TX;
+    float fsum = 0.f;
+#pragma unroll
+    for (int r = 0; r < FWD_ROWS; ++r) {
+        const int pr = rb * FWD_ROWS + r;
+        const int y = y0 - 3 + pr;
+        const bool inimg = !MASK || (colin && y >= 0 && y < H);
+        const bool inner = colint && pr >= 3 && pr < 3 + TY && (!MASK || inimg);
+        float psum = 0.f;
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            const float zz = z[r][i];
+            const float q = fmaf(zz, zz, 1.0f);
+            if (MODE != MODE_ENERGY_EXT) {
+                float rv = __fdividef(th2[i] * zz, q);
+                if (MASK && !inimg) rv = 0.0f;
+                sR[(i * R3Y + pr) * SR_LD + c] = rv;
+            }
+            psum = fmaf(th[i], __log2f(q), psum);
+        }
+        if (inner) fsum += psum;
+    }
+    return fsum * LN2;
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(NT, 1) fp32_tile_kernel(const KParams p) {
+__global__ void __launch_bounds__(NT, 2) fp32_tile_kernel(const KParams p) {
     extern __shared__ __align__(16) float smem[];
     float *sU = smem;
     float *sR = sU + SM_U;
-    float *sWf = sR + SM_R;
-    float *sWa = sWf + SM_WF;
-    float *sTh = sWa + SM_WA;
-    double *sRed = reinterpret_cast<double *>(sTh + SM_TH);
+    double *sRed = reinterpret_cast<double *>(sR + SM_R);
     __shared__ int sLast;
 
     const int tid = threadIdx.x;
@@ -210,13 +272,6 @@ __global__ void __launch_bounds__(NT, 1) fp32_tile_kernel(const KParams p) {
     }
 
     if (active) {
-        // ---- filter bank into shared memory ------------------------------
-        for (int j = tid; j < KT * NFMAX / 4; j += NT)
-            reinterpret_cast<float4 *>(sWf)[j] = reinterpret_cast<const float4 *>(p.wf)[j];
-        for (int j = tid; j < NFMAX * KT_PAD / 4; j += NT)
-            reinterpret_cast<float4 *>(sWa)[j] = reinterpret_cast<const float4 *>(p.wa)[j];
-        if (tid < NFMAX) sTh[tid] = p.theta[tid];
-
         // ---- 1+2: inertial step and prox on tile + 6 ---------------------
         double accF = 0.0, accG = 0.0, accGD = 0.0, accDD = 0.0, accDP = 0.0;
         {
@@ -272,67 +327,29 @@ __global__ void __launch_bounds__(NT, 1) fp32_tile_kernel(const KParams p) {
 #pragma unroll
         for (int k = 0; k < RING_PER_T; ++k) fr[k] = 0.f;
         const int aux = tid & 15, auy = tid >> 4;  // adjoint unit of this thread
+        const bool border = y0 == 0 || x0 == 0 || y0 + TY > H - 3 || x0 + TX > W - 3;
 
         for (int grp = 0; grp < p.nfp / G; ++grp) {
             __syncthreads();  // sU / weights ready; previous group's sR reads done
             // ---- 3+4: forward bank and potential on tile + 3 -------------
             for (int unit = tid; unit < FWD_UNITS; unit += NT) {
                 const int c = unit % R3X, rb = unit / R3X;
-                float z[FWD_ROWS][G];
-#pragma unroll
-                for (int r = 0; r < FWD_ROWS; ++r)
-#pragma unroll
-                    for (int i = 0; i < G; ++i) z[r][i] = 0.f;
-                const float *ucol = sU + rb * FWD_ROWS * SU_LD + c;
-                const float *wcol = sWf + grp * G;
-#pragma unroll 1
-                for (int bb = 0; bb < KS; ++bb) {
-                    float v[FWD_ROWS + KS - 1];
-#pragma unroll
-                    for (int r = 0; r < FWD_ROWS + KS - 1; ++r) v[r] = ucol[r * SU_LD + bb];
-#pragma unroll
-                    for (int aa = 0; aa < KS; ++aa) {
-                        const float4 w0 = *reinterpret_cast<const float4 *>(wcol + (aa * KS + bb) * NFMAX);
-                        const float4 w1 = *reinterpret_cast<const float4 *>(wcol + (aa * KS + bb) * NFMAX + 4);
-                        const float w[G] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-                        for (int r = 0; r < FWD_ROWS; ++r)
-#pragma unroll
-                            for (int i = 0; i < G; ++i) z[r][i] = fmaf(w[i], v[r + aa], z[r][i]);
-                    }
-                }
-                // epilogue: rho' into sR, rho into the energy partial
-                const int x = x0 - 3 + c;
-                const bool colin = x >= 0 && x < W, colint = c >= 3 && c < 3 + TX;
-                float fsum = 0.f;
-#pragma unroll
-                for (int r = 0; r < FWD_ROWS; ++r) {
-                    const int pr = rb * FWD_ROWS + r;
-                    const int y = y0 - 3 + pr;
-                    const bool inimg = colin && y >= 0 && y < H;
-                    const bool inner = inimg && colint && pr >= 3 && pr < 3 + TY;
-#pragma unroll
-                    for (int i = 0; i < G; ++i) {
-                        const float zz = z[r][i];
-                        const float q = fmaf(zz, zz, 1.0f);
-                        const float th = sTh[grp * G + i];
-                        if (MODE != MODE_ENERGY_EXT)
-                            sR[(i * R3Y + pr) * SR_LD + c] = inimg ? th * __fdividef(2.0f * zz, q) : 0.0f;
-                        if (inner) fsum = fmaf(th, __logf(q), fsum);
-                    }
-                }
-                accF += (double)fsum;
+                const int x = x0 - 3 + c, ylo = y0 - 3 + rb * FWD_ROWS;
+                const bool full = x >= 0 && x < W && ylo >= 0 && ylo + FWD_ROWS <= H;
+                const float fs = full ? forward_unit<MODE, false>(sU, sR, p.wf, p.theta, grp, c, rb, y0, x0, H, W)
+                                      : forward_unit<MODE, true>(sU, sR, p.wf, p.theta, grp, c, rb, y0, x0, H, W);
+                accF += (double)fs;
             }
             if (MODE == MODE_ENERGY_EXT) continue;
             __syncthreads();  // sR complete
 
-            // ---- 5: adjoint bank on the tile (4x4 unit per thread) --------
+            // ---- 5: adjoint bank on the tile (4x4 unit per thread) ---------
             for (int i = 0; i < G; ++i) {
-                const float *wrow = sWa + (grp * G + i) * KT_PAD;
+                const float *wrow = p.wa + (grp * G + i) * KT_PAD;
                 float kw[KT_PAD];
 #pragma unroll
                 for (int j = 0; j < KT_PAD / 4; ++j) {
-                    const float4 t = reinterpret_cast<const float4 *>(wrow)[j];
+                    const float4 t = __ldg(reinterpret_cast<const float4 *>(wrow) + j);
                     kw[4 * j] = t.x;
                     kw[4 * j + 1] = t.y;
                     kw[4 * j + 2] = t.z;
@@ -357,7 +374,6 @@ __global__ void __launch_bounds__(NT, 1) fp32_tile_kernel(const KParams p) {
                 }
             }
             // ---- 5b: K^T r on the frame outside the image (border tiles) --
-            const bool border = y0 == 0 || x0 == 0 || y0 + TY > H - 3 || x0 + TX > W - 3;
             if (border) {
 #pragma unroll
                 for (int k = 0; k < RING_PER_T; ++k) {
@@ -366,22 +382,18 @@ __global__ void __launch_bounds__(NT, 1) fp32_tile_kernel(const KParams p) {
                     int pr, pc, j, jx;
                     ring_to_pos(idx, pr, pc);
                     if (!axis_pos(pr, y0, TY, H, j) || !axis_pos(pc, x0, TX, W, jx)) continue;
-                    // s(j, jx) = sum_i sum_ab k_i[a][b] r_i(j - 3 + a, jx - 3 + b)
+                    // s(j, jx) = sum_i sum_ab k_i[a][b] r_i(j - 3 + a, jx - 3 + b); r_i is
+                    // zero off-image and the response region covers every on-image row
+                    // and column this frame pixel needs, so only those taps are visited
+                    const int alo = max(max(0, 3 - j), y0 - j), ahi = min(min(KS, H + 3 - j), R3Y + y0 - j);
+                    const int blo = max(max(0, 3 - jx), x0 - jx), bhi = min(min(KS, W + 3 - jx), R3X + x0 - jx);
                     float s = 0.f;
                     for (int i = 0; i < G; ++i) {
-                        const float *wrow = sWa + (grp * G + i) * KT_PAD;
+                        const float *wrow = p.wa + (grp * G + i) * KT_PAD;
                         const float *Ri = sR + (size_t)i * R3Y * SR_LD;
-                        for (int aa = 0; aa < KS; ++aa) {
-                            const int rrow = j - y0 + aa;  // response-region row
-                            const int yy = j - 3 + aa;     // image row
-                            if (rrow < 0 || rrow >= R3Y || yy < 0 || yy >= H) continue;
-                            for (int bb = 0; bb < KS; ++bb) {
-                                const int rcol = jx - x0 + bb;
-                                const int xx = jx - 3 + bb;
-                                if (rcol < 0 || rcol >= R3X || xx < 0 || xx >= W) continue;
-                                s = fmaf(wrow[aa * KS + bb], Ri[rrow * SR_LD + rcol], s);
-                            }
-                        }
+                        for (int aa = alo; aa < ahi; ++aa)
+                            for (int bb = blo; bb < bhi; ++bb)
+                                s = fmaf(__ldg(wrow + aa * KS + bb), Ri[(j - y0 + aa) * SR_LD + (jx - x0 + bb)], s);
                     }
                     fr[k] += s;
                 }
@@ -390,9 +402,8 @@ __global__ void __launch_bounds__(NT, 1) fp32_tile_kernel(const KParams p) {
 
         if (MODE != MODE_ENERGY_EXT) {
             // ---- fold the frame back onto the pixels it mirrors ----------
-            __syncthreads();  // all sR reads done; reuse sR for the ring
-            const bool border = y0 == 0 || x0 == 0 || y0 + TY > H - 3 || x0 + TX > W - 3;
             if (border) {
+                __syncthreads();  // all sR reads done; reuse sR for the ring
 #pragma unroll
                 for (int k = 0; k < RING_PER_T; ++k) {
                     const int idx = tid + k * NT;
@@ -400,38 +411,40 @@ __global__ void __launch_bounds__(NT, 1) fp32_tile_kernel(const KParams p) {
                 }
                 __syncthreads();
             }
-            float *gout;
-            if (MODE == MODE_GRAD_EXT)
-                gout = p.g_ext;
-            else if (MODE == MODE_INIT)
-                gout = im.g[0];
-            else
-                gout = im.g[gcur_out];
+            {
+                float *gout;
+                if (MODE == MODE_GRAD_EXT)
+                    gout = p.g_ext;
+                else if (MODE == MODE_INIT)
+                    gout = im.g[0];
+                else
+                    gout = im.g[gcur_out];
 #pragma unroll
-            for (int pp = 0; pp < 4; ++pp) {
-                const int y = y0 + 4 * auy + pp;
-                if (y >= H) continue;
+                for (int pp = 0; pp < 4; ++pp) {
+                    const int y = y0 + 4 * auy + pp;
+                    if (y >= H) continue;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int x = x0 + 4 * aux + q;
-                    if (x >= W) continue;
-                    float gv = acc[pp][q];
-                    if (border && (y < 3 || y >= H - 3 || x < 3 || x >= W - 3)) {
-                        // frame positions that the symmetric extension maps onto (y, x)
-                        int py[3], px[3], ny = 1, nx = 1;
-                        py[0] = y - y0 + 3;
-                        px[0] = x - x0 + 3;
-                        if (y < 3) py[ny++] = 2 - y;                  // j = -y-1
-                        if (y >= H - 3) py[ny++] = TY + 2 + H - y;    // j = 2H-1-y
-                        if (x < 3) px[nx++] = 2 - x;
-                        if (x >= W - 3) px[nx++] = TX + 2 + W - x;
-                        for (int m = 0; m < ny; ++m)
-                            for (int n = 0; n < nx; ++n) {
-                                if (m == 0 && n == 0) continue;
-                                gv += sR[pos_to_ring(py[m], px[n])];
-                            }
+                    for (int q = 0; q < 4; ++q) {
+                        const int x = x0 + 4 * aux + q;
+                        if (x >= W) continue;
+                        float gv = acc[pp][q];
+                        if (border && (y < 3 || y >= H - 3 || x < 3 || x >= W - 3)) {
+                            // frame positions that the symmetric extension maps onto (y, x)
+                            int py[3], px[3], ny = 1, nx = 1;
+                            py[0] = y - y0 + 3;
+                            px[0] = x - x0 + 3;
+                            if (y < 3) py[ny++] = 2 - y;                // j = -y-1
+                            if (y >= H - 3) py[ny++] = TY + 2 + H - y;  // j = 2H-1-y
+                            if (x < 3) px[nx++] = 2 - x;
+                            if (x >= W - 3) px[nx++] = TX + 2 + W - x;
+                            for (int m = 0; m < ny; ++m)
+                                for (int n = 0; n < nx; ++n) {
+                                    if (m == 0 && n == 0) continue;
+                                    gv += sR[pos_to_ring(py[m], px[n])];
+                                }
+                        }
+                        gout[(size_t)y * W + x] = gv;
                     }
-                    gout[(size_t)y * W + x] = gv;
                 }
             }
         }
@@ -527,6 +540,7 @@ __global__ void __launch_bounds__(NT, 1) fp32_tile_kernel(const KParams p) {
 
 size_t fp32_smem_bytes() { return SM_BYTES; }
 int fp32_tile() { return TY; }
+int fp32_threads() { return NT; }
 
 cudaError_t fp32_prepare() {
     cudaError_t e;

@@ -91,6 +91,7 @@ struct KParams {
 constexpr int fp32_tile_size = 64;  // square output tile of the FP32 kernel
 size_t fp32_smem_bytes();
 int fp32_tile();
+int fp32_threads();          // block size of the tile kernel
 cudaError_t fp32_prepare();  // opt in to the large shared-memory carve-out
 cudaError_t fp32_launch(int mode, const KParams &p, int grid, cudaStream_t s);
 const void *fp32_trial_entry();
