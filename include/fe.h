@@ -212,6 +212,17 @@ FE_API fe_status fe_gradient_noalloc(const float *u, float *g, double *F, int H,
                                      const float *filters, const float *theta, int nf,
                                      void *stream);
 
+/* Diagnostic of the tensor-core building block used by the FE_TF32 / FE_BF16
+ * forms: D = A * B^T with A 128 x K, B N x K (row-major float, any pointers)
+ * rounded to the form's operand type (BF16 round-to-nearest-even, TF32
+ * round-to-nearest), accumulated in FP32 by tcgen05.mma in tensor memory,
+ * D 128 x N row-major float (any pointer).  prec = FE_BF16 (K multiple of 16)
+ * or FE_TF32 (K multiple of 8), K <= 128, N in 16..64 multiple of 16.
+ * Allocates and frees its own device buffers; synchronises the device.
+ * Errors: FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_ETIMEOUT (MMA completion never
+ * signalled within the wait bound). */
+FE_API fe_status fe_tc_gemm_selftest(int prec, int N, int K, const float *A, const float *B, float *D);
+
 FE_API const char *fe_last_error(const fe_ctx *ctx);
 FE_API const char *fe_status_string(fe_status s);
 FE_API int fe_abi_version(void);

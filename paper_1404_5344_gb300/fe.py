@@ -30,6 +30,7 @@ EXPORTS = (
     "fe_solve", "fe_get_info", "fe_get_u", "fe_energy", "fe_gradient", "fe_get_state",
     "fe_set_state", "fe_num_images", "fe_image_size", "fe_launch_count", "fe_set_loop_mode",
     "fe_last_error", "fe_status_string", "fe_abi_version", "fe_gradient_noalloc",
+    "fe_tc_gemm_selftest",
 )
 
 
@@ -82,7 +83,8 @@ def _load(path: str = LIB_PATH) -> C.CDLL:
     L.fe_status_string.restype = C.c_char_p
     L.fe_abi_version.argtypes = []
     L.fe_gradient_noalloc.argtypes = [VP, VP, VP, I, I, VP, VP, I, VP]
-    for name in ("fe_gradient_noalloc", "fe_init_batch","fe_init", "fe_reset", "fe_step", "fe_solve", "fe_get_info",
+    L.fe_tc_gemm_selftest.argtypes = [I, I, I, VP, VP, VP]
+    for name in ("fe_tc_gemm_selftest", "fe_gradient_noalloc", "fe_init_batch","fe_init", "fe_reset", "fe_step", "fe_solve", "fe_get_info",
                  "fe_get_u", "fe_energy", "fe_gradient", "fe_get_state", "fe_set_state",
                  "fe_image_size", "fe_set_loop_mode", "fe_num_images", "fe_abi_version"):
         getattr(L, name).restype = C.c_int

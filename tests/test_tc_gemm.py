@@ -1,0 +1,65 @@
+"""The tensor-core building block (tcgen05.mma, K-major operands in shared
+memory, FP32 accumulation in tensor memory) against a plain NumPy product of
+the same rounded operands."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fe():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1404_5344_gb300 import build
+    build.build()
+    from paper_1404_5344_gb300 import fe as fe_mod
+    return fe_mod
+
+
+def round_bf16(x):
+    """Round-to-nearest-even to bfloat16, returned as float32."""
+    b = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32)
+
+
+def round_tf32(x):
+    """Round to nearest (ties away from zero) on the 13 dropped mantissa bits."""
+    b = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x1000) & 0xFFFFE000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def _run(fe, prec, N, K, A, B):
+    D = np.empty((128, N), np.float32)
+    st = fe.lib.fe_tc_gemm_selftest(prec, N, K, A.ctypes.data, B.ctypes.data, D.ctypes.data)
+    assert st == fe.FE_OK, fe.lib.fe_status_string(st)
+    return D
+
+
+@pytest.mark.parametrize("prec,K", [(2, 16), (2, 64), (2, 128), (1, 8), (1, 56), (1, 112)])
+@pytest.mark.parametrize("N", [16, 48, 64])
+def test_exact_integer_products(fe, prec, K, N):
+    """Small integers are exact in both operand types and their dot products
+    are exact in FP32: the result must match bit for bit, which pins the
+    operand layout, the descriptors and the accumulation over K steps."""
+    rng = np.random.default_rng(prec * 1000 + K * 10 + N)
+    A = rng.integers(-8, 9, (128, K)).astype(np.float32)
+    B = rng.integers(-8, 9, (N, K)).astype(np.float32)
+    D = _run(fe, prec, N, K, A, B)
+    np.testing.assert_array_equal(D, A.astype(np.float64) @ B.T.astype(np.float64))
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_rounded_real_operands(fe, prec):
+    rng = np.random.default_rng(prec)
+    K = 64
+    A = rng.standard_normal((128, K)).astype(np.float32) * 50
+    B = rng.standard_normal((48, K)).astype(np.float32) * 0.2
+    rnd = round_bf16 if prec == 2 else round_tf32
+    ref = rnd(A).astype(np.float64) @ rnd(B).T.astype(np.float64)
+    D = _run(fe, prec, 48, K, A, B)
+    scale = np.abs(rnd(A)).astype(np.float64) @ np.abs(rnd(B)).T
+    assert np.max(np.abs(D - ref) / scale) < 1e-6
