@@ -76,6 +76,18 @@ def workload(n512, n256):
 SOLVER_KW = dict(lam=5.0, beta=0.8, L0=1.0, eta=2.0, c2=1e-6, max_backtrack=30)
 
 
+def measured_bf16_sustained():
+    """Dense BF16 tensor peak measured on this machine (seconds-long loop), else
+    the profiling recipe's fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["bf16_tflops_sustained"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 1700.0, "of fallback"
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -260,7 +272,19 @@ def main():
     per_launch_ms = loop_ms / trial_launches
     achieved_tflops = FLOP_PER_PIXEL_TRIAL * pix_trials / (loop_ms / 1e3) / 1e12
     sm_mhz_max = (clk or {}).get("sm_max_mhz") or 2070.0
-    peak_tflops = SMS * FP32_LANES * 2 * sm_mhz_max * 1e6 / 1e12
+    if args.prec == "fp32":
+        bound, kernel = "alu", "fp32_tile_kernel<MODE_TRIAL>"
+        peak_tflops = SMS * FP32_LANES * 2 * sm_mhz_max * 1e6 / 1e12
+        basis = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" % sm_mhz_max
+    else:
+        # the trial kernel runs inside a seconds-long loop: sustained dense
+        # BF16 peak (measured); TF32 at the nominal TF32/BF16 ratio 1.1/2.25
+        bf16_sust, src = measured_bf16_sustained()
+        ratio = 1.0 if args.prec == "bf16" else 1.1 / 2.25
+        bound, kernel = "tensor", "tc_tile_kernel<MODE_TRIAL, %s>" % args.prec.upper()
+        peak_tflops = bf16_sust * ratio
+        basis = "dense %s tensor peak = %.1f TFLOP/s sustained BF16 (%s) x %.3f" % (
+            args.prec.upper(), bf16_sust, src, ratio)
 
     # e2e through the C ABI with host buffers
     f_host = [torch.from_numpy(f).pin_memory() for f in fs]
@@ -289,10 +313,12 @@ def main():
         line = {"metric": METRIC, "value": round(value, 2), "unit": "Mpixel*iter/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(T_ms / args.steps, 3), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[args.prec], "data": "synthetic",
                 "config": {"workload": "%dx512^2 + %dx256^2 textured images, L in {1,4,8} gamma speckle, "
                                        "48x7x7 seeded bank, lambda=5, %d iPiano iterations with "
-                                       "Lipschitz backtracking, FP32" % (args.n512, args.n256, args.iters),
+                                       "Lipschitz backtracking, %s filter bank" % (
+                                           args.n512, args.n256, args.iters, args.prec.upper()),
                            "images": len(fs), "pixels": npix, "iters": args.iters, "precision": args.prec,
                            "loop": "cuda-graph while node" if args.loop_mode == 1 else "host chunks",
                            "parallelism": "replicas" if world > 1 else "single GPU",
@@ -302,15 +328,14 @@ def main():
                         "h2d_bytes_per_step": int(npix * 4), "d2h_bytes_per_step": int(npix * 4)},
                 "gpu_launches": int(launches), "trial_kernel_launches": int(trial_launches),
                 "trials": int(trials), "statuses": statuses,
-                "roofline": {"bound": "alu", "achieved": round(achieved_tflops, 3),
+                "roofline": {"bound": bound, "achieved": round(achieved_tflops, 3),
                              "peak": round(peak_tflops, 3), "unit": "TFLOP/s",
                              "frac": round(achieved_tflops / peak_tflops, 4), "traffic": None,
-                             "kernel": "fp32_tile_kernel<MODE_TRIAL>",
-                             "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz "
-                                           "(max SM clock)" % sm_mhz_max,
+                             "kernel": kernel, "peak_basis": basis,
+                             "work": "9408 flop (2 x 48 x 49 MAC) per pixel per trial, every image-trial",
                              "per_launch_ms": round(per_launch_ms, 4)},
                 "clocks": clk}
-        if clk and clk.get("sm_mhz"):
+        if clk and clk.get("sm_mhz") and args.prec == "fp32":
             line["roofline"]["frac_at_observed_clock"] = round(
                 achieved_tflops / (SMS * FP32_LANES * 2 * clk["sm_mhz"] * 1e6 / 1e12), 4)
         if world == 1 and not args.no_cpu_baseline:

@@ -42,6 +42,8 @@ struct fe_ctx {
     float *d_wf = nullptr, *d_wa = nullptr, *d_th = nullptr;
     double *d_res = nullptr;
     int *d_flag = nullptr;
+    int *d_tc_error = nullptr;
+    unsigned char *d_tcw_fwd = nullptr, *d_tcw_adj = nullptr;
     float *d_scratch = nullptr;  // 2 planes of the largest image (host-pointer staging)
     size_t max_plane = 0;
     KParams kp{};
@@ -155,10 +157,16 @@ fe_status validate_params(fe_ctx *c, const fe_params *p) {
     if (p->max_backtrack < 0) return set_err(c, FE_EINVAL, "max_backtrack must be >= 0");
     if (p->prec != FE_FP32 && p->prec != FE_TF32 && p->prec != FE_BF16)
         return set_err(c, FE_EINVAL, "unknown precision %d", p->prec);
-    if (p->prec != FE_FP32) return set_err(c, FE_EUNSUPPORTED, "precision %d not built", p->prec);
-    if (p->tile != 0 && p->tile != fp32_tile())
-        return set_err(c, FE_EUNSUPPORTED, "tile %d not available (0 or %d)", p->tile, fp32_tile());
+    if (p->prec != FE_FP32 && p->nf > 48)
+        return set_err(c, FE_EUNSUPPORTED, "the tensor-core forms take at most 48 filters (nf=%d)", p->nf);
+    if (p->tile != 0) return set_err(c, FE_EUNSUPPORTED, "tile must be 0 (each form has a fixed tile)");
     return FE_OK;
+}
+
+// Launch one tile kernel of the context's precision form.
+cudaError_t launch_tiles(const fe_ctx *c, int mode, const KParams &kp, int grid) {
+    if (c->prm.prec == FE_FP32) return fp32_launch(mode, kp, grid, c->s);
+    return tc_launch(mode, c->prm.prec == FE_BF16 ? 1 : 2, kp, grid, c->s);
 }
 
 fe_status load_inputs(fe_ctx *c, const float *const *f, const float *const *u0) {
@@ -195,7 +203,7 @@ fe_status load_inputs(fe_ctx *c, const float *const *f, const float *const *u0) 
     FE_CUDA(c, cudaMemsetAsync(c->d_arr, 0, sizeof(unsigned) * c->nimg, c->s));
     KParams kp = c->kp;
     kp.tile0 = 0;
-    FE_CUDA(c, fp32_launch(MODE_INIT, kp, c->ntiles, c->s));
+    FE_CUDA(c, launch_tiles(c, MODE_INIT, kp, c->ntiles));
     ++c->host_launches;
     FE_CUDA(c, cudaMemcpyAsync(hs.data(), c->d_st, sizeof(ImgState) * hs.size(), cudaMemcpyDeviceToHost, c->s));
     FE_CUDA(c, cudaStreamSynchronize(c->s));
@@ -237,10 +245,12 @@ fe_status build_graph(fe_ctx *c) {
     void *args[] = {&kp};
     cudaKernelNodeParams knp;
     std::memset(&knp, 0, sizeof knp);
-    knp.func = const_cast<void *>(fp32_trial_entry());
+    const int fmt = c->prm.prec == FE_BF16 ? 1 : 2;
+    const bool tc = c->prm.prec != FE_FP32;
+    knp.func = const_cast<void *>(tc ? tc_trial_entry(fmt) : fp32_trial_entry());
     knp.gridDim = dim3(c->ntiles);
-    knp.blockDim = dim3(fp32_threads());
-    knp.sharedMemBytes = (unsigned)fp32_smem_bytes();
+    knp.blockDim = dim3(tc ? tc_threads() : fp32_threads());
+    knp.sharedMemBytes = (unsigned)(tc ? tc_smem_bytes(fmt) : fp32_smem_bytes());
     knp.kernelParams = args;
     cudaGraphNode_t kn;
     e = cudaGraphAddKernelNode(&kn, body, nullptr, 0, &knp);
@@ -278,7 +288,7 @@ fe_status run_loop(fe_ctx *c, long long n_hint, long long budget, bool sync) {
     long long chunk = std::max<long long>(1, std::min<long long>(n_hint, 64));
     for (;;) {
         const long long todo = std::min(chunk, budget - launched);
-        for (long long k = 0; k < todo; ++k) FE_CUDA(c, fp32_launch(MODE_TRIAL, kp, c->ntiles, c->s));
+        for (long long k = 0; k < todo; ++k) FE_CUDA(c, launch_tiles(c, MODE_TRIAL, kp, c->ntiles));
         launched += todo;
         LoopCtl lc;
         FE_CUDA(c, cudaMemcpyAsync(&lc, c->d_loop, sizeof lc, cudaMemcpyDeviceToHost, c->s));
@@ -383,7 +393,30 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
     c->filt.assign(p->filters, p->filters + (size_t)p->nf * KT);
     c->theta.assign(p->theta, p->theta + p->nf);
     c->nfp = ((p->nf + 7) / 8) * 8;
-    const int T = fp32_tile();
+    const bool tc = p->prec != FE_FP32;
+    const int TYs = tc ? tc_tile_y : fp32_tile(), TXs = tc ? tc_tile_x : fp32_tile();
+    // Tile origins and owned extents along one axis of length N with tile T.
+    // FP32: origins 0, T, 2T, ... (the last tile may hang over the border).
+    // Tensor-core forms: the last origin is moved back to N - T (when N >= T)
+    // so that it ends at the border and owns all its rows; the tile before it
+    // owns only the rows up to that origin.  The first tile always owns the
+    // first 3 rows: their mirror images (rows -3..-1) lie in its halo only.
+    // Outputs: origin o_i, owned start relative to the origin rel_i, owned
+    // length own_i (tile i owns [o_i + rel_i, o_i + rel_i + own_i)).
+    auto axis_tiles = [&](int N, int T, std::vector<int> &o, std::vector<int> &rel, std::vector<int> &own) {
+        const int n = (N + T - 1) / T;
+        std::vector<int> s;
+        o.clear();
+        rel.clear();
+        own.clear();
+        for (int i = 0; i < n; ++i) o.push_back(i * T);
+        if (tc && n > 1) o[n - 1] = N - T;
+        for (int i = 0; i < n; ++i) s.push_back(i == 0 ? 0 : (tc && i == n - 1 ? std::max(o[i], 3) : o[i]));
+        for (int i = 0; i < n; ++i) {
+            own.push_back((i + 1 < n ? s[i + 1] : N) - s[i]);
+            rel.push_back(s[i] - o[i]);
+        }
+    };
     size_t plane_total = 0;
     for (int j = 0; j < nimg; ++j) {
         if (H[j] < 8 || W[j] < 8 || H[j] > 65536 || W[j] > 65536)
@@ -393,22 +426,25 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
         const size_t N = (size_t)H[j] * W[j];
         c->max_plane = std::max(c->max_plane, (N + 63) / 64 * 64);
         plane_total += 6 * ((N + 63) / 64 * 64);
-        const int ty = (H[j] + T - 1) / T, tx = (W[j] + T - 1) / T;
+        std::vector<int> oy, ry, ohv, ox, rx, owv;
+        axis_tiles(H[j], TYs, oy, ry, ohv);
+        axis_tiles(W[j], TXs, ox, rx, owv);
         ImgDesc d{};
         d.H = H[j];
         d.W = W[j];
         d.tile_begin = (int)c->htile.size();
-        d.ntiles = ty * tx;
+        d.ntiles = (int)(oy.size() * ox.size());
         d.lambda = p->lambda;
-        for (int a = 0; a < ty; ++a)
-            for (int b = 0; b < tx; ++b) c->htile.push_back(TileDesc{j, a * T, b * T, 0});
+        for (size_t a = 0; a < oy.size(); ++a)
+            for (size_t b = 0; b < ox.size(); ++b)
+                c->htile.push_back(TileDesc{j, oy[a], ox[b], ohv[a], owv[b], ry[a], rx[b], 0});
         c->himg.push_back(d);
     }
     if (c->htile.size() > (size_t)0x7fffffff) return bail(set_err(c, FE_EINVAL, "too many tiles"));
     c->ntiles = (int)c->htile.size();
     if (cudaGetDevice(&c->dev) != cudaSuccess) return bail(set_err(c, FE_ECUDA, "no CUDA device"));
 
-    if (cudaError_t e = fp32_prepare(); e != cudaSuccess)
+    if (cudaError_t e = tc ? tc_prepare() : fp32_prepare(); e != cudaSuccess)
         return bail(set_err(c, FE_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e)));
 
     float *planes = nullptr;
@@ -433,7 +469,19 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
     if ((st = dalloc(c, &c->d_th, NFMAX)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_res, 2 * (size_t)nimg)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_flag, 4)) != FE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_tc_error, 1)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_scratch, 2 * c->max_plane)) != FE_OK) return bail(st);
+    if (tc) {
+        std::vector<unsigned char> bf, ba;
+        tc_build_weights(p->prec == FE_BF16 ? 1 : 2, p->filters, p->nf, bf, ba);
+        if ((st = dalloc(c, &c->d_tcw_fwd, bf.size())) != FE_OK) return bail(st);
+        if ((st = dalloc(c, &c->d_tcw_adj, ba.size())) != FE_OK) return bail(st);
+        if (cudaMemcpy(c->d_tcw_fwd, bf.data(), bf.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(c->d_tcw_adj, ba.data(), ba.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(set_err(c, FE_ECUDA, "upload of the rounded filter bank failed"));
+    }
+    if (cudaMemset(c->d_tc_error, 0, sizeof(int)) != cudaSuccess)
+        return bail(set_err(c, FE_ECUDA, "cudaMemset failed"));
 
     // weight tables: forward = flipped taps (convolution as correlation),
     // tap-major; adjoint = taps as stored, filter-major (correlation = K^T)
@@ -472,6 +520,9 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
     kp.c2 = p->c2;
     kp.max_bt = p->max_backtrack;
     kp.results = c->d_res;
+    kp.tcw_fwd = c->d_tcw_fwd;
+    kp.tcw_adj = c->d_tcw_adj;
+    kp.tc_error = c->d_tc_error;
 
     if (cudaMemset(c->d_loop, 0, sizeof(LoopCtl)) != cudaSuccess)
         return bail(set_err(c, FE_ECUDA, "cudaMemset: %s", cudaGetErrorString(cudaGetLastError())));
@@ -634,7 +685,7 @@ static fe_status ext_launch(fe_ctx *c, int mode, int img, const float *u, float 
     kp.tile0 = d.tile_begin;
     kp.u_ext = ud;
     kp.g_ext = gd;
-    FE_CUDA(c, fp32_launch(mode, kp, d.ntiles, c->s));
+    FE_CUDA(c, launch_tiles(c, mode, kp, d.ntiles));
     ++c->host_launches;
     double res[2];
     FE_CUDA(c, cudaMemcpyAsync(res, c->d_res + 2 * img, sizeof res, cudaMemcpyDeviceToHost, c->s));

@@ -38,6 +38,7 @@
 #include <stdint.h>
 
 #include "fe_internal.cuh"
+#include "fe_tile_common.cuh"
 
 namespace fe {
 namespace {
@@ -70,44 +71,6 @@ static_assert(RING <= SM_R, "the frame ring reuses sR");
 
 constexpr float LN2 = 0.69314718055994530942f;
 
-// Symmetric (half-sample) reflection for j in [-6, n+6) when n >= 6; indices
-// further out only feed responses outside the image and are clamped.
-__device__ __forceinline__ int reflect(int j, int n) {
-    j = j < 0 ? -j - 1 : j;
-    j = j >= n ? 2 * n - 1 - j : j;
-    return min(max(j, 0), n - 1);
-}
-
-// Closed-form prox of t*G at uhat (Sec. II-C), tl = t * lambda.
-__device__ __forceinline__ float prox_g(float uhat, float f2, float tl) {
-    const float D = fmaf(uhat, uhat, 4.0f * (1.0f + tl) * tl * f2);
-    const float sD = sqrtf(D);
-    return uhat >= 0.0f ? (uhat + sD) / (2.0f * (1.0f + tl)) : (2.0f * tl * f2) / (sD - uhat);
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Position p in [0, T+6) of the frame/tile grid along one axis -> image
-// coordinate j; returns whether that position belongs to this tile (main
-// rows inside the image, or frame rows whose mirror image lies in the tile).
-__device__ __forceinline__ bool axis_pos(int p, int t0, int T, int N, int &j) {
-    if (p < 3) {
-        j = p - 3;
-        return t0 == 0;
-    }
-    if (p < T + 3) {
-        j = t0 + p - 3;
-        return j < N;
-    }
-    j = N + (p - T - 3);
-    const int tgt = 2 * N - 1 - j;
-    return tgt >= t0 && tgt < t0 + T;
-}
-
 __device__ __forceinline__ void ring_to_pos(int idx, int &pr, int &pc) {
     if (idx < 3 * R3X) {
         pr = idx / R3X;
@@ -132,58 +95,6 @@ __device__ __forceinline__ int pos_to_ring(int pr, int pc) {
     if (pr >= TY + 3) return 3 * R3X + (pr - TY - 3) * R3X + pc;
     if (pc < 3) return 6 * R3X + (pr - 3) * 3 + pc;
     return 6 * R3X + 3 * TY + (pr - 3) * 3 + (pc - TX - 3);
-}
-
-// Accept / reject of the backtracking rule for one image (one thread).
-__device__ void decide(const KParams &p, ImgState *st, const double *t, int mode) {
-    const double F1 = t[0], G1 = t[1], gd = t[2], dd = t[3], dp = t[4];
-    if (mode == MODE_INIT) {
-        st->F = F1;
-        st->G = G1;
-        st->H = F1 + G1;
-        st->H_prev = F1 + G1;
-        st->alpha = 2.0 * (1.0 - p.beta) / (st->L + 2.0 * p.c2);
-        if (!isfinite(F1) || !isfinite(G1)) {
-            st->status = FE_ENONFINITE;
-            st->done = 1;
-        }
-        return;
-    }
-    st->trials += 1;
-    if (!isfinite(F1) || !isfinite(G1) || !isfinite(gd) || !isfinite(dd)) {
-        st->status = FE_ENONFINITE;
-        st->done = 1;
-        return;
-    }
-    if (F1 <= st->F + gd + 0.5 * st->L * dd) {
-        const double H1 = F1 + G1;
-        st->rel_change = fabs(H1 - st->H) / fabs(H1);
-        st->H_prev = st->H;
-        st->F = F1;
-        st->G = G1;
-        st->H = H1;
-        st->last_gd = gd;
-        st->last_dd = dd;
-        st->last_dp = dp;
-        st->cur = (st->cur + 1) % 3;
-        st->gcur ^= 1;
-        st->n += 1;
-        st->bt = 0;
-        if (st->tol > 0.0 && st->rel_change < st->tol) {
-            st->converged = 1;
-            st->done = 1;
-        }
-    } else {
-        st->backtracks += 1;
-        if (st->bt >= p.max_bt) {
-            st->status = FE_EBACKTRACK;
-            st->done = 1;
-            return;
-        }
-        st->bt += 1;
-        st->L *= p.eta;
-        st->alpha = 2.0 * (1.0 - p.beta) / (st->L + 2.0 * p.c2);
-    }
 }
 
 // Forward bank of one unit (1 column x FWD_ROWS rows x G filters of group
@@ -256,7 +167,6 @@ __global__ void __launch_bounds__(NT, 2) fp32_tile_kernel(const KParams p) {
     __shared__ int sLast;
 
     const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
     const int gtile = p.tile0 + (int)blockIdx.x;
     const TileDesc td = p.tiles[gtile];
     const int img = td.img;
@@ -449,91 +359,13 @@ __global__ void __launch_bounds__(NT, 2) fp32_tile_kernel(const KParams p) {
             }
         }
 
-        // ---- 6: per-tile FP64 partial sums -------------------------------
-        double vals[NRED] = {accF, accG, accGD, accDD, accDP};
-#pragma unroll
-        for (int k = 0; k < NRED; ++k) {
-            const double v = warp_sum(vals[k]);
-            if (lane == 0) sRed[warp * NRED + k] = v;
-        }
-        __syncthreads();
-        if (tid < NRED) {
-            double s = 0.0;
-            for (int w = 0; w < NWARP; ++w) s += sRed[w * NRED + tid];
-            p.partials[(size_t)gtile * NRED + tid] = s;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            __threadfence();
-            const unsigned prev = atomicAdd(p.img_arrivals + img, 1u);
-            sLast = (prev == (unsigned)im.ntiles - 1u);
-        }
-        __syncthreads();
-        if (sLast) {
-            // the last CTA of this image: fixed-order reduction + decision
-            __threadfence();
-            double part[NRED];
-#pragma unroll
-            for (int k = 0; k < NRED; ++k) part[k] = 0.0;
-            for (int t = tid; t < im.ntiles; t += NT)
-#pragma unroll
-                for (int k = 0; k < NRED; ++k) part[k] += __ldcg(p.partials + (size_t)(im.tile_begin + t) * NRED + k);
-#pragma unroll
-            for (int k = 0; k < NRED; ++k) {
-                const double v = warp_sum(part[k]);
-                if (lane == 0) sRed[warp * NRED + k] = v;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                double tot[NRED];
-                for (int k = 0; k < NRED; ++k) {
-                    double s = 0.0;
-                    for (int w = 0; w < NWARP; ++w) s += sRed[w * NRED + k];
-                    tot[k] = s;
-                }
-                tot[1] *= 0.5 * im.lambda;  // G = (lambda/2) sum_p (u^2 - 2 f^2 log u)
-                if (MODE == MODE_TRIAL || MODE == MODE_INIT) {
-                    decide(p, st, tot, MODE);
-                } else {
-                    p.results[2 * img] = tot[0];
-                    p.results[2 * img + 1] = tot[1];
-                }
-                p.img_arrivals[img] = 0u;
-                __threadfence();
-            }
-        }
+        // ---- 6: per-tile FP64 partial sums, last-CTA decision -------------
+        const double vals[NRED] = {accF, accG, accGD, accDD, accDP};
+        tile_finish<NT>(p, MODE, gtile, img, im, st, vals, sRed, &sLast);
     }
 
     // ---- loop control: the last CTA of the launch --------------------------
-    if (MODE == MODE_TRIAL) {
-        if (tid == 0) {
-            __threadfence();
-            const unsigned prev = atomicAdd(&p.loop->grid_arrivals, 1u);
-            if (prev == gridDim.x - 1u) {
-                __threadfence();
-                LoopCtl *lc = p.loop;
-                lc->grid_arrivals = 0u;
-                long long budget = lc->budget - 1;
-                int nact = 0;
-                for (int j = 0; j < p.nimg; ++j) {
-                    volatile ImgState *s = p.st + j;
-                    if (s->done == 0 && s->n < s->target) {
-                        if (budget <= 0) {
-                            s->status = FE_ETIMEOUT;
-                            s->done = 1;
-                        } else {
-                            ++nact;
-                        }
-                    }
-                }
-                lc->budget = budget;
-                lc->active = nact;
-                lc->launches += 1;
-                __threadfence();
-                if (p.use_cond) cudaGraphSetConditional(p.cond, nact > 0 ? 1u : 0u);
-            }
-        }
-    }
+    if (MODE == MODE_TRIAL) loop_control(p);
 }
 
 }  // namespace

@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "fe.h"
 
 namespace fe {
@@ -54,8 +56,14 @@ struct ImgState {
     int cur, gcur, bt, status, done, converged;
 };
 
+// A tile covers rows [y0, y0 + TY) and columns [x0, x0 + TX) of an image; it
+// owns (writes, sums) rows [y0 + sy, y0 + sy + oh) and columns
+// [x0 + sx, x0 + sx + ow).  The FP32 kernel tiles without overlap (sy = sx =
+// 0); the tensor-core kernel shifts the last tile of a row/column back so
+// that it ends at the image border, leaving the previous tile to own the rows
+// before it, and keeps the first three rows/columns with the first tile.
 struct TileDesc {
-    int img, y0, x0, pad;
+    int img, y0, x0, oh, ow, sy, sx, pad;
 };
 
 struct LoopCtl {
@@ -85,6 +93,11 @@ struct KParams {
     double *results;            // [nimg][2]: F, G of the EXT modes
     unsigned long long cond;    // cudaGraphConditionalHandle of the while node
     int use_cond;
+    // tensor-core forms: filter bank rounded to the operand type, in the
+    // K-major shared-memory byte layout of the forward and adjoint GEMMs
+    const void *tcw_fwd;
+    const void *tcw_adj;
+    int *tc_error;              // set when a tensor-core wait runs out
 };
 
 // FP32 fused tile kernel (fe_fp32.cu)
@@ -95,6 +108,19 @@ int fp32_threads();          // block size of the tile kernel
 cudaError_t fp32_prepare();  // opt in to the large shared-memory carve-out
 cudaError_t fp32_launch(int mode, const KParams &p, int grid, cudaStream_t s);
 const void *fp32_trial_entry();
+
+// Tensor-core tile kernel (fe_tc.cu); fmt 1 = BF16, 2 = TF32 operands
+constexpr int tc_tile_y = 58, tc_tile_x = 26;  // output tile; tile + 3-pixel halo = 64 x 32
+size_t tc_smem_bytes(int fmt);
+int tc_threads();
+cudaError_t tc_prepare();
+cudaError_t tc_launch(int mode, int fmt, const KParams &p, int grid, cudaStream_t s);
+const void *tc_trial_entry(int fmt);
+// Host: filter bank rounded to the operand type (BF16 round-to-nearest-even,
+// TF32 round-to-nearest-away) in the byte layout of the two GEMM B operands.
+void tc_build_weights(int fmt, const float *filters, int nf, std::vector<unsigned char> &fwd,
+                      std::vector<unsigned char> &adj);
+float tc_round(int fmt, float x);
 
 // Message returned by fe_last_error(NULL) for calls without a context (fe_api.cu)
 void set_global_error(const char *msg);

@@ -1,0 +1,495 @@
+// Tensor-core forms of the fused iPiano trial kernel (FE_BF16, FE_TF32).
+//
+// Same trial as the FP32 kernel (inertial step, closed-form prox, forward bank,
+// rho', adjoint bank with the symmetric-boundary fold, FP64 partial sums and
+// the backtracking decision), with both filter banks run as GEMMs on the
+// 5th-generation tensor cores (tcgen05.mma, FP32 accumulation in tensor
+// memory):
+//
+//   forward  Z[q, i] = sum_t A[q, t] Bf[i, t]: A = im2col of u^{n+1} (49 taps
+//            of the 7x7 window of pixel q), Bf = flipped filters.  One GEMM of
+//            M = 128 pixels, N = 48 filters.
+//   adjoint  S[q, t] = sum_i R[q, i] Ba[t, i]: R = r_i(q) = theta_i rho'(z_i),
+//            Ba[t, i] = k_i[t].  M = 128 pixels, N = 64 (49 taps + zeros).
+//            K_i^T r = sum_t shift_t(S[:, t]) (col2im): the horizontal part is a
+//            warp-shuffle sum (one warp = one 32-pixel row), the vertical part a
+//            7-row gather from a ring of shared-memory rows.
+//
+// Precision form: the filter bank is rounded once to the operand type (the
+// bank of the form); the data operands u and r are each carried as a hi + lo
+// pair of that type (K doubles), so z and S are accurate for the rounded bank
+// and the descent test sees a consistent gradient.
+//
+// Geometry: 26 x 58 output tile; tile + 3-pixel halo = 32 x 64 pixels = 16
+// GEMM blocks of 4 rows x 32 columns (M = 128); tile + 6 = 38 x 70 for u^{n+1}.
+// 256 threads: the two warpgroups split the epilogues by TMEM column; one
+// thread issues the MMAs.  BF16 fits two CTAs per SM (85 KB of shared memory).
+//
+// Waits on the MMA completion barriers are bounded; on a time-out the kernel
+// records tc_error, poisons its partial sums (the image stops with a
+// non-finite status) and still releases its tensor memory.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <cstring>
+
+#include "fe_internal.cuh"
+#include "fe_tile_common.cuh"
+#include "tc_ptx.cuh"
+
+namespace fe {
+namespace {
+
+constexpr int TY = tc_tile_y, TX = tc_tile_x, NT = 256;
+constexpr int R3Y = TY + 6, R3X = TX + 6;    // 64 x 32
+constexpr int R6Y = TY + 12, R6X = TX + 12;  // 70 x 38
+constexpr int SU_LD = R6X;
+constexpr int NBLK = R3Y / 4;                // 16 GEMM blocks of 128 pixels
+constexpr int NF = 48;                       // N of the forward GEMM
+constexpr int NTAP = 64;                     // N of the adjoint GEMM (49 taps + zeros)
+constexpr int KADJ = 2 * NF;                 // r hi | r lo
+constexpr int HRING = 12;                    // rows of the horizontal-sum ring
+constexpr int TMEM_COLS = 128;               // D_fwd at column 0, D_adj at column 64
+static_assert(R3X == 32, "one warp per halo row");
+static_assert(R3Y % 4 == 0, "GEMM blocks of 4 rows");
+
+template <int FMT>
+struct Cfg {
+    static constexpr int EB = FMT == 1 ? 2 : 4;            // operand bytes
+    static constexpr int KSTEP = FMT == 1 ? 16 : 8;        // K per MMA
+    static constexpr int KPASS = FMT == 1 ? 64 : 56;       // 49 taps padded to KSTEP
+    static constexpr int KFWD = 2 * KPASS;                 // u hi | u lo
+    static constexpr int E = 16 / EB;                      // elements per 16-byte chunk
+    static constexpr size_t A_BYTES = (size_t)128 * (KFWD > KADJ ? KFWD : KADJ) * EB;
+    static constexpr size_t BF_BYTES = (size_t)NF * KFWD * EB;
+    static constexpr size_t BA_BYTES = (size_t)NTAP * KADJ * EB;
+    static constexpr size_t OFF_A = 0;
+    static constexpr size_t OFF_BF = OFF_A + A_BYTES;
+    static constexpr size_t OFF_BA = OFF_BF + BF_BYTES;
+    static constexpr size_t OFF_U = OFF_BA + BA_BYTES;
+    static constexpr size_t OFF_H = OFF_U + (size_t)R6Y * SU_LD * 4;
+    static constexpr size_t OFF_G = OFF_H + (size_t)HRING * 7 * 32 * 4;
+    static constexpr size_t OFF_RED = OFF_G + (size_t)R3Y * R3X * 4;
+    static constexpr size_t BYTES = OFF_RED + (size_t)(NT / 32) * NRED * 8;
+    static_assert(OFF_BF % 128 == 0 && OFF_BA % 128 == 0 && OFF_U % 16 == 0 && OFF_RED % 8 == 0, "alignment");
+    static_assert(BF_BYTES % 16 == 0 && BA_BYTES % 16 == 0, "vector copies");
+};
+static_assert(2 * (Cfg<1>::BYTES + 1024) <= 228 * 1024, "BF16: two CTAs per SM");
+static_assert(Cfg<2>::BYTES <= 227 * 1024, "TF32: one CTA per SM");
+
+constexpr float LN2 = 0.69314718055994530942f;
+
+// Pack 8 (BF16) or 4 (TF32) consecutive K values into one 16-byte chunk.
+template <int FMT>
+__device__ __forceinline__ uint4 pack_chunk(const float *v);
+template <>
+__device__ __forceinline__ uint4 pack_chunk<1>(const float *v) {
+    uint4 o;
+    __nv_bfloat162 t;
+    t = __floats2bfloat162_rn(v[0], v[1]);
+    o.x = *reinterpret_cast<uint32_t *>(&t);
+    t = __floats2bfloat162_rn(v[2], v[3]);
+    o.y = *reinterpret_cast<uint32_t *>(&t);
+    t = __floats2bfloat162_rn(v[4], v[5]);
+    o.z = *reinterpret_cast<uint32_t *>(&t);
+    t = __floats2bfloat162_rn(v[6], v[7]);
+    o.w = *reinterpret_cast<uint32_t *>(&t);
+    return o;
+}
+template <>
+__device__ __forceinline__ uint4 pack_chunk<2>(const float *v) {
+    uint4 o;
+    o.x = __float_as_uint(tc::round_tf32(v[0]));
+    o.y = __float_as_uint(tc::round_tf32(v[1]));
+    o.z = __float_as_uint(tc::round_tf32(v[2]));
+    o.w = __float_as_uint(tc::round_tf32(v[3]));
+    return o;
+}
+
+template <int FMT>
+__device__ __forceinline__ float rounded_value(float x) {
+    if (FMT == 1) return __bfloat162float(__float2bfloat16_rn(x));
+    return tc::round_tf32(x);
+}
+
+template <int MODE, int FMT>
+__global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KParams p) {
+    using C = Cfg<FMT>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *sA = smem + C::OFF_A;
+    unsigned char *sBf = smem + C::OFF_BF;
+    unsigned char *sBa = smem + C::OFF_BA;
+    float *sU = reinterpret_cast<float *>(smem + C::OFF_U);
+    float *sH = reinterpret_cast<float *>(smem + C::OFF_H);
+    float *sG = reinterpret_cast<float *>(smem + C::OFF_G);
+    double *sRed = reinterpret_cast<double *>(smem + C::OFF_RED);
+    __shared__ uint64_t bar_f, bar_a;
+    __shared__ uint32_t tbase;
+    __shared__ int sLast;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gtile = p.tile0 + (int)blockIdx.x;
+    const TileDesc td = p.tiles[gtile];
+    const int img = td.img;
+    const ImgDesc im = p.imgs[img];
+    ImgState *st = p.st + img;
+    const int H = im.H, W = im.W, y0 = td.y0, x0 = td.x0, oh = td.oh, ow = td.ow, sy = td.sy, sx = td.sx;
+
+    bool active = true;
+    int gcur_out = 0;
+    if (MODE == MODE_TRIAL) {
+        active = (st->done == 0) && (st->n < st->target);
+        gcur_out = st->gcur ^ 1;
+    }
+
+    if (active) {
+        // ---- rounded filter bank (B operands) into shared memory -----------
+        {
+            const uint4 *gf = reinterpret_cast<const uint4 *>(p.tcw_fwd);
+            const uint4 *ga = reinterpret_cast<const uint4 *>(p.tcw_adj);
+            for (int j = tid; j < (int)(C::BF_BYTES / 16); j += NT) reinterpret_cast<uint4 *>(sBf)[j] = __ldg(gf + j);
+            for (int j = tid; j < (int)(C::BA_BYTES / 16); j += NT) reinterpret_cast<uint4 *>(sBa)[j] = __ldg(ga + j);
+        }
+        if (tid == 0) {
+            tc::mbar_init(&bar_f, 1);
+            tc::mbar_init(&bar_a, 1);
+        }
+        if (warp == 0) tc::tmem_alloc(&tbase, TMEM_COLS);
+
+        // ---- inertial step and prox on tile + 6 (owned pixels: sums) -------
+        double accF = 0.0, accG = 0.0, accGD = 0.0, accDD = 0.0, accDP = 0.0;
+        {
+            int cur = 0, gcur = 0;
+            float a = 0.f, b = 0.f, tl = 0.f;
+            if (MODE == MODE_TRIAL) {
+                cur = st->cur;
+                gcur = st->gcur;
+                const double alpha = st->alpha;
+                a = (float)alpha;
+                b = (float)p.beta;
+                tl = (float)(alpha * im.lambda);
+            }
+            const float *uc = (MODE == MODE_TRIAL || MODE == MODE_INIT) ? im.u[cur] : p.u_ext;
+            const float *upv = im.u[(cur + 2) % 3];
+            const float *gc = im.g[gcur];
+            float *un = im.u[(cur + 1) % 3];
+            const float *f2p = im.f2;
+            for (int idx = tid; idx < R6Y * R6X; idx += NT) {
+                const int ry = idx / R6X, rx = idx - ry * R6X;
+                const int y = y0 - 6 + ry, x = x0 - 6 + rx;
+                const size_t off = (size_t)reflect(y, H) * W + reflect(x, W);
+                const bool owned = ry >= 6 + sy && ry < 6 + sy + oh && rx >= 6 + sx && rx < 6 + sx + ow;
+                float v;
+                if (MODE == MODE_TRIAL) {
+                    const float u0 = __ldg(uc + off), u_1 = __ldg(upv + off), g0 = __ldg(gc + off);
+                    const float f2 = __ldg(f2p + off);
+                    const float dprev = u0 - u_1;
+                    const float uhat = fmaf(-a, g0, fmaf(b, dprev, u0));
+                    v = prox_g(uhat, f2, tl);
+                    if (owned) {
+                        un[off] = v;
+                        const float d = v - u0;
+                        accGD += (double)(g0 * d);
+                        accDD += (double)(d * d);
+                        accDP += (double)(d * dprev);
+                        accG += (double)(v * v - 2.0f * f2 * logf(v));
+                    }
+                } else {
+                    v = __ldg(uc + off);
+                    if (owned) accG += (double)(v * v - 2.0f * __ldg(f2p + off) * logf(v));
+                }
+                sU[ry * SU_LD + rx] = v;
+            }
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        const uint32_t taddr = tbase;
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        const uint32_t sA_u32 = tc::smem_u32(sA), sBf_u32 = tc::smem_u32(sBf), sBa_u32 = tc::smem_u32(sBa);
+        constexpr uint32_t SBO_F = (uint32_t)(C::KFWD / C::E) * 128, SBO_A = (uint32_t)(KADJ / C::E) * 128;
+        constexpr uint32_t IDESC_F = tc::make_idesc(FMT, 128, NF), IDESC_A = tc::make_idesc(FMT, 128, NTAP);
+        uint32_t phase_f = 0, phase_a = 0;
+        bool tc_ok = true;
+        const int wg = warp >> 2;  // warpgroup: epilogue split
+
+        for (int blk = 0; blk < NBLK; ++blk) {
+            // ---- im2col of u^{n+1} for 128 pixels, hi (wg 0) / lo (wg 1) ----
+            {
+                const int m = tid & 127, part = tid >> 7;
+                const int pr = 4 * blk + (m >> 5), pc = m & 31;
+                float v[C::KPASS];
+#pragma unroll
+                for (int aa = 0; aa < KS; ++aa)
+#pragma unroll
+                    for (int bb = 0; bb < KS; ++bb) {
+                        const float u = sU[(pr + aa) * SU_LD + pc + bb];
+                        v[aa * KS + bb] = part == 0 ? u : u - rounded_value<FMT>(u);
+                    }
+#pragma unroll
+                for (int t = KT; t < C::KPASS; ++t) v[t] = 0.f;
+                unsigned char *row = sA + tc::kmajor_offset(m, part * C::KPASS, C::KFWD, C::EB);
+#pragma unroll
+                for (int j = 0; j < C::KPASS / C::E; ++j)
+                    *reinterpret_cast<uint4 *>(row + j * 128) = pack_chunk<FMT>(v + j * C::E);
+            }
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after_sync();
+#pragma unroll
+                for (int ks = 0; ks < C::KFWD / C::KSTEP; ++ks)
+                    tc::mma<FMT>(taddr, tc::make_smem_desc(sA_u32 + ks * 256, 128, SBO_F),
+                                 tc::make_smem_desc(sBf_u32 + ks * 256, 128, SBO_F), IDESC_F, ks > 0 ? 1u : 0u);
+                tc::mma_commit(&bar_f);
+            }
+            if (!tc::mbar_wait(&bar_f, phase_f)) tc_ok = false;
+            phase_f ^= 1u;
+            tc::fence_after_sync();
+
+            // ---- epilogue 1: rho' -> R (hi | lo), energy terms ----------------
+            {
+                const int row = 4 * blk + (warp & 3), col = lane;
+                const int y = y0 - 3 + row, x = x0 - 3 + col;
+                const bool inimg = y >= 0 && y < H && x >= 0 && x < W;
+                const bool owned = row >= 3 + sy && row < 3 + sy + oh && col >= 3 + sx && col < 3 + sx + ow;
+                const int m = (warp & 3) * 32 + lane;
+                float z[24];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    float t8[8];
+                    tc::tmem_ld8(taddr + lane_base + (uint32_t)(24 * wg + 8 * j), t8);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) z[8 * j + k] = t8[k];
+                }
+                tc::tmem_ld_wait();
+                float rh[24], rl[24], psum = 0.f;
+#pragma unroll
+                for (int i = 0; i < 24; ++i) {
+                    const float th = __ldg(p.theta + 24 * wg + i);
+                    const float zz = z[i];
+                    const float q = fmaf(zz, zz, 1.0f);
+                    const float r = inimg ? __fdividef(2.0f * th * zz, q) : 0.0f;
+                    psum = fmaf(th, __log2f(q), psum);
+                    const float hi = rounded_value<FMT>(r);
+                    rh[i] = hi;
+                    rl[i] = r - hi;
+                }
+                if (owned) accF += (double)(psum * LN2);
+                unsigned char *rowp = sA + tc::kmajor_offset(m, 0, KADJ, C::EB);
+#pragma unroll
+                for (int j = 0; j < 24 / C::E; ++j) {
+                    *reinterpret_cast<uint4 *>(rowp + ((24 * wg) / C::E + j) * 128) = pack_chunk<FMT>(rh + j * C::E);
+                    *reinterpret_cast<uint4 *>(rowp + ((NF + 24 * wg) / C::E + j) * 128) = pack_chunk<FMT>(rl + j * C::E);
+                }
+            }
+            tc::fence_before_sync();
+            tc::fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after_sync();
+#pragma unroll
+                for (int ks = 0; ks < KADJ / C::KSTEP; ++ks)
+                    tc::mma<FMT>(taddr + 64, tc::make_smem_desc(sA_u32 + ks * 256, 128, SBO_A),
+                                 tc::make_smem_desc(sBa_u32 + ks * 256, 128, SBO_A), IDESC_A, ks > 0 ? 1u : 0u);
+                tc::mma_commit(&bar_a);
+            }
+            if (!tc::mbar_wait(&bar_a, phase_a)) tc_ok = false;
+            phase_a ^= 1u;
+            tc::fence_after_sync();
+
+            // ---- epilogue 2: horizontal col2im by warp shuffles ---------------
+            {
+                const int row = 4 * blk + (warp & 3);
+                const int a_lo = wg == 0 ? 0 : 4, a_hi = wg == 0 ? 4 : KS;
+                for (int aa = a_lo; aa < a_hi; ++aa) {
+                    float s8[8];
+                    tc::tmem_ld8(taddr + lane_base + (uint32_t)(64 + KS * aa), s8);
+                    tc::tmem_ld_wait();
+                    float h = 0.f;
+#pragma unroll
+                    for (int bb = 0; bb < KS; ++bb) {
+                        const int src = lane - 3 + bb;
+                        const float v = __shfl_sync(0xffffffffu, s8[bb], src & 31);
+                        h += (src >= 0 && src < 32) ? v : 0.0f;
+                    }
+                    sH[((row % HRING) * KS + aa) * 32 + lane] = h;
+                }
+            }
+            tc::fence_before_sync();
+            __syncthreads();
+            // ---- vertical col2im of the ext rows whose 7 source rows are done --
+            if (tid < 128) {
+                const int ty = 4 * blk - 6 + (tid >> 5);
+                if (ty >= -3) {
+                    float g = 0.f;
+#pragma unroll
+                    for (int aa = 0; aa < KS; ++aa) {
+                        const int srow = ty + aa;
+                        if (srow >= 0 && srow < R3Y) g += sH[((srow % HRING) * KS + aa) * 32 + lane];
+                    }
+                    sG[(ty + 3) * 32 + lane] = g;
+                }
+            }
+        }
+        __syncthreads();
+        // ---- remaining ext rows (their missing source rows lie off the tile) --
+        if (tid < 96) {
+            const int ty = 4 * (NBLK - 1) - 2 + (tid >> 5);  // 58, 59, 60
+            float g = 0.f;
+#pragma unroll
+            for (int aa = 0; aa < KS; ++aa) {
+                const int srow = ty + aa;
+                if (srow >= 0 && srow < R3Y) g += sH[((srow % HRING) * KS + aa) * 32 + lane];
+            }
+            sG[(ty + 3) * 32 + lane] = g;
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (warp == 0) tc::tmem_dealloc(taddr, TMEM_COLS);
+
+        // ---- fold the frame, write the owned gradient ------------------------
+        if (MODE != MODE_ENERGY_EXT) {
+            float *gout;
+            if (MODE == MODE_GRAD_EXT)
+                gout = p.g_ext;
+            else if (MODE == MODE_INIT)
+                gout = im.g[0];
+            else
+                gout = im.g[gcur_out];
+            for (int idx = tid; idx < oh * ow; idx += NT) {
+                const int ty = sy + idx / ow, tx = sx + idx % ow;
+                const int y = y0 + ty, x = x0 + tx;
+                float gv = sG[(ty + 3) * 32 + tx + 3];
+                if (y < 3 || y >= H - 3 || x < 3 || x >= W - 3) {
+                    // ext positions the symmetric extension maps onto (y, x)
+                    int ey[3], ex[3], ny = 1, nx = 1;
+                    ey[0] = ty + 3;
+                    ex[0] = tx + 3;
+                    if (y < 3) ey[ny++] = (-y - 1) - y0 + 3;
+                    if (y >= H - 3) ey[ny++] = (2 * H - 1 - y) - y0 + 3;
+                    if (x < 3) ex[nx++] = (-x - 1) - x0 + 3;
+                    if (x >= W - 3) ex[nx++] = (2 * W - 1 - x) - x0 + 3;
+                    for (int mm = 0; mm < ny; ++mm)
+                        for (int nn = 0; nn < nx; ++nn) {
+                            if (mm == 0 && nn == 0) continue;
+                            gv += sG[ey[mm] * 32 + ex[nn]];
+                        }
+                }
+                gout[(size_t)y * W + x] = gv;
+            }
+        }
+        if (!tc_ok) {
+            accF = __longlong_as_double(0x7ff8000000000000LL);  // NaN: the image stops
+            if (tid == 0) atomicExch(p.tc_error, 1);
+        }
+        const double vals[NRED] = {accF, accG, accGD, accDD, accDP};
+        tile_finish<NT>(p, MODE, gtile, img, im, st, vals, sRed, &sLast);
+    }
+    if (MODE == MODE_TRIAL) loop_control(p);
+}
+
+template <int FMT>
+cudaError_t prepare_fmt() {
+    cudaError_t e = cudaSuccess;
+    const int b = (int)Cfg<FMT>::BYTES;
+    if ((e = cudaFuncSetAttribute(tc_tile_kernel<MODE_TRIAL, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)))
+        return e;
+    if ((e = cudaFuncSetAttribute(tc_tile_kernel<MODE_INIT, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)))
+        return e;
+    if ((e = cudaFuncSetAttribute(tc_tile_kernel<MODE_GRAD_EXT, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)))
+        return e;
+    return cudaFuncSetAttribute(tc_tile_kernel<MODE_ENERGY_EXT, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+}
+
+template <int FMT>
+cudaError_t launch_fmt(int mode, const KParams &p, int ngrid, cudaStream_t s) {
+    const size_t b = Cfg<FMT>::BYTES;
+    switch (mode) {
+        case MODE_TRIAL: tc_tile_kernel<MODE_TRIAL, FMT><<<ngrid, NT, b, s>>>(p); break;
+        case MODE_INIT: tc_tile_kernel<MODE_INIT, FMT><<<ngrid, NT, b, s>>>(p); break;
+        case MODE_GRAD_EXT: tc_tile_kernel<MODE_GRAD_EXT, FMT><<<ngrid, NT, b, s>>>(p); break;
+        case MODE_ENERGY_EXT: tc_tile_kernel<MODE_ENERGY_EXT, FMT><<<ngrid, NT, b, s>>>(p); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// Host rounding of the filter bank: BF16 round-to-nearest-even, TF32
+// round-to-nearest with ties away from zero (as cvt.rna.tf32.f32).
+uint32_t f2u(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    return u;
+}
+float u2f(uint32_t u) {
+    float x;
+    std::memcpy(&x, &u, 4);
+    return x;
+}
+
+}  // namespace
+
+float tc_round(int fmt, float x) {
+    uint32_t u = f2u(x);
+    if (fmt == 1) {
+        u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+    } else {
+        u = (u + 0x1000u) & 0xFFFFE000u;
+    }
+    return u2f(u);
+}
+
+void tc_build_weights(int fmt, const float *filters, int nf, std::vector<unsigned char> &fwd,
+                      std::vector<unsigned char> &adj) {
+    const int eb = fmt == 1 ? 2 : 4, kpass = fmt == 1 ? 64 : 56, kfwd = 2 * kpass;
+    fwd.assign((size_t)NF * kfwd * eb, 0);
+    adj.assign((size_t)NTAP * KADJ * eb, 0);
+    auto put = [&](std::vector<unsigned char> &buf, int r, int k, int K, float v) {
+        const uint32_t off = tc::kmajor_offset(r, k, K, eb);
+        const uint32_t bits = f2u(tc_round(fmt, v));
+        if (eb == 2) {
+            const uint16_t h = (uint16_t)(bits >> 16);
+            std::memcpy(&buf[off], &h, 2);
+        } else {
+            std::memcpy(&buf[off], &bits, 4);
+        }
+    };
+    for (int i = 0; i < nf && i < NF; ++i)
+        for (int t = 0; t < KT; ++t) {
+            // forward: im2col tap t = 7a + b reads u(p + (a, b)) of the window, i.e.
+            // correlation with the flipped filter; the same taps for u hi and u lo
+            const float kf = filters[(size_t)i * KT + (KT - 1 - t)];
+            put(fwd, i, t, kfwd, kf);
+            put(fwd, i, kpass + t, kfwd, kf);
+            // adjoint: S[q, t] = sum_i k_i[t] r_i(q), for r hi and r lo
+            const float ka = filters[(size_t)i * KT + t];
+            put(adj, t, i, KADJ, ka);
+            put(adj, t, NF + i, KADJ, ka);
+        }
+}
+
+size_t tc_smem_bytes(int fmt) { return fmt == 1 ? Cfg<1>::BYTES : Cfg<2>::BYTES; }
+int tc_threads() { return NT; }
+
+cudaError_t tc_prepare() {
+    cudaError_t e = prepare_fmt<1>();
+    if (e != cudaSuccess) return e;
+    return prepare_fmt<2>();
+}
+
+cudaError_t tc_launch(int mode, int fmt, const KParams &p, int ngrid, cudaStream_t s) {
+    return fmt == 1 ? launch_fmt<1>(mode, p, ngrid, s) : launch_fmt<2>(mode, p, ngrid, s);
+}
+
+const void *tc_trial_entry(int fmt) {
+    return fmt == 1 ? reinterpret_cast<const void *>(&tc_tile_kernel<MODE_TRIAL, 1>)
+                    : reinterpret_cast<const void *>(&tc_tile_kernel<MODE_TRIAL, 2>);
+}
+
+}  // namespace fe

@@ -4,6 +4,8 @@ the same rounded operands."""
 import numpy as np
 import pytest
 
+from rounding import round_bf16, round_tf32
+
 pytestmark = pytest.mark.gpu
 
 
@@ -16,20 +18,6 @@ def fe():
     build.build()
     from paper_1404_5344_gb300 import fe as fe_mod
     return fe_mod
-
-
-def round_bf16(x):
-    """Round-to-nearest-even to bfloat16, returned as float32."""
-    b = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
-    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
-    return b.astype(np.uint32).view(np.float32)
-
-
-def round_tf32(x):
-    """Round to nearest (ties away from zero) on the 13 dropped mantissa bits."""
-    b = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
-    b = (b + 0x1000) & 0xFFFFE000
-    return b.astype(np.uint32).view(np.float32)
 
 
 def _run(fe, prec, N, K, A, B):
