@@ -62,18 +62,23 @@ struct Cfg {
     static constexpr int KPASS = FMT == 1 ? 64 : 56;       // 49 taps padded to KSTEP
     static constexpr int KFWD = 2 * KPASS;                 // u hi | u lo
     static constexpr int E = 16 / EB;                      // elements per 16-byte chunk
-    static constexpr size_t A_BYTES = (size_t)128 * (KFWD > KADJ ? KFWD : KADJ) * EB;
+    static constexpr int NCH = KPASS / E;                  // chunks per pass
+    static constexpr size_t AF_BYTES = (size_t)128 * KFWD * EB;
+    static constexpr size_t R_BYTES = (size_t)128 * KADJ * EB;
     static constexpr size_t BF_BYTES = (size_t)NF * KFWD * EB;
     static constexpr size_t BA_BYTES = (size_t)NTAP * KADJ * EB;
-    static constexpr size_t OFF_A = 0;
-    static constexpr size_t OFF_BF = OFF_A + A_BYTES;
+    static constexpr size_t OFF_AF = 0;
+    static constexpr size_t OFF_R = OFF_AF + AF_BYTES;
+    static constexpr size_t OFF_BF = OFF_R + R_BYTES;
     static constexpr size_t OFF_BA = OFF_BF + BF_BYTES;
     static constexpr size_t OFF_U = OFF_BA + BA_BYTES;
     static constexpr size_t OFF_H = OFF_U + (size_t)R6Y * SU_LD * 4;
     static constexpr size_t OFF_G = OFF_H + (size_t)HRING * 7 * 32 * 4;
-    static constexpr size_t OFF_RED = OFF_G + (size_t)R3Y * R3X * 4;
+    static constexpr size_t OFF_TH = OFF_G + (size_t)R3Y * R3X * 4;
+    static constexpr size_t OFF_RED = OFF_TH + (size_t)2 * NF * 4;
     static constexpr size_t BYTES = OFF_RED + (size_t)(NT / 32) * NRED * 8;
-    static_assert(OFF_BF % 128 == 0 && OFF_BA % 128 == 0 && OFF_U % 16 == 0 && OFF_RED % 8 == 0, "alignment");
+    static_assert(OFF_R % 128 == 0 && OFF_BF % 128 == 0 && OFF_BA % 128 == 0, "operand alignment");
+    static_assert(OFF_U % 16 == 0 && OFF_TH % 16 == 0 && OFF_RED % 8 == 0, "alignment");
     static_assert(BF_BYTES % 16 == 0 && BA_BYTES % 16 == 0, "vector copies");
 };
 static_assert(2 * (Cfg<1>::BYTES + 1024) <= 228 * 1024, "BF16: two CTAs per SM");
@@ -81,49 +86,75 @@ static_assert(Cfg<2>::BYTES <= 227 * 1024, "TF32: one CTA per SM");
 
 constexpr float LN2 = 0.69314718055994530942f;
 
-// Pack 8 (BF16) or 4 (TF32) consecutive K values into one 16-byte chunk.
+// hi = x rounded to the operand type, lo = (x - hi) rounded, for one 16-byte
+// chunk of E consecutive K values.
 template <int FMT>
-__device__ __forceinline__ uint4 pack_chunk(const float *v);
+__device__ __forceinline__ void hilo_chunk(const float *v, uint4 &hi, uint4 &lo);
 template <>
-__device__ __forceinline__ uint4 pack_chunk<1>(const float *v) {
-    uint4 o;
-    __nv_bfloat162 t;
-    t = __floats2bfloat162_rn(v[0], v[1]);
-    o.x = *reinterpret_cast<uint32_t *>(&t);
-    t = __floats2bfloat162_rn(v[2], v[3]);
-    o.y = *reinterpret_cast<uint32_t *>(&t);
-    t = __floats2bfloat162_rn(v[4], v[5]);
-    o.z = *reinterpret_cast<uint32_t *>(&t);
-    t = __floats2bfloat162_rn(v[6], v[7]);
-    o.w = *reinterpret_cast<uint32_t *>(&t);
-    return o;
+__device__ __forceinline__ void hilo_chunk<1>(const float *v, uint4 &hi, uint4 &lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[2 * j] - __low2float(h2), v[2 * j + 1] - __high2float(h2));
+        h[j] = *reinterpret_cast<const uint32_t *>(&h2);
+        l[j] = *reinterpret_cast<const uint32_t *>(&l2);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 template <>
-__device__ __forceinline__ uint4 pack_chunk<2>(const float *v) {
-    uint4 o;
-    o.x = __float_as_uint(tc::round_tf32(v[0]));
-    o.y = __float_as_uint(tc::round_tf32(v[1]));
-    o.z = __float_as_uint(tc::round_tf32(v[2]));
-    o.w = __float_as_uint(tc::round_tf32(v[3]));
-    return o;
+__device__ __forceinline__ void hilo_chunk<2>(const float *v, uint4 &hi, uint4 &lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float hv = tc::round_tf32(v[j]);
+        h[j] = __float_as_uint(hv);
+        l[j] = __float_as_uint(tc::round_tf32(v[j] - hv));
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// im2col of u^{n+1} for GEMM block blk: pixel m of the block (R3 row 4 blk +
+// m/32, column m%32) gets the 49 taps of its 7x7 window as K values, hi in
+// chunks [0, NCH) and lo in [NCH, 2 NCH).  The two threads of a pixel take
+// the even / odd chunks.
 template <int FMT>
-__device__ __forceinline__ float rounded_value(float x) {
-    if (FMT == 1) return __bfloat162float(__float2bfloat16_rn(x));
-    return tc::round_tf32(x);
+__device__ __forceinline__ void im2col(const float *__restrict__ sU, unsigned char *__restrict__ sAF, int blk,
+                                       int m, int part) {
+    using C = Cfg<FMT>;
+    const int pr = 4 * blk + (m >> 5), pc = m & 31;
+    const float *win = sU + pr * SU_LD + pc;
+    unsigned char *row = sAF + tc::kmajor_offset(m, 0, C::KFWD, C::EB);
+#pragma unroll
+    for (int c = 0; c < C::NCH; ++c) {
+        if ((c & 1) != part) continue;
+        float v[C::E];
+#pragma unroll
+        for (int j = 0; j < C::E; ++j) {
+            const int t = c * C::E + j;
+            v[j] = t < KT ? win[(t / KS) * SU_LD + (t % KS)] : 0.0f;
+        }
+        uint4 hi, lo;
+        hilo_chunk<FMT>(v, hi, lo);
+        *reinterpret_cast<uint4 *>(row + c * 128) = hi;
+        *reinterpret_cast<uint4 *>(row + (C::NCH + c) * 128) = lo;
+    }
 }
 
 template <int MODE, int FMT>
 __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KParams p) {
     using C = Cfg<FMT>;
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *sA = smem + C::OFF_A;
+    unsigned char *sAF = smem + C::OFF_AF;
+    unsigned char *sR = smem + C::OFF_R;
     unsigned char *sBf = smem + C::OFF_BF;
     unsigned char *sBa = smem + C::OFF_BA;
     float *sU = reinterpret_cast<float *>(smem + C::OFF_U);
     float *sH = reinterpret_cast<float *>(smem + C::OFF_H);
     float *sG = reinterpret_cast<float *>(smem + C::OFF_G);
+    float *sTh = reinterpret_cast<float *>(smem + C::OFF_TH);  // theta_i, then 2 theta_i
     double *sRed = reinterpret_cast<double *>(smem + C::OFF_RED);
     __shared__ uint64_t bar_f, bar_a;
     __shared__ uint32_t tbase;
@@ -145,12 +176,17 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
     }
 
     if (active) {
-        // ---- rounded filter bank (B operands) into shared memory -----------
+        // ---- rounded filter bank (B operands) and theta into shared memory --
         {
             const uint4 *gf = reinterpret_cast<const uint4 *>(p.tcw_fwd);
             const uint4 *ga = reinterpret_cast<const uint4 *>(p.tcw_adj);
             for (int j = tid; j < (int)(C::BF_BYTES / 16); j += NT) reinterpret_cast<uint4 *>(sBf)[j] = __ldg(gf + j);
             for (int j = tid; j < (int)(C::BA_BYTES / 16); j += NT) reinterpret_cast<uint4 *>(sBa)[j] = __ldg(ga + j);
+            if (tid < NF) {
+                const float th = __ldg(p.theta + tid);
+                sTh[tid] = th;
+                sTh[NF + tid] = 2.0f * th;
+            }
         }
         if (tid == 0) {
             tc::mbar_init(&bar_f, 1);
@@ -176,88 +212,140 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
             const float *gc = im.g[gcur];
             float *un = im.u[(cur + 1) % 3];
             const float *f2p = im.f2;
-            for (int idx = tid; idx < R6Y * R6X; idx += NT) {
-                const int ry = idx / R6X, rx = idx - ry * R6X;
-                const int y = y0 - 6 + ry, x = x0 - 6 + rx;
-                const size_t off = (size_t)reflect(y, H) * W + reflect(x, W);
-                const bool owned = ry >= 6 + sy && ry < 6 + sy + oh && rx >= 6 + sx && rx < 6 + sx + ow;
-                float v;
-                if (MODE == MODE_TRIAL) {
-                    const float u0 = __ldg(uc + off), u_1 = __ldg(upv + off), g0 = __ldg(gc + off);
-                    const float f2 = __ldg(f2p + off);
-                    const float dprev = u0 - u_1;
-                    const float uhat = fmaf(-a, g0, fmaf(b, dprev, u0));
-                    v = prox_g(uhat, f2, tl);
-                    if (owned) {
-                        un[off] = v;
-                        const float d = v - u0;
-                        accGD += (double)(g0 * d);
-                        accDD += (double)(d * d);
-                        accDP += (double)(d * dprev);
-                        accG += (double)(v * v - 2.0f * f2 * logf(v));
+            constexpr int NPIX = R6Y * R6X, UNR = 4;
+            for (int base = 0; base < NPIX; base += UNR * NT) {
+                size_t off[UNR];
+                bool inb[UNR], owned[UNR];
+                float u0[UNR], u_1[UNR], g0[UNR], f2[UNR];
+#pragma unroll
+                for (int k = 0; k < UNR; ++k) {
+                    const int idx = base + k * NT + tid;
+                    inb[k] = idx < NPIX;
+                    const int ry = inb[k] ? idx / R6X : 0, rx = inb[k] ? idx - ry * R6X : 0;
+                    off[k] = (size_t)reflect(y0 - 6 + ry, H) * W + reflect(x0 - 6 + rx, W);
+                    owned[k] = inb[k] && ry >= 6 + sy && ry < 6 + sy + oh && rx >= 6 + sx && rx < 6 + sx + ow;
+                    u0[k] = __ldg(uc + off[k]);
+                    f2[k] = (MODE == MODE_TRIAL || owned[k]) ? __ldg(f2p + off[k]) : 1.0f;
+                    if (MODE == MODE_TRIAL) {
+                        u_1[k] = __ldg(upv + off[k]);
+                        g0[k] = __ldg(gc + off[k]);
                     }
-                } else {
-                    v = __ldg(uc + off);
-                    if (owned) accG += (double)(v * v - 2.0f * __ldg(f2p + off) * logf(v));
                 }
-                sU[ry * SU_LD + rx] = v;
+#pragma unroll
+                for (int k = 0; k < UNR; ++k) {
+                    if (!inb[k]) continue;
+                    float v;
+                    if (MODE == MODE_TRIAL) {
+                        const float dprev = u0[k] - u_1[k];
+                        const float uhat = fmaf(-a, g0[k], fmaf(b, dprev, u0[k]));
+                        v = prox_g(uhat, f2[k], tl);
+                        if (owned[k]) {
+                            un[off[k]] = v;
+                            const float d = v - u0[k];
+                            accGD += (double)(g0[k] * d);
+                            accDD += (double)(d * d);
+                            accDP += (double)(d * dprev);
+                        }
+                    } else {
+                        v = u0[k];
+                    }
+                    if (owned[k]) accG += (double)(v * v - 2.0f * f2[k] * logf(v));
+                    sU[base + k * NT + tid] = v;  // R6 row-major with pitch SU_LD = R6X
+                }
             }
         }
+        static_assert(SU_LD == R6X, "prologue stores the R6 region with pitch R6X");
+
+        const uint32_t sAF_u32 = tc::smem_u32(sAF), sR_u32 = tc::smem_u32(sR);
+        const uint32_t sBf_u32 = tc::smem_u32(sBf), sBa_u32 = tc::smem_u32(sBa);
+        constexpr uint32_t SBO_F = (uint32_t)(C::KFWD / C::E) * 128, SBO_A = (uint32_t)(KADJ / C::E) * 128;
+        constexpr uint32_t IDESC_F = tc::make_idesc(FMT, 128, NF), IDESC_A = tc::make_idesc(FMT, 128, NTAP);
+        const int m = tid & 127, part = tid >> 7;  // im2col: pixel, chunk parity
+        const int wg = warp >> 2, lg = warp & 3;   // epilogues: column half, TMEM lane group
+        const bool edge_x = x0 == 0 || x0 + TX >= W;
+        const bool full_y = y0 >= 3 && y0 + TY + 3 <= H, full_x = x0 >= 3 && x0 + TX + 3 <= W;
+        const bool all_in = full_y && full_x;  // every halo pixel lies in the image
+
+        // block 0: im2col and forward MMA
+        im2col<FMT>(sU, sAF, 0, m, part);
         tc::fence_proxy_async();
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
         const uint32_t taddr = tbase;
-        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-        const uint32_t sA_u32 = tc::smem_u32(sA), sBf_u32 = tc::smem_u32(sBf), sBa_u32 = tc::smem_u32(sBa);
-        constexpr uint32_t SBO_F = (uint32_t)(C::KFWD / C::E) * 128, SBO_A = (uint32_t)(KADJ / C::E) * 128;
-        constexpr uint32_t IDESC_F = tc::make_idesc(FMT, 128, NF), IDESC_A = tc::make_idesc(FMT, 128, NTAP);
+        const uint32_t lane_base = (uint32_t)(lg * 32) << 16;
+        if (tid == 0) {
+#pragma unroll
+            for (int ks = 0; ks < C::KFWD / C::KSTEP; ++ks)
+                tc::mma<FMT>(taddr, tc::make_smem_desc(sAF_u32 + ks * 256, 128, SBO_F),
+                             tc::make_smem_desc(sBf_u32 + ks * 256, 128, SBO_F), IDESC_F, ks > 0 ? 1u : 0u);
+            tc::mma_commit(&bar_f);
+        }
         uint32_t phase_f = 0, phase_a = 0;
         bool tc_ok = true;
-        const int wg = warp >> 2;  // warpgroup: epilogue split
 
-        for (int blk = 0; blk < NBLK; ++blk) {
-            // ---- im2col of u^{n+1} for 128 pixels, hi (wg 0) / lo (wg 1) ----
-            {
-                const int m = tid & 127, part = tid >> 7;
-                const int pr = 4 * blk + (m >> 5), pc = m & 31;
-                float v[C::KPASS];
+        // epilogue 2 of block pb: horizontal col2im of S (TMEM) into the H ring
+        auto epi2 = [&](int pb) {
+            const int row = 4 * pb + lg;
+            const int slot = row % HRING;
+            const int a_lo = wg == 0 ? 0 : 4, na = wg == 0 ? 4 : 3;
+            float s8[4][8];
 #pragma unroll
-                for (int aa = 0; aa < KS; ++aa)
+            for (int j = 0; j < 4; ++j)
+                if (j < na) tc::tmem_ld8(taddr + lane_base + (uint32_t)(64 + KS * (a_lo + j)), s8[j]);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (j >= na) break;
+                float h = 0.f;
+                if (edge_x) {
 #pragma unroll
                     for (int bb = 0; bb < KS; ++bb) {
-                        const float u = sU[(pr + aa) * SU_LD + pc + bb];
-                        v[aa * KS + bb] = part == 0 ? u : u - rounded_value<FMT>(u);
+                        const int src = lane - 3 + bb;
+                        const float v = __shfl_sync(0xffffffffu, s8[j][bb], src & 31);
+                        h += (src >= 0 && src < 32) ? v : 0.0f;
                     }
+                } else {
+                    // interior tile: lanes 3..28 (the only ones used) have all sources in the warp
 #pragma unroll
-                for (int t = KT; t < C::KPASS; ++t) v[t] = 0.f;
-                unsigned char *row = sA + tc::kmajor_offset(m, part * C::KPASS, C::KFWD, C::EB);
-#pragma unroll
-                for (int j = 0; j < C::KPASS / C::E; ++j)
-                    *reinterpret_cast<uint4 *>(row + j * 128) = pack_chunk<FMT>(v + j * C::E);
+                    for (int bb = 0; bb < KS; ++bb) h += __shfl_sync(0xffffffffu, s8[j][bb], (lane - 3 + bb) & 31);
+                }
+                sH[(slot * KS + a_lo + j) * 32 + lane] = h;
             }
-            tc::fence_proxy_async();
-            tc::fence_before_sync();
-            __syncthreads();
-            if (tid == 0) {
+        };
+        // vertical col2im of the ext rows whose 7 source rows are complete
+        auto emit = [&](int ty) {
+            if (ty < -3 || ty >= TY + 3) return;
+            float g = 0.f;
+            int s = ((ty % HRING) + HRING) % HRING;
+#pragma unroll
+            for (int aa = 0; aa < KS; ++aa) {
+                const int srow = ty + aa;
+                if (srow >= 0 && srow < R3Y) g += sH[(s * KS + aa) * 32 + lane];
+                s = s + 1 == HRING ? 0 : s + 1;
+            }
+            sG[(ty + 3) * 32 + lane] = g;
+        };
+
+        for (int blk = 0; blk < NBLK; ++blk) {
+            // (a) col2im of the previous block, overlapping MMA_fwd(blk)
+            if (blk > 0) {
+                if (!tc::mbar_wait(&bar_a, phase_a)) tc_ok = false;
+                phase_a ^= 1u;
                 tc::fence_after_sync();
-#pragma unroll
-                for (int ks = 0; ks < C::KFWD / C::KSTEP; ++ks)
-                    tc::mma<FMT>(taddr, tc::make_smem_desc(sA_u32 + ks * 256, 128, SBO_F),
-                                 tc::make_smem_desc(sBf_u32 + ks * 256, 128, SBO_F), IDESC_F, ks > 0 ? 1u : 0u);
-                tc::mma_commit(&bar_f);
+                epi2(blk - 1);
+                tc::fence_before_sync();
+                __syncthreads();
+                if (tid < 128) emit(4 * (blk - 1) - 6 + (tid >> 5));
             }
+            // (b) epilogue 1 of this block: rho' -> R (hi | lo), energy terms
             if (!tc::mbar_wait(&bar_f, phase_f)) tc_ok = false;
             phase_f ^= 1u;
             tc::fence_after_sync();
-
-            // ---- epilogue 1: rho' -> R (hi | lo), energy terms ----------------
             {
-                const int row = 4 * blk + (warp & 3), col = lane;
-                const int y = y0 - 3 + row, x = x0 - 3 + col;
-                const bool inimg = y >= 0 && y < H && x >= 0 && x < W;
+                const int row = 4 * blk + lg, col = lane;
+                const bool inimg = all_in || ((unsigned)(y0 - 3 + row) < (unsigned)H && (unsigned)(x0 - 3 + col) < (unsigned)W);
                 const bool owned = row >= 3 + sy && row < 3 + sy + oh && col >= 3 + sx && col < 3 + sx + ow;
-                const int m = (warp & 3) * 32 + lane;
                 float z[24];
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
@@ -267,24 +355,33 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
                     for (int k = 0; k < 8; ++k) z[8 * j + k] = t8[k];
                 }
                 tc::tmem_ld_wait();
-                float rh[24], rl[24], psum = 0.f;
+                const float4 *th4 = reinterpret_cast<const float4 *>(sTh + 24 * wg);
+                const float4 *tw4 = reinterpret_cast<const float4 *>(sTh + NF + 24 * wg);
+                float r[24], psum = 0.f;
 #pragma unroll
-                for (int i = 0; i < 24; ++i) {
-                    const float th = __ldg(p.theta + 24 * wg + i);
-                    const float zz = z[i];
-                    const float q = fmaf(zz, zz, 1.0f);
-                    const float r = inimg ? __fdividef(2.0f * th * zz, q) : 0.0f;
-                    psum = fmaf(th, __log2f(q), psum);
-                    const float hi = rounded_value<FMT>(r);
-                    rh[i] = hi;
-                    rl[i] = r - hi;
+                for (int j = 0; j < 6; ++j) {
+                    const float4 t1 = th4[j], t2 = tw4[j];
+                    const float th[4] = {t1.x, t1.y, t1.z, t1.w}, tw[4] = {t2.x, t2.y, t2.z, t2.w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float zz = z[4 * j + k];
+                        const float q = fmaf(zz, zz, 1.0f);
+                        r[4 * j + k] = __fdividef(tw[k] * zz, q);
+                        psum = fmaf(th[k], __log2f(q), psum);
+                    }
+                }
+                if (!inimg) {
+#pragma unroll
+                    for (int i = 0; i < 24; ++i) r[i] = 0.0f;
                 }
                 if (owned) accF += (double)(psum * LN2);
-                unsigned char *rowp = sA + tc::kmajor_offset(m, 0, KADJ, C::EB);
+                unsigned char *rowp = sR + tc::kmajor_offset((lg << 5) + lane, 0, KADJ, C::EB);
 #pragma unroll
                 for (int j = 0; j < 24 / C::E; ++j) {
-                    *reinterpret_cast<uint4 *>(rowp + ((24 * wg) / C::E + j) * 128) = pack_chunk<FMT>(rh + j * C::E);
-                    *reinterpret_cast<uint4 *>(rowp + ((NF + 24 * wg) / C::E + j) * 128) = pack_chunk<FMT>(rl + j * C::E);
+                    uint4 hi, lo;
+                    hilo_chunk<FMT>(r + j * C::E, hi, lo);
+                    *reinterpret_cast<uint4 *>(rowp + ((24 * wg) / C::E + j) * 128) = hi;
+                    *reinterpret_cast<uint4 *>(rowp + ((NF + 24 * wg) / C::E + j) * 128) = lo;
                 }
             }
             tc::fence_before_sync();
@@ -294,60 +391,35 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
                 tc::fence_after_sync();
 #pragma unroll
                 for (int ks = 0; ks < KADJ / C::KSTEP; ++ks)
-                    tc::mma<FMT>(taddr + 64, tc::make_smem_desc(sA_u32 + ks * 256, 128, SBO_A),
+                    tc::mma<FMT>(taddr + 64, tc::make_smem_desc(sR_u32 + ks * 256, 128, SBO_A),
                                  tc::make_smem_desc(sBa_u32 + ks * 256, 128, SBO_A), IDESC_A, ks > 0 ? 1u : 0u);
                 tc::mma_commit(&bar_a);
             }
-            if (!tc::mbar_wait(&bar_a, phase_a)) tc_ok = false;
-            phase_a ^= 1u;
-            tc::fence_after_sync();
-
-            // ---- epilogue 2: horizontal col2im by warp shuffles ---------------
-            {
-                const int row = 4 * blk + (warp & 3);
-                const int a_lo = wg == 0 ? 0 : 4, a_hi = wg == 0 ? 4 : KS;
-                for (int aa = a_lo; aa < a_hi; ++aa) {
-                    float s8[8];
-                    tc::tmem_ld8(taddr + lane_base + (uint32_t)(64 + KS * aa), s8);
-                    tc::tmem_ld_wait();
-                    float h = 0.f;
+            // (c) im2col of the next block, overlapping MMA_adj(blk)
+            if (blk + 1 < NBLK) {
+                im2col<FMT>(sU, sAF, blk + 1, m, part);
+                tc::fence_proxy_async();
+                tc::fence_before_sync();
+                __syncthreads();
+                if (tid == 0) {
+                    tc::fence_after_sync();
 #pragma unroll
-                    for (int bb = 0; bb < KS; ++bb) {
-                        const int src = lane - 3 + bb;
-                        const float v = __shfl_sync(0xffffffffu, s8[bb], src & 31);
-                        h += (src >= 0 && src < 32) ? v : 0.0f;
-                    }
-                    sH[((row % HRING) * KS + aa) * 32 + lane] = h;
-                }
-            }
-            tc::fence_before_sync();
-            __syncthreads();
-            // ---- vertical col2im of the ext rows whose 7 source rows are done --
-            if (tid < 128) {
-                const int ty = 4 * blk - 6 + (tid >> 5);
-                if (ty >= -3) {
-                    float g = 0.f;
-#pragma unroll
-                    for (int aa = 0; aa < KS; ++aa) {
-                        const int srow = ty + aa;
-                        if (srow >= 0 && srow < R3Y) g += sH[((srow % HRING) * KS + aa) * 32 + lane];
-                    }
-                    sG[(ty + 3) * 32 + lane] = g;
+                    for (int ks = 0; ks < C::KFWD / C::KSTEP; ++ks)
+                        tc::mma<FMT>(taddr, tc::make_smem_desc(sAF_u32 + ks * 256, 128, SBO_F),
+                                     tc::make_smem_desc(sBf_u32 + ks * 256, 128, SBO_F), IDESC_F, ks > 0 ? 1u : 0u);
+                    tc::mma_commit(&bar_f);
                 }
             }
         }
+        // last block's col2im, then the ext rows whose missing sources lie off the tile
+        if (!tc::mbar_wait(&bar_a, phase_a)) tc_ok = false;
+        phase_a ^= 1u;
+        tc::fence_after_sync();
+        epi2(NBLK - 1);
+        tc::fence_before_sync();
         __syncthreads();
-        // ---- remaining ext rows (their missing source rows lie off the tile) --
-        if (tid < 96) {
-            const int ty = 4 * (NBLK - 1) - 2 + (tid >> 5);  // 58, 59, 60
-            float g = 0.f;
-#pragma unroll
-            for (int aa = 0; aa < KS; ++aa) {
-                const int srow = ty + aa;
-                if (srow >= 0 && srow < R3Y) g += sH[((srow % HRING) * KS + aa) * 32 + lane];
-            }
-            sG[(ty + 3) * 32 + lane] = g;
-        }
+        if (tid < 128) emit(4 * (NBLK - 1) - 6 + (tid >> 5));
+        if (tid >= 128 && tid < 224) emit(4 * (NBLK - 1) - 2 + ((tid - 128) >> 5));  // 58, 59, 60
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
