@@ -24,7 +24,11 @@
  *       F(u^{n+1}) <= F(u^n) + <grad F(u^n), u^{n+1} - u^n> + L_n/2 |u^{n+1} - u^n|^2
  *     else L_n <- eta L_n and the trial is redone (at most max_backtrack
  *     times per iteration).  L is never decreased.  u^{-1} = u^0.
- *   - Convergence: |H^{n+1} - H^n| / |H^{n+1}| < tol.
+ *   - Convergence: |H^{n+1} - H^n| / |H^{n+1} - G(f)| < tol, i.e. the relative
+ *     change of the energy measured above the floor of the data term,
+ *     G(f) = min_u G(u) = (lambda/2) sum_p f_p^2 (1 - log f_p^2).  (With
+ *     intensities of order 100 the constant G(f) dominates |H|, and a test on
+ *     |H| alone would stop after the first step.)
  *
  * Data layout: every image is a dense row-major float32 array, pitch = W.
  * Pointers named "any" may be host (pageable or pinned) or device pointers of
@@ -99,12 +103,13 @@ typedef struct {
     double alpha;           /* alpha_n for the current L_n */
     double F, G, H;         /* energies at u^n */
     double H_prev;          /* H at u^{n-1} */
-    double rel_change;      /* |H^n - H^{n-1}| / |H^n| of the last accepted step */
+    double rel_change;      /* |H^n - H^{n-1}| / |H^n - G(f)| of the last accepted step */
     double last_gd;         /* <grad F(u^{n-1}), u^n - u^{n-1}> of the last accepted step */
     double last_dd;         /* |u^n - u^{n-1}|^2 */
     double last_dp;         /* <u^n - u^{n-1}, u^{n-1} - u^{n-2}> */
     int status;             /* fe_status of this image */
     int converged;          /* 1 once the tolerance of the last fe_solve was met */
+    double G_floor;         /* G(f), the floor of the data term (read-only) */
 } fe_info;
 
 typedef struct fe_ctx fe_ctx;
@@ -140,7 +145,7 @@ FE_API void fe_destroy(fe_ctx *ctx);
  * synchronises and stores the first non-OK per-image status (or FE_OK). */
 FE_API fe_status fe_step(fe_ctx *ctx, int n, fe_status *worst);
 
-/* Iterate until |H^{n+1}-H^n|/|H^{n+1}| < rel_tol or max_iter accepted
+/* Iterate until |H^{n+1}-H^n|/|H^{n+1}-G(f)| < rel_tol or max_iter accepted
  * iterations (counted from this call) on every image.  Synchronises.
  * Returns FE_OK if all images converged, FE_ENOTCONVERGED if some hit
  * max_iter, else the first error status. */
@@ -211,6 +216,39 @@ FE_API fe_status fe_set_loop_mode(fe_ctx *ctx, int mode);
 FE_API fe_status fe_gradient_noalloc(const float *u, float *g, double *F, int H, int W,
                                      const float *filters, const float *theta, int nf,
                                      void *stream);
+
+/* ---- Learned warm start ---------------------------------------------------
+ * A small CNN predicts the starting point u^0 of iPiano from f.  The paper
+ * has no counterpart (it starts from the observation); this is the warm-start
+ * form of the solver, trained on (f, u*) pairs produced by the solver itself.
+ *
+ * Network: five 3x3 convolutions with zero padding, 1 -> 32 -> 32 -> 32 -> 32
+ * -> 1 channels, bias, ReLU after the first four.  Input log f - 4.5, output
+ * d, prediction u^0 = f exp(d) (positive by construction).  Loss
+ * mean_p (d_p - (log u*_p - log f_p))^2.  Weights are stored in FP32 and used
+ * in BF16 (round-to-nearest-even) by every convolution; activations and
+ * accumulation are FP32; training uses Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * Parameter vector: for each layer, W[cout][cin][3][3] then b[cout].
+ * Batches are B images of H x W, row-major, consecutive ("any" pointers).
+ * All calls synchronise the stream given at creation. */
+typedef struct fe_cnn fe_cnn;
+
+/* Create with seeded He-normal weights (last layer scaled by 0.1). */
+FE_API fe_status fe_cnn_create(fe_cnn **out, unsigned long long seed, void *stream);
+FE_API void fe_cnn_destroy(fe_cnn *net);
+FE_API int fe_cnn_num_params(const fe_cnn *net);
+FE_API const char *fe_cnn_last_error(const fe_cnn *net);
+/* Copy the FP32 parameters in/out (any pointer, fe_cnn_num_params floats). */
+FE_API fe_status fe_cnn_set_params(fe_cnn *net, const float *params);
+FE_API fe_status fe_cnn_get_params(fe_cnn *net, float *params);
+/* Inference: u0 = f exp(d) and/or d (any pointers, may be NULL). */
+FE_API fe_status fe_cnn_forward(fe_cnn *net, const float *f, int B, int H, int W, float *u0, float *d);
+/* Loss and its gradient with respect to every parameter (grad may be NULL). */
+FE_API fe_status fe_cnn_loss_grad(fe_cnn *net, const float *f, const float *u_target, int B, int H, int W,
+                                  double *loss, float *grad);
+/* One Adam step with learning rate lr; *loss = the loss before the step. */
+FE_API fe_status fe_cnn_train_step(fe_cnn *net, const float *f, const float *u_target, int B, int H, int W,
+                                   float lr, double *loss);
 
 /* Diagnostic of the tensor-core building block used by the FE_TF32 / FE_BF16
  * forms: D = A * B^T with A 128 x K, B N x K (row-major float, any pointers)

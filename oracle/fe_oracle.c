@@ -32,7 +32,9 @@
  *     otherwise L_n <- eta L_n and the trial is recomputed.  L is never
  *     decreased; u^{-1} = u^0.
  *   - Stopping: a fixed number of accepted iterations, or
- *     |H^{n+1} - H^n| / |H^{n+1}| < tol.
+ *     |H^{n+1} - H^n| / |H^{n+1} - G(f)| < tol: the relative change of the
+ *     energy above the floor of the data term, G(f) = min_u G(u) (a constant
+ *     of the problem; with intensities of order 100 it dominates |H|).
  *
  * Parallelism: OpenMP over image rows inside each operator (each row is an
  * independent plain loop; sums over rows are combined serially in row order
@@ -414,6 +416,7 @@ ORC_API int orc_ipiano(const double *f, int H, int W, const double *bank,
     double L = (L_io && *L_io > 0.0) ? *L_io : p->L0;
     double F = orc_gradF(u, H, W, bank, theta, nf, ks, g);
     double G = orc_G(u, f, N, p->lambda);
+    const double Gfloor = orc_G(f, f, N, p->lambda); /* G is minimal at u = f */
     if (h0) {
         h0[0] = F;
         h0[1] = G;
@@ -433,7 +436,7 @@ ORC_API int orc_ipiano(const double *f, int H, int W, const double *bank,
         F = F1;
         G = G1;
         ++n;
-        if (p->tol > 0.0 && fabs(H1 - Hn) / fabs(H1) < p->tol) {
+        if (p->tol > 0.0 && fabs(H1 - Hn) / fabs(H1 - Gfloor) < p->tol) {
             if (converged) *converged = 1;
             break;
         }

@@ -43,6 +43,7 @@ struct fe_ctx {
     double *d_res = nullptr;
     int *d_flag = nullptr;
     int *d_tc_error = nullptr;
+    double *d_gpart = nullptr;  // partial sums of the data-term floor G(f)
     unsigned char *d_tcw_fwd = nullptr, *d_tcw_adj = nullptr;
     float *d_scratch = nullptr;  // 2 planes of the largest image (host-pointer staging)
     size_t max_plane = 0;
@@ -93,6 +94,26 @@ __global__ void prep_kernel(const float *f, const float *u0, float *f2, float *u
         ub[i] = uv;
         if (!ok) atomicOr(bad, 1);
     }
+}
+
+// Per-block partial sums of f^2 (1 - log f^2) (the floor G(f) of the data
+// term, up to lambda/2), GF_BLOCKS partials per image, summed on the host in
+// block order.
+constexpr int GF_BLOCKS = 64;
+__global__ void gfloor_kernel(const float *f2, size_t N, double *part) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+        const double v = (double)f2[i];
+        s += v * (1.0 - log(v));
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
 __global__ void begin_kernel(ImgState *st, int nimg, long long n, double tol, LoopCtl *lc,
@@ -191,13 +212,27 @@ fe_status load_inputs(fe_ctx *c, const float *const *f, const float *const *u0) 
     FE_CUDA(c, cudaMemcpyAsync(&bad, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->s));
     FE_CUDA(c, cudaStreamSynchronize(c->s));
     if (bad) return set_err(c, FE_EINVAL, "f and u0 must be finite and > 0 (f^2 must not underflow)");
+    // floor of the data term, G(f), for the convergence test
+    for (int j = 0; j < c->nimg; ++j) {
+        gfloor_kernel<<<GF_BLOCKS, 256, 0, c->s>>>(c->himg[j].f2, (size_t)c->H[j] * c->W[j],
+                                                   c->d_gpart + (size_t)j * GF_BLOCKS);
+        FE_CUDA(c, cudaGetLastError());
+        ++c->host_launches;
+    }
+    std::vector<double> gp((size_t)c->nimg * GF_BLOCKS);
+    FE_CUDA(c, cudaMemcpyAsync(gp.data(), c->d_gpart, sizeof(double) * gp.size(), cudaMemcpyDeviceToHost, c->s));
+    FE_CUDA(c, cudaStreamSynchronize(c->s));
     // fresh state, then grad F(u^0), F(u^0), G(u^0) on the device
     std::vector<ImgState> hs(c->nimg);
-    for (auto &s : hs) {
+    for (int j = 0; j < c->nimg; ++j) {
+        ImgState &s = hs[j];
         std::memset(&s, 0, sizeof s);
         s.L = c->prm.L0;
         s.alpha = 2.0 * (1.0 - c->prm.beta) / (c->prm.L0 + 2.0 * c->prm.c2);
         s.status = FE_OK;
+        double g = 0.0;
+        for (int k = 0; k < GF_BLOCKS; ++k) g += gp[(size_t)j * GF_BLOCKS + k];
+        s.Gf = 0.5 * c->prm.lambda * g;
     }
     FE_CUDA(c, cudaMemcpyAsync(c->d_st, hs.data(), sizeof(ImgState) * hs.size(), cudaMemcpyHostToDevice, c->s));
     FE_CUDA(c, cudaMemsetAsync(c->d_arr, 0, sizeof(unsigned) * c->nimg, c->s));
@@ -470,6 +505,7 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
     if ((st = dalloc(c, &c->d_res, 2 * (size_t)nimg)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_flag, 4)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_tc_error, 1)) != FE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_gpart, (size_t)nimg * GF_BLOCKS)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_scratch, 2 * c->max_plane)) != FE_OK) return bail(st);
     if (tc) {
         std::vector<unsigned char> bf, ba;
@@ -613,6 +649,7 @@ fe_status fe_get_info(fe_ctx *c, int img, fe_info *out) {
     out->last_dp = s.last_dp;
     out->status = s.status;
     out->converged = s.converged;
+    out->G_floor = s.Gf;
     return FE_OK;
 }
 

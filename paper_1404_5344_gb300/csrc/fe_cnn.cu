@@ -1,0 +1,525 @@
+// Learned warm start: a small CNN that predicts u^0 from the observation f,
+// with hand-written inference and training kernels.
+//
+// Network (depth D = 5, width C = 32): 3x3 convolutions with zero padding,
+// 1 -> C -> C -> C -> C -> 1 channels, bias, ReLU after every layer but the
+// last.  Input x = log f - M0; output d; the prediction is
+//   u^0 = f exp(d)        (positive by construction),
+// trained with the loss mean_p (d_p - t_p)^2, t = log u* - log f, where u* is
+// the output of the iPiano solver run on f.  Weights are kept in FP32 (Adam
+// state) and used in BF16 (rounded to nearest even) by every convolution;
+// activations and accumulation are FP32.
+//
+// Kernels: conv3x3 forward (bias + ReLU fused; with an optional ReLU mask on
+// the input it also serves as the data gradient, given transposed and
+// flipped weights), weight/bias gradient with per-block partial sums and a
+// fixed-order reduction (deterministic), loss + output gradient, Adam.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "fe_internal.cuh"
+
+namespace fe {
+namespace {
+
+constexpr int CW = 32;       // width
+constexpr int DEPTH = 5;     // layers
+constexpr float M0 = 4.5f;   // input offset of log f
+constexpr int TS = 16;       // output tile side of the conv kernels
+constexpr int NT = TS * TS;  // 256 threads
+
+__host__ __device__ constexpr int cin_of(int l) { return l == 0 ? 1 : CW; }
+__host__ __device__ constexpr int cout_of(int l) { return l == DEPTH - 1 ? 1 : CW; }
+
+// y[b][o][p] = act(bias[o] + sum_c sum_tap w[c][tap][o] * x'[b][c][p + off(tap)])
+// x' = x, or x * (mask > 0) when mask != nullptr.  w is [CIN][9][COUT]
+// (FP32 values of the BF16 weights).  Zero padding.
+template <int CIN, int COUT, bool RELU>
+__global__ void __launch_bounds__(NT) conv3x3_kernel(const float *__restrict__ x, const float *__restrict__ mask,
+                                                     const float *__restrict__ w, const float *__restrict__ bias,
+                                                     float *__restrict__ y, int H, int W) {
+    extern __shared__ __align__(16) float csm[];
+    float *sw = csm;                                                     // [CIN * 9 * COUT]
+    float(*sx)[TS + 2][TS + 2] = reinterpret_cast<float(*)[TS + 2][TS + 2]>(csm + CIN * 9 * COUT);
+    const int b = blockIdx.z, tx0 = blockIdx.x * TS, ty0 = blockIdx.y * TS;
+    const int tid = threadIdx.x, ly = tid / TS, lx = tid % TS;
+    const size_t plane = (size_t)H * W;
+    for (int j = tid; j < CIN * 9 * COUT; j += NT) sw[j] = w[j];
+    for (int j = tid; j < CIN * (TS + 2) * (TS + 2); j += NT) {
+        const int c = j / ((TS + 2) * (TS + 2)), r = j % ((TS + 2) * (TS + 2));
+        const int yy = ty0 - 1 + r / (TS + 2), xx = tx0 - 1 + r % (TS + 2);
+        float v = 0.f;
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+            const size_t o = ((size_t)b * CIN + c) * plane + (size_t)yy * W + xx;
+            v = x[o];
+            if (mask && !(mask[o] > 0.f)) v = 0.f;
+        }
+        sx[c][r / (TS + 2)][r % (TS + 2)] = v;
+    }
+    __syncthreads();
+    float acc[COUT];
+#pragma unroll
+    for (int o = 0; o < COUT; ++o) acc[o] = bias ? bias[o] : 0.f;
+    for (int c = 0; c < CIN; ++c) {
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const float v = sx[c][ly + t / 3][lx + t % 3];
+            const float *wp = sw + (c * 9 + t) * COUT;
+#pragma unroll
+            for (int o = 0; o < COUT; ++o) acc[o] = fmaf(wp[o], v, acc[o]);
+        }
+    }
+    const int yy = ty0 + ly, xx = tx0 + lx;
+    if (yy < H && xx < W) {
+#pragma unroll
+        for (int o = 0; o < COUT; ++o)
+            y[((size_t)b * COUT + o) * plane + (size_t)yy * W + xx] = RELU ? fmaxf(acc[o], 0.f) : acc[o];
+    }
+}
+
+// Per-block partial sums of the weight and bias gradients of one layer:
+//   dW[o][c][tap] += sum_p g[b][o][p] x[b][c][p + off(tap)],  dB[o] += sum_p g[b][o][p]
+// with g = dY * (Y > 0) for a ReLU layer (Y = the layer's output) or dY.
+// part[block][COUT*CIN*9 + COUT].
+template <int CIN, int COUT, bool RELU>
+__global__ void __launch_bounds__(NT) wgrad_kernel(const float *__restrict__ x, const float *__restrict__ dy,
+                                                   const float *__restrict__ yout, float *__restrict__ part, int H,
+                                                   int W) {
+    extern __shared__ __align__(16) float wsm[];
+    float(*sg)[TS * TS] = reinterpret_cast<float(*)[TS * TS]>(wsm);  // [COUT][TS*TS]
+    float(*sx)[TS + 2][TS + 2] = reinterpret_cast<float(*)[TS + 2][TS + 2]>(wsm + COUT * TS * TS);
+    const int b = blockIdx.z, tx0 = blockIdx.x * TS, ty0 = blockIdx.y * TS;
+    const int tid = threadIdx.x;
+    const size_t plane = (size_t)H * W;
+    for (int j = tid; j < CIN * (TS + 2) * (TS + 2); j += NT) {
+        const int c = j / ((TS + 2) * (TS + 2)), r = j % ((TS + 2) * (TS + 2));
+        const int yy = ty0 - 1 + r / (TS + 2), xx = tx0 - 1 + r % (TS + 2);
+        sx[c][r / (TS + 2)][r % (TS + 2)] =
+            (yy >= 0 && yy < H && xx >= 0 && xx < W) ? x[((size_t)b * CIN + c) * plane + (size_t)yy * W + xx] : 0.f;
+    }
+    for (int j = tid; j < COUT * TS * TS; j += NT) {
+        const int o = j / (TS * TS), r = j % (TS * TS);
+        const int yy = ty0 + r / TS, xx = tx0 + r % TS;
+        float g = 0.f;
+        if (yy < H && xx < W) {
+            const size_t idx = ((size_t)b * COUT + o) * plane + (size_t)yy * W + xx;
+            g = dy[idx];
+            if (RELU && !(yout[idx] > 0.f)) g = 0.f;
+        }
+        sg[o][r] = g;
+    }
+    __syncthreads();
+    const size_t nw = (size_t)COUT * CIN * 9;
+    float *out = part + (size_t)((blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (nw + COUT);
+    for (size_t e = tid; e < nw + COUT; e += NT) {
+        float s = 0.f;
+        if (e < nw) {
+            const int o = (int)(e / (CIN * 9)), c = (int)((e / 9) % CIN), t = (int)(e % 9);
+            for (int r = 0; r < TS * TS; ++r) s = fmaf(sg[o][r], sx[c][r / TS + t / 3][r % TS + t % 3], s);
+        } else {
+            const int o = (int)(e - nw);
+            for (int r = 0; r < TS * TS; ++r) s += sg[o][r];
+        }
+        out[e] = s;
+    }
+}
+
+// Fixed-order reduction of per-block partials: out[e] = sum_k part[k][e].
+__global__ void reduce_parts_kernel(const float *__restrict__ part, int nblocks, int n, float *__restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double s = 0.0;
+    for (int k = 0; k < nblocks; ++k) s += part[(size_t)k * n + e];
+    out[e] = (float)s;
+}
+
+__global__ void prep_input_kernel(const float *__restrict__ f, float *__restrict__ x, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        x[i] = logf(f[i]) - M0;
+}
+
+// u0 = f exp(d)
+__global__ void output_kernel(const float *__restrict__ f, const float *__restrict__ d, float *__restrict__ u0, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        u0[i] = f[i] * expf(d[i]);
+}
+
+// loss = sum_p (d - t)^2 (per-block partials in FP64), dd = 2 (d - t) / n,
+// t = log u* - log f
+__global__ void loss_kernel(const float *__restrict__ d, const float *__restrict__ f, const float *__restrict__ ut,
+                            float *__restrict__ dd, double *__restrict__ part, size_t n) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float e = d[i] - (logf(ut[i]) - logf(f[i]));
+        s += (double)e * (double)e;
+        dd[i] = 2.0f * e / (float)n;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// Adam on the FP32 master parameters; refreshes the BF16-valued copy used by
+// the convolutions (weights only: biases stay FP32).
+__global__ void adam_kernel(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
+                            const float *__restrict__ g, const unsigned char *__restrict__ is_w,
+                            float *__restrict__ pq, int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pi;
+    pq[i] = is_w[i] ? __bfloat162float(__float2bfloat16_rn(pi)) : pi;
+}
+
+}  // namespace
+}  // namespace fe
+
+using namespace fe;
+
+struct fe_cnn {
+    cudaStream_t s = nullptr;
+    int np = 0;
+    std::vector<int> woff, boff;  // per layer: offset of W ([COUT][CIN][9]) and b in the parameter vector
+    float *p = nullptr, *pq = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
+    unsigned char *is_w = nullptr;
+    float *wl[DEPTH] = {}, *wt[DEPTH] = {};  // conv layouts [CIN][9][COUT] and transposed-flipped [COUT][9][CIN]
+    float *act = nullptr, *dact = nullptr, *part = nullptr, *tmp = nullptr;
+    double *lpart = nullptr;
+    size_t cap_pix = 0, cap_part = 0;
+    long long step = 0;
+    std::string err;
+};
+
+namespace fe {
+namespace {
+
+fe_status cnn_err(fe_cnn *n, fe_status s, const std::string &msg) {
+    if (n) n->err = msg;
+    return s;
+}
+
+#define CNN_CUDA(n, call)                                                                  \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) return cnn_err((n), FE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// conv layouts from the (BF16-valued) parameters: forward [CIN][9][COUT],
+// data-gradient [COUT][9][CIN] with the taps flipped
+__global__ void layout_kernel(const float *__restrict__ pq, int woff, int cin, int cout, float *__restrict__ wl,
+                              float *__restrict__ wt) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= cin * cout * 9) return;
+    const int o = e / (cin * 9), c = (e / 9) % cin, t = e % 9;
+    const float w = pq[woff + e];
+    wl[(c * 9 + t) * cout + o] = w;
+    wt[(o * 9 + (8 - t)) * cin + c] = w;
+}
+
+fe_status refresh_layouts(fe_cnn *n) {
+    for (int l = 0; l < DEPTH; ++l) {
+        const int ne = cin_of(l) * cout_of(l) * 9;
+        layout_kernel<<<(ne + 255) / 256, 256, 0, n->s>>>(n->pq, n->woff[l], cin_of(l), cout_of(l), n->wl[l], n->wt[l]);
+        CNN_CUDA(n, cudaGetLastError());
+    }
+    return FE_OK;
+}
+
+fe_status ensure_capacity(fe_cnn *n, size_t pix, size_t parts) {
+    if (pix > n->cap_pix) {
+        cudaFree(n->act);
+        cudaFree(n->dact);
+        cudaFree(n->tmp);
+        // activations of all layers + input: (1 + 4 C + 1) planes; two work planes of C channels
+        CNN_CUDA(n, cudaMalloc(&n->act, sizeof(float) * pix * (2 + (DEPTH - 1) * CW)));
+        CNN_CUDA(n, cudaMalloc(&n->dact, sizeof(float) * pix * 2 * CW));
+        CNN_CUDA(n, cudaMalloc(&n->tmp, sizeof(float) * pix * 4));
+        n->cap_pix = pix;
+    }
+    if (parts > n->cap_part) {
+        cudaFree(n->part);
+        CNN_CUDA(n, cudaMalloc(&n->part, sizeof(float) * parts));
+        n->cap_part = parts;
+    }
+    return FE_OK;
+}
+
+template <int CIN, int COUT>
+constexpr size_t conv_smem() { return sizeof(float) * ((size_t)CIN * 9 * COUT + (size_t)CIN * (TS + 2) * (TS + 2)); }
+template <int CIN, int COUT>
+constexpr size_t wgrad_smem() { return sizeof(float) * ((size_t)COUT * TS * TS + (size_t)CIN * (TS + 2) * (TS + 2)); }
+
+template <int CIN, int COUT, bool RELU>
+void conv(const fe_cnn *n, const float *x, const float *mask, const float *w, const float *bias, float *y, int B, int H,
+          int W) {
+    const dim3 grid((W + TS - 1) / TS, (H + TS - 1) / TS, B);
+    conv3x3_kernel<CIN, COUT, RELU><<<grid, NT, conv_smem<CIN, COUT>(), n->s>>>(x, mask, w, bias, y, H, W);
+}
+
+cudaError_t cnn_prepare() {
+    cudaError_t e = cudaSuccess;
+#define FE_SMEM(k, b) \
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(b))) != cudaSuccess) return e
+    FE_SMEM((conv3x3_kernel<1, CW, true>), (conv_smem<1, CW>()));
+    FE_SMEM((conv3x3_kernel<CW, CW, true>), (conv_smem<CW, CW>()));
+    FE_SMEM((conv3x3_kernel<CW, 1, false>), (conv_smem<CW, 1>()));
+    FE_SMEM((conv3x3_kernel<1, CW, false>), (conv_smem<1, CW>()));
+    FE_SMEM((conv3x3_kernel<CW, CW, false>), (conv_smem<CW, CW>()));
+    FE_SMEM((wgrad_kernel<CW, 1, false>), (wgrad_smem<CW, 1>()));
+    FE_SMEM((wgrad_kernel<CW, CW, true>), (wgrad_smem<CW, CW>()));
+    FE_SMEM((wgrad_kernel<1, CW, true>), (wgrad_smem<1, CW>()));
+#undef FE_SMEM
+    return e;
+}
+
+// pointer to the activation of layer l (l = -1: the input x)
+float *act_ptr(fe_cnn *n, int l, size_t pix) {
+    if (l < 0) return n->act;
+    return n->act + pix * (1 + (size_t)l * CW);
+}
+
+fe_status forward(fe_cnn *n, const float *f_dev, int B, int H, int W) {
+    const size_t pix = (size_t)B * H * W;
+    prep_input_kernel<<<(unsigned)std::min<size_t>((pix + 255) / 256, 4096), 256, 0, n->s>>>(f_dev, act_ptr(n, -1, pix), pix);
+    conv<1, CW, true>(n, act_ptr(n, -1, pix), nullptr, n->wl[0], n->pq + n->boff[0], act_ptr(n, 0, pix), B, H, W);
+    conv<CW, CW, true>(n, act_ptr(n, 0, pix), nullptr, n->wl[1], n->pq + n->boff[1], act_ptr(n, 1, pix), B, H, W);
+    conv<CW, CW, true>(n, act_ptr(n, 1, pix), nullptr, n->wl[2], n->pq + n->boff[2], act_ptr(n, 2, pix), B, H, W);
+    conv<CW, CW, true>(n, act_ptr(n, 2, pix), nullptr, n->wl[3], n->pq + n->boff[3], act_ptr(n, 3, pix), B, H, W);
+    conv<CW, 1, false>(n, act_ptr(n, 3, pix), nullptr, n->wl[4], n->pq + n->boff[4], act_ptr(n, 4, pix), B, H, W);
+    CNN_CUDA(n, cudaGetLastError());
+    return FE_OK;
+}
+
+template <int CIN, int COUT, bool RELU>
+fe_status wgrad(fe_cnn *n, const float *x, const float *dy, const float *y, int B, int H, int W, int layer) {
+    const dim3 grid((W + TS - 1) / TS, (H + TS - 1) / TS, B);
+    const int nb = grid.x * grid.y * grid.z, ne = COUT * CIN * 9 + COUT;
+    wgrad_kernel<CIN, COUT, RELU><<<grid, NT, wgrad_smem<CIN, COUT>(), n->s>>>(x, dy, y, n->part, H, W);
+    // weights then bias of this layer are contiguous in the parameter vector
+    reduce_parts_kernel<<<(ne + 255) / 256, 256, 0, n->s>>>(n->part, nb, ne, n->g + n->woff[layer]);
+    CNN_CUDA(n, cudaGetLastError());
+    return FE_OK;
+}
+
+// loss and gradients of all parameters into n->g (device); *loss host
+fe_status loss_grad(fe_cnn *n, const float *f_dev, const float *ut_dev, int B, int H, int W, double *loss) {
+    const size_t pix = (size_t)B * H * W;
+    const int nb = (W + TS - 1) / TS * ((H + TS - 1) / TS) * B;
+    fe_status st = ensure_capacity(n, pix, (size_t)nb * (CW * CW * 9 + CW));
+    if (st != FE_OK) return st;
+    if ((st = forward(n, f_dev, B, H, W)) != FE_OK) return st;
+    const int lb = 256;
+    if (!n->lpart) CNN_CUDA(n, cudaMalloc(&n->lpart, sizeof(double) * lb));
+    float *dd = n->dact;  // d loss / d output, 1 channel
+    loss_kernel<<<lb, 256, 0, n->s>>>(act_ptr(n, 4, pix), f_dev, ut_dev, dd, n->lpart, pix);
+    CNN_CUDA(n, cudaGetLastError());
+    // backward: layer 4 (no ReLU), then 3..0 (ReLU on their outputs)
+    float *g_in = dd, *g_out = n->dact + pix * CW;  // ping-pong C-channel gradient planes
+    if ((st = wgrad<CW, 1, false>(n, act_ptr(n, 3, pix), g_in, nullptr, B, H, W, 4)) != FE_OK) return st;
+    conv<1, CW, false>(n, g_in, nullptr, n->wt[4], nullptr, g_out, B, H, W);
+    std::swap(g_in, g_out);
+    // g_in = d loss / d act3 (post-ReLU)
+    if ((st = wgrad<CW, CW, true>(n, act_ptr(n, 2, pix), g_in, act_ptr(n, 3, pix), B, H, W, 3)) != FE_OK) return st;
+    conv<CW, CW, false>(n, g_in, act_ptr(n, 3, pix), n->wt[3], nullptr, g_out, B, H, W);
+    std::swap(g_in, g_out);
+    if ((st = wgrad<CW, CW, true>(n, act_ptr(n, 1, pix), g_in, act_ptr(n, 2, pix), B, H, W, 2)) != FE_OK) return st;
+    conv<CW, CW, false>(n, g_in, act_ptr(n, 2, pix), n->wt[2], nullptr, g_out, B, H, W);
+    std::swap(g_in, g_out);
+    if ((st = wgrad<CW, CW, true>(n, act_ptr(n, 0, pix), g_in, act_ptr(n, 1, pix), B, H, W, 1)) != FE_OK) return st;
+    conv<CW, CW, false>(n, g_in, act_ptr(n, 1, pix), n->wt[1], nullptr, g_out, B, H, W);
+    std::swap(g_in, g_out);
+    if ((st = wgrad<1, CW, true>(n, act_ptr(n, -1, pix), g_in, act_ptr(n, 0, pix), B, H, W, 0)) != FE_OK) return st;
+    CNN_CUDA(n, cudaGetLastError());
+    std::vector<double> lp(lb);
+    CNN_CUDA(n, cudaMemcpyAsync(lp.data(), n->lpart, sizeof(double) * lb, cudaMemcpyDeviceToHost, n->s));
+    CNN_CUDA(n, cudaStreamSynchronize(n->s));
+    double s = 0.0;
+    for (double v : lp) s += v;
+    if (loss) *loss = s / (double)pix;
+    return FE_OK;
+}
+
+const float *stage(fe_cnn *n, const float *src, size_t count, int slot, fe_status *st) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, src) == cudaSuccess && (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged))
+        return src;
+    cudaGetLastError();
+    float *dst = n->tmp + (size_t)slot * (n->cap_pix);
+    if (cudaMemcpyAsync(dst, src, sizeof(float) * count, cudaMemcpyDefault, n->s) != cudaSuccess) {
+        *st = cnn_err(n, FE_ECUDA, "staging copy failed");
+        return nullptr;
+    }
+    return dst;
+}
+
+}  // namespace
+}  // namespace fe
+
+extern "C" {
+
+fe_status fe_cnn_create(fe_cnn **out, unsigned long long seed, void *stream) {
+    if (!out) return FE_EINVAL;
+    *out = nullptr;
+    if (cnn_prepare() != cudaSuccess) return FE_ECUDA;
+    fe_cnn *n = new fe_cnn();
+    n->s = static_cast<cudaStream_t>(stream);
+    int off = 0;
+    for (int l = 0; l < DEPTH; ++l) {
+        n->woff.push_back(off);
+        off += cin_of(l) * cout_of(l) * 9;
+        n->boff.push_back(off);
+        off += cout_of(l);
+    }
+    n->np = off;
+    // He-style initialisation scaled down for the last layer (start near d = 0)
+    std::vector<float> p(off, 0.f);
+    std::vector<unsigned char> isw(off, 0);
+    std::mt19937_64 rng(seed);
+    std::normal_distribution<float> nd(0.f, 1.f);
+    for (int l = 0; l < DEPTH; ++l) {
+        const float sd = std::sqrt(2.0f / (9.0f * cin_of(l))) * (l == DEPTH - 1 ? 0.1f : 1.0f);
+        for (int e = 0; e < cin_of(l) * cout_of(l) * 9; ++e) {
+            p[n->woff[l] + e] = sd * nd(rng);
+            isw[n->woff[l] + e] = 1;
+        }
+    }
+    auto fail = [&](fe_status s) {
+        fe_cnn_destroy(n);
+        return s;
+    };
+    if (cudaMalloc(&n->p, sizeof(float) * off) || cudaMalloc(&n->pq, sizeof(float) * off) ||
+        cudaMalloc(&n->m, sizeof(float) * off) || cudaMalloc(&n->v, sizeof(float) * off) ||
+        cudaMalloc(&n->g, sizeof(float) * off) || cudaMalloc(&n->is_w, off))
+        return fail(FE_ENOMEM);
+    for (int l = 0; l < DEPTH; ++l) {
+        const size_t ne = (size_t)cin_of(l) * cout_of(l) * 9;
+        if (cudaMalloc(&n->wl[l], sizeof(float) * ne) || cudaMalloc(&n->wt[l], sizeof(float) * ne)) return fail(FE_ENOMEM);
+    }
+    if (cudaMemcpy(n->is_w, isw.data(), off, cudaMemcpyHostToDevice) || cudaMemset(n->m, 0, sizeof(float) * off) ||
+        cudaMemset(n->v, 0, sizeof(float) * off) || cudaMemset(n->g, 0, sizeof(float) * off))
+        return fail(FE_ECUDA);
+    *out = n;
+    fe_status st = fe_cnn_set_params(n, p.data());
+    if (st != FE_OK) {
+        *out = nullptr;
+        return fail(st);
+    }
+    return FE_OK;
+}
+
+void fe_cnn_destroy(fe_cnn *n) {
+    if (!n) return;
+    if (n->s) cudaStreamSynchronize(n->s);
+    cudaFree(n->p);
+    cudaFree(n->pq);
+    cudaFree(n->m);
+    cudaFree(n->v);
+    cudaFree(n->g);
+    cudaFree(n->is_w);
+    for (int l = 0; l < DEPTH; ++l) {
+        cudaFree(n->wl[l]);
+        cudaFree(n->wt[l]);
+    }
+    cudaFree(n->act);
+    cudaFree(n->dact);
+    cudaFree(n->part);
+    cudaFree(n->tmp);
+    cudaFree(n->lpart);
+    delete n;
+}
+
+int fe_cnn_num_params(const fe_cnn *n) { return n ? n->np : 0; }
+
+const char *fe_cnn_last_error(const fe_cnn *n) { return n ? n->err.c_str() : ""; }
+
+fe_status fe_cnn_set_params(fe_cnn *n, const float *params) {
+    if (!n || !params) return FE_EINVAL;
+    std::vector<float> p(n->np), pq(n->np);
+    CNN_CUDA(n, cudaMemcpy(p.data(), params, sizeof(float) * n->np, cudaMemcpyDefault));
+    for (int l = 0; l < DEPTH; ++l)
+        for (int i = n->woff[l]; i < n->boff[l] + cout_of(l); ++i)
+            pq[i] = i < n->boff[l] ? tc_round(1, p[i]) : p[i];
+    CNN_CUDA(n, cudaMemcpy(n->p, p.data(), sizeof(float) * n->np, cudaMemcpyHostToDevice));
+    CNN_CUDA(n, cudaMemcpy(n->pq, pq.data(), sizeof(float) * n->np, cudaMemcpyHostToDevice));
+    return refresh_layouts(n);
+}
+
+fe_status fe_cnn_get_params(fe_cnn *n, float *params) {
+    if (!n || !params) return FE_EINVAL;
+    CNN_CUDA(n, cudaMemcpyAsync(params, n->p, sizeof(float) * n->np, cudaMemcpyDefault, n->s));
+    CNN_CUDA(n, cudaStreamSynchronize(n->s));
+    return FE_OK;
+}
+
+fe_status fe_cnn_forward(fe_cnn *n, const float *f, int B, int H, int W, float *u0, float *d) {
+    if (!n || !f || B < 1 || H < 1 || W < 1) return FE_EINVAL;
+    const size_t pix = (size_t)B * H * W;
+    fe_status st = ensure_capacity(n, pix, 1);
+    if (st != FE_OK) return st;
+    const float *fd = stage(n, f, pix, 0, &st);
+    if (!fd) return st;
+    if ((st = forward(n, fd, B, H, W)) != FE_OK) return st;
+    float *dout = act_ptr(n, 4, pix);
+    if (u0) {
+        cudaPointerAttributes a;
+        const bool dev = cudaPointerGetAttributes(&a, u0) == cudaSuccess && a.type == cudaMemoryTypeDevice;
+        cudaGetLastError();
+        float *dst = dev ? u0 : n->tmp + n->cap_pix;
+        output_kernel<<<(unsigned)std::min<size_t>((pix + 255) / 256, 4096), 256, 0, n->s>>>(fd, dout, dst, pix);
+        CNN_CUDA(n, cudaGetLastError());
+        if (!dev) CNN_CUDA(n, cudaMemcpyAsync(u0, dst, sizeof(float) * pix, cudaMemcpyDefault, n->s));
+    }
+    if (d) CNN_CUDA(n, cudaMemcpyAsync(d, dout, sizeof(float) * pix, cudaMemcpyDefault, n->s));
+    CNN_CUDA(n, cudaStreamSynchronize(n->s));
+    return FE_OK;
+}
+
+fe_status fe_cnn_loss_grad(fe_cnn *n, const float *f, const float *u_target, int B, int H, int W, double *loss,
+                           float *grad) {
+    if (!n || !f || !u_target || B < 1 || H < 1 || W < 1) return FE_EINVAL;
+    const size_t pix = (size_t)B * H * W;
+    const int nb = (W + TS - 1) / TS * ((H + TS - 1) / TS) * B;
+    fe_status st = ensure_capacity(n, pix, (size_t)nb * (CW * CW * 9 + CW));
+    if (st != FE_OK) return st;
+    const float *fd = stage(n, f, pix, 0, &st);
+    if (!fd) return st;
+    const float *ud = stage(n, u_target, pix, 1, &st);
+    if (!ud) return st;
+    if ((st = loss_grad(n, fd, ud, B, H, W, loss)) != FE_OK) return st;
+    if (grad) {
+        CNN_CUDA(n, cudaMemcpyAsync(grad, n->g, sizeof(float) * n->np, cudaMemcpyDefault, n->s));
+        CNN_CUDA(n, cudaStreamSynchronize(n->s));
+    }
+    return FE_OK;
+}
+
+fe_status fe_cnn_train_step(fe_cnn *n, const float *f, const float *u_target, int B, int H, int W, float lr,
+                            double *loss) {
+    fe_status st = fe_cnn_loss_grad(n, f, u_target, B, H, W, loss, nullptr);
+    if (st != FE_OK) return st;
+    n->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.f - std::pow(b1, (float)n->step), c2 = 1.f - std::pow(b2, (float)n->step);
+    adam_kernel<<<(n->np + 255) / 256, 256, 0, n->s>>>(n->p, n->m, n->v, n->g, n->is_w, n->pq, n->np, lr, b1, b2, eps, c1, c2);
+    CNN_CUDA(n, cudaGetLastError());
+    return refresh_layouts(n);
+}
+
+}  // extern "C"

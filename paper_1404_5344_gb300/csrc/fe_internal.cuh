@@ -52,6 +52,7 @@ struct ImgState {
     double L, alpha;
     double rel_change, last_gd, last_dd, last_dp;
     double tol;
+    double Gf;  // G(f) = (lambda/2) sum f^2 (1 - log f^2): the floor of the data term
     long long n, trials, backtracks, target;
     int cur, gcur, bt, status, done, converged;
 };

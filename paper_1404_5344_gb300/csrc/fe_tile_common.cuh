@@ -75,7 +75,10 @@ __device__ void decide(const KParams &p, ImgState *st, const double *t, int mode
     }
     if (F1 <= st->F + gd + 0.5 * st->L * dd) {
         const double H1 = F1 + G1;
-        st->rel_change = fabs(H1 - st->H) / fabs(H1);
+        // relative change of the energy above its data-term floor G(f) =
+        // min_u G(u): H - G(f) = F(u) + (G(u) - G(f)) >= 0
+        const double num = fabs(H1 - st->H), den = fabs(H1 - st->Gf);
+        st->rel_change = num == 0.0 ? 0.0 : num / den;
         st->H_prev = st->H;
         st->F = F1;
         st->G = G1;

@@ -30,7 +30,9 @@ EXPORTS = (
     "fe_solve", "fe_get_info", "fe_get_u", "fe_energy", "fe_gradient", "fe_get_state",
     "fe_set_state", "fe_num_images", "fe_image_size", "fe_launch_count", "fe_set_loop_mode",
     "fe_last_error", "fe_status_string", "fe_abi_version", "fe_gradient_noalloc",
-    "fe_tc_gemm_selftest",
+    "fe_tc_gemm_selftest", "fe_cnn_create", "fe_cnn_destroy", "fe_cnn_num_params",
+    "fe_cnn_last_error", "fe_cnn_set_params", "fe_cnn_get_params", "fe_cnn_forward",
+    "fe_cnn_loss_grad", "fe_cnn_train_step",
 )
 
 
@@ -46,7 +48,7 @@ class FeInfo(C.Structure):
                 ("L", C.c_double), ("alpha", C.c_double), ("F", C.c_double), ("G", C.c_double),
                 ("H", C.c_double), ("H_prev", C.c_double), ("rel_change", C.c_double),
                 ("last_gd", C.c_double), ("last_dd", C.c_double), ("last_dp", C.c_double),
-                ("status", C.c_int), ("converged", C.c_int)]
+                ("status", C.c_int), ("converged", C.c_int), ("G_floor", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -84,6 +86,20 @@ def _load(path: str = LIB_PATH) -> C.CDLL:
     L.fe_abi_version.argtypes = []
     L.fe_gradient_noalloc.argtypes = [VP, VP, VP, I, I, VP, VP, I, VP]
     L.fe_tc_gemm_selftest.argtypes = [I, I, I, VP, VP, VP]
+    L.fe_cnn_create.argtypes = [P(VP), C.c_ulonglong, VP]
+    L.fe_cnn_destroy.argtypes = [VP]
+    L.fe_cnn_destroy.restype = None
+    L.fe_cnn_num_params.argtypes = [VP]
+    L.fe_cnn_last_error.argtypes = [VP]
+    L.fe_cnn_last_error.restype = C.c_char_p
+    L.fe_cnn_set_params.argtypes = [VP, VP]
+    L.fe_cnn_get_params.argtypes = [VP, VP]
+    L.fe_cnn_forward.argtypes = [VP, VP, I, I, I, VP, VP]
+    L.fe_cnn_loss_grad.argtypes = [VP, VP, VP, I, I, I, P(D), VP]
+    L.fe_cnn_train_step.argtypes = [VP, VP, VP, I, I, I, C.c_float, P(D)]
+    for name in ("fe_cnn_create", "fe_cnn_num_params", "fe_cnn_set_params", "fe_cnn_get_params",
+                 "fe_cnn_forward", "fe_cnn_loss_grad", "fe_cnn_train_step"):
+        getattr(L, name).restype = C.c_int
     for name in ("fe_tc_gemm_selftest", "fe_gradient_noalloc", "fe_init_batch","fe_init", "fe_reset", "fe_step", "fe_solve", "fe_get_info",
                  "fe_get_u", "fe_energy", "fe_gradient", "fe_get_state", "fe_set_state",
                  "fe_image_size", "fe_set_loop_mode", "fe_num_images", "fe_abi_version"):
@@ -265,3 +281,65 @@ class Solver:
 
     def set_loop_mode(self, mode: int):
         self._check(lib.fe_set_loop_mode(self.ctx, int(mode)))
+
+
+class CNN:
+    """The warm-start network of the C ABI (``fe_cnn_*``): 5 x (3x3 conv), 32
+    channels, BF16 weights, FP32 activations; predicts u0 = f exp(d)."""
+
+    def __init__(self, seed: int = 0, stream=None):
+        self.ptr = C.c_void_p()
+        st = lib.fe_cnn_create(C.byref(self.ptr), int(seed), _stream_handle(stream))
+        if st != FE_OK:
+            raise FeError(st, "fe_cnn_create")
+        self.num_params = lib.fe_cnn_num_params(self.ptr)
+
+    def _check(self, st):
+        if st != FE_OK:
+            raise FeError(st, lib.fe_cnn_last_error(self.ptr).decode())
+
+    def close(self):
+        if getattr(self, "ptr", None) and self.ptr.value:
+            lib.fe_cnn_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _bhw(x):
+        s = tuple(int(v) for v in x.shape)
+        return (1,) + s if len(s) == 2 else s
+
+    def get_params(self):
+        p = np.empty(self.num_params, np.float32)
+        self._check(lib.fe_cnn_get_params(self.ptr, _ptr(p)))
+        return p
+
+    def set_params(self, p):
+        p = p if hasattr(p, "data_ptr") else np.ascontiguousarray(p, np.float32)
+        self._check(lib.fe_cnn_set_params(self.ptr, _ptr(p)))
+
+    def forward(self, f, u0=None, d=None):
+        """u0 = f exp(d) into u0 (and d into d); f is [H, W] or [B, H, W]."""
+        B, H, W = self._bhw(f)
+        if u0 is None and d is None:
+            u0 = np.empty(f.shape, np.float32)
+        self._check(lib.fe_cnn_forward(self.ptr, _ptr(f), B, H, W, _ptr(u0), _ptr(d)))
+        return u0 if u0 is not None else d
+
+    def loss_grad(self, f, u_target):
+        B, H, W = self._bhw(f)
+        loss = C.c_double()
+        g = np.empty(self.num_params, np.float32)
+        self._check(lib.fe_cnn_loss_grad(self.ptr, _ptr(f), _ptr(u_target), B, H, W, C.byref(loss), _ptr(g)))
+        return loss.value, g
+
+    def train_step(self, f, u_target, lr: float) -> float:
+        B, H, W = self._bhw(f)
+        loss = C.c_double()
+        self._check(lib.fe_cnn_train_step(self.ptr, _ptr(f), _ptr(u_target), B, H, W, float(lr), C.byref(loss)))
+        return loss.value

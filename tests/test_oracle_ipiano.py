@@ -159,13 +159,17 @@ def test_step_matches_solve(orc):
 
 
 def test_tolerance_stop(orc):
+    """Stops at the first accepted step whose energy change, relative to the
+    energy above the data-term floor G(f) = min_u G(u), is below tol."""
     k, th = _bank(6, seed=1)
     _, f = _problem(12, 12, seed=3)
-    # small lambda so that the prior, not the constant part of G, sets |H|
-    out = orc.ipiano(f, k, th, orc.params(lam=0.002, L0=1e-3, max_iter=500, tol=1e-6))
-    assert out["converged"] and 2 < out["n"] < 500
+    lam = 0.1  # a data weight at which the prior moves u away from f (lambda = 5 stops in 1-2 steps)
+    out = orc.ipiano(f, k, th, orc.params(lam=lam, L0=1e-2, max_iter=3000, tol=1e-6))
+    assert out["converged"] and 2 < out["n"] < 3000
     H = np.concatenate([[out["F0"] + out["G0"]], out["rec"][:, 4]])
-    rel = np.abs(np.diff(H)) / np.abs(H[1:])
+    floor = orc.G(f, f, lam)
+    assert np.all(H - floor >= 0)  # F >= 0 and G(u) >= G(f)
+    rel = np.abs(np.diff(H)) / np.abs(H[1:] - floor)
     assert rel[-1] < 1e-6 and np.all(rel[:-1] >= 1e-6)
 
 
