@@ -167,6 +167,20 @@ def cpu_baseline(fs, k, th, iters_total, seconds):
                       "(%.1f s)" % (f.shape[0], f.shape[1], out["n"], dt)}
 
 
+def combine_ranks(local_ms, local_units, dist=None, device="cpu"):
+    """Replicas: every rank solves its own batch with no exchange on the data
+    path.  The job's time is the slowest rank's (MAX) and its work the sum of
+    every rank's units (SUM); one rank returns its own numbers."""
+    if dist is None:
+        return float(local_ms), float(local_units)
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -236,6 +250,7 @@ def run_batch64(args):
 
     kw = dict(SOLVER_KW, lam=args.lam)
     batch = fe.Solver(f_dev, k, th, prec=args.prec, stream=stream, **kw)
+    tile = batch.tile
     for _ in range(max(1, args.warmup)):
         batch.reset(f_dev)
         batch.solve(args.max_iter, args.tol)
@@ -269,7 +284,8 @@ def run_batch64(args):
             "config": {"workload": "64 textured images, sides log-uniform in [128, 1536] (seed 7), L in {1, 4}, "
                                    "48x7x7 seeded bank, lambda=%g, tol=%g on |dH|/|H - G(f)|, max_iter=%d" % (
                                        args.lam, args.tol, args.max_iter),
-                       "pixels": npix, "precision": args.prec, "loop": "one CUDA-graph launch per solve"},
+                       "pixels": npix, "precision": args.prec, "loop": "one CUDA-graph launch per solve",
+                       "tile": "%dx%d (autotuned for the batch; each sequential solve autotunes its own)" % tile},
             "sequential_fp32_s": round(t_seq / 1e3, 4),
             "speedup_vs_sequential_fp32": round(t_seq / tb, 3),
             "iterations": {"batched_min": min(its), "batched_max": max(its), "batched_mean": round(sum(its) / len(its), 2),
@@ -385,6 +401,7 @@ def main():
     f_dev = [torch.from_numpy(f).cuda() for f in fs]
     torch.cuda.synchronize()
     solver = fe.Solver(f_dev, k, th, prec=args.prec, stream=stream, loop_mode=args.loop_mode, **SOLVER_KW)
+    tile = solver.tile
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def one_step():
@@ -428,12 +445,8 @@ def main():
     launches = solver.launch_count() - lc0
     statuses = sorted({x["status"] for x in infos})
 
-    # max over ranks
-    t_tensor = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
-    T_ms = float(t_tensor.item())
-    value = pix_iters_done * world / (T_ms / 1e3) / 1e6
+    T_ms, units = combine_ranks(total_ms, pix_iters_done, dist, device="cuda")
+    value = units / (T_ms / 1e3) / 1e6
 
     # Trial-kernel rate: algorithmic work of every image-trial that ran
     # (9408 flop per pixel, accepted and rejected trials alike) over the
@@ -478,7 +491,8 @@ def main():
             e2e_solver.get_u(i, out=u_host[i].numpy())
         stream.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3
-    e2e_value = npix * args.iters / (e2e_ms / e2e_steps / 1e3) / 1e6 * world
+    e2e_T, e2e_units = combine_ranks(e2e_ms / e2e_steps, npix * args.iters, dist, device="cuda")
+    e2e_value = e2e_units / (e2e_T / 1e3) / 1e6
     e2e_solver.close()
 
     line = None
@@ -494,6 +508,7 @@ def main():
                                            args.n512, args.n256, args.iters, args.prec.upper()),
                            "images": len(fs), "pixels": npix, "iters": args.iters, "precision": args.prec,
                            "loop": "cuda-graph while node" if args.loop_mode == 1 else "host chunks",
+                           "tile": "%dx%d (autotuned)" % tile,
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "256 MiB buffer written between timed steps; state 6 planes x "
                                  "%.0f MB" % (npix * 4 / 1e6)},

@@ -91,7 +91,14 @@ typedef struct {
     double c2;              /* step-size margin c2 >= 0 */
     int max_backtrack;      /* rejections allowed per iteration, >= 0 */
     int prec;               /* fe_precision */
-    int tile;               /* 0 = default tiling */
+    int tile;               /* output tile of the trial kernel: 0 = autotune.  FP32:
+                               0, 32 or 64 (T x T); at 0 fe_init_batch times both
+                               shapes on the context's own images (the initial
+                               gradient kernel, 4 launches each) and keeps the
+                               faster, cached per device and list of image sizes.
+                               Tensor-core forms: 0 only (one shape, 58 rows x
+                               26 columns).
+                               Other values: FE_EUNSUPPORTED. */
 } fe_params;
 
 /* Per-image solver state summary (host struct, filled by fe_get_info). */
@@ -179,6 +186,10 @@ FE_API fe_status fe_set_state(fe_ctx *ctx, int img, const float *u, const float 
 /* Number of images / size of image img. */
 FE_API int fe_num_images(const fe_ctx *ctx);
 FE_API fe_status fe_image_size(const fe_ctx *ctx, int img, int *H, int *W);
+
+/* Output tile (rows x columns) of the context's trial kernel, as chosen by
+ * the autotuner or given in fe_params.tile.  FE_EINVAL on NULL arguments. */
+FE_API fe_status fe_tile_size(const fe_ctx *ctx, int *tile_y, int *tile_x);
 
 /* Device kernel launches issued by this context since creation (trial,
  * gradient, energy and bookkeeping kernels), for launch accounting. */

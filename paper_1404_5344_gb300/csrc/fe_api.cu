@@ -16,6 +16,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -29,6 +31,7 @@ struct fe_ctx {
     fe_params prm{};
     std::vector<float> filt, theta;
     int nimg = 0, ntiles = 0, nfp = 0;
+    int tile_y = 0, tile_x = 0;  // output tile of the trial kernel (autotuned or given)
     std::vector<int> H, W;
     std::vector<ImgDesc> himg;
     std::vector<TileDesc> htile;
@@ -180,14 +183,74 @@ fe_status validate_params(fe_ctx *c, const fe_params *p) {
         return set_err(c, FE_EINVAL, "unknown precision %d", p->prec);
     if (p->prec != FE_FP32 && p->nf > 48)
         return set_err(c, FE_EUNSUPPORTED, "the tensor-core forms take at most 48 filters (nf=%d)", p->nf);
-    if (p->tile != 0) return set_err(c, FE_EUNSUPPORTED, "tile must be 0 (each form has a fixed tile)");
+    if (p->prec == FE_FP32 && p->tile != 0 && !fp32_tile_supported(p->tile))
+        return set_err(c, FE_EUNSUPPORTED, "FP32 tile %d: use 0 (autotune), 32 or 64", p->tile);
+    if (p->prec != FE_FP32 && p->tile != 0)
+        return set_err(c, FE_EUNSUPPORTED, "the tensor-core forms have one tile shape: tile must be 0");
     return FE_OK;
 }
 
 // Launch one tile kernel of the context's precision form.
 cudaError_t launch_tiles(const fe_ctx *c, int mode, const KParams &kp, int grid) {
-    if (c->prm.prec == FE_FP32) return fp32_launch(mode, kp, grid, c->s);
+    if (c->prm.prec == FE_FP32) return fp32_launch(mode, kp, grid, c->s, c->tile_y);
     return tc_launch(mode, c->prm.prec == FE_BF16 ? 1 : 2, kp, grid, c->s);
+}
+
+// Tile origins and owned extents along one axis of length N with tile T.
+// FP32: origins 0, T, 2T, ... (the last tile may hang over the border).
+// Tensor-core forms: the last origin is moved back to N - T (when N >= T)
+// so that it ends at the border and owns all its rows; the tile before it
+// owns only the rows up to that origin.  The first tile always owns the
+// first 3 rows: their mirror images (rows -3..-1) lie in its halo only.
+// Outputs: origin o_i, owned start relative to the origin rel_i, owned
+// length own_i (tile i owns [o_i + rel_i, o_i + rel_i + own_i)).
+void axis_tiles(bool tc, int N, int T, std::vector<int> &o, std::vector<int> &rel, std::vector<int> &own) {
+    const int n = (N + T - 1) / T;
+    std::vector<int> s;
+    o.clear();
+    rel.clear();
+    own.clear();
+    for (int i = 0; i < n; ++i) o.push_back(i * T);
+    if (tc && n > 1) o[n - 1] = N - T;
+    for (int i = 0; i < n; ++i) s.push_back(i == 0 ? 0 : (tc && i == n - 1 ? std::max(o[i], 3) : o[i]));
+    for (int i = 0; i < n; ++i) {
+        own.push_back((i + 1 < n ? s[i + 1] : N) - s[i]);
+        rel.push_back(s[i] - o[i]);
+    }
+}
+
+// The tile list of every image for a TY x TX tile (host copy only).
+void build_tiles(fe_ctx *c, int TY, int TX) {
+    const bool tc = c->prm.prec != FE_FP32;
+    c->htile.clear();
+    for (int j = 0; j < c->nimg; ++j) {
+        std::vector<int> oy, ry, ohv, ox, rx, owv;
+        axis_tiles(tc, c->H[j], TY, oy, ry, ohv);
+        axis_tiles(tc, c->W[j], TX, ox, rx, owv);
+        ImgDesc &d = c->himg[j];
+        d.tile_begin = (int)c->htile.size();
+        d.ntiles = (int)(oy.size() * ox.size());
+        for (size_t a = 0; a < oy.size(); ++a)
+            for (size_t b = 0; b < ox.size(); ++b)
+                c->htile.push_back(TileDesc{j, oy[a], ox[b], ohv[a], owv[b], ry[a], rx[b], 0});
+    }
+    c->ntiles = (int)c->htile.size();
+    c->tile_y = TY;
+    c->tile_x = TX;
+}
+
+size_t count_tiles(const fe_ctx *c, int TY, int TX) {
+    size_t n = 0;
+    for (int j = 0; j < c->nimg; ++j) n += (size_t)((c->H[j] + TY - 1) / TY) * ((c->W[j] + TX - 1) / TX);
+    return n;
+}
+
+fe_status upload_tiles(fe_ctx *c) {
+    FE_CUDA(c, cudaMemcpyAsync(c->d_imgs, c->himg.data(), sizeof(ImgDesc) * c->nimg, cudaMemcpyHostToDevice, c->s));
+    FE_CUDA(c, cudaMemcpyAsync(c->d_tiles, c->htile.data(), sizeof(TileDesc) * c->ntiles, cudaMemcpyHostToDevice,
+                               c->s));
+    c->kp.ntiles = c->ntiles;
+    return FE_OK;
 }
 
 fe_status load_inputs(fe_ctx *c, const float *const *f, const float *const *u0) {
@@ -282,10 +345,10 @@ fe_status build_graph(fe_ctx *c) {
     std::memset(&knp, 0, sizeof knp);
     const int fmt = c->prm.prec == FE_BF16 ? 1 : 2;
     const bool tc = c->prm.prec != FE_FP32;
-    knp.func = const_cast<void *>(tc ? tc_trial_entry(fmt) : fp32_trial_entry());
+    knp.func = const_cast<void *>(tc ? tc_trial_entry(fmt) : fp32_trial_entry(c->tile_y));
     knp.gridDim = dim3(c->ntiles);
-    knp.blockDim = dim3(tc ? tc_threads() : fp32_threads());
-    knp.sharedMemBytes = (unsigned)(tc ? tc_smem_bytes(fmt) : fp32_smem_bytes());
+    knp.blockDim = dim3(tc ? tc_threads() : fp32_threads(c->tile_y));
+    knp.sharedMemBytes = (unsigned)(tc ? tc_smem_bytes(fmt) : fp32_smem_bytes(c->tile_y));
     knp.kernelParams = args;
     cudaGraphNode_t kn;
     e = cudaGraphAddKernelNode(&kn, body, nullptr, 0, &knp);
@@ -360,6 +423,70 @@ fe_status stage_in(fe_ctx *c, const float *src, size_t N, int slot, const float 
     return FE_OK;
 }
 
+// Tile autotuner (FP32 form).  The choice depends on the image sizes: a
+// batch with too few 64 x 64 tiles to fill 152 SMs x 2 CTAs runs faster
+// with 32 x 32 tiles despite their larger recomputed halo.  Each candidate
+// is timed on this context's own images with the initial-gradient kernel
+// (forward bank, potential, adjoint bank and sums on every tile: the cost of
+// a trial without the pointwise prox), which is idempotent, so timing it
+// changes no state.  One warm-up launch, then the median of three
+// CUDA-event timings.  The choice is cached per device and list of image
+// sizes for the life of the process.
+fe_status autotune_tile(fe_ctx *c, const std::vector<int> &cand) {
+    static std::mutex mu;
+    static std::map<std::string, int> cache;
+    std::string key = std::to_string(c->dev) + ":" + std::to_string(c->nfp);
+    for (int j = 0; j < c->nimg; ++j) key += ":" + std::to_string(c->H[j]) + "x" + std::to_string(c->W[j]);
+    int best = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) best = it->second;
+    }
+    if (best == 0) {
+        cudaEvent_t e0, e1;
+        FE_CUDA(c, cudaEventCreate(&e0));
+        if (cudaEventCreate(&e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            return set_err(c, FE_ECUDA, "cudaEventCreate failed");
+        }
+        float best_ms = 0.f;
+        fe_status st = FE_OK;
+        for (int T : cand) {
+            build_tiles(c, T, T);
+            if ((st = upload_tiles(c)) != FE_OK) break;
+            KParams kp = c->kp;
+            kp.tile0 = 0;
+            float ms[3];
+            cudaError_t e = launch_tiles(c, MODE_INIT, kp, c->ntiles);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+                if ((e = cudaEventRecord(e0, c->s)) != cudaSuccess) break;
+                if ((e = launch_tiles(c, MODE_INIT, kp, c->ntiles)) != cudaSuccess) break;
+                if ((e = cudaEventRecord(e1, c->s)) != cudaSuccess) break;
+                if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+                e = cudaEventElapsedTime(&ms[r], e0, e1);
+            }
+            c->host_launches += 4;
+            if (e != cudaSuccess) {
+                st = set_err(c, FE_ECUDA, "tile autotune (T=%d): %s", T, cudaGetErrorString(e));
+                break;
+            }
+            std::sort(ms, ms + 3);
+            if (best == 0 || ms[1] < best_ms) {
+                best = T;
+                best_ms = ms[1];
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st != FE_OK) return st;
+        std::lock_guard<std::mutex> lk(mu);
+        cache[key] = best;
+    }
+    build_tiles(c, best, best);
+    return upload_tiles(c);
+}
+
 }  // namespace
 
 void fe::set_global_error(const char *msg) { g_init_err = msg ? msg : ""; }
@@ -429,29 +556,6 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
     c->theta.assign(p->theta, p->theta + p->nf);
     c->nfp = ((p->nf + 7) / 8) * 8;
     const bool tc = p->prec != FE_FP32;
-    const int TYs = tc ? tc_tile_y : fp32_tile(), TXs = tc ? tc_tile_x : fp32_tile();
-    // Tile origins and owned extents along one axis of length N with tile T.
-    // FP32: origins 0, T, 2T, ... (the last tile may hang over the border).
-    // Tensor-core forms: the last origin is moved back to N - T (when N >= T)
-    // so that it ends at the border and owns all its rows; the tile before it
-    // owns only the rows up to that origin.  The first tile always owns the
-    // first 3 rows: their mirror images (rows -3..-1) lie in its halo only.
-    // Outputs: origin o_i, owned start relative to the origin rel_i, owned
-    // length own_i (tile i owns [o_i + rel_i, o_i + rel_i + own_i)).
-    auto axis_tiles = [&](int N, int T, std::vector<int> &o, std::vector<int> &rel, std::vector<int> &own) {
-        const int n = (N + T - 1) / T;
-        std::vector<int> s;
-        o.clear();
-        rel.clear();
-        own.clear();
-        for (int i = 0; i < n; ++i) o.push_back(i * T);
-        if (tc && n > 1) o[n - 1] = N - T;
-        for (int i = 0; i < n; ++i) s.push_back(i == 0 ? 0 : (tc && i == n - 1 ? std::max(o[i], 3) : o[i]));
-        for (int i = 0; i < n; ++i) {
-            own.push_back((i + 1 < n ? s[i + 1] : N) - s[i]);
-            rel.push_back(s[i] - o[i]);
-        }
-    };
     size_t plane_total = 0;
     for (int j = 0; j < nimg; ++j) {
         if (H[j] < 8 || W[j] < 8 || H[j] > 65536 || W[j] > 65536)
@@ -461,22 +565,29 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
         const size_t N = (size_t)H[j] * W[j];
         c->max_plane = std::max(c->max_plane, (N + 63) / 64 * 64);
         plane_total += 6 * ((N + 63) / 64 * 64);
-        std::vector<int> oy, ry, ohv, ox, rx, owv;
-        axis_tiles(H[j], TYs, oy, ry, ohv);
-        axis_tiles(W[j], TXs, ox, rx, owv);
         ImgDesc d{};
         d.H = H[j];
         d.W = W[j];
-        d.tile_begin = (int)c->htile.size();
-        d.ntiles = (int)(oy.size() * ox.size());
         d.lambda = p->lambda;
-        for (size_t a = 0; a < oy.size(); ++a)
-            for (size_t b = 0; b < ox.size(); ++b)
-                c->htile.push_back(TileDesc{j, oy[a], ox[b], ohv[a], owv[b], ry[a], rx[b], 0});
         c->himg.push_back(d);
     }
-    if (c->htile.size() > (size_t)0x7fffffff) return bail(set_err(c, FE_EINVAL, "too many tiles"));
-    c->ntiles = (int)c->htile.size();
+    // candidate tile shapes: the tensor-core forms have one; FP32 has 64 and
+    // 32 (autotuned when p->tile == 0)
+    std::vector<int> cand;
+    if (tc)
+        cand.push_back(0);
+    else if (p->tile != 0)
+        cand.push_back(p->tile);
+    else
+        cand = {64, 32};
+    size_t max_tiles = 0;
+    for (int T : cand)
+        max_tiles = std::max(max_tiles, tc ? count_tiles(c, tc_tile_y, tc_tile_x) : count_tiles(c, T, T));
+    if (max_tiles > (size_t)0x7fffffff) return bail(set_err(c, FE_EINVAL, "too many tiles"));
+    if (tc)
+        build_tiles(c, tc_tile_y, tc_tile_x);
+    else
+        build_tiles(c, cand[0], cand[0]);
     if (cudaGetDevice(&c->dev) != cudaSuccess) return bail(set_err(c, FE_ECUDA, "no CUDA device"));
 
     if (cudaError_t e = tc ? tc_prepare() : fp32_prepare(); e != cudaSuccess)
@@ -495,8 +606,8 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
     }
     if ((st = dalloc(c, &c->d_imgs, nimg)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_st, nimg)) != FE_OK) return bail(st);
-    if ((st = dalloc(c, &c->d_tiles, c->ntiles)) != FE_OK) return bail(st);
-    if ((st = dalloc(c, &c->d_part, (size_t)c->ntiles * NRED)) != FE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_tiles, max_tiles)) != FE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_part, max_tiles * NRED)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_arr, nimg)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_loop, 1)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_wf, (size_t)KT * NFMAX)) != FE_OK) return bail(st);
@@ -563,6 +674,10 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
     if (cudaMemset(c->d_loop, 0, sizeof(LoopCtl)) != cudaSuccess)
         return bail(set_err(c, FE_ECUDA, "cudaMemset: %s", cudaGetErrorString(cudaGetLastError())));
     if ((st = load_inputs(c, f, u0)) != FE_OK) return bail(st);
+    if (cand.size() > 1) {
+        if ((st = autotune_tile(c, cand)) != FE_OK) return bail(st);
+        if ((st = load_inputs(c, f, u0)) != FE_OK) return bail(st);  // state of the chosen tiling
+    }
     *out = c;
     return FE_OK;
 }
@@ -749,6 +864,13 @@ fe_status fe_gradient(fe_ctx *c, int img, const float *u, float *g, double *F) {
 }
 
 int fe_num_images(const fe_ctx *c) { return c ? c->nimg : 0; }
+
+fe_status fe_tile_size(const fe_ctx *c, int *tile_y, int *tile_x) {
+    if (!c || !tile_y || !tile_x) return FE_EINVAL;
+    *tile_y = c->tile_y;
+    *tile_x = c->tile_x;
+    return FE_OK;
+}
 
 fe_status fe_image_size(const fe_ctx *c, int img, int *H, int *W) {
     if (!c || img < 0 || img >= c->nimg) return FE_EINVAL;

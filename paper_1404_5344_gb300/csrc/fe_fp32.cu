@@ -24,15 +24,21 @@
 // the tile + halo fit in shared memory; the adjoint accumulators stay in
 // registers across groups.
 //
-// Work split (256 threads, two CTAs per SM so that one CTA's barrier waits
-// are covered by the other; TY = TX = 64, G = 4):
-//   forward: units of 1 column x 10 rows x 4 filters over the 70 x 70 halo
-//            region (490 units, two rounds); a unit slides its 16-row column
-//            window over the 7 kernel columns; weight vectors are uniform
-//            128-bit loads from the tap-major table in global memory (L1)
-//   adjoint: units of 4 x 4 output pixels (256 units, one per thread); each
-//            window row is three LDS.128, each filter's 49 weights are held
-//            in registers while its 10 window rows stream through
+// Two tile shapes, T x T output pixels per CTA (the autotuner of the host
+// side picks one per context):
+//   T = 64: 256 threads, two CTAs per SM so that one CTA's barrier waits are
+//           covered by the other; forward units of 1 column x 10 rows x 4
+//           filters over the 70 x 70 response region (490 units, two rounds);
+//           adjoint units of 4 x 4 output pixels (one per thread)
+//   T = 32: 128 threads, four CTAs per SM, for images too small to fill the
+//           GPU with 64 x 64 tiles; forward units of 1 column x 13 rows over
+//           a 39-row (one padding row) x 38-column region (114 units, one
+//           round); adjoint units of 2 x 4 output pixels (one per thread)
+// A forward unit slides its column window over the 7 kernel columns; weight
+// vectors are uniform 128-bit loads from the tap-major table in global
+// memory (L1).  An adjoint unit reads each window row with three LDS.128 and
+// holds each filter's 49 weights in registers while its window rows stream
+// through.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -43,35 +49,62 @@
 namespace fe {
 namespace {
 
-constexpr int TY = 64, TX = 64, NT = 256, G = 4;
-constexpr int R6Y = TY + 12, R6X = TX + 12;  // u^{n+1} region (tile + 6)
-constexpr int R3Y = TY + 6, R3X = TX + 6;    // response region (tile + 3)
-constexpr int SU_LD = 87;  // >= R6X; 10*87 = 70 (mod 32): unit rows wrap without bank conflicts
-constexpr int SR_LD = 72;                    // >= R3X, multiple of 4, covers 4*15 + 12
-constexpr int NWARP = NT / 32;
-constexpr int FWD_ROWS = 10;                       // rows per forward unit
-constexpr int FWD_WIN = FWD_ROWS + KS - 1;         // 16-row column window
-constexpr int FWD_UNITS = R3X * (R3Y / FWD_ROWS);  // 490
-constexpr int ADJ_UNITS = (TY / 4) * (TX / 4);     // 256
-constexpr int RING = 2 * 3 * R3X + 2 * 3 * TY;     // 804 frame positions
-constexpr int RING_PER_T = (RING + NT - 1) / NT;   // 4
-static_assert(R3Y % FWD_ROWS == 0, "forward units tile the halo rows");
-static_assert(NT == ADJ_UNITS, "one adjoint unit per thread");
-static_assert(SR_LD >= 4 * (TX / 4 - 1) + 12, "adjoint window loads stay in the row");
-static_assert(TY == TX, "ring layout assumes a square tile");
-static_assert(TY == fp32_tile_size, "tile size shared with the host code");
+constexpr int G = 4;  // filters per group (response planes held in shared memory)
 
-constexpr size_t SM_U = (size_t)R6Y * SU_LD;
-constexpr size_t SM_R = (size_t)G * R3Y * SR_LD;
-constexpr size_t SM_FLOATS = SM_U + SM_R;
-constexpr size_t SM_BYTES = SM_FLOATS * 4 + (size_t)NWARP * NRED * 8;
-static_assert(SM_FLOATS % 2 == 0, "double scratch alignment");
-static_assert(2 * (SM_BYTES + 1024) <= 228 * 1024, "two CTAs per SM");
-static_assert(RING <= SM_R, "the frame ring reuses sR");
+template <int T>
+struct Cfg;
+template <>
+struct Cfg<64> {
+    static constexpr int NT = 256, MINB = 2, FWD_ROWS = 10, AUR = 4;
+    static constexpr int SU_LD = 87;  // 10*87 = 70 (mod 32): unit rows wrap without bank conflicts
+    static constexpr int SR_LD = 72;
+};
+template <>
+struct Cfg<32> {
+    static constexpr int NT = 128, MINB = 4, FWD_ROWS = 13, AUR = 2;
+    static constexpr int SU_LD = 62;  // 13*62 = 6 (mod 32), 38 = 6 (mod 32): as above
+    static constexpr int SR_LD = 40;
+};
+
+template <int T>
+struct Geo {
+    using C = Cfg<T>;
+    static constexpr int TY = T, TX = T, NT = C::NT, MINB = C::MINB;
+    static constexpr int FWD_ROWS = C::FWD_ROWS, AUR = C::AUR, SU_LD = C::SU_LD, SR_LD = C::SR_LD;
+    static constexpr int R3Y = TY + 6, R3X = TX + 6;  // response region (tile + 3)
+    // rows the forward units cover: R3Y rounded up to whole units (the extra
+    // row is computed from clamped loads and never read)
+    static constexpr int R3YA = (R3Y + FWD_ROWS - 1) / FWD_ROWS * FWD_ROWS;
+    static constexpr int R6Y = R3YA + 6, R6X = TX + 12;  // u^{n+1} region (tile + 6, padded)
+    static constexpr int NWARP = NT / 32;
+    static constexpr int FWD_WIN = FWD_ROWS + KS - 1;       // column window of a forward unit
+    static constexpr int FWD_UNITS = R3X * (R3YA / FWD_ROWS);
+    static constexpr int AUX = TX / 4;                      // adjoint units per tile row
+    static constexpr int ADJ_UNITS = (TY / AUR) * AUX;
+    static constexpr int RING = 2 * 3 * R3X + 2 * 3 * TY;   // frame positions
+    static constexpr int RING_PER_T = (RING + NT - 1) / NT;
+    // sR follows sU: round sU up to 4 floats so that sR is 16-byte aligned
+    // for the adjoint's 128-bit loads
+    static constexpr size_t SM_U = ((size_t)R6Y * SU_LD + 3) / 4 * 4;
+    static constexpr size_t SM_R = (size_t)G * R3YA * SR_LD;
+    static constexpr size_t SM_FLOATS = SM_U + SM_R;
+    static constexpr size_t SM_BYTES = SM_FLOATS * 4 + (size_t)NWARP * NRED * 8;
+    static_assert(NT == ADJ_UNITS, "one adjoint unit per thread");
+    static_assert(SU_LD >= R6X && SR_LD >= R3X, "row pitches hold a region row");
+    static_assert(SR_LD % 4 == 0 && SR_LD >= 4 * (AUX - 1) + 12, "adjoint window loads stay in the row");
+    static_assert((AUR - 1) + (TY - AUR) + KS <= R3Y, "adjoint windows stay in the response region");
+    static_assert(SM_U % 4 == 0 && SM_R % 4 == 0 && (SR_LD * R3YA) % 4 == 0,
+                  "every plane and row of sR starts on a 16-byte boundary");
+    static_assert(SM_FLOATS % 2 == 0, "double scratch alignment");
+    static_assert(MINB * (SM_BYTES + 1024) <= 228 * 1024, "MINB CTAs per SM");
+    static_assert(RING <= SM_R, "the frame ring reuses sR");
+};
 
 constexpr float LN2 = 0.69314718055994530942f;
 
+template <int T>
 __device__ __forceinline__ void ring_to_pos(int idx, int &pr, int &pc) {
+    constexpr int TY = T, TX = T, R3X = T + 6;
     if (idx < 3 * R3X) {
         pr = idx / R3X;
         pc = idx % R3X;
@@ -90,7 +123,9 @@ __device__ __forceinline__ void ring_to_pos(int idx, int &pr, int &pc) {
     }
 }
 
+template <int T>
 __device__ __forceinline__ int pos_to_ring(int pr, int pc) {
+    constexpr int TY = T, TX = T, R3X = T + 6;
     if (pr < 3) return pr * R3X + pc;
     if (pr >= TY + 3) return 3 * R3X + (pr - TY - 3) * R3X + pc;
     if (pc < 3) return 6 * R3X + (pr - 3) * 3 + pc;
@@ -100,10 +135,13 @@ __device__ __forceinline__ int pos_to_ring(int pr, int pc) {
 // Forward bank of one unit (1 column x FWD_ROWS rows x G filters of group
 // grp) and its epilogue: r_i into sR, theta_i log2(1 + z_i^2) summed over the
 // unit's tile pixels.  MASK: some pixel of the unit lies outside the image.
-template <int MODE, bool MASK>
+template <int T, int MODE, bool MASK>
 __device__ __forceinline__ float forward_unit(const float *__restrict__ sU, float *__restrict__ sR,
                                               const float *__restrict__ wf, const float *__restrict__ theta,
                                               int grp, int c, int rb, int y0, int x0, int H, int W) {
+    using Q = Geo<T>;
+    constexpr int FWD_ROWS = Q::FWD_ROWS, FWD_WIN = Q::FWD_WIN, SU_LD = Q::SU_LD, SR_LD = Q::SR_LD;
+    constexpr int TY = Q::TY, TX = Q::TX, R3YA = Q::R3YA;
     float z[FWD_ROWS][G];
 #pragma unroll
     for (int r = 0; r < FWD_ROWS; ++r)
@@ -149,7 +187,7 @@ __device__ __forceinline__ float forward_unit(const float *__restrict__ sU, floa
             if (MODE != MODE_ENERGY_EXT) {
                 float rv = __fdividef(th2[i] * zz, q);
                 if (MASK && !inimg) rv = 0.0f;
-                sR[(i * R3Y + pr) * SR_LD + c] = rv;
+                sR[(i * R3YA + pr) * SR_LD + c] = rv;
             }
             psum = fmaf(th[i], __log2f(q), psum);
         }
@@ -158,8 +196,13 @@ __device__ __forceinline__ float forward_unit(const float *__restrict__ sU, floa
     return fsum * LN2;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(NT, 2) fp32_tile_kernel(const KParams p) {
+template <int MODE, int T>
+__global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(const KParams p) {
+    using Q = Geo<T>;
+    constexpr int TY = Q::TY, TX = Q::TX, NT = Q::NT, R3Y = Q::R3Y, R3X = Q::R3X, R3YA = Q::R3YA;
+    constexpr int R6Y = Q::R6Y, R6X = Q::R6X, SU_LD = Q::SU_LD, SR_LD = Q::SR_LD, AUR = Q::AUR;
+    constexpr int FWD_ROWS = Q::FWD_ROWS, FWD_UNITS = Q::FWD_UNITS, RING = Q::RING, RING_PER_T = Q::RING_PER_T;
+    constexpr size_t SM_U = Q::SM_U, SM_R = Q::SM_R;
     extern __shared__ __align__(16) float smem[];
     float *sU = smem;
     float *sR = sU + SM_U;
@@ -228,15 +271,15 @@ __global__ void __launch_bounds__(NT, 2) fp32_tile_kernel(const KParams p) {
             }
         }
 
-        float acc[4][4];
+        float acc[AUR][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < AUR; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
         float fr[RING_PER_T];
 #pragma unroll
         for (int k = 0; k < RING_PER_T; ++k) fr[k] = 0.f;
-        const int aux = tid & 15, auy = tid >> 4;  // adjoint unit of this thread
+        const int aux = tid % Q::AUX, auy = tid / Q::AUX;  // adjoint unit of this thread
         const bool border = y0 == 0 || x0 == 0 || y0 + TY > H - 3 || x0 + TX > W - 3;
 
         for (int grp = 0; grp < p.nfp / G; ++grp) {
@@ -246,14 +289,14 @@ __global__ void __launch_bounds__(NT, 2) fp32_tile_kernel(const KParams p) {
                 const int c = unit % R3X, rb = unit / R3X;
                 const int x = x0 - 3 + c, ylo = y0 - 3 + rb * FWD_ROWS;
                 const bool full = x >= 0 && x < W && ylo >= 0 && ylo + FWD_ROWS <= H;
-                const float fs = full ? forward_unit<MODE, false>(sU, sR, p.wf, p.theta, grp, c, rb, y0, x0, H, W)
-                                      : forward_unit<MODE, true>(sU, sR, p.wf, p.theta, grp, c, rb, y0, x0, H, W);
+                const float fs = full ? forward_unit<T, MODE, false>(sU, sR, p.wf, p.theta, grp, c, rb, y0, x0, H, W)
+                                      : forward_unit<T, MODE, true>(sU, sR, p.wf, p.theta, grp, c, rb, y0, x0, H, W);
                 accF += (double)fs;
             }
             if (MODE == MODE_ENERGY_EXT) continue;
             __syncthreads();  // sR complete
 
-            // ---- 5: adjoint bank on the tile (4x4 unit per thread) ---------
+            // ---- 5: adjoint bank on the tile (AUR x 4 unit per thread) -----
             for (int i = 0; i < G; ++i) {
                 const float *wrow = p.wa + (grp * G + i) * KT_PAD;
                 float kw[KT_PAD];
@@ -265,15 +308,15 @@ __global__ void __launch_bounds__(NT, 2) fp32_tile_kernel(const KParams p) {
                     kw[4 * j + 2] = t.z;
                     kw[4 * j + 3] = t.w;
                 }
-                const float *Ri = sR + (size_t)i * R3Y * SR_LD + (4 * auy) * SR_LD + 4 * aux;
+                const float *Ri = sR + (size_t)i * R3YA * SR_LD + (AUR * auy) * SR_LD + 4 * aux;
 #pragma unroll
-                for (int rr = 0; rr < 4 + KS - 1; ++rr) {
+                for (int rr = 0; rr < AUR + KS - 1; ++rr) {
                     const float4 a0 = *reinterpret_cast<const float4 *>(Ri + rr * SR_LD);
                     const float4 a1 = *reinterpret_cast<const float4 *>(Ri + rr * SR_LD + 4);
                     const float4 a2 = *reinterpret_cast<const float4 *>(Ri + rr * SR_LD + 8);
                     const float v[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
 #pragma unroll
-                    for (int pp = 0; pp < 4; ++pp) {
+                    for (int pp = 0; pp < AUR; ++pp) {
                         const int aa = rr - pp;
                         if (aa < 0 || aa >= KS) continue;
 #pragma unroll
@@ -290,7 +333,7 @@ __global__ void __launch_bounds__(NT, 2) fp32_tile_kernel(const KParams p) {
                     const int idx = tid + k * NT;
                     if (idx >= RING) break;
                     int pr, pc, j, jx;
-                    ring_to_pos(idx, pr, pc);
+                    ring_to_pos<T>(idx, pr, pc);
                     if (!axis_pos(pr, y0, TY, H, j) || !axis_pos(pc, x0, TX, W, jx)) continue;
                     // s(j, jx) = sum_i sum_ab k_i[a][b] r_i(j - 3 + a, jx - 3 + b); r_i is
                     // zero off-image and the response region covers every on-image row
@@ -300,7 +343,7 @@ __global__ void __launch_bounds__(NT, 2) fp32_tile_kernel(const KParams p) {
                     float s = 0.f;
                     for (int i = 0; i < G; ++i) {
                         const float *wrow = p.wa + (grp * G + i) * KT_PAD;
-                        const float *Ri = sR + (size_t)i * R3Y * SR_LD;
+                        const float *Ri = sR + (size_t)i * R3YA * SR_LD;
                         for (int aa = alo; aa < ahi; ++aa)
                             for (int bb = blo; bb < bhi; ++bb)
                                 s = fmaf(__ldg(wrow + aa * KS + bb), Ri[(j - y0 + aa) * SR_LD + (jx - x0 + bb)], s);
@@ -330,8 +373,8 @@ __global__ void __launch_bounds__(NT, 2) fp32_tile_kernel(const KParams p) {
                 else
                     gout = im.g[gcur_out];
 #pragma unroll
-                for (int pp = 0; pp < 4; ++pp) {
-                    const int y = y0 + 4 * auy + pp;
+                for (int pp = 0; pp < AUR; ++pp) {
+                    const int y = y0 + AUR * auy + pp;
                     if (y >= H) continue;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
@@ -350,7 +393,7 @@ __global__ void __launch_bounds__(NT, 2) fp32_tile_kernel(const KParams p) {
                             for (int m = 0; m < ny; ++m)
                                 for (int n = 0; n < nx; ++n) {
                                     if (m == 0 && n == 0) continue;
-                                    gv += sR[pos_to_ring(py[m], px[n])];
+                                    gv += sR[pos_to_ring<T>(py[m], px[n])];
                                 }
                         }
                         gout[(size_t)y * W + x] = gv;
@@ -368,35 +411,57 @@ __global__ void __launch_bounds__(NT, 2) fp32_tile_kernel(const KParams p) {
     if (MODE == MODE_TRIAL) loop_control(p);
 }
 
-}  // namespace
-
-size_t fp32_smem_bytes() { return SM_BYTES; }
-int fp32_tile() { return TY; }
-int fp32_threads() { return NT; }
-
-cudaError_t fp32_prepare() {
+template <int T>
+cudaError_t prepare_tile() {
+    const int b = (int)Geo<T>::SM_BYTES;
     cudaError_t e;
-    e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_TRIAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_BYTES);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_INIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_BYTES);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_GRAD_EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_BYTES);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(fp32_tile_kernel<MODE_ENERGY_EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_BYTES);
+    if ((e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_TRIAL, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_INIT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_GRAD_EXT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  b)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(fp32_tile_kernel<MODE_ENERGY_EXT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
 }
 
-cudaError_t fp32_launch(int mode, const KParams &p, int ngrid, cudaStream_t s) {
-    const dim3 grid(ngrid), block(NT);
+template <int T>
+cudaError_t launch_tile(int mode, const KParams &p, int ngrid, cudaStream_t s) {
+    const dim3 grid(ngrid), block(Geo<T>::NT);
+    const size_t b = Geo<T>::SM_BYTES;
     switch (mode) {
-        case MODE_TRIAL: fp32_tile_kernel<MODE_TRIAL><<<grid, block, SM_BYTES, s>>>(p); break;
-        case MODE_INIT: fp32_tile_kernel<MODE_INIT><<<grid, block, SM_BYTES, s>>>(p); break;
-        case MODE_GRAD_EXT: fp32_tile_kernel<MODE_GRAD_EXT><<<grid, block, SM_BYTES, s>>>(p); break;
-        case MODE_ENERGY_EXT: fp32_tile_kernel<MODE_ENERGY_EXT><<<grid, block, SM_BYTES, s>>>(p); break;
+        case MODE_TRIAL: fp32_tile_kernel<MODE_TRIAL, T><<<grid, block, b, s>>>(p); break;
+        case MODE_INIT: fp32_tile_kernel<MODE_INIT, T><<<grid, block, b, s>>>(p); break;
+        case MODE_GRAD_EXT: fp32_tile_kernel<MODE_GRAD_EXT, T><<<grid, block, b, s>>>(p); break;
+        case MODE_ENERGY_EXT: fp32_tile_kernel<MODE_ENERGY_EXT, T><<<grid, block, b, s>>>(p); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-const void *fp32_trial_entry() { return reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL>); }
+}  // namespace
+
+bool fp32_tile_supported(int T) { return T == 64 || T == 32; }
+size_t fp32_smem_bytes(int T) { return T == 32 ? Geo<32>::SM_BYTES : Geo<64>::SM_BYTES; }
+int fp32_tile() { return fp32_tile_size; }
+int fp32_threads(int T) { return T == 32 ? Geo<32>::NT : Geo<64>::NT; }
+
+cudaError_t fp32_prepare() {
+    cudaError_t e = prepare_tile<64>();
+    return e != cudaSuccess ? e : prepare_tile<32>();
+}
+
+cudaError_t fp32_launch(int mode, const KParams &p, int ngrid, cudaStream_t s, int T) {
+    if (T == 64) return launch_tile<64>(mode, p, ngrid, s);
+    if (T == 32) return launch_tile<32>(mode, p, ngrid, s);
+    return cudaErrorInvalidValue;
+}
+
+const void *fp32_trial_entry(int T) {
+    return T == 32 ? reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL, 32>)
+                   : reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL, 64>);
+}
 
 }  // namespace fe

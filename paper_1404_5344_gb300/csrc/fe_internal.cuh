@@ -102,13 +102,14 @@ struct KParams {
 };
 
 // FP32 fused tile kernel (fe_fp32.cu)
-constexpr int fp32_tile_size = 64;  // square output tile of the FP32 kernel
-size_t fp32_smem_bytes();
-int fp32_tile();
-int fp32_threads();          // block size of the tile kernel
-cudaError_t fp32_prepare();  // opt in to the large shared-memory carve-out
-cudaError_t fp32_launch(int mode, const KParams &p, int grid, cudaStream_t s);
-const void *fp32_trial_entry();
+constexpr int fp32_tile_size = 64;  // default square output tile of the FP32 kernel
+bool fp32_tile_supported(int T);     // T = 64 or 32
+size_t fp32_smem_bytes(int T = fp32_tile_size);
+int fp32_tile();                                    // the default tile, fp32_tile_size
+int fp32_threads(int T = fp32_tile_size);           // block size of the tile kernel
+cudaError_t fp32_prepare();  // opt in to the large shared-memory carve-out (every tile shape)
+cudaError_t fp32_launch(int mode, const KParams &p, int grid, cudaStream_t s, int T = fp32_tile_size);
+const void *fp32_trial_entry(int T = fp32_tile_size);
 
 // Tensor-core tile kernel (fe_tc.cu); fmt 1 = BF16, 2 = TF32 operands
 constexpr int tc_tile_y = 58, tc_tile_x = 26;  // output tile; tile + 3-pixel halo = 64 x 32

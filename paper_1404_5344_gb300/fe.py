@@ -28,7 +28,7 @@ PRECISIONS = {"fp32": FE_FP32, "tf32": FE_TF32, "bf16": FE_BF16}
 EXPORTS = (
     "fe_default_params", "fe_init_batch", "fe_init", "fe_reset", "fe_destroy", "fe_step",
     "fe_solve", "fe_get_info", "fe_get_u", "fe_energy", "fe_gradient", "fe_get_state",
-    "fe_set_state", "fe_num_images", "fe_image_size", "fe_launch_count", "fe_set_loop_mode",
+    "fe_set_state", "fe_num_images", "fe_image_size", "fe_launch_count", "fe_set_loop_mode", "fe_tile_size",
     "fe_last_error", "fe_status_string", "fe_abi_version", "fe_gradient_noalloc",
     "fe_tc_gemm_selftest", "fe_cnn_create", "fe_cnn_destroy", "fe_cnn_num_params",
     "fe_cnn_last_error", "fe_cnn_set_params", "fe_cnn_get_params", "fe_cnn_forward",
@@ -76,6 +76,7 @@ def _load(path: str = LIB_PATH) -> C.CDLL:
     L.fe_set_state.argtypes = [VP, I, VP, VP, VP, P(FeInfo)]
     L.fe_num_images.argtypes = [VP]
     L.fe_image_size.argtypes = [VP, I, P(I), P(I)]
+    L.fe_tile_size.argtypes = [VP, P(I), P(I)]
     L.fe_launch_count.argtypes = [VP]
     L.fe_launch_count.restype = C.c_longlong
     L.fe_set_loop_mode.argtypes = [VP, I]
@@ -102,7 +103,7 @@ def _load(path: str = LIB_PATH) -> C.CDLL:
         getattr(L, name).restype = C.c_int
     for name in ("fe_tc_gemm_selftest", "fe_gradient_noalloc", "fe_init_batch","fe_init", "fe_reset", "fe_step", "fe_solve", "fe_get_info",
                  "fe_get_u", "fe_energy", "fe_gradient", "fe_get_state", "fe_set_state",
-                 "fe_image_size", "fe_set_loop_mode", "fe_num_images", "fe_abi_version"):
+                 "fe_image_size", "fe_set_loop_mode", "fe_num_images", "fe_abi_version", "fe_tile_size"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -213,6 +214,13 @@ class Solver:
     @property
     def nimg(self):
         return lib.fe_num_images(self.ctx)
+
+    @property
+    def tile(self):
+        """(rows, columns) of the trial kernel's output tile."""
+        ty, tx = C.c_int(), C.c_int()
+        self._check(lib.fe_tile_size(self.ctx, C.byref(ty), C.byref(tx)))
+        return ty.value, tx.value
 
     # -- ABI calls -----------------------------------------------------
     def reset(self, f, u0=None):

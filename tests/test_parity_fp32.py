@@ -54,25 +54,31 @@ def _relmax(a, b):
 SIZES = [(64, 64), (8, 8), (131, 77), (200, 13), (13, 200), (67, 129), (128, 128)]
 
 
+TILES = [64, 32]  # both output-tile shapes of the FP32 kernel
+
+
+@pytest.mark.parametrize("tile", TILES)
 @pytest.mark.parametrize("shape", SIZES)
-def test_gradient_parity(fe, orc, bank, shape):
+def test_gradient_parity(fe, orc, bank, shape, tile):
     k, th = bank
     H, W = shape
     _, f = _problem(H, W, seed=H * 7 + W)
-    with fe.Solver([f], k, th) as s:
+    with fe.Solver([f], k, th, tile=tile) as s:
+        assert s.tile == (tile, tile)
         g, Fg = s.gradient(0, f)
     g_ref, F_ref = orc.gradF(f, k, th)
     assert _relmax(g, g_ref) <= GRAD_TOL
     assert Fg == pytest.approx(F_ref, rel=E_TOL)
 
 
+@pytest.mark.parametrize("tile", TILES)
 @pytest.mark.parametrize("shape", [(64, 64), (131, 77), (8, 9)])
-def test_energy_parity(fe, orc, bank, shape):
+def test_energy_parity(fe, orc, bank, shape, tile):
     k, th = bank
     H, W = shape
     u, f = _problem(H, W, seed=3)
     lam = 5.0
-    with fe.Solver([f], k, th, lam=lam) as s:
+    with fe.Solver([f], k, th, lam=lam, tile=tile) as s:
         E, F, G = s.energy(0, u)
         info = s.info(0)
     assert F == pytest.approx(orc.F(u, k, th), rel=E_TOL)
@@ -122,8 +128,9 @@ def _dd_tol(dd_ref, N, umax):
     return 2 * np.sqrt(dd_ref) * dD + dD * dD
 
 
+@pytest.mark.parametrize("tile", TILES)
 @pytest.mark.parametrize("shape,L0", [((64, 64), 1.0), ((131, 77), 1e-3), ((96, 200), 0.05)])
-def test_single_step_parity(fe, orc, bank, shape, L0):
+def test_single_step_parity(fe, orc, bank, shape, L0, tile):
     """After k GPU steps, one more GPU step vs the FP64 oracle started from
     the GPU's own state: same backtracking decisions (up to FP32 noise in the
     energy test) and the same u^{n+1} at the accepted L."""
@@ -131,7 +138,7 @@ def test_single_step_parity(fe, orc, bank, shape, L0):
     H, W = shape
     _, f = _problem(H, W, seed=11, kind="textured")
     prm = orc.params(lam=5.0, beta=0.8, L0=L0, eta=2.0, c2=1e-6, max_backtrack=30, max_iter=1)
-    with fe.Solver([f], k, th, lam=5.0, beta=0.8, L0=L0, eta=2.0, c2=1e-6) as s:
+    with fe.Solver([f], k, th, lam=5.0, beta=0.8, L0=L0, eta=2.0, c2=1e-6, tile=tile) as s:
         for nsteps in (0, 3, 10):
             if nsteps:
                 assert s.step(nsteps) == fe.FE_OK
@@ -147,7 +154,8 @@ def test_single_step_parity(fe, orc, bank, shape, L0):
                 ref["rec"][0, 7], H * W, np.max(np.abs(ref["u"])))
 
 
-def test_trajectory_64x64_100_iterations(fe, orc, bank):
+@pytest.mark.parametrize("tile", TILES)
+def test_trajectory_64x64_100_iterations(fe, orc, bank, tile):
     """64x64 piecewise image, L = 1 speckle, lambda = 5, 100 iterations.  The
     GPU's accepted L_n are replayed in the FP64 oracle (prescribed-L update);
     every GPU decision agrees with the oracle's FP64 test up to FP32 noise and
@@ -156,7 +164,7 @@ def test_trajectory_64x64_100_iterations(fe, orc, bank):
     _, f = _problem(64, 64, seed=0)
     prm = orc.params(lam=5.0, beta=0.8, L0=1.0, eta=2.0, c2=1e-6, max_iter=1)
     Ls, Hs, states = [], [], []
-    with fe.Solver([f], k, th, lam=5.0, L0=1.0) as s:
+    with fe.Solver([f], k, th, lam=5.0, L0=1.0, tile=tile) as s:
         L_prev = s.info(0)["L"]
         for n in range(100):
             u, up, _, _ = s.get_state(0)
@@ -207,16 +215,17 @@ def test_checkpoint_resume_bit_exact(fe, bank):
     assert ia["H"] == ib["H"] and ia["L"] == ib["L"] and ia["n"] == ib["n"] == 25
 
 
-def test_batch_of_uneven_images_matches_single(fe, orc, bank):
+@pytest.mark.parametrize("tile", TILES)
+def test_batch_of_uneven_images_matches_single(fe, orc, bank, tile):
     k, th = bank
     shapes = [(64, 64), (131, 77), (9, 300), (200, 150)]
     fs = [_problem(H, W, seed=20 + i)[1] for i, (H, W) in enumerate(shapes)]
-    with fe.Solver(fs, k, th, L0=1e-2) as s:
+    with fe.Solver(fs, k, th, L0=1e-2, tile=tile) as s:
         assert s.step(5) == fe.FE_OK
         ub = [s.get_u(i) for i in range(len(fs))]
         ib = [s.info(i) for i in range(len(fs))]
     for i, f in enumerate(fs):
-        with fe.Solver([f], k, th, L0=1e-2) as s1:
+        with fe.Solver([f], k, th, L0=1e-2, tile=tile) as s1:
             s1.step(5)
             assert np.array_equal(s1.get_u(0), ub[i])
             assert s1.info(0)["L"] == ib[i]["L"]
@@ -277,3 +286,28 @@ def test_gradient_parity_large_sampled(fe, orc, bank, shape):
     got = np.array([g[p] for p in pts], np.float64)
     scale = np.max(np.abs(ref))
     assert np.max(np.abs(got - ref)) <= GRAD_TOL * scale
+
+
+def test_tile_autotune_and_shapes(fe, bank):
+    """tile = 0 picks one of the two shapes and caches the choice per list of
+    image sizes; a forced tile is kept; the per-pixel arithmetic does not
+    depend on the tile, so gradients and one step agree bit for bit."""
+    k, th = bank
+    _, f = _problem(150, 97, seed=31, kind="textured")
+    with fe.Solver([f], k, th) as a:
+        ta = a.tile
+        assert ta in ((64, 64), (32, 32))
+        with fe.Solver([f], k, th) as b:
+            assert b.tile == ta  # cached
+    gs, us = [], []
+    for t in TILES:
+        with fe.Solver([f], k, th, L0=1e-2, beta=0.0, tile=t) as s:
+            assert s.tile == (t, t)
+            gs.append(s.gradient(0, f)[0])
+            assert s.step(1) == fe.FE_OK
+            us.append(s.get_u(0))
+    assert np.array_equal(gs[0], gs[1])
+    assert np.array_equal(us[0], us[1])
+    for bad in (16, 48, 128, -1):
+        with pytest.raises(fe.FeError):
+            fe.Solver([f], k, th, tile=bad)

@@ -175,3 +175,16 @@ def test_tc_gradient_parity_4096_sampled(fe, orc, bank, prec):
     ref = orc.gradF_at(f, kq, th, pts)
     got = np.array([g[p] for p in pts], np.float64)
     assert np.max(np.abs(got - ref)) <= GRAD_TOL[prec] * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_tc_single_tile_shape(fe, bank, prec):
+    """The tensor-core forms have one tile shape: tile = 0 gives it, any
+    other value is rejected before device work."""
+    k, th = bank
+    _, f = _problem(70, 90, seed=3)
+    with fe.Solver([f], k, th, prec=prec) as s:
+        assert s.tile == (58, 26)
+    for bad in (32, 64):
+        with pytest.raises(fe.FeError):
+            fe.Solver([f], k, th, prec=prec, tile=bad)

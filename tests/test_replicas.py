@@ -1,0 +1,68 @@
+"""Multi-GPU form = replicas: one process per GPU, each solving its own batch
+with no exchange on the data path; the job's time is the slowest rank's and
+its work the sum over ranks.  The host-side logic (rank aggregation, the
+reference arm's rank filter) runs here as world-size-2 gloo groups on CPU."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _combine_worker(rank, world, port, q):
+    import time
+
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
+    try:
+        # rank r: a replica that took 10 + 5 r ms for 100 (r + 1) units
+        dist.barrier()
+        t0 = time.perf_counter()
+        time.sleep(0.02 * rank)  # uneven ranks: the barrier below waits for the slowest
+        dist.barrier()
+        waited = time.perf_counter() - t0
+        T, U = bench.combine_ranks(10.0 + 5.0 * rank, 100.0 * (rank + 1), dist)
+        q.put((rank, T, U, waited))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_combine_ranks_gloo_world2():
+    torch = pytest.importorskip("torch")
+    mp = torch.multiprocessing.get_context("spawn")
+    q = mp.Queue()
+    port = _free_port()
+    procs = [mp.Process(target=_combine_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, T, U, waited in out:
+        assert T == 15.0          # MAX over ranks
+        assert U == 300.0         # SUM over ranks
+        assert waited >= 0.015    # both ranks left the barrier after the slow one arrived
+    # one rank: its own numbers
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.combine_ranks(7.0, 11.0, None) == (7.0, 11.0)
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
