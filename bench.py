@@ -508,7 +508,7 @@ def main():
                                            args.n512, args.n256, args.iters, args.prec.upper()),
                            "images": len(fs), "pixels": npix, "iters": args.iters, "precision": args.prec,
                            "loop": "cuda-graph while node" if args.loop_mode == 1 else "host chunks",
-                           "tile": "%dx%d (autotuned)" % tile,
+                           "tile": "%dx%d (%s)" % (tile + ("autotuned" if args.prec == "fp32" else "fixed",)),
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "256 MiB buffer written between timed steps; state 6 planes x "
                                  "%.0f MB" % (npix * 4 / 1e6)},

@@ -226,7 +226,10 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
 
     if (active) {
         // ---- 1+2: inertial step and prox on tile + 6 ---------------------
-        double accF = 0.0, accG = 0.0, accGD = 0.0, accDD = 0.0, accDP = 0.0;
+        // per-thread sums: compensated FP32 for F and G (large terms), plain
+        // FP32 for the small step-test terms
+        Sum2 accF{0.f, 0.f}, accG{0.f, 0.f};
+        float accGD = 0.f, accDD = 0.f, accDP = 0.f;
         {
             int cur = 0, gcur = 0;
             float a = 0.f, b = 0.f, tl = 0.f;
@@ -258,14 +261,14 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
                     if (inner) {
                         un[off] = v;
                         const float d = v - u0;
-                        accGD += (double)(g0 * d);
-                        accDD += (double)(d * d);
-                        accDP += (double)(d * dprev);
-                        accG += (double)(v * v - 2.0f * f2 * logf(v));
+                        accGD = fmaf(g0, d, accGD);
+                        accDD = fmaf(d, d, accDD);
+                        accDP = fmaf(d, dprev, accDP);
+                        sum2_add(accG, v * v - 2.0f * f2 * logf(v));
                     }
                 } else {
                     v = __ldg(uc + off);
-                    if (inner) accG += (double)(v * v - 2.0f * __ldg(f2p + off) * logf(v));
+                    if (inner) sum2_add(accG, v * v - 2.0f * __ldg(f2p + off) * logf(v));
                 }
                 sU[ry * SU_LD + rx] = v;
             }
@@ -291,7 +294,7 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
                 const bool full = x >= 0 && x < W && ylo >= 0 && ylo + FWD_ROWS <= H;
                 const float fs = full ? forward_unit<T, MODE, false>(sU, sR, p.wf, p.theta, grp, c, rb, y0, x0, H, W)
                                       : forward_unit<T, MODE, true>(sU, sR, p.wf, p.theta, grp, c, rb, y0, x0, H, W);
-                accF += (double)fs;
+                sum2_add(accF, fs);
             }
             if (MODE == MODE_ENERGY_EXT) continue;
             __syncthreads();  // sR complete
@@ -403,7 +406,7 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
         }
 
         // ---- 6: per-tile FP64 partial sums, last-CTA decision -------------
-        const double vals[NRED] = {accF, accG, accGD, accDD, accDP};
+        const Sum2 vals[NRED] = {accF, accG, {accGD, 0.f}, {accDD, 0.f}, {accDP, 0.f}};
         tile_finish<NT>(p, MODE, gtile, img, im, st, vals, sRed, &sLast);
     }
 

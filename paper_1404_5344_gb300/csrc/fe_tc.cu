@@ -195,7 +195,10 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
         if (warp == 0) tc::tmem_alloc(&tbase, TMEM_COLS);
 
         // ---- inertial step and prox on tile + 6 (owned pixels: sums) -------
-        double accF = 0.0, accG = 0.0, accGD = 0.0, accDD = 0.0, accDP = 0.0;
+        // per-thread sums: compensated FP32 for F and G (large terms), plain
+        // FP32 for the small step-test terms
+        Sum2 accF{0.f, 0.f}, accG{0.f, 0.f};
+        float accGD = 0.f, accDD = 0.f, accDP = 0.f;
         {
             int cur = 0, gcur = 0;
             float a = 0.f, b = 0.f, tl = 0.f;
@@ -242,14 +245,14 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
                         if (owned[k]) {
                             un[off[k]] = v;
                             const float d = v - u0[k];
-                            accGD += (double)(g0[k] * d);
-                            accDD += (double)(d * d);
-                            accDP += (double)(d * dprev);
+                            accGD = fmaf(g0[k], d, accGD);
+                            accDD = fmaf(d, d, accDD);
+                            accDP = fmaf(d, dprev, accDP);
                         }
                     } else {
                         v = u0[k];
                     }
-                    if (owned[k]) accG += (double)(v * v - 2.0f * f2[k] * logf(v));
+                    if (owned[k]) sum2_add(accG, v * v - 2.0f * f2[k] * logf(v));
                     sU[base + k * NT + tid] = v;  // R6 row-major with pitch SU_LD = R6X
                 }
             }
@@ -374,7 +377,7 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
 #pragma unroll
                     for (int i = 0; i < 24; ++i) r[i] = 0.0f;
                 }
-                if (owned) accF += (double)(psum * LN2);
+                if (owned) sum2_add(accF, psum * LN2);
                 unsigned char *rowp = sR + tc::kmajor_offset((lg << 5) + lane, 0, KADJ, C::EB);
 #pragma unroll
                 for (int j = 0; j < 24 / C::E; ++j) {
@@ -457,10 +460,10 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
             }
         }
         if (!tc_ok) {
-            accF = __longlong_as_double(0x7ff8000000000000LL);  // NaN: the image stops
+            accF.s = __int_as_float(0x7fc00000);  // NaN: the image stops
             if (tid == 0) atomicExch(p.tc_error, 1);
         }
-        const double vals[NRED] = {accF, accG, accGD, accDD, accDP};
+        const Sum2 vals[NRED] = {accF, accG, {accGD, 0.f}, {accDD, 0.f}, {accDP, 0.f}};
         tile_finish<NT>(p, MODE, gtile, img, im, st, vals, sRed, &sLast);
     }
     if (MODE == MODE_TRIAL) loop_control(p);

@@ -35,6 +35,34 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Compensated FP32 sum s + c (TwoSum, Knuth): c collects the exact rounding
+// error of every addition, so a thread's partial sum keeps about twice the
+// FP32 precision without FP64 instructions (FP64 issues at about 2 lanes per
+// clock per SM on this GPU, 64x below FP32).  Per-thread and per-warp sums
+// use it; the per-warp results are combined in FP64.
+struct Sum2 {
+    float s, c;
+};
+__device__ __forceinline__ void sum2_add(Sum2 &a, float x) {
+    const float t = a.s + x;
+    const float bp = t - a.s;
+    a.c += (a.s - (t - bp)) + (x - bp);
+    a.s = t;
+}
+__device__ __forceinline__ Sum2 sum2_merge(Sum2 a, Sum2 b) {
+    const float t = a.s + b.s;
+    const float bp = t - a.s;
+    return Sum2{t, (a.c + b.c) + ((a.s - (t - bp)) + (b.s - bp))};
+}
+__device__ __forceinline__ Sum2 warp_sum2(Sum2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const Sum2 w{__shfl_xor_sync(0xffffffffu, v.s, o), __shfl_xor_sync(0xffffffffu, v.c, o)};
+        v = sum2_merge(v, w);
+    }
+    return v;
+}
+
 // Position p in [0, T+6) of the frame/tile grid along one axis -> image
 // coordinate j; returns whether that position belongs to this tile (main
 // rows inside the image, or frame rows whose mirror image lies in the tile).
@@ -107,19 +135,21 @@ __device__ void decide(const KParams &p, ImgState *st, const double *t, int mode
     }
 }
 
-// Per-tile FP64 partial sums -> partials[gtile]; the last CTA of the image
-// reduces the image's partials in a fixed order (so the result does not
-// depend on which CTA finishes last) and applies the decision (TRIAL/INIT)
-// or stores F, G (EXT modes).  sRed: NT/32 * NRED doubles of shared memory.
+// Per-tile partial sums -> partials[gtile] (FP64): each thread's compensated
+// FP32 sums are reduced per warp, the warps' results in FP64.  The last CTA
+// of the image reduces the image's partials in FP64 in a fixed order (so the
+// result does not depend on which CTA finishes last) and applies the
+// decision (TRIAL/INIT) or stores F, G (EXT modes).  sRed: NT/32 * NRED
+// doubles of shared memory.
 template <int NT>
 __device__ void tile_finish(const KParams &p, int mode, int gtile, int img, const ImgDesc &im, ImgState *st,
-                            const double (&vals)[NRED], double *sRed, int *sLast) {
+                            const Sum2 (&vals)[NRED], double *sRed, int *sLast) {
     constexpr int NWARP = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int k = 0; k < NRED; ++k) {
-        const double v = warp_sum(vals[k]);
-        if (lane == 0) sRed[warp * NRED + k] = v;
+        const Sum2 v = warp_sum2(vals[k]);
+        if (lane == 0) sRed[warp * NRED + k] = (double)v.s + (double)v.c;
     }
     __syncthreads();
     if (tid < NRED) {
@@ -136,23 +166,27 @@ __device__ void tile_finish(const KParams &p, int mode, int gtile, int img, cons
     __syncthreads();
     if (*sLast) {
         __threadfence();
-        double part[NRED];
+        // only the warps that hold partials reduce (FP64 issue is scarce)
+        const int nw = min(NWARP, (im.ntiles + 31) / 32);
+        if (warp < nw) {
+            double part[NRED];
 #pragma unroll
-        for (int k = 0; k < NRED; ++k) part[k] = 0.0;
-        for (int t = tid; t < im.ntiles; t += NT)
+            for (int k = 0; k < NRED; ++k) part[k] = 0.0;
+            for (int t = tid; t < im.ntiles; t += nw * 32)
 #pragma unroll
-            for (int k = 0; k < NRED; ++k) part[k] += __ldcg(p.partials + (size_t)(im.tile_begin + t) * NRED + k);
+                for (int k = 0; k < NRED; ++k) part[k] += __ldcg(p.partials + (size_t)(im.tile_begin + t) * NRED + k);
 #pragma unroll
-        for (int k = 0; k < NRED; ++k) {
-            const double v = warp_sum(part[k]);
-            if (lane == 0) sRed[warp * NRED + k] = v;
+            for (int k = 0; k < NRED; ++k) {
+                const double v = warp_sum(part[k]);
+                if (lane == 0) sRed[warp * NRED + k] = v;
+            }
         }
         __syncthreads();
         if (tid == 0) {
             double tot[NRED];
             for (int k = 0; k < NRED; ++k) {
                 double s = 0.0;
-                for (int w = 0; w < NWARP; ++w) s += sRed[w * NRED + k];
+                for (int w = 0; w < nw; ++w) s += sRed[w * NRED + k];
                 tot[k] = s;
             }
             tot[1] *= 0.5 * im.lambda;  // G = (lambda/2) sum_p (u^2 - 2 f^2 log u)
