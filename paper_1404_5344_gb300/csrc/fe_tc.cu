@@ -6,9 +6,11 @@
 // 5th-generation tensor cores (tcgen05.mma, FP32 accumulation in tensor
 // memory):
 //
-//   forward  Z[q, i] = sum_t A[q, t] Bf[i, t]: A = im2col of u^{n+1} (49 taps
-//            of the 7x7 window of pixel q), Bf = flipped filters.  One GEMM of
-//            M = 128 pixels, N = 48 filters.
+//   forward  Z[q, i] = sum_k A[q, k] Bf[i, k]: A = im2col of u^{n+1}, K index
+//            k = 8a + b for the window row a and column b of pixel q (b = 7 is
+//            a padding tap of weight 0, so that one kernel row is 8
+//            consecutive pixels of one row of u), Bf = flipped filters.  One
+//            GEMM of M = 128 pixels, N = 48 filters.
 //   adjoint  S[q, t] = sum_i R[q, i] Ba[t, i]: R = r_i(q) = theta_i rho'(z_i),
 //            Ba[t, i] = k_i[t].  M = 128 pixels, N = 64 (49 taps + zeros).
 //            K_i^T r = sum_t shift_t(S[:, t]) (col2im): the horizontal part is a
@@ -17,8 +19,12 @@
 //
 // Precision form: the filter bank is rounded once to the operand type (the
 // bank of the form); the data operands u and r are each carried as a hi + lo
-// pair of that type (K doubles), so z and S are accurate for the rounded bank
-// and the descent test sees a consistent gradient.
+// pair of that type (K doubles; the B operand is stored once and the MMAs of
+// the lo half re-read it), so z and S are accurate for the rounded bank and
+// the descent test sees a consistent gradient.  The prologue writes u^{n+1}
+// as hi and lo planes of the operand type (BF16: plus copies shifted by one
+// element, so that every 8-pixel run starts on a 4-byte boundary); the
+// im2col is then a copy of 4-byte words.
 //
 // Geometry: 26 x 58 output tile; tile + 3-pixel halo = 32 x 64 pixels = 16
 // GEMM blocks of 4 rows x 32 columns (M = 128); tile + 6 = 38 x 70 for u^{n+1}.
@@ -45,7 +51,7 @@ namespace {
 constexpr int TY = tc_tile_y, TX = tc_tile_x, NT = 256;
 constexpr int R3Y = TY + 6, R3X = TX + 6;    // 64 x 32
 constexpr int R6Y = TY + 12, R6X = TX + 12;  // 70 x 38
-constexpr int SU_LD = R6X;
+constexpr int PP = 40;  // plane pitch (elements): R6X + 2 zero columns read by the padding tap
 constexpr int NBLK = R3Y / 4;                // 16 GEMM blocks of 128 pixels
 constexpr int NF = 48;                       // N of the forward GEMM
 constexpr int NTAP = 64;                     // N of the adjoint GEMM (49 taps + zeros)
@@ -59,25 +65,32 @@ template <int FMT>
 struct Cfg {
     static constexpr int EB = FMT == 1 ? 2 : 4;            // operand bytes
     static constexpr int KSTEP = FMT == 1 ? 16 : 8;        // K per MMA
-    static constexpr int KPASS = FMT == 1 ? 64 : 56;       // 49 taps padded to KSTEP
+    static constexpr int KPASS = FMT == 1 ? 64 : 56;       // 7 rows x 8 taps, padded to KSTEP
     static constexpr int KFWD = 2 * KPASS;                 // u hi | u lo
     static constexpr int E = 16 / EB;                      // elements per 16-byte chunk
     static constexpr int NCH = KPASS / E;                  // chunks per pass
+    static constexpr int RCH = 8 / E;                      // chunks per kernel row
+    static constexpr int NPL = FMT == 1 ? 4 : 2;           // planes: hi, (hi shifted,) lo, (lo shifted)
+    // plane stride in 4-byte words; BF16: = 16 (mod 32) so that the even and
+    // odd lanes of the im2col (unshifted / shifted copy) use disjoint banks
+    static constexpr int PL_WORDS = FMT == 1 ? 1424 : R6Y * PP;
+    static_assert(PL_WORDS * 4 >= R6Y * PP * EB, "plane holds the u region");
     static constexpr size_t AF_BYTES = (size_t)128 * KFWD * EB;
     static constexpr size_t R_BYTES = (size_t)128 * KADJ * EB;
-    static constexpr size_t BF_BYTES = (size_t)NF * KFWD * EB;
-    static constexpr size_t BA_BYTES = (size_t)NTAP * KADJ * EB;
+    static constexpr size_t BF_BYTES = (size_t)NF * KPASS * EB;   // one pass: hi and lo MMAs share it
+    static constexpr size_t BA_BYTES = (size_t)NTAP * NF * EB;    // likewise for r hi and r lo
     static constexpr size_t OFF_AF = 0;
     static constexpr size_t OFF_R = OFF_AF + AF_BYTES;
     static constexpr size_t OFF_BF = OFF_R + R_BYTES;
     static constexpr size_t OFF_BA = OFF_BF + BF_BYTES;
-    static constexpr size_t OFF_U = OFF_BA + BA_BYTES;
-    static constexpr size_t OFF_H = OFF_U + (size_t)R6Y * SU_LD * 4;
+    static constexpr size_t OFF_U = OFF_BA + BA_BYTES;       // NPL planes of u^{n+1}
+    static constexpr size_t OFF_H = OFF_U + (size_t)NPL * PL_WORDS * 4;
     static constexpr size_t OFF_G = OFF_H + (size_t)HRING * 7 * 32 * 4;
     static constexpr size_t OFF_TH = OFF_G + (size_t)R3Y * R3X * 4;
     static constexpr size_t OFF_RED = OFF_TH + (size_t)2 * NF * 4;
     static constexpr size_t BYTES = OFF_RED + (size_t)(NT / 32) * NRED * 8;
-    static_assert(OFF_R % 128 == 0 && OFF_BF % 128 == 0 && OFF_BA % 128 == 0, "operand alignment");
+    static_assert(OFF_R % 128 == 0 && OFF_BF % 128 == 0 && OFF_BA % 128 == 0 && OFF_U % 128 == 0,
+                  "operand alignment");
     static_assert(OFF_U % 16 == 0 && OFF_TH % 16 == 0 && OFF_RED % 8 == 0, "alignment");
     static_assert(BF_BYTES % 16 == 0 && BA_BYTES % 16 == 0, "vector copies");
 };
@@ -117,30 +130,30 @@ __device__ __forceinline__ void hilo_chunk<2>(const float *v, uint4 &hi, uint4 &
 }
 
 // im2col of u^{n+1} for GEMM block blk: pixel m of the block (R3 row 4 blk +
-// m/32, column m%32) gets the 49 taps of its 7x7 window as K values, hi in
-// chunks [0, NCH) and lo in [NCH, 2 NCH).  The two threads of a pixel take
-// the even / odd chunks.
+// m/32, column pc = m%32) gets, for window row a, the 8 values u(4 blk + m/32
+// + a, pc .. pc + 7) as K values 8a .. 8a + 7 (hi part in chunks [0, NCH), lo
+// in [NCH, 2 NCH)).  part 0 copies the hi plane, part 1 the lo plane.  The
+// runs are copied as 4-byte words: BF16 reads the unshifted plane at even pc
+// and the copy shifted by one element at odd pc.
 template <int FMT>
-__device__ __forceinline__ void im2col(const float *__restrict__ sU, unsigned char *__restrict__ sAF, int blk,
+__device__ __forceinline__ void im2col(const uint32_t *__restrict__ sP, unsigned char *__restrict__ sAF, int blk,
                                        int m, int part) {
     using C = Cfg<FMT>;
     const int pr = 4 * blk + (m >> 5), pc = m & 31;
-    const float *win = sU + pr * SU_LD + pc;
-    unsigned char *row = sAF + tc::kmajor_offset(m, 0, C::KFWD, C::EB);
+    const uint32_t *src;
+    if (FMT == 1)
+        src = sP + (2 * part + (pc & 1)) * C::PL_WORDS + pr * (PP / 2) + (pc >> 1);
+    else
+        src = sP + part * C::PL_WORDS + pr * PP + pc;
+    constexpr int ROW_WORDS = PP * C::EB / 4;
+    unsigned char *row = sAF + tc::kmajor_offset(m, 0, C::KFWD, C::EB) + part * C::NCH * 128;
 #pragma unroll
-    for (int c = 0; c < C::NCH; ++c) {
-        if ((c & 1) != part) continue;
-        float v[C::E];
+    for (int a = 0; a < KS; ++a)
 #pragma unroll
-        for (int j = 0; j < C::E; ++j) {
-            const int t = c * C::E + j;
-            v[j] = t < KT ? win[(t / KS) * SU_LD + (t % KS)] : 0.0f;
+        for (int h = 0; h < C::RCH; ++h) {
+            const uint32_t *w = src + a * ROW_WORDS + h * 4;
+            *reinterpret_cast<uint4 *>(row + (a * C::RCH + h) * 128) = make_uint4(w[0], w[1], w[2], w[3]);
         }
-        uint4 hi, lo;
-        hilo_chunk<FMT>(v, hi, lo);
-        *reinterpret_cast<uint4 *>(row + c * 128) = hi;
-        *reinterpret_cast<uint4 *>(row + (C::NCH + c) * 128) = lo;
-    }
 }
 
 template <int MODE, int FMT>
@@ -151,7 +164,7 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
     unsigned char *sR = smem + C::OFF_R;
     unsigned char *sBf = smem + C::OFF_BF;
     unsigned char *sBa = smem + C::OFF_BA;
-    float *sU = reinterpret_cast<float *>(smem + C::OFF_U);
+    uint32_t *sP = reinterpret_cast<uint32_t *>(smem + C::OFF_U);  // u^{n+1} planes
     float *sH = reinterpret_cast<float *>(smem + C::OFF_H);
     float *sG = reinterpret_cast<float *>(smem + C::OFF_G);
     float *sTh = reinterpret_cast<float *>(smem + C::OFF_TH);  // theta_i, then 2 theta_i
@@ -187,7 +200,22 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
                 sTh[tid] = th;
                 sTh[NF + tid] = 2.0f * th;
             }
+            // BF16: the last K chunk of each pass (window row 7) is zero in A
+            if (FMT == 1 && tid < 2 * 128) {
+                const int mm = tid & 127, pt = tid >> 7;
+                *reinterpret_cast<uint4 *>(sAF + tc::kmajor_offset(mm, 0, C::KFWD, C::EB) +
+                                           (pt * C::NCH + C::NCH - 1) * 128) = make_uint4(0u, 0u, 0u, 0u);
+            }
+            // the padding columns of the planes (read with weight 0) hold zeros
+            for (int j = tid; j < C::NPL * R6Y; j += NT) {
+                uint32_t *rowp = sP + (j / R6Y) * C::PL_WORDS + (j % R6Y) * (PP * C::EB / 4);
+                if (FMT == 1)
+                    rowp[(PP / 2) - 2] = rowp[(PP / 2) - 1] = 0u;  // elements 36..39 (the writes below fill 36, 37)
+                else
+                    rowp[PP - 2] = rowp[PP - 1] = 0u;
+            }
         }
+        __syncthreads();  // pad zeros before the plane writes of the prologue
         if (tid == 0) {
             tc::mbar_init(&bar_f, 1);
             tc::mbar_init(&bar_a, 1);
@@ -253,15 +281,35 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
                         v = u0[k];
                     }
                     if (owned[k]) sum2_add(accG, v * v - 2.0f * f2[k] * logf(v));
-                    sU[base + k * NT + tid] = v;  // R6 row-major with pitch SU_LD = R6X
+                    // hi / lo planes of the operand type
+                    const int idx = base + k * NT + tid, ry = idx / R6X, rx = idx - ry * R6X;
+                    if (FMT == 1) {
+                        const __nv_bfloat16 hb = __float2bfloat16_rn(v);
+                        const __nv_bfloat16 lb = __float2bfloat16_rn(v - __bfloat162float(hb));
+                        __nv_bfloat16 *ph = reinterpret_cast<__nv_bfloat16 *>(sP);
+                        __nv_bfloat16 *pl = reinterpret_cast<__nv_bfloat16 *>(sP + 2 * C::PL_WORDS);
+                        const int e = ry * PP + rx;
+                        ph[e] = hb;
+                        pl[e] = lb;
+                        if (rx > 0) {  // shifted copies: element rx - 1 holds column rx
+                            ph[2 * C::PL_WORDS + e - 1] = hb;
+                            pl[2 * C::PL_WORDS + e - 1] = lb;
+                        }
+                    } else {
+                        const float hv = tc::round_tf32(v);
+                        const int e = ry * PP + rx;
+                        sP[e] = __float_as_uint(hv);
+                        sP[C::PL_WORDS + e] = __float_as_uint(tc::round_tf32(v - hv));
+                    }
                 }
             }
         }
-        static_assert(SU_LD == R6X, "prologue stores the R6 region with pitch R6X");
 
         const uint32_t sAF_u32 = tc::smem_u32(sAF), sR_u32 = tc::smem_u32(sR);
         const uint32_t sBf_u32 = tc::smem_u32(sBf), sBa_u32 = tc::smem_u32(sBa);
         constexpr uint32_t SBO_F = (uint32_t)(C::KFWD / C::E) * 128, SBO_A = (uint32_t)(KADJ / C::E) * 128;
+        constexpr uint32_t SBO_BF = (uint32_t)(C::KPASS / C::E) * 128, SBO_BA = (uint32_t)(NF / C::E) * 128;
+        constexpr int KS_F = C::KPASS / C::KSTEP, KS_A = NF / C::KSTEP;  // K steps of one pass
         constexpr uint32_t IDESC_F = tc::make_idesc(FMT, 128, NF), IDESC_A = tc::make_idesc(FMT, 128, NTAP);
         const int m = tid & 127, part = tid >> 7;  // im2col: pixel, chunk parity
         const int wg = warp >> 2, lg = warp & 3;   // epilogues: column half, TMEM lane group
@@ -270,7 +318,7 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
         const bool all_in = full_y && full_x;  // every halo pixel lies in the image
 
         // block 0: im2col and forward MMA
-        im2col<FMT>(sU, sAF, 0, m, part);
+        im2col<FMT>(sP, sAF, 0, m, part);
         tc::fence_proxy_async();
         tc::fence_before_sync();
         __syncthreads();
@@ -281,7 +329,8 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
 #pragma unroll
             for (int ks = 0; ks < C::KFWD / C::KSTEP; ++ks)
                 tc::mma<FMT>(taddr, tc::make_smem_desc(sAF_u32 + ks * 256, 128, SBO_F),
-                             tc::make_smem_desc(sBf_u32 + ks * 256, 128, SBO_F), IDESC_F, ks > 0 ? 1u : 0u);
+                             tc::make_smem_desc(sBf_u32 + (ks % KS_F) * 256, 128, SBO_BF), IDESC_F,
+                             ks > 0 ? 1u : 0u);
             tc::mma_commit(&bar_f);
         }
         uint32_t phase_f = 0, phase_a = 0;
@@ -395,12 +444,13 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
 #pragma unroll
                 for (int ks = 0; ks < KADJ / C::KSTEP; ++ks)
                     tc::mma<FMT>(taddr + 64, tc::make_smem_desc(sR_u32 + ks * 256, 128, SBO_A),
-                                 tc::make_smem_desc(sBa_u32 + ks * 256, 128, SBO_A), IDESC_A, ks > 0 ? 1u : 0u);
+                                 tc::make_smem_desc(sBa_u32 + (ks % KS_A) * 256, 128, SBO_BA), IDESC_A,
+                                 ks > 0 ? 1u : 0u);
                 tc::mma_commit(&bar_a);
             }
             // (c) im2col of the next block, overlapping MMA_adj(blk)
             if (blk + 1 < NBLK) {
-                im2col<FMT>(sU, sAF, blk + 1, m, part);
+                im2col<FMT>(sP, sAF, blk + 1, m, part);
                 tc::fence_proxy_async();
                 tc::fence_before_sync();
                 __syncthreads();
@@ -409,7 +459,8 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
 #pragma unroll
                     for (int ks = 0; ks < C::KFWD / C::KSTEP; ++ks)
                         tc::mma<FMT>(taddr, tc::make_smem_desc(sAF_u32 + ks * 256, 128, SBO_F),
-                                     tc::make_smem_desc(sBf_u32 + ks * 256, 128, SBO_F), IDESC_F, ks > 0 ? 1u : 0u);
+                                     tc::make_smem_desc(sBf_u32 + (ks % KS_F) * 256, 128, SBO_BF), IDESC_F,
+                                     ks > 0 ? 1u : 0u);
                     tc::mma_commit(&bar_f);
                 }
             }
@@ -522,9 +573,9 @@ float tc_round(int fmt, float x) {
 
 void tc_build_weights(int fmt, const float *filters, int nf, std::vector<unsigned char> &fwd,
                       std::vector<unsigned char> &adj) {
-    const int eb = fmt == 1 ? 2 : 4, kpass = fmt == 1 ? 64 : 56, kfwd = 2 * kpass;
-    fwd.assign((size_t)NF * kfwd * eb, 0);
-    adj.assign((size_t)NTAP * KADJ * eb, 0);
+    const int eb = fmt == 1 ? 2 : 4, kpass = fmt == 1 ? 64 : 56;
+    fwd.assign((size_t)NF * kpass * eb, 0);
+    adj.assign((size_t)NTAP * NF * eb, 0);
     auto put = [&](std::vector<unsigned char> &buf, int r, int k, int K, float v) {
         const uint32_t off = tc::kmajor_offset(r, k, K, eb);
         const uint32_t bits = f2u(tc_round(fmt, v));
@@ -537,15 +588,12 @@ void tc_build_weights(int fmt, const float *filters, int nf, std::vector<unsigne
     };
     for (int i = 0; i < nf && i < NF; ++i)
         for (int t = 0; t < KT; ++t) {
-            // forward: im2col tap t = 7a + b reads u(p + (a, b)) of the window, i.e.
-            // correlation with the flipped filter; the same taps for u hi and u lo
-            const float kf = filters[(size_t)i * KT + (KT - 1 - t)];
-            put(fwd, i, t, kfwd, kf);
-            put(fwd, i, kpass + t, kfwd, kf);
-            // adjoint: S[q, t] = sum_i k_i[t] r_i(q), for r hi and r lo
-            const float ka = filters[(size_t)i * KT + t];
-            put(adj, t, i, KADJ, ka);
-            put(adj, t, NF + i, KADJ, ka);
+            // forward: K index 8a + b reads u(p + (a, b)) of the window, i.e.
+            // correlation with the flipped filter (index 8a + 7 stays 0)
+            const int a = t / KS, b = t % KS;
+            put(fwd, i, 8 * a + b, kpass, filters[(size_t)i * KT + (KT - 1 - t)]);
+            // adjoint: S[q, t] = sum_i k_i[t] r_i(q)
+            put(adj, t, i, NF, filters[(size_t)i * KT + t]);
         }
 }
 
