@@ -385,19 +385,17 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
                         if (x >= W) continue;
                         float gv = acc[pp][q];
                         if (border && (y < 3 || y >= H - 3 || x < 3 || x >= W - 3)) {
-                            // frame positions that the symmetric extension maps onto (y, x)
-                            int py[3], px[3], ny = 1, nx = 1;
-                            py[0] = y - y0 + 3;
-                            px[0] = x - x0 + 3;
-                            if (y < 3) py[ny++] = 2 - y;                // j = -y-1
-                            if (y >= H - 3) py[ny++] = TY + 2 + H - y;  // j = 2H-1-y
-                            if (x < 3) px[nx++] = 2 - x;
-                            if (x >= W - 3) px[nx++] = TX + 2 + W - x;
-                            for (int m = 0; m < ny; ++m)
-                                for (int n = 0; n < nx; ++n) {
-                                    if (m == 0 && n == 0) continue;
-                                    gv += sR[pos_to_ring<T>(py[m], px[n])];
-                                }
+                            // frame positions that the symmetric extension maps onto
+                            // (y, x): at most one per axis (H, W >= 8); scalars, so
+                            // that nothing is indexed dynamically (local memory)
+                            const int oy = y - y0 + 3, ox = x - x0 + 3;
+                            const int qy = y < 3 ? 2 - y : (y >= H - 3 ? TY + 2 + H - y : -1);  // j = -y-1 | 2H-1-y
+                            const int qx = x < 3 ? 2 - x : (x >= W - 3 ? TX + 2 + W - x : -1);
+                            if (qx >= 0) gv += sR[pos_to_ring<T>(oy, qx)];
+                            if (qy >= 0) {
+                                gv += sR[pos_to_ring<T>(qy, ox)];
+                                if (qx >= 0) gv += sR[pos_to_ring<T>(qy, qx)];
+                            }
                         }
                         gout[(size_t)y * W + x] = gv;
                     }

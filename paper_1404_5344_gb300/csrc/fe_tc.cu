@@ -493,19 +493,17 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
                 const int y = y0 + ty, x = x0 + tx;
                 float gv = sG[(ty + 3) * 32 + tx + 3];
                 if (y < 3 || y >= H - 3 || x < 3 || x >= W - 3) {
-                    // ext positions the symmetric extension maps onto (y, x)
-                    int ey[3], ex[3], ny = 1, nx = 1;
-                    ey[0] = ty + 3;
-                    ex[0] = tx + 3;
-                    if (y < 3) ey[ny++] = (-y - 1) - y0 + 3;
-                    if (y >= H - 3) ey[ny++] = (2 * H - 1 - y) - y0 + 3;
-                    if (x < 3) ex[nx++] = (-x - 1) - x0 + 3;
-                    if (x >= W - 3) ex[nx++] = (2 * W - 1 - x) - x0 + 3;
-                    for (int mm = 0; mm < ny; ++mm)
-                        for (int nn = 0; nn < nx; ++nn) {
-                            if (mm == 0 && nn == 0) continue;
-                            gv += sG[ey[mm] * 32 + ex[nn]];
-                        }
+                    // ext positions the symmetric extension maps onto (y, x): at
+                    // most one per axis (H, W >= 8); scalars, so that nothing is
+                    // indexed dynamically (local memory)
+                    const int oy = ty + 3, ox = tx + 3;
+                    const int qy = y < 3 ? (-y - 1) - y0 + 3 : (y >= H - 3 ? (2 * H - 1 - y) - y0 + 3 : -1);
+                    const int qx = x < 3 ? (-x - 1) - x0 + 3 : (x >= W - 3 ? (2 * W - 1 - x) - x0 + 3 : -1);
+                    if (qx >= 0) gv += sG[oy * 32 + qx];
+                    if (qy >= 0) {
+                        gv += sG[qy * 32 + ox];
+                        if (qx >= 0) gv += sG[qy * 32 + qx];
+                    }
                 }
                 gout[(size_t)y * W + x] = gv;
             }
