@@ -16,6 +16,10 @@ float64.  Citations are to the paper's sections and equations:
 * ``prox``              - closed-form proximal map (Sec. II-C, variant model)
 * ``ipiano``/``ipiano_step`` - the inertial forward-backward iteration
                           (Sec. II-C) with Lipschitz backtracking
+* ``Fw``, ``gradFw``, ``Gc``, ``proxc`` - the combined model (Eq. newmodel,
+                          Sec. III-A) in w = log u: F(e^w), e^w (.) grad F(e^w),
+                          its data term, and the prox by Newton's method;
+                          lambda2 = 0 is Eq. original (Sec. II-C)
 
 Parity: every function here is pinned by the ``-m "not gpu"`` tests
 (tests/test_oracle_*.py) against closed forms, library routines, dense brute
@@ -56,10 +60,14 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+MODEL_VARIANT, MODEL_COMBINED = 0, 1
+
+
 class OrcParams(C.Structure):
     _fields_ = [("lambda_", C.c_double), ("beta", C.c_double), ("L0", C.c_double),
                 ("eta", C.c_double), ("c2", C.c_double), ("max_backtrack", C.c_int),
-                ("max_iter", C.c_int), ("tol", C.c_double)]
+                ("max_iter", C.c_int), ("tol", C.c_double), ("model", C.c_int),
+                ("lambda1", C.c_double)]
 
 
 _D = C.POINTER(C.c_double)
@@ -95,6 +103,14 @@ def lib():
             for n in ("orc_prox", "orc_prox_literal"):
                 getattr(L, n).restype = C.c_double
                 getattr(L, n).argtypes = [C.c_double] * 4
+            L.orc_Fw.restype = C.c_double
+            L.orc_Fw.argtypes = [_D, C.c_int, C.c_int, _D, _D, C.c_int, C.c_int]
+            L.orc_gradFw.restype = C.c_double
+            L.orc_gradFw.argtypes = [_D, C.c_int, C.c_int, _D, _D, C.c_int, C.c_int, _D]
+            L.orc_Gc.restype = C.c_double
+            L.orc_Gc.argtypes = [_D, _D, C.c_long, C.c_double, C.c_double]
+            L.orc_proxc.restype = C.c_double
+            L.orc_proxc.argtypes = [C.c_double] * 5
             L.orc_ipiano.restype = C.c_int
             L.orc_ipiano.argtypes = [_D, C.c_int, C.c_int, _D, _D, C.c_int, C.c_int,
                                      C.POINTER(OrcParams), _D, _D, _D,
@@ -238,19 +254,54 @@ def prox_array(uhat, f, tau, lam):
                      for a, b in zip(uhat.ravel(), f.ravel())]).reshape(uhat.shape)
 
 
+def Fw(w, filters, theta):
+    """F(e^w) of the combined model."""
+    w = _d(w)
+    k, th, nf, ks = _bank(filters, theta)
+    H, W = w.shape
+    return lib().orc_Fw(_p(w), H, W, _p(k), _p(th), nf, ks)
+
+
+def gradFw(w, filters, theta):
+    """Returns (grad_w F(e^w) = e^w (.) grad F(e^w), F(e^w))."""
+    w = _d(w)
+    k, th, nf, ks = _bank(filters, theta)
+    H, W = w.shape
+    g = np.empty((H, W))
+    Fv = lib().orc_gradFw(_p(w), H, W, _p(k), _p(th), nf, ks, _p(g))
+    return g, Fv
+
+
+def Gc(w, f, lam1: float, lam2: float):
+    """sum_p lam1/2 (2w + f^2 e^{-2w}) + lam2/2 (e^{2w} - 2 f^2 w)."""
+    w, f = _d(w), _d(f)
+    return lib().orc_Gc(_p(w), _p(f), w.size, float(lam1), float(lam2))
+
+
+def proxc(what, f, tau, lam1, lam2):
+    """Prox of tau*G of the combined model at one pixel (Newton's method)."""
+    return lib().orc_proxc(float(what), float(f), float(tau), float(lam1), float(lam2))
+
+
 def params(lam=5.0, beta=0.8, L0=1.0, eta=2.0, c2=1e-6, max_backtrack=30,
-           max_iter=100, tol=0.0) -> OrcParams:
+           max_iter=100, tol=0.0, model=MODEL_VARIANT, lam1=0.0) -> OrcParams:
+    """iPiano parameters.  model = MODEL_COMBINED: the iterate is w = log u,
+    lam weights the variant term (lambda_2) and lam1 the log-domain term
+    (lambda_1) of Eq. newmodel."""
     return OrcParams(float(lam), float(beta), float(L0), float(eta), float(c2),
-                     int(max_backtrack), int(max_iter), float(tol))
+                     int(max_backtrack), int(max_iter), float(tol), int(model), float(lam1))
 
 
 def ipiano(f, filters, theta, prm: OrcParams, u0=None, L_start=None):
     """Full iPiano solve.  Returns dict with u, u_prev, rec (n x 9),
-    n, L, status, F0, G0, converged."""
+    n, L, status, F0, G0, converged.  For the combined model the iterate
+    (u, u_prev, u0) is w = log u and the default start is log f."""
     f = _d(f)
     k, th, nf, ks = _bank(filters, theta)
     H, W = f.shape
-    u = _d(f if u0 is None else u0).copy()
+    if u0 is None:
+        u0 = np.log(f) if prm.model == MODEL_COMBINED else f
+    u = _d(u0).copy()
     up = np.empty_like(u)
     rec = np.zeros((max(prm.max_iter, 1), ORC_REC))
     n = C.c_int(0)

@@ -1,6 +1,8 @@
 /*
- * FP64 CPU oracle for the FoE despeckling model with the I-divergence data
- * term (Eq. variant, Sec. II-B) minimised by iPiano (Sec. II-C).
+ * FP64 CPU oracle for the FoE despeckling models minimised by iPiano
+ * (Sec. II-C): the model with the I-divergence data term (Eq. variant,
+ * Sec. II-B) in u, and the combined model (Eq. newmodel, Sec. III-A) in
+ * w = log u, whose special case lambda_2 = 0 is Eq. original.
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the
  * CUDA path is checked against.  Only the test-suite, the smoke check and the
@@ -316,15 +318,141 @@ ORC_API double orc_prox(double uhat, double f, double tau, double lambda)
 }
 
 /* ----------------------------------------------------------------------- */
+/* Combined model (Eq. newmodel) in w = log u                              */
+/*   F(w) = E_FoE(e^w)                                                     */
+/*   G(w) = sum_p lambda1/2 (2w + f^2 e^{-2w}) + lambda2/2 (e^{2w} - 2f^2 w) */
+/* lambda2 = 0: Eq. original (Sec. II-C).                                  */
+/* ----------------------------------------------------------------------- */
+
+ORC_API double orc_Fw(const double *w, int H, int W, const double *bank,
+                      const double *theta, int nf, int ks)
+{
+    const long N = (long)H * W;
+    double *u = (double *)malloc(sizeof(double) * N);
+    for (long q = 0; q < N; ++q)
+        u[q] = exp(w[q]);
+    const double F = orc_F(u, H, W, bank, theta, nf, ks);
+    free(u);
+    return F;
+}
+
+/* grad_w F = sum_i theta_i W K_i^T rho'(K_i e^w), W = diag(e^w) (Sec. II-C).
+ * Returns F(w). */
+ORC_API double orc_gradFw(const double *w, int H, int W, const double *bank,
+                          const double *theta, int nf, int ks, double *g)
+{
+    const long N = (long)H * W;
+    double *u = (double *)malloc(sizeof(double) * N);
+    for (long q = 0; q < N; ++q)
+        u[q] = exp(w[q]);
+    const double F = orc_gradF(u, H, W, bank, theta, nf, ks, g);
+    for (long q = 0; q < N; ++q)
+        g[q] *= u[q];
+    free(u);
+    return F;
+}
+
+/* Data term of one pixel and its first two derivatives in w. */
+static double gc_term(double w, double f, double l1, double l2)
+{
+    return 0.5 * l1 * (2.0 * w + f * f * exp(-2.0 * w)) + 0.5 * l2 * (exp(2.0 * w) - 2.0 * f * f * w);
+}
+static double gc_d1(double w, double f, double l1, double l2)
+{
+    return l1 * (1.0 - f * f * exp(-2.0 * w)) + l2 * (exp(2.0 * w) - f * f);
+}
+static double gc_d2(double w, double f, double l1, double l2)
+{
+    return 2.0 * l1 * f * f * exp(-2.0 * w) + 2.0 * l2 * exp(2.0 * w);
+}
+
+ORC_API double orc_Gc(const double *w, const double *f, long N, double lambda1, double lambda2)
+{
+    double s = 0.0;
+    for (long p = 0; p < N; ++p)
+        s += gc_term(w[p], f[p], lambda1, lambda2);
+    return s;
+}
+
+/* Proximal map of tau*G for the combined model, one pixel: the root of
+ * phi(w) = w - what + tau g'(w) by Newton's method (Sec. III-A: the prox is
+ * solved with Newton's method).  phi is strictly increasing (phi' = 1 +
+ * tau g'' > 0) and g'(log f) = 0, so the root lies between what and log f;
+ * a Newton step that leaves that bracket is replaced by bisection.
+ * Iterates until the step is below 1e-15 (1 + |w|) or 200 iterations. */
+ORC_API double orc_proxc(double what, double f, double tau, double lambda1, double lambda2)
+{
+    const double lf = log(f);
+    double lo = what < lf ? what : lf, hi = what < lf ? lf : what;
+    double w = what;
+    for (int it = 0; it < 200; ++it) {
+        const double ph = w - what + tau * gc_d1(w, f, lambda1, lambda2);
+        if (ph == 0.0)
+            break;
+        if (ph > 0.0)
+            hi = w;
+        else
+            lo = w;
+        double wn = w - ph / (1.0 + tau * gc_d2(w, f, lambda1, lambda2));
+        if (!(wn > lo && wn < hi))
+            wn = 0.5 * (lo + hi);
+        const double step = fabs(wn - w);
+        w = wn;
+        if (step <= 1e-15 * (1.0 + fabs(w)))
+            break;
+    }
+    return w;
+}
+
+/* ----------------------------------------------------------------------- */
 /* iPiano                                                                  */
 /* ----------------------------------------------------------------------- */
+
+enum { ORC_MODEL_VARIANT = 0, ORC_MODEL_COMBINED = 1 };
 
 typedef struct {
     double lambda, beta, L0, eta, c2;
     int max_backtrack;
     int max_iter;     /* accepted iterations */
     double tol;       /* <= 0: no energy-change test */
+    int model;        /* ORC_MODEL_VARIANT: x = u, G with lambda;
+                         ORC_MODEL_COMBINED: x = w = log u, G with lambda1
+                         (Eq. original term) and lambda2 = lambda (variant term) */
+    double lambda1;
 } orc_params;
+
+/* The model's F, grad F, G, prox and data-term floor in its variable x. */
+static double obj_gradF(const orc_params *p, const double *x, int H, int W, const double *bank,
+                        const double *theta, int nf, int ks, double *g)
+{
+    return p->model == ORC_MODEL_COMBINED ? orc_gradFw(x, H, W, bank, theta, nf, ks, g)
+                                          : orc_gradF(x, H, W, bank, theta, nf, ks, g);
+}
+static double obj_F(const orc_params *p, const double *x, int H, int W, const double *bank,
+                    const double *theta, int nf, int ks)
+{
+    return p->model == ORC_MODEL_COMBINED ? orc_Fw(x, H, W, bank, theta, nf, ks)
+                                          : orc_F(x, H, W, bank, theta, nf, ks);
+}
+static double obj_G(const orc_params *p, const double *x, const double *f, long N)
+{
+    return p->model == ORC_MODEL_COMBINED ? orc_Gc(x, f, N, p->lambda1, p->lambda) : orc_G(x, f, N, p->lambda);
+}
+static double obj_prox(const orc_params *p, double xhat, double f, double tau)
+{
+    return p->model == ORC_MODEL_COMBINED ? orc_proxc(xhat, f, tau, p->lambda1, p->lambda)
+                                          : orc_prox(xhat, f, tau, p->lambda);
+}
+/* min_x G(x): reached at u = f (variant) and at w = log f (combined: g'(log f) = 0). */
+static double obj_Gfloor(const orc_params *p, const double *f, long N)
+{
+    if (p->model != ORC_MODEL_COMBINED)
+        return orc_G(f, f, N, p->lambda);
+    double s = 0.0;
+    for (long q = 0; q < N; ++q)
+        s += gc_term(log(f[q]), f[q], p->lambda1, p->lambda);
+    return s;
+}
 
 /* Per accepted iteration record (9 doubles):
  *  [L_n, alpha_n, F, G, H, backtracks, <g,D>, |D|^2, <D, D_prev>]
@@ -355,9 +483,9 @@ static int ipiano_iteration(const double *u, const double *up, const double *g,
         /* forward (explicit) step with inertia, then the prox of alpha G */
         for (long q = 0; q < N; ++q) {
             uhat[q] = u[q] - alpha * g[q] + p->beta * (u[q] - up[q]);
-            u1[q] = orc_prox(uhat[q], f[q], alpha, p->lambda);
+            u1[q] = obj_prox(p, uhat[q], f[q], alpha);
         }
-        const double F1 = orc_F(u1, H, W, bank, theta, nf, ks);
+        const double F1 = obj_F(p, u1, H, W, bank, theta, nf, ks);
         double gd = 0.0, dd = 0.0, dp = 0.0;
         for (long q = 0; q < N; ++q) {
             const double d = u1[q] - u[q];
@@ -370,9 +498,9 @@ static int ipiano_iteration(const double *u, const double *up, const double *g,
             break;
         }
         if (F1 <= F + gd + 0.5 * (*L) * dd) {
-            orc_gradF(u1, H, W, bank, theta, nf, ks, g1);
+            obj_gradF(p, u1, H, W, bank, theta, nf, ks, g1);
             *F1_out = F1;
-            *G1_out = orc_G(u1, f, N, p->lambda);
+            *G1_out = obj_G(p, u1, f, N);
             if (rec) {
                 rec[0] = *L;
                 rec[1] = alpha;
@@ -414,9 +542,9 @@ ORC_API int orc_ipiano(const double *f, int H, int W, const double *bank,
     double *g1 = (double *)malloc(sizeof(double) * N);
     memcpy(up, u, sizeof(double) * N);
     double L = (L_io && *L_io > 0.0) ? *L_io : p->L0;
-    double F = orc_gradF(u, H, W, bank, theta, nf, ks, g);
-    double G = orc_G(u, f, N, p->lambda);
-    const double Gfloor = orc_G(f, f, N, p->lambda); /* G is minimal at u = f */
+    double F = obj_gradF(p, u, H, W, bank, theta, nf, ks, g);
+    double G = obj_G(p, u, f, N);
+    const double Gfloor = obj_Gfloor(p, f, N);
     if (h0) {
         h0[0] = F;
         h0[1] = G;
@@ -465,7 +593,7 @@ ORC_API int orc_ipiano_step(const double *f, int H, int W, const double *bank,
     const long N = (long)H * W;
     double *g = (double *)malloc(sizeof(double) * N);
     double *g1 = (double *)malloc(sizeof(double) * N);
-    const double F = orc_gradF(u, H, W, bank, theta, nf, ks, g);
+    const double F = obj_gradF(p, u, H, W, bank, theta, nf, ks, g);
     double L = L_in, F1, G1;
     const int status = ipiano_iteration(u, up, g, F, H, W, f, bank, theta, nf, ks,
                                         p, &L, u1, g1, &F1, &G1, rec);
@@ -492,20 +620,20 @@ ORC_API int orc_ipiano_fixed(const double *f, int H, int W, const double *bank,
     double *u1 = (double *)malloc(sizeof(double) * N);
     double *g = (double *)malloc(sizeof(double) * N);
     int status = ORC_OK;
-    double F = orc_gradF(u, H, W, bank, theta, nf, ks, g);
+    double F = obj_gradF(p, u, H, W, bank, theta, nf, ks, g);
     for (int k = 0; k < n; ++k) {
         const double L = Lseq[k], alpha = step_size(p, L);
         double gd = 0.0, dd = 0.0, dp = 0.0;
         for (long q = 0; q < N; ++q) {
             const double uhat = u[q] - alpha * g[q] + p->beta * (u[q] - up[q]);
-            u1[q] = orc_prox(uhat, f[q], alpha, p->lambda);
+            u1[q] = obj_prox(p, uhat, f[q], alpha);
             const double d = u1[q] - u[q];
             gd += g[q] * d;
             dd += d * d;
             dp += d * (u[q] - up[q]);
         }
-        const double F1 = orc_gradF(u1, H, W, bank, theta, nf, ks, g);
-        const double G1 = orc_G(u1, f, N, p->lambda);
+        const double F1 = obj_gradF(p, u1, H, W, bank, theta, nf, ks, g);
+        const double G1 = obj_G(p, u1, f, N);
         if (!isfinite(F1) || !isfinite(G1)) {
             status = ORC_ENONFINITE;
             break;

@@ -23,7 +23,7 @@ from . import synth
 from .fe import CNN, FE_OK, Solver  # noqa: F401  (re-exported for users)
 
 # lambda = 0.02: the I-divergence weight (lambda_2) of the combined model for
-# L = 8 in Sec. 3.2; at lambda = 5 the data term pins u to f and the solver
+# L = 8 in Sec. III-B; at lambda = 5 the data term pins u to f and the solver
 # meets the tolerance after 1-2 steps, which leaves nothing to warm-start
 SOLVER_KW = dict(lam=0.02, beta=0.8, L0=1.0, eta=2.0, c2=1e-6, max_backtrack=30)
 
