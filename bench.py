@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--n512", type=int, default=24)
     ap.add_argument("--n256", type=int, default=24)
     ap.add_argument("--prec", default="fp32")
+    ap.add_argument("--model", default="variant", choices=["variant", "combined"],
+                    help="variant: Eq. variant in u (lambda = 5); combined: Eq. newmodel in w = log u "
+                         "(lambda1 = 160, lambda2 = 0.004, FP32 form)")
     ap.add_argument("--loop-mode", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -89,6 +92,21 @@ def workload(n512, n256):
 
 
 SOLVER_KW = dict(lam=5.0, beta=0.8, L0=1.0, eta=2.0, c2=1e-6, max_backtrack=30)
+# combined model (Eq. newmodel): the paper's lambda1, lambda2 for L = 1 (Sec. III-B)
+COMBINED_KW = dict(SOLVER_KW, lam=0.004, lam1=160.0, model="combined")
+
+
+def model_kw(args):
+    """Solver keywords of the throughput workload's model."""
+    return COMBINED_KW if getattr(args, "model", "variant") == "combined" else SOLVER_KW
+
+
+def oracle_prm(orc, kw, max_iter):
+    """The oracle's parameters for the same model and solver settings."""
+    return orc.params(max_iter=max_iter, lam=kw["lam"], beta=kw["beta"], L0=kw["L0"], eta=kw["eta"],
+                      c2=kw["c2"], max_backtrack=kw["max_backtrack"],
+                      model=orc.MODEL_COMBINED if kw.get("model") == "combined" else orc.MODEL_VARIANT,
+                      lam1=kw.get("lam1", 0.0))
 
 
 def measured_bf16_sustained():
@@ -145,20 +163,18 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows), "samples_under_load": len(load)}
 
 
-def cpu_baseline(fs, k, th, iters_total, seconds):
+def cpu_baseline(fs, k, th, iters_total, seconds, kw=SOLVER_KW):
     """The FP64 oracle, as it stands, on a bounded sample: one 256x256 image
     of the workload, as many iterations as fit in about `seconds`."""
     import oracle as orc
     orc.build()
     f = next(x for x in fs if x.shape == (256, 256)) if any(x.shape == (256, 256) for x in fs) else fs[0]
-    prm = dict(lam=SOLVER_KW["lam"], beta=SOLVER_KW["beta"], L0=SOLVER_KW["L0"], eta=SOLVER_KW["eta"],
-               c2=SOLVER_KW["c2"], max_backtrack=SOLVER_KW["max_backtrack"])
     t0 = time.perf_counter()
-    orc.ipiano(f, k, th, orc.params(max_iter=2, **prm))
+    orc.ipiano(f, k, th, oracle_prm(orc, kw, 2))
     per_it = (time.perf_counter() - t0) / 2.0
     n = int(max(2, min(iters_total, seconds / max(per_it, 1e-6))))
     t0 = time.perf_counter()
-    out = orc.ipiano(f, k, th, orc.params(max_iter=n, **prm))
+    out = orc.ipiano(f, k, th, oracle_prm(orc, kw, n))
     dt = time.perf_counter() - t0
     npx = f.size
     return {"value": round(npx * out["n"] / dt / 1e6, 4), "unit": "Mpixel*iter/s",
@@ -189,8 +205,7 @@ def run_reference(args):
     import oracle as orc
     orc.build()
     f = fs[-1]
-    prm = orc.params(max_iter=4, lam=SOLVER_KW["lam"], beta=SOLVER_KW["beta"], L0=SOLVER_KW["L0"],
-                     eta=SOLVER_KW["eta"], c2=SOLVER_KW["c2"], max_backtrack=SOLVER_KW["max_backtrack"])
+    prm = oracle_prm(orc, model_kw(args), 4)
     for _ in range(args.warmup):
         orc.ipiano(f, k, th, prm)
     times, its = [], 0
@@ -400,7 +415,8 @@ def main():
     stream = torch.cuda.Stream()
     f_dev = [torch.from_numpy(f).cuda() for f in fs]
     torch.cuda.synchronize()
-    solver = fe.Solver(f_dev, k, th, prec=args.prec, stream=stream, loop_mode=args.loop_mode, **SOLVER_KW)
+    kw = model_kw(args)
+    solver = fe.Solver(f_dev, k, th, prec=args.prec, stream=stream, loop_mode=args.loop_mode, **kw)
     tile = solver.tile
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -476,7 +492,7 @@ def main():
     f_host = [torch.from_numpy(f).pin_memory() for f in fs]
     u_host = [torch.empty(f.shape, dtype=torch.float32).pin_memory() for f in fs]
     e2e_solver = fe.Solver([x.numpy() for x in f_host], k, th, prec=args.prec, stream=stream,
-                           loop_mode=args.loop_mode, **SOLVER_KW)
+                           loop_mode=args.loop_mode, **kw)
     torch.cuda.synchronize()
     e2e_ms = 0.0
     e2e_steps = max(1, min(args.steps, 3))
@@ -503,10 +519,14 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[args.prec], "data": "synthetic",
                 "config": {"workload": "%dx512^2 + %dx256^2 textured images, L in {1,4,8} gamma speckle, "
-                                       "48x7x7 seeded bank, lambda=5, %d iPiano iterations with "
+                                       "48x7x7 seeded bank, %s, %d iPiano iterations with "
                                        "Lipschitz backtracking, %s filter bank" % (
-                                           args.n512, args.n256, args.iters, args.prec.upper()),
+                                           args.n512, args.n256,
+                                           "combined model (Eq. newmodel) in w = log u, lambda1=160, "
+                                           "lambda2=0.004" if args.model == "combined" else "lambda=5",
+                                           args.iters, args.prec.upper()),
                            "images": len(fs), "pixels": npix, "iters": args.iters, "precision": args.prec,
+                           "model": args.model,
                            "loop": "cuda-graph while node" if args.loop_mode == 1 else "host chunks",
                            "tile": "%dx%d (%s)" % (tile + ("autotuned" if args.prec == "fp32" else "fixed",)),
                            "parallelism": "replicas" if world > 1 else "single GPU",
@@ -527,7 +547,7 @@ def main():
             line["roofline"]["frac_at_observed_clock"] = round(
                 achieved_tflops / (SMS * FP32_LANES * 2 * clk["sm_mhz"] * 1e6 / 1e12), 4)
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(fs, k, th, args.iters, args.cpu_seconds)
+            line["cpu_baseline"] = cpu_baseline(fs, k, th, args.iters, args.cpu_seconds, kw)
         print(json.dumps(line), flush=True)
     solver.close()
     if dist:

@@ -15,6 +15,22 @@
  *     grad F(u) = sum_i theta_i K_i^T rho'(K_i u),  rho'(z) = 2z / (1 + z^2)
  *     prox: u_p = (uhat_p + sqrt(uhat_p^2 + 4(1+tau l) tau l f_p^2)) / (2(1+tau l))
  *
+ * Second model (fe_params.model = FE_MODEL_COMBINED, FP32 form only): the
+ * combined model of Eq. newmodel (Sec. III-A), iterated in w = log u:
+ *
+ *     argmin_w  F(e^w) + sum_p lambda1/2 (2 w_p + f_p^2 e^{-2 w_p})
+ *                      + lambda2/2 (e^{2 w_p} - 2 f_p^2 w_p)
+ *     grad_w F = e^w (.) sum_i theta_i K_i^T rho'(K_i e^w)            (Sec. II-C)
+ *
+ * with the prox of the (convex) data term solved per pixel by Newton's
+ * method (Sec. III-A), safeguarded by the bracket [min(what, log f),
+ * max(what, log f)] that always holds the root.  lambda2 = fe_params.lambda,
+ * lambda1 = fe_params.lambda1; lambda2 = 0 gives Eq. original (Sec. II-C).
+ * For this model the solver's iterate is w: fe_get_state / fe_set_state
+ * exchange (w^n, w^{n-1}, grad_w F), fe_energy and fe_gradient take w, and
+ * fe_get_u returns u = e^w.  The data-term floor of the convergence test is
+ * its value at w = log f, where it is minimal.
+ *
  * Conventions that the paper leaves open (fixed here, identical to the FP64
  * oracle used by the tests):
  *   - k_i * u is a true 2-D convolution of the image extended by 3 pixels with
@@ -52,7 +68,7 @@
 extern "C" {
 #endif
 
-#define FE_ABI_VERSION 1
+#define FE_ABI_VERSION 2
 
 #if defined(__GNUC__)
 #define FE_API __attribute__((visibility("default")))
@@ -78,13 +94,19 @@ typedef enum {
     FE_BF16 = 2             /* filter bank on the tensor cores, BF16 operands */
 } fe_precision;
 
+typedef enum {
+    FE_MODEL_VARIANT = 0,   /* Eq. variant in u (all precision forms) */
+    FE_MODEL_COMBINED = 1   /* Eq. newmodel in w = log u (FE_FP32 only) */
+} fe_model;
+
 /* Solver parameters.  All pointers are HOST pointers, copied by fe_init. */
 typedef struct {
     int nf;                 /* number of filters, 1..64 (48 in the paper) */
     int ksize;              /* filter side; must be 7 */
     const float *filters;   /* nf * 7 * 7, filter i at filters + 49 i, row-major k_i[a][b] */
     const float *theta;     /* nf weights theta_i >= 0 (Eq. FOEmodel) */
-    double lambda;          /* data-term weight lambda > 0 (Eq. variant) */
+    double lambda;          /* weight of the I-divergence term: lambda > 0 (Eq. variant);
+                               lambda2 >= 0 of Eq. newmodel (FE_MODEL_COMBINED) */
     double beta;            /* inertia, 0 <= beta < 1 */
     double L0;              /* initial Lipschitz estimate L_{-1} > 0 */
     double eta;             /* backtracking factor > 1 */
@@ -99,6 +121,10 @@ typedef struct {
                                Tensor-core forms: 0 only (one shape, 58 rows x
                                26 columns).
                                Other values: FE_EUNSUPPORTED. */
+    int model;              /* fe_model (FE_MODEL_COMBINED: prec must be FE_FP32) */
+    double lambda1;         /* FE_MODEL_COMBINED: weight lambda1 >= 0 of the
+                               log-domain term (lambda + lambda1 > 0); ignored
+                               by FE_MODEL_VARIANT */
 } fe_params;
 
 /* Per-image solver state summary (host struct, filled by fe_get_info). */
@@ -161,17 +187,18 @@ FE_API fe_status fe_solve(fe_ctx *ctx, int max_iter, double rel_tol);
 /* Summary of image img (synchronises). */
 FE_API fe_status fe_get_info(fe_ctx *ctx, int img, fe_info *out);
 
-/* Copy u^n of image img to out (any pointer, H*W floats). */
+/* Copy u^n of image img to out (any pointer, H*W floats); FE_MODEL_COMBINED:
+ * u^n = e^{w^n}. */
 FE_API fe_status fe_get_u(fe_ctx *ctx, int img, float *out);
 
-/* Energies of an arbitrary u (any pointer, H*W floats of image img's size,
- * u > 0) against image img's f: E = F + G.  Any output pointer may be NULL.
- * Synchronises. */
+/* Energies of an arbitrary iterate u (any pointer, H*W floats of image img's
+ * size; u > 0 for FE_MODEL_VARIANT, w = log u for FE_MODEL_COMBINED) against
+ * image img's f: E = F + G.  Any output pointer may be NULL.  Synchronises. */
 FE_API fe_status fe_energy(fe_ctx *ctx, int img, const float *u, double *E, double *F, double *G);
 
-/* grad F(u) (Sec. II-C) for an arbitrary u (any pointer) into g (any pointer),
- * both H*W floats of image img's size; F(u) into *F if F != NULL.
- * Synchronises. */
+/* grad F (Sec. II-C) at an arbitrary iterate (u, or w for FE_MODEL_COMBINED;
+ * any pointer) into g (any pointer), both H*W floats of image img's size;
+ * F into *F if F != NULL.  Synchronises. */
 FE_API fe_status fe_gradient(fe_ctx *ctx, int img, const float *u, float *g, double *F);
 
 /* Checkpoint: copy u^n, u^{n-1}, grad F(u^n) (any pointers, H*W floats each;

@@ -83,8 +83,10 @@ thread_local std::string g_init_err;
                            __FILE__, __LINE__);                                            \
     } while (0)
 
+// f^2 and the initial iterate: u^0 (variant model) or w^0 = log u^0
+// (combined model, logw != 0); u^{-1} = u^0.
 __global__ void prep_kernel(const float *f, const float *u0, float *f2, float *ua, float *ub,
-                            size_t N, int *bad) {
+                            size_t N, int logw, int *bad) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
          i += (size_t)gridDim.x * blockDim.x) {
         const float fv = f[i];
@@ -92,23 +94,37 @@ __global__ void prep_kernel(const float *f, const float *u0, float *f2, float *u
         const float uv = u0 ? u0[i] : fv;
         const bool ok = fv > 0.0f && isfinite(fv) && f2v > 0.0f && isfinite(f2v) && uv > 0.0f &&
                         isfinite(uv);
+        const float xv = logw ? logf(uv) : uv;
         f2[i] = f2v;
-        ua[i] = uv;
-        ub[i] = uv;
+        ua[i] = xv;
+        ub[i] = xv;
         if (!ok) atomicOr(bad, 1);
     }
 }
 
-// Per-block partial sums of f^2 (1 - log f^2) (the floor G(f) of the data
-// term, up to lambda/2), GF_BLOCKS partials per image, summed on the host in
-// block order.
+// u = e^w (combined model: the iterate is w)
+__global__ void exp_kernel(const float *w, float *u, size_t N) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+        u[i] = expf(w[i]);
+}
+
+// Per-block partial sums of the minimum of the data term (the floor of the
+// convergence test), GF_BLOCKS partials per image, summed on the host in
+// block order.  Variant: (lambda/2) f^2 (1 - log f^2), the value at u = f.
+// Combined: lambda1/2 (2 log f + 1) + lambda2/2 (f^2 - 2 f^2 log f), the value
+// at w = log f, where g'(w) = 0.
 constexpr int GF_BLOCKS = 64;
-__global__ void gfloor_kernel(const float *f2, size_t N, double *part) {
+__global__ void gfloor_kernel(const float *f2, size_t N, int model, double lam, double lam1, double *part) {
     __shared__ double red[256];
     double s = 0.0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
         const double v = (double)f2[i];
-        s += v * (1.0 - log(v));
+        if (model == FE_MODEL_COMBINED) {
+            const double lf = 0.5 * log(v);
+            s += 0.5 * lam1 * (2.0 * lf + 1.0) + 0.5 * lam * (v - 2.0 * v * lf);
+        } else {
+            s += 0.5 * lam * v * (1.0 - log(v));
+        }
     }
     red[threadIdx.x] = s;
     __syncthreads();
@@ -173,7 +189,17 @@ fe_status validate_params(fe_ctx *c, const fe_params *p) {
     for (int i = 0; i < p->nf; ++i)
         if (!(p->theta[i] >= 0.0f) || !std::isfinite(p->theta[i]))
             return set_err(c, FE_EINVAL, "theta[%d] must be finite and >= 0", i);
-    if (!(p->lambda > 0.0) || !std::isfinite(p->lambda)) return set_err(c, FE_EINVAL, "lambda must be > 0");
+    if (p->model != FE_MODEL_VARIANT && p->model != FE_MODEL_COMBINED)
+        return set_err(c, FE_EINVAL, "unknown model %d", p->model);
+    if (p->model == FE_MODEL_VARIANT) {
+        if (!(p->lambda > 0.0) || !std::isfinite(p->lambda)) return set_err(c, FE_EINVAL, "lambda must be > 0");
+    } else {
+        if (!(p->lambda >= 0.0) || !std::isfinite(p->lambda) || !(p->lambda1 >= 0.0) || !std::isfinite(p->lambda1) ||
+            !(p->lambda + p->lambda1 > 0.0))
+            return set_err(c, FE_EINVAL, "combined model: lambda, lambda1 must be finite, >= 0, not both 0");
+        if (p->prec != FE_FP32)
+            return set_err(c, FE_EUNSUPPORTED, "the combined model runs in the FP32 form only");
+    }
     if (!(p->beta >= 0.0 && p->beta < 1.0)) return set_err(c, FE_EINVAL, "beta must be in [0,1)");
     if (!(p->L0 > 0.0) || !std::isfinite(p->L0)) return set_err(c, FE_EINVAL, "L0 must be > 0");
     if (!(p->eta > 1.0) || !std::isfinite(p->eta)) return set_err(c, FE_EINVAL, "eta must be > 1");
@@ -192,7 +218,7 @@ fe_status validate_params(fe_ctx *c, const fe_params *p) {
 
 // Launch one tile kernel of the context's precision form.
 cudaError_t launch_tiles(const fe_ctx *c, int mode, const KParams &kp, int grid) {
-    if (c->prm.prec == FE_FP32) return fp32_launch(mode, kp, grid, c->s, c->tile_y);
+    if (c->prm.prec == FE_FP32) return fp32_launch(mode, kp, grid, c->s, c->tile_y, c->prm.model);
     return tc_launch(mode, c->prm.prec == FE_BF16 ? 1 : 2, kp, grid, c->s);
 }
 
@@ -267,7 +293,7 @@ fe_status load_inputs(fe_ctx *c, const float *const *f, const float *const *u0) 
         if (has_u0) FE_CUDA(c, cudaMemcpyAsync(im.u[0], u0[j], N * 4, cudaMemcpyDefault, c->s));
         const int blocks = (int)std::min<size_t>((N + 255) / 256, 4096);
         prep_kernel<<<blocks, 256, 0, c->s>>>(im.u[1], has_u0 ? im.u[0] : nullptr, im.f2, im.u[0], im.u[2],
-                                              N, c->d_flag);
+                                              N, c->prm.model == FE_MODEL_COMBINED ? 1 : 0, c->d_flag);
         FE_CUDA(c, cudaGetLastError());
         ++c->host_launches;
     }
@@ -277,7 +303,8 @@ fe_status load_inputs(fe_ctx *c, const float *const *f, const float *const *u0) 
     if (bad) return set_err(c, FE_EINVAL, "f and u0 must be finite and > 0 (f^2 must not underflow)");
     // floor of the data term, G(f), for the convergence test
     for (int j = 0; j < c->nimg; ++j) {
-        gfloor_kernel<<<GF_BLOCKS, 256, 0, c->s>>>(c->himg[j].f2, (size_t)c->H[j] * c->W[j],
+        gfloor_kernel<<<GF_BLOCKS, 256, 0, c->s>>>(c->himg[j].f2, (size_t)c->H[j] * c->W[j], c->prm.model,
+                                                   c->prm.lambda, c->prm.lambda1,
                                                    c->d_gpart + (size_t)j * GF_BLOCKS);
         FE_CUDA(c, cudaGetLastError());
         ++c->host_launches;
@@ -295,7 +322,7 @@ fe_status load_inputs(fe_ctx *c, const float *const *f, const float *const *u0) 
         s.status = FE_OK;
         double g = 0.0;
         for (int k = 0; k < GF_BLOCKS; ++k) g += gp[(size_t)j * GF_BLOCKS + k];
-        s.Gf = 0.5 * c->prm.lambda * g;
+        s.Gf = g;
     }
     FE_CUDA(c, cudaMemcpyAsync(c->d_st, hs.data(), sizeof(ImgState) * hs.size(), cudaMemcpyHostToDevice, c->s));
     FE_CUDA(c, cudaMemsetAsync(c->d_arr, 0, sizeof(unsigned) * c->nimg, c->s));
@@ -345,7 +372,7 @@ fe_status build_graph(fe_ctx *c) {
     std::memset(&knp, 0, sizeof knp);
     const int fmt = c->prm.prec == FE_BF16 ? 1 : 2;
     const bool tc = c->prm.prec != FE_FP32;
-    knp.func = const_cast<void *>(tc ? tc_trial_entry(fmt) : fp32_trial_entry(c->tile_y));
+    knp.func = const_cast<void *>(tc ? tc_trial_entry(fmt) : fp32_trial_entry(c->tile_y, c->prm.model));
     knp.gridDim = dim3(c->ntiles);
     knp.blockDim = dim3(tc ? tc_threads() : fp32_threads(c->tile_y));
     knp.sharedMemBytes = (unsigned)(tc ? tc_smem_bytes(fmt) : fp32_smem_bytes(c->tile_y));
@@ -435,7 +462,7 @@ fe_status stage_in(fe_ctx *c, const float *src, size_t N, int slot, const float 
 fe_status autotune_tile(fe_ctx *c, const std::vector<int> &cand) {
     static std::mutex mu;
     static std::map<std::string, int> cache;
-    std::string key = std::to_string(c->dev) + ":" + std::to_string(c->nfp);
+    std::string key = std::to_string(c->dev) + ":" + std::to_string(c->nfp) + ":" + std::to_string(c->prm.model);
     for (int j = 0; j < c->nimg; ++j) key += ":" + std::to_string(c->H[j]) + "x" + std::to_string(c->W[j]);
     int best = 0;
     {
@@ -524,6 +551,8 @@ void fe_default_params(fe_params *p) {
     p->max_backtrack = 30;
     p->prec = FE_FP32;
     p->tile = 0;
+    p->model = FE_MODEL_VARIANT;
+    p->lambda1 = 0.0;
 }
 
 void fe_destroy(fe_ctx *c) {
@@ -569,6 +598,8 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
         d.H = H[j];
         d.W = W[j];
         d.lambda = p->lambda;
+        d.lambda1 = p->model == FE_MODEL_COMBINED ? p->lambda1 : 0.0;
+        d.gscale = p->model == FE_MODEL_COMBINED ? 1.0 : 0.5 * p->lambda;
         c->himg.push_back(d);
     }
     // candidate tile shapes: the tensor-core forms have one; FP32 has 64 and
@@ -818,7 +849,26 @@ fe_status fe_set_state(fe_ctx *c, int img, const float *u, const float *u_prev, 
     return FE_OK;
 }
 
-fe_status fe_get_u(fe_ctx *c, int img, float *out) { return fe_get_state(c, img, out, nullptr, nullptr, nullptr); }
+fe_status fe_get_u(fe_ctx *c, int img, float *out) {
+    if (c && c->prm.model != FE_MODEL_COMBINED) return fe_get_state(c, img, out, nullptr, nullptr, nullptr);
+    fe_status st = check_img(c, img);
+    if (st != FE_OK) return st;
+    if (!out) return set_err(c, FE_EINVAL, "out is NULL");
+    ImgState s;
+    FE_CUDA(c, cudaMemcpyAsync(&s, c->d_st + img, sizeof s, cudaMemcpyDeviceToHost, c->s));
+    FE_CUDA(c, cudaStreamSynchronize(c->s));
+    const ImgDesc &d = c->himg[img];
+    const size_t N = (size_t)d.H * d.W;
+    // u = e^w into the caller's device buffer, or via the scratch plane
+    const bool dev = is_device_ptr(out);
+    float *dst = dev ? out : c->d_scratch;
+    exp_kernel<<<(int)std::min<size_t>((N + 255) / 256, 4096), 256, 0, c->s>>>(d.u[s.cur], dst, N);
+    FE_CUDA(c, cudaGetLastError());
+    ++c->host_launches;
+    if (!dev) FE_CUDA(c, cudaMemcpyAsync(out, dst, N * 4, cudaMemcpyDefault, c->s));
+    FE_CUDA(c, cudaStreamSynchronize(c->s));
+    return FE_OK;
+}
 
 static fe_status ext_launch(fe_ctx *c, int mode, int img, const float *u, float *g, double *F, double *G) {
     fe_status st = check_img(c, img);

@@ -1,448 +1,12 @@
-// Fused FP32 iPiano trial kernel for the FoE / I-divergence despeckling model.
-//
-// One CTA handles one TY x TX output tile of one image and does, in shared
-// memory, every step of one iPiano trial (Sec. II-C):
-//
-//   1. load u^n, u^{n-1}, g^n, f^2 on the tile + 6-pixel halo (symmetric
-//      reflection at the image border) and form the inertial forward step
-//      uhat = u^n - alpha g^n + beta (u^n - u^{n-1})             (update rule)
-//   2. closed-form prox of alpha G, pointwise, on tile + halo 6 (Sec. II-C):
-//      u = (uhat + sqrt(uhat^2 + 4(1+t l) t l f^2)) / (2 (1 + t l)), evaluated
-//      as 2 t l f^2 / (sqrt(D) - uhat) when uhat < 0 (no cancellation)
-//   3. forward filter bank z_i = k_i * u on tile + halo 3, 7x7 taps, FFMA
-//   4. r_i = theta_i rho'(z_i) = theta_i 2 z_i / (1 + z_i^2) (zero outside the
-//      image), and the energy term theta_i log(1 + z_i^2) on the tile
-//   5. adjoint bank g = sum_i K_i^T r_i on the tile (correlation with k_i),
-//      plus the transpose of the symmetric extension: values of K_i^T r on
-//      the 3-pixel frame outside the image are folded back onto the pixels
-//      they mirror
-//   6. per-tile FP64 partial sums of F(u^{n+1}), G(u^{n+1}), <g^n, D>, |D|^2,
-//      <D, u^n - u^{n-1}>; the last CTA of the image reduces them in a fixed
-//      order and applies the backtracking test (accept / L <- eta L).
-//
-// Filters are processed in groups of G = 4 so that the 4 response planes of
-// the tile + halo fit in shared memory; the adjoint accumulators stay in
-// registers across groups.
-//
-// Two tile shapes, T x T output pixels per CTA (the autotuner of the host
-// side picks one per context):
-//   T = 64: 256 threads, two CTAs per SM so that one CTA's barrier waits are
-//           covered by the other; forward units of 1 column x 10 rows x 4
-//           filters over the 70 x 70 response region (490 units, two rounds);
-//           adjoint units of 4 x 4 output pixels (one per thread)
-//   T = 32: 128 threads, four CTAs per SM, for images too small to fill the
-//           GPU with 64 x 64 tiles; forward units of 1 column x 13 rows over
-//           a 39-row (one padding row) x 38-column region (114 units, one
-//           round); adjoint units of 2 x 4 output pixels (one per thread)
-// A forward unit slides its column window over the 7 kernel columns; weight
-// vectors are uniform 128-bit loads from the tap-major table in global
-// memory (L1).  An adjoint unit reads each window row with three LDS.128 and
-// holds each filter's 49 weights in registers while its window rows stream
-// through.
+// FP32 trial kernel: entry points of the FP32 form.  The kernel template is in
+// fe_fp32_kernel.cuh; this unit instantiates it for the model with the
+// I-divergence data term (Eq. variant) and dispatches the combined model to
+// fe_fp32_comb.cu (instantiated there, compiled in parallel).
 #include <cuda_runtime.h>
-#include <math.h>
-#include <stdint.h>
 
-#include "fe_internal.cuh"
-#include "fe_tile_common.cuh"
+#include "fe_fp32_kernel.cuh"
 
 namespace fe {
-namespace {
-
-constexpr int G = 4;  // filters per group (response planes held in shared memory)
-
-template <int T>
-struct Cfg;
-template <>
-struct Cfg<64> {
-    static constexpr int NT = 256, MINB = 2, FWD_ROWS = 10, AUR = 4;
-    static constexpr int SU_LD = 87;  // 10*87 = 70 (mod 32): unit rows wrap without bank conflicts
-    static constexpr int SR_LD = 72;
-};
-template <>
-struct Cfg<32> {
-    static constexpr int NT = 128, MINB = 4, FWD_ROWS = 13, AUR = 2;
-    static constexpr int SU_LD = 62;  // 13*62 = 6 (mod 32), 38 = 6 (mod 32): as above
-    static constexpr int SR_LD = 40;
-};
-
-template <int T>
-struct Geo {
-    using C = Cfg<T>;
-    static constexpr int TY = T, TX = T, NT = C::NT, MINB = C::MINB;
-    static constexpr int FWD_ROWS = C::FWD_ROWS, AUR = C::AUR, SU_LD = C::SU_LD, SR_LD = C::SR_LD;
-    static constexpr int R3Y = TY + 6, R3X = TX + 6;  // response region (tile + 3)
-    // rows the forward units cover: R3Y rounded up to whole units (the extra
-    // row is computed from clamped loads and never read)
-    static constexpr int R3YA = (R3Y + FWD_ROWS - 1) / FWD_ROWS * FWD_ROWS;
-    static constexpr int R6Y = R3YA + 6, R6X = TX + 12;  // u^{n+1} region (tile + 6, padded)
-    static constexpr int NWARP = NT / 32;
-    static constexpr int FWD_WIN = FWD_ROWS + KS - 1;       // column window of a forward unit
-    static constexpr int FWD_UNITS = R3X * (R3YA / FWD_ROWS);
-    static constexpr int AUX = TX / 4;                      // adjoint units per tile row
-    static constexpr int ADJ_UNITS = (TY / AUR) * AUX;
-    static constexpr int RING = 2 * 3 * R3X + 2 * 3 * TY;   // frame positions
-    static constexpr int RING_PER_T = (RING + NT - 1) / NT;
-    // sR follows sU: round sU up to 4 floats so that sR is 16-byte aligned
-    // for the adjoint's 128-bit loads
-    static constexpr size_t SM_U = ((size_t)R6Y * SU_LD + 3) / 4 * 4;
-    static constexpr size_t SM_R = (size_t)G * R3YA * SR_LD;
-    static constexpr size_t SM_FLOATS = SM_U + SM_R;
-    static constexpr size_t SM_BYTES = SM_FLOATS * 4 + (size_t)NWARP * NRED * 8;
-    static_assert(NT == ADJ_UNITS, "one adjoint unit per thread");
-    static_assert(SU_LD >= R6X && SR_LD >= R3X, "row pitches hold a region row");
-    static_assert(SR_LD % 4 == 0 && SR_LD >= 4 * (AUX - 1) + 12, "adjoint window loads stay in the row");
-    static_assert((AUR - 1) + (TY - AUR) + KS <= R3Y, "adjoint windows stay in the response region");
-    static_assert(SM_U % 4 == 0 && SM_R % 4 == 0 && (SR_LD * R3YA) % 4 == 0,
-                  "every plane and row of sR starts on a 16-byte boundary");
-    static_assert(SM_FLOATS % 2 == 0, "double scratch alignment");
-    static_assert(MINB * (SM_BYTES + 1024) <= 228 * 1024, "MINB CTAs per SM");
-    static_assert(RING <= SM_R, "the frame ring reuses sR");
-};
-
-constexpr float LN2 = 0.69314718055994530942f;
-
-template <int T>
-__device__ __forceinline__ void ring_to_pos(int idx, int &pr, int &pc) {
-    constexpr int TY = T, TX = T, R3X = T + 6;
-    if (idx < 3 * R3X) {
-        pr = idx / R3X;
-        pc = idx % R3X;
-    } else if (idx < 6 * R3X) {
-        idx -= 3 * R3X;
-        pr = TY + 3 + idx / R3X;
-        pc = idx % R3X;
-    } else if (idx < 6 * R3X + 3 * TY) {
-        idx -= 6 * R3X;
-        pr = 3 + idx / 3;
-        pc = idx % 3;
-    } else {
-        idx -= 6 * R3X + 3 * TY;
-        pr = 3 + idx / 3;
-        pc = TX + 3 + idx % 3;
-    }
-}
-
-template <int T>
-__device__ __forceinline__ int pos_to_ring(int pr, int pc) {
-    constexpr int TY = T, TX = T, R3X = T + 6;
-    if (pr < 3) return pr * R3X + pc;
-    if (pr >= TY + 3) return 3 * R3X + (pr - TY - 3) * R3X + pc;
-    if (pc < 3) return 6 * R3X + (pr - 3) * 3 + pc;
-    return 6 * R3X + 3 * TY + (pr - 3) * 3 + (pc - TX - 3);
-}
-
-// Forward bank of one unit (1 column x FWD_ROWS rows x G filters of group
-// grp) and its epilogue: r_i into sR, theta_i log2(1 + z_i^2) summed over the
-// unit's tile pixels.  MASK: some pixel of the unit lies outside the image.
-template <int T, int MODE, bool MASK>
-__device__ __forceinline__ float forward_unit(const float *__restrict__ sU, float *__restrict__ sR,
-                                              const float *__restrict__ wf, const float *__restrict__ theta,
-                                              int grp, int c, int rb, int y0, int x0, int H, int W) {
-    using Q = Geo<T>;
-    constexpr int FWD_ROWS = Q::FWD_ROWS, FWD_WIN = Q::FWD_WIN, SU_LD = Q::SU_LD, SR_LD = Q::SR_LD;
-    constexpr int TY = Q::TY, TX = Q::TX, R3YA = Q::R3YA;
-    float z[FWD_ROWS][G];
-#pragma unroll
-    for (int r = 0; r < FWD_ROWS; ++r)
-#pragma unroll
-        for (int i = 0; i < G; ++i) z[r][i] = 0.f;
-    const float *ucol = sU + rb * FWD_ROWS * SU_LD + c;
-    const float *wcol = wf + grp * G;
-#pragma unroll 1
-    for (int bb = 0; bb < KS; ++bb) {
-        float v[FWD_WIN];
-#pragma unroll
-        for (int r = 0; r < FWD_WIN; ++r) v[r] = ucol[r * SU_LD + bb];
-#pragma unroll
-        for (int aa = 0; aa < KS; ++aa) {
-            const float4 w0 = __ldg(reinterpret_cast<const float4 *>(wcol + (aa * KS + bb) * NFMAX));
-            const float w[G] = {w0.x, w0.y, w0.z, w0.w};
-#pragma unroll
-            for (int r = 0; r < FWD_ROWS; ++r)
-#pragma unroll
-                for (int i = 0; i < G; ++i) z[r][i] = fmaf(w[i], v[r + aa], z[r][i]);
-        }
-    }
-    float th[G], th2[G];
-#pragma unroll
-    for (int i = 0; i < G; ++i) {
-        th[i] = __ldg(theta + grp * G + i);
-        th2[i] = 2.0f * th[i];
-    }
-    const int x = x0 - 3 + c;
-    const bool colin = x >= 0 && x < W, colint = c >= 3 && c < 3 + TX;
-    float fsum = 0.f;
-#pragma unroll
-    for (int r = 0; r < FWD_ROWS; ++r) {
-        const int pr = rb * FWD_ROWS + r;
-        const int y = y0 - 3 + pr;
-        const bool inimg = !MASK || (colin && y >= 0 && y < H);
-        const bool inner = colint && pr >= 3 && pr < 3 + TY && (!MASK || inimg);
-        float psum = 0.f;
-#pragma unroll
-        for (int i = 0; i < G; ++i) {
-            const float zz = z[r][i];
-            const float q = fmaf(zz, zz, 1.0f);
-            if (MODE != MODE_ENERGY_EXT) {
-                float rv = __fdividef(th2[i] * zz, q);
-                if (MASK && !inimg) rv = 0.0f;
-                sR[(i * R3YA + pr) * SR_LD + c] = rv;
-            }
-            psum = fmaf(th[i], __log2f(q), psum);
-        }
-        if (inner) fsum += psum;
-    }
-    return fsum * LN2;
-}
-
-template <int MODE, int T>
-__global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(const KParams p) {
-    using Q = Geo<T>;
-    constexpr int TY = Q::TY, TX = Q::TX, NT = Q::NT, R3Y = Q::R3Y, R3X = Q::R3X, R3YA = Q::R3YA;
-    constexpr int R6Y = Q::R6Y, R6X = Q::R6X, SU_LD = Q::SU_LD, SR_LD = Q::SR_LD, AUR = Q::AUR;
-    constexpr int FWD_ROWS = Q::FWD_ROWS, FWD_UNITS = Q::FWD_UNITS, RING = Q::RING, RING_PER_T = Q::RING_PER_T;
-    constexpr size_t SM_U = Q::SM_U, SM_R = Q::SM_R;
-    extern __shared__ __align__(16) float smem[];
-    float *sU = smem;
-    float *sR = sU + SM_U;
-    double *sRed = reinterpret_cast<double *>(sR + SM_R);
-    __shared__ int sLast;
-
-    const int tid = threadIdx.x;
-    const int gtile = p.tile0 + (int)blockIdx.x;
-    const TileDesc td = p.tiles[gtile];
-    const int img = td.img;
-    const ImgDesc im = p.imgs[img];
-    ImgState *st = p.st + img;
-    const int H = im.H, W = im.W, y0 = td.y0, x0 = td.x0;
-
-    bool active = true;
-    int gcur_out = 0;
-    if (MODE == MODE_TRIAL) {
-        active = (st->done == 0) && (st->n < st->target);
-        gcur_out = st->gcur ^ 1;
-    }
-
-    if (active) {
-        // ---- 1+2: inertial step and prox on tile + 6 ---------------------
-        // per-thread sums: compensated FP32 for F and G (large terms), plain
-        // FP32 for the small step-test terms
-        Sum2 accF{0.f, 0.f}, accG{0.f, 0.f};
-        float accGD = 0.f, accDD = 0.f, accDP = 0.f;
-        {
-            int cur = 0, gcur = 0;
-            float a = 0.f, b = 0.f, tl = 0.f;
-            if (MODE == MODE_TRIAL) {
-                cur = st->cur;
-                gcur = st->gcur;
-                const double alpha = st->alpha;
-                a = (float)alpha;
-                b = (float)p.beta;
-                tl = (float)(alpha * im.lambda);
-            }
-            const float *uc = (MODE == MODE_TRIAL || MODE == MODE_INIT) ? im.u[cur] : p.u_ext;
-            const float *upv = im.u[(cur + 2) % 3];
-            const float *gc = im.g[gcur];
-            float *un = im.u[(cur + 1) % 3];
-            const float *f2p = im.f2;
-            for (int idx = tid; idx < R6Y * R6X; idx += NT) {
-                const int ry = idx / R6X, rx = idx - ry * R6X;
-                const int y = y0 - 6 + ry, x = x0 - 6 + rx;
-                const size_t off = (size_t)reflect(y, H) * W + reflect(x, W);
-                const bool inner = ry >= 6 && ry < 6 + TY && rx >= 6 && rx < 6 + TX && y < H && x < W;
-                float v;
-                if (MODE == MODE_TRIAL) {
-                    const float u0 = __ldg(uc + off), u_1 = __ldg(upv + off), g0 = __ldg(gc + off);
-                    const float f2 = __ldg(f2p + off);
-                    const float dprev = u0 - u_1;
-                    const float uhat = fmaf(-a, g0, fmaf(b, dprev, u0));
-                    v = prox_g(uhat, f2, tl);
-                    if (inner) {
-                        un[off] = v;
-                        const float d = v - u0;
-                        accGD = fmaf(g0, d, accGD);
-                        accDD = fmaf(d, d, accDD);
-                        accDP = fmaf(d, dprev, accDP);
-                        sum2_add(accG, v * v - 2.0f * f2 * logf(v));
-                    }
-                } else {
-                    v = __ldg(uc + off);
-                    if (inner) sum2_add(accG, v * v - 2.0f * __ldg(f2p + off) * logf(v));
-                }
-                sU[ry * SU_LD + rx] = v;
-            }
-        }
-
-        float acc[AUR][4];
-#pragma unroll
-        for (int i = 0; i < AUR; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-        float fr[RING_PER_T];
-#pragma unroll
-        for (int k = 0; k < RING_PER_T; ++k) fr[k] = 0.f;
-        const int aux = tid % Q::AUX, auy = tid / Q::AUX;  // adjoint unit of this thread
-        const bool border = y0 == 0 || x0 == 0 || y0 + TY > H - 3 || x0 + TX > W - 3;
-
-        for (int grp = 0; grp < p.nfp / G; ++grp) {
-            __syncthreads();  // sU / weights ready; previous group's sR reads done
-            // ---- 3+4: forward bank and potential on tile + 3 -------------
-            for (int unit = tid; unit < FWD_UNITS; unit += NT) {
-                const int c = unit % R3X, rb = unit / R3X;
-                const int x = x0 - 3 + c, ylo = y0 - 3 + rb * FWD_ROWS;
-                const bool full = x >= 0 && x < W && ylo >= 0 && ylo + FWD_ROWS <= H;
-                const float fs = full ? forward_unit<T, MODE, false>(sU, sR, p.wf, p.theta, grp, c, rb, y0, x0, H, W)
-                                      : forward_unit<T, MODE, true>(sU, sR, p.wf, p.theta, grp, c, rb, y0, x0, H, W);
-                sum2_add(accF, fs);
-            }
-            if (MODE == MODE_ENERGY_EXT) continue;
-            __syncthreads();  // sR complete
-
-            // ---- 5: adjoint bank on the tile (AUR x 4 unit per thread) -----
-            for (int i = 0; i < G; ++i) {
-                const float *wrow = p.wa + (grp * G + i) * KT_PAD;
-                float kw[KT_PAD];
-#pragma unroll
-                for (int j = 0; j < KT_PAD / 4; ++j) {
-                    const float4 t = __ldg(reinterpret_cast<const float4 *>(wrow) + j);
-                    kw[4 * j] = t.x;
-                    kw[4 * j + 1] = t.y;
-                    kw[4 * j + 2] = t.z;
-                    kw[4 * j + 3] = t.w;
-                }
-                const float *Ri = sR + (size_t)i * R3YA * SR_LD + (AUR * auy) * SR_LD + 4 * aux;
-#pragma unroll
-                for (int rr = 0; rr < AUR + KS - 1; ++rr) {
-                    const float4 a0 = *reinterpret_cast<const float4 *>(Ri + rr * SR_LD);
-                    const float4 a1 = *reinterpret_cast<const float4 *>(Ri + rr * SR_LD + 4);
-                    const float4 a2 = *reinterpret_cast<const float4 *>(Ri + rr * SR_LD + 8);
-                    const float v[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
-#pragma unroll
-                    for (int pp = 0; pp < AUR; ++pp) {
-                        const int aa = rr - pp;
-                        if (aa < 0 || aa >= KS) continue;
-#pragma unroll
-                        for (int bb = 0; bb < KS; ++bb)
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) acc[pp][q] = fmaf(kw[aa * KS + bb], v[q + bb], acc[pp][q]);
-                    }
-                }
-            }
-            // ---- 5b: K^T r on the frame outside the image (border tiles) --
-            if (border) {
-#pragma unroll
-                for (int k = 0; k < RING_PER_T; ++k) {
-                    const int idx = tid + k * NT;
-                    if (idx >= RING) break;
-                    int pr, pc, j, jx;
-                    ring_to_pos<T>(idx, pr, pc);
-                    if (!axis_pos(pr, y0, TY, H, j) || !axis_pos(pc, x0, TX, W, jx)) continue;
-                    // s(j, jx) = sum_i sum_ab k_i[a][b] r_i(j - 3 + a, jx - 3 + b); r_i is
-                    // zero off-image and the response region covers every on-image row
-                    // and column this frame pixel needs, so only those taps are visited
-                    const int alo = max(max(0, 3 - j), y0 - j), ahi = min(min(KS, H + 3 - j), R3Y + y0 - j);
-                    const int blo = max(max(0, 3 - jx), x0 - jx), bhi = min(min(KS, W + 3 - jx), R3X + x0 - jx);
-                    float s = 0.f;
-                    for (int i = 0; i < G; ++i) {
-                        const float *wrow = p.wa + (grp * G + i) * KT_PAD;
-                        const float *Ri = sR + (size_t)i * R3YA * SR_LD;
-                        for (int aa = alo; aa < ahi; ++aa)
-                            for (int bb = blo; bb < bhi; ++bb)
-                                s = fmaf(__ldg(wrow + aa * KS + bb), Ri[(j - y0 + aa) * SR_LD + (jx - x0 + bb)], s);
-                    }
-                    fr[k] += s;
-                }
-            }
-        }
-
-        if (MODE != MODE_ENERGY_EXT) {
-            // ---- fold the frame back onto the pixels it mirrors ----------
-            if (border) {
-                __syncthreads();  // all sR reads done; reuse sR for the ring
-#pragma unroll
-                for (int k = 0; k < RING_PER_T; ++k) {
-                    const int idx = tid + k * NT;
-                    if (idx < RING) sR[idx] = fr[k];
-                }
-                __syncthreads();
-            }
-            {
-                float *gout;
-                if (MODE == MODE_GRAD_EXT)
-                    gout = p.g_ext;
-                else if (MODE == MODE_INIT)
-                    gout = im.g[0];
-                else
-                    gout = im.g[gcur_out];
-#pragma unroll
-                for (int pp = 0; pp < AUR; ++pp) {
-                    const int y = y0 + AUR * auy + pp;
-                    if (y >= H) continue;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int x = x0 + 4 * aux + q;
-                        if (x >= W) continue;
-                        float gv = acc[pp][q];
-                        if (border && (y < 3 || y >= H - 3 || x < 3 || x >= W - 3)) {
-                            // frame positions that the symmetric extension maps onto
-                            // (y, x): at most one per axis (H, W >= 8); scalars, so
-                            // that nothing is indexed dynamically (local memory)
-                            const int oy = y - y0 + 3, ox = x - x0 + 3;
-                            const int qy = y < 3 ? 2 - y : (y >= H - 3 ? TY + 2 + H - y : -1);  // j = -y-1 | 2H-1-y
-                            const int qx = x < 3 ? 2 - x : (x >= W - 3 ? TX + 2 + W - x : -1);
-                            if (qx >= 0) gv += sR[pos_to_ring<T>(oy, qx)];
-                            if (qy >= 0) {
-                                gv += sR[pos_to_ring<T>(qy, ox)];
-                                if (qx >= 0) gv += sR[pos_to_ring<T>(qy, qx)];
-                            }
-                        }
-                        gout[(size_t)y * W + x] = gv;
-                    }
-                }
-            }
-        }
-
-        // ---- 6: per-tile FP64 partial sums, last-CTA decision -------------
-        const Sum2 vals[NRED] = {accF, accG, {accGD, 0.f}, {accDD, 0.f}, {accDP, 0.f}};
-        tile_finish<NT>(p, MODE, gtile, img, im, st, vals, sRed, &sLast);
-    }
-
-    // ---- loop control: the last CTA of the launch --------------------------
-    if (MODE == MODE_TRIAL) loop_control(p);
-}
-
-template <int T>
-cudaError_t prepare_tile() {
-    const int b = (int)Geo<T>::SM_BYTES;
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_TRIAL, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)) !=
-        cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_INIT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)) !=
-        cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_GRAD_EXT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  b)) != cudaSuccess)
-        return e;
-    return cudaFuncSetAttribute(fp32_tile_kernel<MODE_ENERGY_EXT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-}
-
-template <int T>
-cudaError_t launch_tile(int mode, const KParams &p, int ngrid, cudaStream_t s) {
-    const dim3 grid(ngrid), block(Geo<T>::NT);
-    const size_t b = Geo<T>::SM_BYTES;
-    switch (mode) {
-        case MODE_TRIAL: fp32_tile_kernel<MODE_TRIAL, T><<<grid, block, b, s>>>(p); break;
-        case MODE_INIT: fp32_tile_kernel<MODE_INIT, T><<<grid, block, b, s>>>(p); break;
-        case MODE_GRAD_EXT: fp32_tile_kernel<MODE_GRAD_EXT, T><<<grid, block, b, s>>>(p); break;
-        case MODE_ENERGY_EXT: fp32_tile_kernel<MODE_ENERGY_EXT, T><<<grid, block, b, s>>>(p); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
-}  // namespace
 
 bool fp32_tile_supported(int T) { return T == 64 || T == 32; }
 size_t fp32_smem_bytes(int T) { return T == 32 ? Geo<32>::SM_BYTES : Geo<64>::SM_BYTES; }
@@ -450,19 +14,23 @@ int fp32_tile() { return fp32_tile_size; }
 int fp32_threads(int T) { return T == 32 ? Geo<32>::NT : Geo<64>::NT; }
 
 cudaError_t fp32_prepare() {
-    cudaError_t e = prepare_tile<64>();
-    return e != cudaSuccess ? e : prepare_tile<32>();
+    cudaError_t e = prepare_tile<64, 0>();
+    if (e == cudaSuccess) e = prepare_tile<32, 0>();
+    if (e == cudaSuccess) e = fp32c_prepare();
+    return e;
 }
 
-cudaError_t fp32_launch(int mode, const KParams &p, int ngrid, cudaStream_t s, int T) {
-    if (T == 64) return launch_tile<64>(mode, p, ngrid, s);
-    if (T == 32) return launch_tile<32>(mode, p, ngrid, s);
+cudaError_t fp32_launch(int mode, const KParams &p, int ngrid, cudaStream_t s, int T, int model) {
+    if (model == 1) return fp32c_launch(mode, p, ngrid, s, T);
+    if (T == 64) return launch_tile<64, 0>(mode, p, ngrid, s);
+    if (T == 32) return launch_tile<32, 0>(mode, p, ngrid, s);
     return cudaErrorInvalidValue;
 }
 
-const void *fp32_trial_entry(int T) {
-    return T == 32 ? reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL, 32>)
-                   : reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL, 64>);
+const void *fp32_trial_entry(int T, int model) {
+    if (model == 1) return fp32c_trial_entry(T);
+    return T == 32 ? reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL, 32, 0>)
+                   : reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL, 64, 0>);
 }
 
 }  // namespace fe

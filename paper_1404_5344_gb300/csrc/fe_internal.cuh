@@ -44,7 +44,10 @@ struct ImgDesc {
     float *u[3];
     float *g[2];
     float *f2;
-    double lambda;
+    double lambda;   // variant model: lambda; combined model: lambda2 (variant term)
+    double lambda1;  // combined model: weight of the log-domain term
+    double gscale;   // factor applied to the summed data-term partials (variant: lambda/2;
+                     // combined: 1, the kernel sums the full per-pixel value)
 };
 
 struct ImgState {
@@ -52,7 +55,7 @@ struct ImgState {
     double L, alpha;
     double rel_change, last_gd, last_dd, last_dp;
     double tol;
-    double Gf;  // G(f) = (lambda/2) sum f^2 (1 - log f^2): the floor of the data term
+    double Gf;  // min of the data term: at u = f (variant), at w = log f (combined)
     long long n, trials, backtracks, target;
     int cur, gcur, bt, status, done, converged;
 };
@@ -107,9 +110,14 @@ bool fp32_tile_supported(int T);     // T = 64 or 32
 size_t fp32_smem_bytes(int T = fp32_tile_size);
 int fp32_tile();                                    // the default tile, fp32_tile_size
 int fp32_threads(int T = fp32_tile_size);           // block size of the tile kernel
-cudaError_t fp32_prepare();  // opt in to the large shared-memory carve-out (every tile shape)
-cudaError_t fp32_launch(int mode, const KParams &p, int grid, cudaStream_t s, int T = fp32_tile_size);
-const void *fp32_trial_entry(int T = fp32_tile_size);
+cudaError_t fp32_prepare();  // opt in to the large shared-memory carve-out (every tile and model)
+// model: 0 = Eq. variant (iterate u), 1 = combined model (iterate w = log u)
+cudaError_t fp32_launch(int mode, const KParams &p, int grid, cudaStream_t s, int T = fp32_tile_size,
+                        int model = 0);
+const void *fp32_trial_entry(int T = fp32_tile_size, int model = 0);
+cudaError_t fp32c_prepare();  // combined-model instantiations (fe_fp32_comb.cu)
+cudaError_t fp32c_launch(int mode, const KParams &p, int grid, cudaStream_t s, int T);
+const void *fp32c_trial_entry(int T);
 
 // Tensor-core tile kernel (fe_tc.cu); fmt 1 = BF16, 2 = TF32 operands
 constexpr int tc_tile_y = 58, tc_tile_x = 26;  // output tile; tile + 3-pixel halo = 64 x 32

@@ -81,6 +81,8 @@ __global__ void na_setup_kernel(unsigned char *base, const float *filters, const
         for (int k = 0; k < 2; ++k) d.g[k] = nullptr;
         d.f2 = const_cast<float *>(u);  // G is not returned; any valid plane keeps its reads in bounds
         d.lambda = 1.0;
+        d.lambda1 = 0.0;
+        d.gscale = 0.5;
         *reinterpret_cast<ImgDesc *>(base + NA_OFF_IMG) = d;
         *reinterpret_cast<unsigned *>(base + NA_OFF_ARR) = 0u;
         reinterpret_cast<double *>(base + NA_OFF_RES)[0] = 0.0;

@@ -29,6 +29,41 @@ __device__ __forceinline__ float prox_g(float uhat, float f2, float tl) {
     return uhat >= 0.0f ? (uhat + sD) / (2.0f * (1.0f + tl)) : (2.0f * tl * f2) / (sD - uhat);
 }
 
+// Combined model (Eq. newmodel, Sec. III-A) in w = log u, one pixel: the
+// data term lambda1/2 (2w + f^2 e^{-2w}) + lambda2/2 (e^{2w} - 2 f^2 w).
+__device__ __forceinline__ float data_w(float w, float f2, float l1, float l2) {
+    const float e2 = expf(2.0f * w), em2 = expf(-2.0f * w);
+    return 0.5f * l1 * fmaf(f2, em2, 2.0f * w) + 0.5f * l2 * fmaf(-2.0f * f2, w, e2);
+}
+
+// Prox of tau*G for the combined model, one pixel, by Newton's method (the
+// paper's choice, Sec. III-A): the root of phi(w) = w - what + tau g'(w),
+// g'(w) = l1 (1 - f^2 e^{-2w}) + l2 (e^{2w} - f^2).  phi is increasing
+// (phi' = 1 + tau g'' > 0) and g'(log f) = 0, so the root lies between what
+// and log f; a Newton step that leaves that bracket is replaced by
+// bisection.  At most 20 steps; stops once a step is below 2^-22 (1 + |w|).
+__device__ __forceinline__ float prox_w(float what, float f2, float tau, float l1, float l2) {
+    const float lf = 0.5f * logf(f2);
+    float lo = fminf(what, lf), hi = fmaxf(what, lf);
+    float w = what;
+    for (int it = 0; it < 20; ++it) {
+        const float e2 = expf(2.0f * w), em2 = expf(-2.0f * w);
+        const float ph = w - what + tau * (l1 * fmaf(-f2, em2, 1.0f) + l2 * (e2 - f2));
+        if (ph == 0.0f) break;
+        if (ph > 0.0f)
+            hi = w;
+        else
+            lo = w;
+        const float d2 = fmaf(2.0f * tau, fmaf(l1 * f2, em2, l2 * e2), 1.0f);
+        float wn = w - ph / d2;
+        if (!(wn > lo && wn < hi)) wn = 0.5f * (lo + hi);
+        const float step = fabsf(wn - w);
+        w = wn;
+        if (step <= 2.4e-7f * (1.0f + fabsf(w))) break;
+    }
+    return w;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -189,7 +224,7 @@ __device__ void tile_finish(const KParams &p, int mode, int gtile, int img, cons
                 for (int w = 0; w < nw; ++w) s += sRed[w * NRED + k];
                 tot[k] = s;
             }
-            tot[1] *= 0.5 * im.lambda;  // G = (lambda/2) sum_p (u^2 - 2 f^2 log u)
+            tot[1] *= im.gscale;  // variant: G = (lambda/2) sum_p (u^2 - 2 f^2 log u)
             if (mode == MODE_TRIAL || mode == MODE_INIT) {
                 decide(p, st, tot, mode);
             } else {

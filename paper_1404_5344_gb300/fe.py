@@ -40,7 +40,11 @@ class FeParams(C.Structure):
     _fields_ = [("nf", C.c_int), ("ksize", C.c_int), ("filters", C.POINTER(C.c_float)),
                 ("theta", C.POINTER(C.c_float)), ("lambda_", C.c_double), ("beta", C.c_double),
                 ("L0", C.c_double), ("eta", C.c_double), ("c2", C.c_double),
-                ("max_backtrack", C.c_int), ("prec", C.c_int), ("tile", C.c_int)]
+                ("max_backtrack", C.c_int), ("prec", C.c_int), ("tile", C.c_int), ("model", C.c_int),
+                ("lambda1", C.c_double)]
+
+
+MODELS = {"variant": 0, "combined": 1}
 
 
 class FeInfo(C.Structure):
@@ -153,10 +157,14 @@ class Solver:
 
     f: list of H x W float32 arrays (NumPy = host, torch CUDA = device).
     filters: (nf, 7, 7) float32, theta: (nf,) float32.
+    model: "variant" (Eq. variant, iterate u, weight lam) or "combined"
+    (Eq. newmodel, iterate w = log u, weights lam1 for the log-domain term
+    and lam for the variant term; lam = 0 is Eq. original).
     """
 
     def __init__(self, f, filters, theta, lam=5.0, beta=0.8, L0=1.0, eta=2.0, c2=1e-6,
-                 max_backtrack=30, prec="fp32", tile=0, u0=None, stream=None, loop_mode=None):
+                 max_backtrack=30, prec="fp32", tile=0, u0=None, stream=None, loop_mode=None,
+                 model="variant", lam1=0.0):
         if not isinstance(f, (list, tuple)):
             f = [f]
         self._keep = list(f) + (list(u0) if isinstance(u0, (list, tuple)) else [u0])
@@ -172,6 +180,8 @@ class Solver:
         p.max_backtrack = int(max_backtrack)
         p.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
         p.tile = int(tile)
+        p.model = MODELS[model] if isinstance(model, str) else int(model)
+        p.lambda1 = float(lam1)
         self.params = p
         n = len(f)
         Hs = (C.c_int * n)(*[s[0] for s in self.shapes])

@@ -33,7 +33,9 @@ def test_exports_every_declared_symbol(fe):
 
 
 def test_abi_version_and_strings(fe):
-    assert fe.lib.fe_abi_version() == 1
+    import re
+    hdr = open(os.path.join(ROOT, "include", "fe.h")).read()
+    assert fe.lib.fe_abi_version() == int(re.search(r"#define FE_ABI_VERSION (\d+)", hdr).group(1)) == 2
     assert fe.lib.fe_status_string(0) == b"ok"
     assert fe.lib.fe_status_string(5) == b"backtracking limit reached"
 
@@ -42,6 +44,7 @@ def test_default_params(fe):
     p = fe.default_params()
     assert (p.ksize, p.lambda_, p.beta, p.L0, p.eta, p.c2, p.max_backtrack, p.prec) == \
         (7, 5.0, 0.8, 1.0, 2.0, 1e-6, 30, 0)
+    assert (p.tile, p.model, p.lambda1) == (0, 0, 0.0)
 
 
 def _init(fe, **over):
