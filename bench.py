@@ -36,6 +36,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FLOP_PER_PIXEL_TRIAL = 2 * 48 * 49 * 2  # forward + adjoint bank, 2 flop per MAC
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one trial
+# launch with every image active, per pixel, from one ncu capture of the
+# current kernels on 24 x 512^2 (profiles/*_trial_24x512.md); None where no
+# capture of the current kernel exists
+TRAFFIC_PER_PIXEL = {("fp32", "variant"): 125.052160e6 / 6291456,
+                     ("bf16", "variant"): 128.659712e6 / 6291456}
 SMS, FP32_LANES = 152, 128
 METRIC = "Mpixel*iter/s of fused iPiano step"
 
@@ -538,7 +544,11 @@ def main():
                 "trials": int(trials), "statuses": statuses,
                 "roofline": {"bound": bound, "achieved": round(achieved_tflops, 3),
                              "peak": round(peak_tflops, 3), "unit": "TFLOP/s",
-                             "frac": round(achieved_tflops / peak_tflops, 4), "traffic": None,
+                             "frac": round(achieved_tflops / peak_tflops, 4),
+                             "traffic": (round(TRAFFIC_PER_PIXEL[(args.prec, args.model)] * npix)
+                                         if (args.prec, args.model) in TRAFFIC_PER_PIXEL else None),
+                             "traffic_basis": "ncu DRAM bytes of one trial launch of 24x512^2 with all images "
+                                              "active, scaled to this workload's full-batch launch by pixels",
                              "kernel": kernel, "peak_basis": basis,
                              "work": "9408 flop (2 x 48 x 49 MAC) per pixel per trial, every image-trial",
                              "per_launch_ms": round(per_launch_ms, 4)},
