@@ -39,7 +39,8 @@
  *   - alpha_n = 2 (1 - beta) / (L_n + 2 c2).  A trial is accepted iff
  *       F(u^{n+1}) <= F(u^n) + <grad F(u^n), u^{n+1} - u^n> + L_n/2 |u^{n+1} - u^n|^2
  *     else L_n <- eta L_n and the trial is redone (at most max_backtrack
- *     times per iteration).  L is never decreased.  u^{-1} = u^0.
+ *     times per iteration).  L is never decreased.  u^{-1} = u^0.  A trial
+ *     whose F(u^{n+1}) is not finite fails the test (it is rejected).
  *   - Convergence: |H^{n+1} - H^n| / |H^{n+1} - G(f)| < tol, i.e. the relative
  *     change of the energy measured above the floor of the data term,
  *     G(f) = min_u G(u) = (lambda/2) sum_p f_p^2 (1 - log f_p^2).  (With
@@ -81,7 +82,9 @@ typedef enum {
     FE_EINVAL = 1,          /* bad argument (null, size < 8, f <= 0 or not finite, ...) */
     FE_ENOMEM = 2,          /* device allocation failed */
     FE_ECUDA = 3,           /* a CUDA runtime call failed */
-    FE_ENONFINITE = 4,      /* a trial produced a non-finite energy/step */
+    FE_ENONFINITE = 4,      /* a trial produced non-finite step sums, or an accepted
+                               step a non-finite energy (a trial whose F is not
+                               finite, e.g. e^w overflowing, is only rejected) */
     FE_EBACKTRACK = 5,      /* more than max_backtrack rejections in one iteration */
     FE_ETIMEOUT = 6,        /* the device-side trial budget ran out */
     FE_ENOTCONVERGED = 7,   /* fe_solve hit max_iter before the tolerance */
@@ -213,6 +216,23 @@ FE_API fe_status fe_set_state(fe_ctx *ctx, int img, const float *u, const float 
 /* Number of images / size of image img. */
 FE_API int fe_num_images(const fe_ctx *ctx);
 FE_API fe_status fe_image_size(const fe_ctx *ctx, int img, int *H, int *W);
+
+/* Quality measures the paper reports (Sec. III), context-free.
+ *
+ * fe_ssim: mean SSIM index of x against the reference y (Wang, Bovik,
+ * Sheikh, Simoncelli 2004, as cited in Sec. III): for every position where
+ * an 11 x 11 window fits, the local means, variances and covariance under a
+ * circular Gaussian window (sigma 1.5, weights summing to 1) give
+ * ((2 mx my + C1)(2 sxy + C2)) / ((mx^2 + my^2 + C1)(sx^2 + sy^2 + C2)),
+ * C1 = (0.01 peak)^2, C2 = (0.03 peak)^2; *out = the mean over the
+ * (H - 10) x (W - 10) positions.  Moments in FP64.
+ * fe_psnr: 10 log10(peak^2 / MSE) over n pixels (+inf if x == y).
+ * x, y: DEVICE pointers (H*W or n floats, row-major); stream-ordered on
+ * stream, synchronises it; allocates its partial sums with cudaMallocAsync.
+ * Errors: FE_EINVAL (NULL, H or W < 11, peak <= 0, host pointers),
+ * FE_ENOMEM, FE_ECUDA; message in fe_last_error(NULL). */
+FE_API fe_status fe_ssim(const float *x, const float *y, int H, int W, double peak, double *out, void *stream);
+FE_API fe_status fe_psnr(const float *x, const float *y, long long n, double peak, double *out, void *stream);
 
 /* Output tile (rows x columns) of the context's trial kernel, as chosen by
  * the autotuner or given in fe_params.tile.  FE_EINVAL on NULL arguments. */

@@ -32,7 +32,8 @@
  *     a trial is accepted iff
  *       F(u^{n+1}) <= F(u^n) + <grad F(u^n), u^{n+1}-u^n> + L_n/2 |u^{n+1}-u^n|^2,
  *     otherwise L_n <- eta L_n and the trial is recomputed.  L is never
- *     decreased; u^{-1} = u^0.
+ *     decreased; u^{-1} = u^0.  A trial with a non-finite F (overflow) fails
+ *     the test: it is rejected, not an error.
  *   - Stopping: a fixed number of accepted iterations, or
  *     |H^{n+1} - H^n| / |H^{n+1} - G(f)| < tol: the relative change of the
  *     energy above the floor of the data term, G(f) = min_u G(u) (a constant
@@ -493,11 +494,14 @@ static int ipiano_iteration(const double *u, const double *up, const double *g,
             dd += d * d;
             dp += d * (u[q] - up[q]);
         }
-        if (!isfinite(F1) || !isfinite(gd) || !isfinite(dd)) {
+        /* a non-finite F1 (e^w overflowed in the combined model: inf, or
+         * inf - inf = NaN inside the bank) fails the descent test like any
+         * other trial and is rejected; non-finite step sums stop the solve */
+        if (!isfinite(gd) || !isfinite(dd)) {
             status = ORC_ENONFINITE;
             break;
         }
-        if (F1 <= F + gd + 0.5 * (*L) * dd) {
+        if (isfinite(F1) && F1 <= F + gd + 0.5 * (*L) * dd) {
             obj_gradF(p, u1, H, W, bank, theta, nf, ks, g1);
             *F1_out = F1;
             *G1_out = obj_G(p, u1, f, N);

@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
             }
         }
         if (!tc_ok) {
-            accF.s = __int_as_float(0x7fc00000);  // NaN: the image stops
+            accGD = __int_as_float(0x7fc00000);  // NaN step sum: the image stops (FE_ENONFINITE)
             if (tid == 0) atomicExch(p.tc_error, 1);
         }
         const Sum2 vals[NRED] = {accF, accG, {accGD, 0.f}, {accDD, 0.f}, {accDP, 0.f}};

@@ -131,12 +131,21 @@ __device__ void decide(const KParams &p, ImgState *st, const double *t, int mode
         return;
     }
     st->trials += 1;
-    if (!isfinite(F1) || !isfinite(G1) || !isfinite(gd) || !isfinite(dd)) {
+    // a non-finite F1 (e^w overflowed in the combined model: inf, or inf - inf
+    // = NaN inside the bank) fails the descent test like any other trial and
+    // is rejected (L <- eta L, bounded by max_backtrack); non-finite step sums,
+    // or an accepted step with a non-finite data term, stop the image
+    if (!isfinite(gd) || !isfinite(dd)) {
         st->status = FE_ENONFINITE;
         st->done = 1;
         return;
     }
-    if (F1 <= st->F + gd + 0.5 * st->L * dd) {
+    if (isfinite(F1) && F1 <= st->F + gd + 0.5 * st->L * dd) {
+        if (!isfinite(G1)) {
+            st->status = FE_ENONFINITE;
+            st->done = 1;
+            return;
+        }
         const double H1 = F1 + G1;
         // relative change of the energy above its data-term floor G(f) =
         // min_u G(u): H - G(f) = F(u) + (G(u) - G(f)) >= 0

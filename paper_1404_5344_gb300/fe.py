@@ -29,6 +29,7 @@ EXPORTS = (
     "fe_default_params", "fe_init_batch", "fe_init", "fe_reset", "fe_destroy", "fe_step",
     "fe_solve", "fe_get_info", "fe_get_u", "fe_energy", "fe_gradient", "fe_get_state",
     "fe_set_state", "fe_num_images", "fe_image_size", "fe_launch_count", "fe_set_loop_mode", "fe_tile_size",
+    "fe_ssim", "fe_psnr",
     "fe_last_error", "fe_status_string", "fe_abi_version", "fe_gradient_noalloc",
     "fe_tc_gemm_selftest", "fe_cnn_create", "fe_cnn_destroy", "fe_cnn_num_params",
     "fe_cnn_last_error", "fe_cnn_set_params", "fe_cnn_get_params", "fe_cnn_forward",
@@ -81,6 +82,8 @@ def _load(path: str = LIB_PATH) -> C.CDLL:
     L.fe_num_images.argtypes = [VP]
     L.fe_image_size.argtypes = [VP, I, P(I), P(I)]
     L.fe_tile_size.argtypes = [VP, P(I), P(I)]
+    L.fe_ssim.argtypes = [VP, VP, I, I, D, P(D), VP]
+    L.fe_psnr.argtypes = [VP, VP, C.c_longlong, D, P(D), VP]
     L.fe_launch_count.argtypes = [VP]
     L.fe_launch_count.restype = C.c_longlong
     L.fe_set_loop_mode.argtypes = [VP, I]
@@ -107,7 +110,8 @@ def _load(path: str = LIB_PATH) -> C.CDLL:
         getattr(L, name).restype = C.c_int
     for name in ("fe_tc_gemm_selftest", "fe_gradient_noalloc", "fe_init_batch","fe_init", "fe_reset", "fe_step", "fe_solve", "fe_get_info",
                  "fe_get_u", "fe_energy", "fe_gradient", "fe_get_state", "fe_set_state",
-                 "fe_image_size", "fe_set_loop_mode", "fe_num_images", "fe_abi_version", "fe_tile_size"):
+                 "fe_image_size", "fe_set_loop_mode", "fe_num_images", "fe_abi_version", "fe_tile_size",
+                 "fe_ssim", "fe_psnr"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -299,6 +303,31 @@ class Solver:
 
     def set_loop_mode(self, mode: int):
         self._check(lib.fe_set_loop_mode(self.ctx, int(mode)))
+
+
+def ssim(x, y, peak: float = 255.0, stream=None) -> float:
+    """fe_ssim: mean SSIM index of x against y (contiguous float32 CUDA
+    tensors of the same H x W shape)."""
+    H, W = (int(v) for v in x.shape)
+    if tuple(y.shape) != (H, W):
+        raise ValueError("x and y must have the same shape")
+    out = C.c_double()
+    st = lib.fe_ssim(_ptr(x), _ptr(y), H, W, float(peak), C.byref(out), _stream_handle(stream))
+    if st != FE_OK:
+        raise FeError(st, lib.fe_last_error(None).decode())
+    return out.value
+
+
+def psnr(x, y, peak: float = 255.0, stream=None) -> float:
+    """fe_psnr: 10 log10(peak^2 / MSE) of x against y (float32 CUDA tensors)."""
+    n = int(np.prod(x.shape))
+    if int(np.prod(y.shape)) != n:
+        raise ValueError("x and y must have the same size")
+    out = C.c_double()
+    st = lib.fe_psnr(_ptr(x), _ptr(y), n, float(peak), C.byref(out), _stream_handle(stream))
+    if st != FE_OK:
+        raise FeError(st, lib.fe_last_error(None).decode())
+    return out.value
 
 
 class CNN:

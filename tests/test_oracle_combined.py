@@ -164,12 +164,12 @@ def test_dense_step_8x8_combined(orc):
 
 
 @pytest.mark.parametrize("beta,l1,l2,L0", [(0.0, 160.0, 0.004, 1e-3), (0.5, 550.0, 0.02, 1e-3),
-                                           (0.8, 310.0, 0.008, 1e-3), (0.8, 160.0, 0.0, 1e2)])
+                                           (0.8, 310.0, 0.008, 1e-3), (0.8, 160.0, 0.0, 1e-3)])
 def test_trajectory_inequalities_combined(orc, beta, l1, l2, L0):
     """The accepted-step inequality (G is convex in w, so the derivation of
-    the variant model carries over); l2 = 0 is Eq. original.  Without the
-    e^{2w} term nothing bounds w from above, so that case starts from a
-    larger L0: a first step of alpha |g| >~ 700 in w overflows e^w."""
+    the variant model carries over); l2 = 0 is Eq. original, where nothing
+    bounds w from above: its first trials from L0 = 1e-3 overflow e^w
+    (F not finite) and must be rejected by the step rule, not end the solve."""
     k, th = _bank(6, seed=1)
     u, f = _problem(16, 14, seed=4)
     prm = orc.params(lam=l2, lam1=l1, model=COMB, beta=beta, L0=L0, c2=1e-6, max_iter=40)
@@ -185,6 +185,8 @@ def test_trajectory_inequalities_combined(orc, beta, l1, l2, L0):
         assert Hs[n + 1] <= Hs[n] - (1 / a - L / 2) * dd + (beta / a) * dp + 1e-9 * abs(Hs[n])
     if beta == 0.0:
         assert np.all(np.diff(Hs) <= 1e-9 * np.abs(Hs[1:]))
+    if l2 == 0.0:
+        assert rec[0, 5] > 0, "the overflowing first trials were rejected"
     w = out["u"]
     assert orc.Fw(w, k, th) == pytest.approx(rec[-1, 2], rel=1e-12)
     assert orc.Gc(w, f, l1, l2) == pytest.approx(rec[-1, 3], rel=1e-12)
