@@ -208,6 +208,19 @@ def combine_ranks(local_ms, local_units, dist=None, device="cpu"):
     return float(t.item()), float(u.item())
 
 
+def workload_config(args, npix, nimg):
+    """The throughput workload's config, shared by both arms."""
+    return {"workload": "%dx512^2 + %dx256^2 textured images, L in {1,4,8} gamma speckle, "
+                        "48x7x7 seeded bank, %s, %d iPiano iterations with "
+                        "Lipschitz backtracking, %s filter bank" % (
+                            args.n512, args.n256,
+                            "combined model (Eq. newmodel) in w = log u, lambda1=160, "
+                            "lambda2=0.004" if args.model == "combined" else "lambda=5",
+                            args.iters, args.prec.upper()),
+            "images": nimg, "pixels": npix, "iters": args.iters, "precision": args.prec,
+            "model": args.model}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -231,11 +244,12 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * T / args.steps, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "FP64 CPU oracle on one 256x256 textured image of the batch, 4 iPiano "
-                                   "iterations per step (bounded sample of the 24x512^2 + 24x256^2, "
-                                   "300-iteration workload)", "iters_per_step": 4},
+            "config": workload_config(args, args.n512 * 512 * 512 + args.n256 * 256 * 256, args.n512 + args.n256),
             "cpu_baseline": {"value": round(value, 4), "unit": "Mpixel*iter/s", "cores": orc.num_threads(),
-                             "kind": "oracle", "sample": "one 256x256 image, 4 iterations per step"},
+                             "kind": "oracle",
+                             "sample": "FP64 oracle (the reference arm: the paper ships no code), each step a "
+                                       "bounded sample of the workload: one 256x256 image of the batch, "
+                                       "4 iPiano iterations"},
             "e2e": {"value": round(value, 4), "unit": "Mpixel*iter/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -692,20 +706,12 @@ def main():
                 "ms_per_step": round(T_ms / args.steps, 3), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[args.prec], "data": "synthetic",
-                "config": {"workload": "%dx512^2 + %dx256^2 textured images, L in {1,4,8} gamma speckle, "
-                                       "48x7x7 seeded bank, %s, %d iPiano iterations with "
-                                       "Lipschitz backtracking, %s filter bank" % (
-                                           args.n512, args.n256,
-                                           "combined model (Eq. newmodel) in w = log u, lambda1=160, "
-                                           "lambda2=0.004" if args.model == "combined" else "lambda=5",
-                                           args.iters, args.prec.upper()),
-                           "images": len(fs), "pixels": npix, "iters": args.iters, "precision": args.prec,
-                           "model": args.model,
+                "config": dict(workload_config(args, npix, len(fs)), **{
                            "loop": "cuda-graph while node" if args.loop_mode == 1 else "host chunks",
                            "tile": "%dx%d (%s)" % (tile + ("autotuned" if args.prec == "fp32" else "fixed",)),
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "256 MiB buffer written between timed steps; state 6 planes x "
-                                 "%.0f MB" % (npix * 4 / 1e6)},
+                                 "%.0f MB" % (npix * 4 / 1e6)}),
                 "e2e": {"value": round(e2e_value, 2), "unit": "Mpixel*iter/s",
                         "h2d_bytes_per_step": int(npix * 4), "d2h_bytes_per_step": int(npix * 4)},
                 "gpu_launches": int(launches), "trial_kernel_launches": int(trial_launches),
