@@ -319,6 +319,14 @@ FE_API fe_status fe_cnn_train_step(fe_cnn *net, const float *f, const float *u_t
  * signalled within the wait bound). */
 FE_API fe_status fe_tc_gemm_selftest(int prec, int N, int K, const float *A, const float *B, float *D);
 
+/* Bounded-wait self-test (no counterpart in the paper): one CTA allocates
+ * tensor memory, waits on an mbarrier that nothing ever completes with at
+ * most max_iter polls (1 .. 2^24), frees the tensor memory and stores 1 in
+ * *timed_out if the wait gave up (0 if it did not).  Returns FE_ETIMEOUT when
+ * it gave up (the expected outcome), FE_EINVAL, FE_ENOMEM, FE_ECUDA.  The
+ * trial kernels' MMA waits take the same bounded path. */
+FE_API fe_status fe_tc_wait_selftest(unsigned max_iter, int *timed_out);
+
 FE_API const char *fe_last_error(const fe_ctx *ctx);
 FE_API const char *fe_status_string(fe_status s);
 FE_API int fe_abi_version(void);

@@ -82,10 +82,46 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 0) tc::tmem_dealloc(taddr, 64);
 }
 
+// Bounded-wait self-test: one CTA allocates tensor memory, waits with a
+// bounded loop on an mbarrier that nothing ever arrives on, then frees the
+// tensor memory and reports whether the wait gave up.  It exercises the
+// time-out path of the trial kernels' MMA waits without faulting or hanging
+// the GPU.
+__global__ void __launch_bounds__(128, 1) tc_wait_selftest_kernel(uint32_t max_iter, int *timed_out) {
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tbase;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) tc::mbar_init(&bar, 1);
+    if (warp == 0) tc::tmem_alloc(&tbase, 32);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const bool ok = tc::mbar_wait(&bar, 0, max_iter);  // no arrival: must give up
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, 32);
+    if (tid == 0) *timed_out = ok ? 0 : 1;
+}
+
 }  // namespace
 }  // namespace fe
 
 using namespace fe;
+
+extern "C" fe_status fe_tc_wait_selftest(unsigned max_iter, int *timed_out) {
+    if (!timed_out || max_iter == 0 || max_iter > (1u << 24)) return FE_EINVAL;
+    int *d = nullptr, h = -1;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return FE_ENOMEM;
+    fe_status st = FE_OK;
+    tc_wait_selftest_kernel<<<1, 128>>>(max_iter, d);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        st = FE_ECUDA;
+    cudaFree(d);
+    *timed_out = h;
+    if (st == FE_OK && h == 1) st = FE_ETIMEOUT;
+    return st;
+}
 
 extern "C" fe_status fe_tc_gemm_selftest(int prec, int N, int K, const float *A, const float *B, float *D) {
     if ((prec != FE_BF16 && prec != FE_TF32) || !A || !B || !D) return FE_EINVAL;

@@ -51,3 +51,21 @@ def test_rounded_real_operands(fe, prec):
     D = _run(fe, prec, 48, K, A, B)
     scale = np.abs(rnd(A)).astype(np.float64) @ np.abs(rnd(B)).T
     assert np.max(np.abs(D - ref) / scale) < 1e-6
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable(fe):
+    """An mbarrier wait that nothing completes gives up after its bound,
+    frees its tensor memory and leaves the context usable: a tensor-core
+    GEMM runs correctly right after it."""
+    import ctypes as C
+    t = C.c_int(-1)
+    assert fe.lib.fe_tc_wait_selftest(2000, C.byref(t)) == fe.FE_ETIMEOUT
+    assert t.value == 1
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((128, 32)).astype(np.float32)
+    B = rng.standard_normal((16, 32)).astype(np.float32)
+    D = np.empty((128, 16), np.float32)
+    st = fe.lib.fe_tc_gemm_selftest(fe.FE_BF16, 16, 32, A.ctypes.data, B.ctypes.data, D.ctypes.data)
+    assert st == fe.FE_OK
+    ref = round_bf16(A).astype(np.float64) @ round_bf16(B).astype(np.float64).T
+    np.testing.assert_allclose(D, ref, rtol=1e-5, atol=1e-5 * np.abs(ref).max())
