@@ -14,6 +14,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 #include <vector>
 
 #include "fe_internal.cuh"
@@ -156,17 +157,25 @@ fe_status fe_ssim(const float *x, const float *y, int H, int W, double peak, dou
     if (!(peak > 0.0) || !std::isfinite(peak)) return fail(FE_EINVAL, "fe_ssim: peak must be > 0");
     if (!device_ptr(x) || !device_ptr(y)) return fail(FE_EINVAL, "fe_ssim: x and y must be device pointers");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    static bool init = false;
-    if (!init) {
-        double g[SW], sum = 0.0;
-        for (int i = 0; i < SW; ++i) sum += (g[i] = std::exp(-0.5 * (i - SR) * (i - SR) / (1.5 * 1.5)));
-        for (int i = 0; i < SW; ++i) g[i] /= sum;
-        if (cudaMemcpyToSymbol(c_gauss, g, sizeof g) != cudaSuccess)
-            return fail(FE_ECUDA, "fe_ssim: window upload failed");
-        const int smem = (int)(5 * SIN * ST * sizeof(double) + 2 * SIN * SIN * sizeof(float));
-        if (cudaFuncSetAttribute(ssim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-            return fail(FE_ECUDA, "fe_ssim: shared-memory attribute failed");
-        init = true;
+    // per-device set-up (the window in constant memory, the kernel's
+    // shared-memory opt-in), once per device and process
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return fail(FE_ECUDA, "fe_ssim: no device");
+    {
+        static std::mutex mu;
+        static bool ready[64] = {};
+        std::lock_guard<std::mutex> lk(mu);
+        if (!ready[dev]) {
+            double g[SW], sum = 0.0;
+            for (int i = 0; i < SW; ++i) sum += (g[i] = std::exp(-0.5 * (i - SR) * (i - SR) / (1.5 * 1.5)));
+            for (int i = 0; i < SW; ++i) g[i] /= sum;
+            if (cudaMemcpyToSymbol(c_gauss, g, sizeof g) != cudaSuccess)
+                return fail(FE_ECUDA, "fe_ssim: window upload failed");
+            const int smem = (int)(5 * SIN * ST * sizeof(double) + 2 * SIN * SIN * sizeof(float));
+            if (cudaFuncSetAttribute(ssim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+                return fail(FE_ECUDA, "fe_ssim: shared-memory attribute failed");
+            ready[dev] = true;
+        }
     }
     const int Ho = H - SW + 1, Wo = W - SW + 1;
     const dim3 grid((Wo + ST - 1) / ST, (Ho + ST - 1) / ST);
