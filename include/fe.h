@@ -15,7 +15,7 @@
  *     grad F(u) = sum_i theta_i K_i^T rho'(K_i u),  rho'(z) = 2z / (1 + z^2)
  *     prox: u_p = (uhat_p + sqrt(uhat_p^2 + 4(1+tau l) tau l f_p^2)) / (2(1+tau l))
  *
- * Second model (fe_params.model = FE_MODEL_COMBINED, FP32 form only): the
+ * Second model (fe_params.model = FE_MODEL_COMBINED, every precision form): the
  * combined model of Eq. newmodel (Sec. III-A), iterated in w = log u:
  *
  *     argmin_w  F(e^w) + sum_p lambda1/2 (2 w_p + f_p^2 e^{-2 w_p})
@@ -99,7 +99,7 @@ typedef enum {
 
 typedef enum {
     FE_MODEL_VARIANT = 0,   /* Eq. variant in u (all precision forms) */
-    FE_MODEL_COMBINED = 1   /* Eq. newmodel in w = log u (FE_FP32 only) */
+    FE_MODEL_COMBINED = 1   /* Eq. newmodel in w = log u */
 } fe_model;
 
 /* Solver parameters.  All pointers are HOST pointers, copied by fe_init. */
@@ -124,7 +124,7 @@ typedef struct {
                                Tensor-core forms: 0 only (one shape, 58 rows x
                                26 columns).
                                Other values: FE_EUNSUPPORTED. */
-    int model;              /* fe_model (FE_MODEL_COMBINED: prec must be FE_FP32) */
+    int model;              /* fe_model */
     double lambda1;         /* FE_MODEL_COMBINED: weight lambda1 >= 0 of the
                                log-domain term (lambda + lambda1 > 0); ignored
                                by FE_MODEL_VARIANT */

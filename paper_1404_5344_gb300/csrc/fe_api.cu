@@ -197,8 +197,6 @@ fe_status validate_params(fe_ctx *c, const fe_params *p) {
         if (!(p->lambda >= 0.0) || !std::isfinite(p->lambda) || !(p->lambda1 >= 0.0) || !std::isfinite(p->lambda1) ||
             !(p->lambda + p->lambda1 > 0.0))
             return set_err(c, FE_EINVAL, "combined model: lambda, lambda1 must be finite, >= 0, not both 0");
-        if (p->prec != FE_FP32)
-            return set_err(c, FE_EUNSUPPORTED, "the combined model runs in the FP32 form only");
     }
     if (!(p->beta >= 0.0 && p->beta < 1.0)) return set_err(c, FE_EINVAL, "beta must be in [0,1)");
     if (!(p->L0 > 0.0) || !std::isfinite(p->L0)) return set_err(c, FE_EINVAL, "L0 must be > 0");
@@ -219,7 +217,7 @@ fe_status validate_params(fe_ctx *c, const fe_params *p) {
 // Launch one tile kernel of the context's precision form.
 cudaError_t launch_tiles(const fe_ctx *c, int mode, const KParams &kp, int grid) {
     if (c->prm.prec == FE_FP32) return fp32_launch(mode, kp, grid, c->s, c->tile_y, c->prm.model);
-    return tc_launch(mode, c->prm.prec == FE_BF16 ? 1 : 2, kp, grid, c->s);
+    return tc_launch(mode, c->prm.prec == FE_BF16 ? 1 : 2, kp, grid, c->s, c->prm.model);
 }
 
 // Tile origins and owned extents along one axis of length N with tile T.
@@ -372,7 +370,7 @@ fe_status build_graph(fe_ctx *c) {
     std::memset(&knp, 0, sizeof knp);
     const int fmt = c->prm.prec == FE_BF16 ? 1 : 2;
     const bool tc = c->prm.prec != FE_FP32;
-    knp.func = const_cast<void *>(tc ? tc_trial_entry(fmt) : fp32_trial_entry(c->tile_y, c->prm.model));
+    knp.func = const_cast<void *>(tc ? tc_trial_entry(fmt, c->prm.model) : fp32_trial_entry(c->tile_y, c->prm.model));
     knp.gridDim = dim3(c->ntiles);
     knp.blockDim = dim3(tc ? tc_threads() : fp32_threads(c->tile_y));
     knp.sharedMemBytes = (unsigned)(tc ? tc_smem_bytes(fmt) : fp32_smem_bytes(c->tile_y));

@@ -123,9 +123,13 @@ const void *fp32c_trial_entry(int T);
 constexpr int tc_tile_y = 58, tc_tile_x = 26;  // output tile; tile + 3-pixel halo = 64 x 32
 size_t tc_smem_bytes(int fmt);
 int tc_threads();
-cudaError_t tc_prepare();
-cudaError_t tc_launch(int mode, int fmt, const KParams &p, int grid, cudaStream_t s);
-const void *tc_trial_entry(int fmt);
+cudaError_t tc_prepare();  // every format and model
+// model: 0 = Eq. variant (iterate u), 1 = combined model (iterate w = log u)
+cudaError_t tc_launch(int mode, int fmt, const KParams &p, int grid, cudaStream_t s, int model = 0);
+const void *tc_trial_entry(int fmt, int model = 0);
+cudaError_t tcc_prepare();  // combined-model instantiations (fe_tc_comb.cu)
+cudaError_t tcc_launch(int mode, int fmt, const KParams &p, int grid, cudaStream_t s);
+const void *tcc_trial_entry(int fmt);
 // Host: filter bank rounded to the operand type (BF16 round-to-nearest-even,
 // TF32 round-to-nearest-away) in the byte layout of the two GEMM B operands.
 void tc_build_weights(int fmt, const float *filters, int nf, std::vector<unsigned char> &fwd,

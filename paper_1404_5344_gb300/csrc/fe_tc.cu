@@ -1,548 +1,14 @@
-// Tensor-core forms of the fused iPiano trial kernel (FE_BF16, FE_TF32).
-//
-// Same trial as the FP32 kernel (inertial step, closed-form prox, forward bank,
-// rho', adjoint bank with the symmetric-boundary fold, FP64 partial sums and
-// the backtracking decision), with both filter banks run as GEMMs on the
-// 5th-generation tensor cores (tcgen05.mma, FP32 accumulation in tensor
-// memory):
-//
-//   forward  Z[q, i] = sum_k A[q, k] Bf[i, k]: A = im2col of u^{n+1}, K index
-//            k = 8a + b for the window row a and column b of pixel q (b = 7 is
-//            a padding tap of weight 0, so that one kernel row is 8
-//            consecutive pixels of one row of u), Bf = flipped filters.  One
-//            GEMM of M = 128 pixels, N = 48 filters.
-//   adjoint  S[q, t] = sum_i R[q, i] Ba[t, i]: R = r_i(q) = theta_i rho'(z_i),
-//            Ba[t, i] = k_i[t].  M = 128 pixels, N = 64 (49 taps + zeros).
-//            K_i^T r = sum_t shift_t(S[:, t]) (col2im): the horizontal part is a
-//            warp-shuffle sum (one warp = one 32-pixel row), the vertical part a
-//            7-row gather from a ring of shared-memory rows.
-//
-// Precision form: the filter bank is rounded once to the operand type (the
-// bank of the form); the data operands u and r are each carried as a hi + lo
-// pair of that type (K doubles; the B operand is stored once and the MMAs of
-// the lo half re-read it), so z and S are accurate for the rounded bank and
-// the descent test sees a consistent gradient.  The prologue writes u^{n+1}
-// as hi and lo planes of the operand type (BF16: plus copies shifted by one
-// element, so that every 8-pixel run starts on a 4-byte boundary); the
-// im2col is then a copy of 4-byte words.
-//
-// Geometry: 26 x 58 output tile; tile + 3-pixel halo = 32 x 64 pixels = 16
-// GEMM blocks of 4 rows x 32 columns (M = 128); tile + 6 = 38 x 70 for u^{n+1}.
-// 256 threads: the two warpgroups split the epilogues by TMEM column; one
-// thread issues the MMAs.  BF16 fits two CTAs per SM (85 KB of shared memory).
-//
-// Waits on the MMA completion barriers are bounded; on a time-out the kernel
-// records tc_error, poisons its partial sums (the image stops with a
-// non-finite status) and still releases its tensor memory.
-#include <cuda_bf16.h>
-#include <cuda_runtime.h>
-#include <math.h>
-#include <stdint.h>
-
+// Tensor-core forms: host side (rounding of the bank, operand tables, entry
+// points) and the instantiation for the model with the I-divergence data
+// term; the kernel template is in fe_tc_kernel.cuh, the combined model's
+// instantiation in fe_tc_comb.cu.
 #include <cstring>
+#include <vector>
 
-#include "fe_internal.cuh"
-#include "fe_tile_common.cuh"
-#include "tc_ptx.cuh"
+#include "fe_tc_kernel.cuh"
 
 namespace fe {
 namespace {
-
-constexpr int TY = tc_tile_y, TX = tc_tile_x, NT = 256;
-constexpr int R3Y = TY + 6, R3X = TX + 6;    // 64 x 32
-constexpr int R6Y = TY + 12, R6X = TX + 12;  // 70 x 38
-constexpr int PP = 40;  // plane pitch (elements): R6X + 2 zero columns read by the padding tap
-constexpr int NBLK = R3Y / 4;                // 16 GEMM blocks of 128 pixels
-constexpr int NF = 48;                       // N of the forward GEMM
-constexpr int NTAP = 64;                     // N of the adjoint GEMM (49 taps + zeros)
-constexpr int KADJ = 2 * NF;                 // r hi | r lo
-constexpr int HRING = 12;                    // rows of the horizontal-sum ring
-constexpr int TMEM_COLS = 128;               // D_fwd at column 0, D_adj at column 64
-static_assert(R3X == 32, "one warp per halo row");
-static_assert(R3Y % 4 == 0, "GEMM blocks of 4 rows");
-
-template <int FMT>
-struct Cfg {
-    static constexpr int EB = FMT == 1 ? 2 : 4;            // operand bytes
-    static constexpr int KSTEP = FMT == 1 ? 16 : 8;        // K per MMA
-    static constexpr int KPASS = FMT == 1 ? 64 : 56;       // 7 rows x 8 taps, padded to KSTEP
-    static constexpr int KFWD = 2 * KPASS;                 // u hi | u lo
-    static constexpr int E = 16 / EB;                      // elements per 16-byte chunk
-    static constexpr int NCH = KPASS / E;                  // chunks per pass
-    static constexpr int RCH = 8 / E;                      // chunks per kernel row
-    static constexpr int NPL = FMT == 1 ? 4 : 2;           // planes: hi, (hi shifted,) lo, (lo shifted)
-    // plane stride in 4-byte words; BF16: = 16 (mod 32) so that the even and
-    // odd lanes of the im2col (unshifted / shifted copy) use disjoint banks
-    static constexpr int PL_WORDS = FMT == 1 ? 1424 : R6Y * PP;
-    static_assert(PL_WORDS * 4 >= R6Y * PP * EB, "plane holds the u region");
-    static constexpr size_t AF_BYTES = (size_t)128 * KFWD * EB;
-    static constexpr size_t R_BYTES = (size_t)128 * KADJ * EB;
-    static constexpr size_t BF_BYTES = (size_t)NF * KPASS * EB;   // one pass: hi and lo MMAs share it
-    static constexpr size_t BA_BYTES = (size_t)NTAP * NF * EB;    // likewise for r hi and r lo
-    static constexpr size_t OFF_AF = 0;
-    static constexpr size_t OFF_R = OFF_AF + AF_BYTES;
-    static constexpr size_t OFF_BF = OFF_R + R_BYTES;
-    static constexpr size_t OFF_BA = OFF_BF + BF_BYTES;
-    static constexpr size_t OFF_U = OFF_BA + BA_BYTES;       // NPL planes of u^{n+1}
-    static constexpr size_t OFF_H = OFF_U + (size_t)NPL * PL_WORDS * 4;
-    static constexpr size_t OFF_G = OFF_H + (size_t)HRING * 7 * 32 * 4;
-    static constexpr size_t OFF_TH = OFF_G + (size_t)R3Y * R3X * 4;
-    static constexpr size_t OFF_RED = OFF_TH + (size_t)2 * NF * 4;
-    static constexpr size_t BYTES = OFF_RED + (size_t)(NT / 32) * NRED * 8;
-    static_assert(OFF_R % 128 == 0 && OFF_BF % 128 == 0 && OFF_BA % 128 == 0 && OFF_U % 128 == 0,
-                  "operand alignment");
-    static_assert(OFF_U % 16 == 0 && OFF_TH % 16 == 0 && OFF_RED % 8 == 0, "alignment");
-    static_assert(BF_BYTES % 16 == 0 && BA_BYTES % 16 == 0, "vector copies");
-};
-static_assert(2 * (Cfg<1>::BYTES + 1024) <= 228 * 1024, "BF16: two CTAs per SM");
-static_assert(Cfg<2>::BYTES <= 227 * 1024, "TF32: one CTA per SM");
-
-constexpr float LN2 = 0.69314718055994530942f;
-
-// hi = x rounded to the operand type, lo = (x - hi) rounded, for one 16-byte
-// chunk of E consecutive K values.
-template <int FMT>
-__device__ __forceinline__ void hilo_chunk(const float *v, uint4 &hi, uint4 &lo);
-template <>
-__device__ __forceinline__ void hilo_chunk<1>(const float *v, uint4 &hi, uint4 &lo) {
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-        const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[2 * j] - __low2float(h2), v[2 * j + 1] - __high2float(h2));
-        h[j] = *reinterpret_cast<const uint32_t *>(&h2);
-        l[j] = *reinterpret_cast<const uint32_t *>(&l2);
-    }
-    hi = make_uint4(h[0], h[1], h[2], h[3]);
-    lo = make_uint4(l[0], l[1], l[2], l[3]);
-}
-template <>
-__device__ __forceinline__ void hilo_chunk<2>(const float *v, uint4 &hi, uint4 &lo) {
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const float hv = tc::round_tf32(v[j]);
-        h[j] = __float_as_uint(hv);
-        l[j] = __float_as_uint(tc::round_tf32(v[j] - hv));
-    }
-    hi = make_uint4(h[0], h[1], h[2], h[3]);
-    lo = make_uint4(l[0], l[1], l[2], l[3]);
-}
-
-// im2col of u^{n+1} for GEMM block blk: pixel m of the block (R3 row 4 blk +
-// m/32, column pc = m%32) gets, for window row a, the 8 values u(4 blk + m/32
-// + a, pc .. pc + 7) as K values 8a .. 8a + 7 (hi part in chunks [0, NCH), lo
-// in [NCH, 2 NCH)).  part 0 copies the hi plane, part 1 the lo plane.  The
-// runs are copied as 4-byte words: BF16 reads the unshifted plane at even pc
-// and the copy shifted by one element at odd pc.
-template <int FMT>
-__device__ __forceinline__ void im2col(const uint32_t *__restrict__ sP, unsigned char *__restrict__ sAF, int blk,
-                                       int m, int part) {
-    using C = Cfg<FMT>;
-    const int pr = 4 * blk + (m >> 5), pc = m & 31;
-    const uint32_t *src;
-    if (FMT == 1)
-        src = sP + (2 * part + (pc & 1)) * C::PL_WORDS + pr * (PP / 2) + (pc >> 1);
-    else
-        src = sP + part * C::PL_WORDS + pr * PP + pc;
-    constexpr int ROW_WORDS = PP * C::EB / 4;
-    unsigned char *row = sAF + tc::kmajor_offset(m, 0, C::KFWD, C::EB) + part * C::NCH * 128;
-#pragma unroll
-    for (int a = 0; a < KS; ++a)
-#pragma unroll
-        for (int h = 0; h < C::RCH; ++h) {
-            const uint32_t *w = src + a * ROW_WORDS + h * 4;
-            *reinterpret_cast<uint4 *>(row + (a * C::RCH + h) * 128) = make_uint4(w[0], w[1], w[2], w[3]);
-        }
-}
-
-template <int MODE, int FMT>
-__global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KParams p) {
-    using C = Cfg<FMT>;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *sAF = smem + C::OFF_AF;
-    unsigned char *sR = smem + C::OFF_R;
-    unsigned char *sBf = smem + C::OFF_BF;
-    unsigned char *sBa = smem + C::OFF_BA;
-    uint32_t *sP = reinterpret_cast<uint32_t *>(smem + C::OFF_U);  // u^{n+1} planes
-    float *sH = reinterpret_cast<float *>(smem + C::OFF_H);
-    float *sG = reinterpret_cast<float *>(smem + C::OFF_G);
-    float *sTh = reinterpret_cast<float *>(smem + C::OFF_TH);  // theta_i, then 2 theta_i
-    double *sRed = reinterpret_cast<double *>(smem + C::OFF_RED);
-    __shared__ uint64_t bar_f, bar_a;
-    __shared__ uint32_t tbase;
-    __shared__ int sLast;
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int gtile = p.tile0 + (int)blockIdx.x;
-    const TileDesc td = p.tiles[gtile];
-    const int img = td.img;
-    const ImgDesc im = p.imgs[img];
-    ImgState *st = p.st + img;
-    const int H = im.H, W = im.W, y0 = td.y0, x0 = td.x0, oh = td.oh, ow = td.ow, sy = td.sy, sx = td.sx;
-
-    bool active = true;
-    int gcur_out = 0;
-    if (MODE == MODE_TRIAL) {
-        active = (st->done == 0) && (st->n < st->target);
-        gcur_out = st->gcur ^ 1;
-    }
-
-    if (active) {
-        // ---- rounded filter bank (B operands) and theta into shared memory --
-        {
-            const uint4 *gf = reinterpret_cast<const uint4 *>(p.tcw_fwd);
-            const uint4 *ga = reinterpret_cast<const uint4 *>(p.tcw_adj);
-            for (int j = tid; j < (int)(C::BF_BYTES / 16); j += NT) reinterpret_cast<uint4 *>(sBf)[j] = __ldg(gf + j);
-            for (int j = tid; j < (int)(C::BA_BYTES / 16); j += NT) reinterpret_cast<uint4 *>(sBa)[j] = __ldg(ga + j);
-            if (tid < NF) {
-                const float th = __ldg(p.theta + tid);
-                sTh[tid] = th;
-                sTh[NF + tid] = 2.0f * th;
-            }
-            // BF16: the last K chunk of each pass (window row 7) is zero in A
-            if (FMT == 1 && tid < 2 * 128) {
-                const int mm = tid & 127, pt = tid >> 7;
-                *reinterpret_cast<uint4 *>(sAF + tc::kmajor_offset(mm, 0, C::KFWD, C::EB) +
-                                           (pt * C::NCH + C::NCH - 1) * 128) = make_uint4(0u, 0u, 0u, 0u);
-            }
-            // the padding columns of the planes (read with weight 0) hold zeros
-            for (int j = tid; j < C::NPL * R6Y; j += NT) {
-                uint32_t *rowp = sP + (j / R6Y) * C::PL_WORDS + (j % R6Y) * (PP * C::EB / 4);
-                if (FMT == 1)
-                    rowp[(PP / 2) - 2] = rowp[(PP / 2) - 1] = 0u;  // elements 36..39 (the writes below fill 36, 37)
-                else
-                    rowp[PP - 2] = rowp[PP - 1] = 0u;
-            }
-        }
-        __syncthreads();  // pad zeros before the plane writes of the prologue
-        if (tid == 0) {
-            tc::mbar_init(&bar_f, 1);
-            tc::mbar_init(&bar_a, 1);
-        }
-        if (warp == 0) tc::tmem_alloc(&tbase, TMEM_COLS);
-
-        // ---- inertial step and prox on tile + 6 (owned pixels: sums) -------
-        // per-thread sums: compensated FP32 for F and G (large terms), plain
-        // FP32 for the small step-test terms
-        Sum2 accF{0.f, 0.f}, accG{0.f, 0.f};
-        float accGD = 0.f, accDD = 0.f, accDP = 0.f;
-        {
-            int cur = 0, gcur = 0;
-            float a = 0.f, b = 0.f, tl = 0.f;
-            if (MODE == MODE_TRIAL) {
-                cur = st->cur;
-                gcur = st->gcur;
-                const double alpha = st->alpha;
-                a = (float)alpha;
-                b = (float)p.beta;
-                tl = (float)(alpha * im.lambda);
-            }
-            const float *uc = (MODE == MODE_TRIAL || MODE == MODE_INIT) ? im.u[cur] : p.u_ext;
-            const float *upv = im.u[(cur + 2) % 3];
-            const float *gc = im.g[gcur];
-            float *un = im.u[(cur + 1) % 3];
-            const float *f2p = im.f2;
-            constexpr int NPIX = R6Y * R6X, UNR = 4;
-            for (int base = 0; base < NPIX; base += UNR * NT) {
-                size_t off[UNR];
-                bool inb[UNR], owned[UNR];
-                float u0[UNR], u_1[UNR], g0[UNR], f2[UNR];
-#pragma unroll
-                for (int k = 0; k < UNR; ++k) {
-                    const int idx = base + k * NT + tid;
-                    inb[k] = idx < NPIX;
-                    const int ry = inb[k] ? idx / R6X : 0, rx = inb[k] ? idx - ry * R6X : 0;
-                    off[k] = (size_t)reflect(y0 - 6 + ry, H) * W + reflect(x0 - 6 + rx, W);
-                    owned[k] = inb[k] && ry >= 6 + sy && ry < 6 + sy + oh && rx >= 6 + sx && rx < 6 + sx + ow;
-                    u0[k] = __ldg(uc + off[k]);
-                    f2[k] = (MODE == MODE_TRIAL || owned[k]) ? __ldg(f2p + off[k]) : 1.0f;
-                    if (MODE == MODE_TRIAL) {
-                        u_1[k] = __ldg(upv + off[k]);
-                        g0[k] = __ldg(gc + off[k]);
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < UNR; ++k) {
-                    if (!inb[k]) continue;
-                    float v;
-                    if (MODE == MODE_TRIAL) {
-                        const float dprev = u0[k] - u_1[k];
-                        const float uhat = fmaf(-a, g0[k], fmaf(b, dprev, u0[k]));
-                        v = prox_g(uhat, f2[k], tl);
-                        if (owned[k]) {
-                            un[off[k]] = v;
-                            const float d = v - u0[k];
-                            accGD = fmaf(g0[k], d, accGD);
-                            accDD = fmaf(d, d, accDD);
-                            accDP = fmaf(d, dprev, accDP);
-                        }
-                    } else {
-                        v = u0[k];
-                    }
-                    if (owned[k]) sum2_add(accG, v * v - 2.0f * f2[k] * logf(v));
-                    // hi / lo planes of the operand type
-                    const int idx = base + k * NT + tid, ry = idx / R6X, rx = idx - ry * R6X;
-                    if (FMT == 1) {
-                        const __nv_bfloat16 hb = __float2bfloat16_rn(v);
-                        const __nv_bfloat16 lb = __float2bfloat16_rn(v - __bfloat162float(hb));
-                        __nv_bfloat16 *ph = reinterpret_cast<__nv_bfloat16 *>(sP);
-                        __nv_bfloat16 *pl = reinterpret_cast<__nv_bfloat16 *>(sP + 2 * C::PL_WORDS);
-                        const int e = ry * PP + rx;
-                        ph[e] = hb;
-                        pl[e] = lb;
-                        if (rx > 0) {  // shifted copies: element rx - 1 holds column rx
-                            ph[2 * C::PL_WORDS + e - 1] = hb;
-                            pl[2 * C::PL_WORDS + e - 1] = lb;
-                        }
-                    } else {
-                        const float hv = tc::round_tf32(v);
-                        const int e = ry * PP + rx;
-                        sP[e] = __float_as_uint(hv);
-                        sP[C::PL_WORDS + e] = __float_as_uint(tc::round_tf32(v - hv));
-                    }
-                }
-            }
-        }
-
-        const uint32_t sAF_u32 = tc::smem_u32(sAF), sR_u32 = tc::smem_u32(sR);
-        const uint32_t sBf_u32 = tc::smem_u32(sBf), sBa_u32 = tc::smem_u32(sBa);
-        constexpr uint32_t SBO_F = (uint32_t)(C::KFWD / C::E) * 128, SBO_A = (uint32_t)(KADJ / C::E) * 128;
-        constexpr uint32_t SBO_BF = (uint32_t)(C::KPASS / C::E) * 128, SBO_BA = (uint32_t)(NF / C::E) * 128;
-        constexpr int KS_F = C::KPASS / C::KSTEP, KS_A = NF / C::KSTEP;  // K steps of one pass
-        constexpr uint32_t IDESC_F = tc::make_idesc(FMT, 128, NF), IDESC_A = tc::make_idesc(FMT, 128, NTAP);
-        const int m = tid & 127, part = tid >> 7;  // im2col: pixel, chunk parity
-        const int wg = warp >> 2, lg = warp & 3;   // epilogues: column half, TMEM lane group
-        const bool edge_x = x0 == 0 || x0 + TX >= W;
-        const bool full_y = y0 >= 3 && y0 + TY + 3 <= H, full_x = x0 >= 3 && x0 + TX + 3 <= W;
-        const bool all_in = full_y && full_x;  // every halo pixel lies in the image
-
-        // block 0: im2col and forward MMA
-        im2col<FMT>(sP, sAF, 0, m, part);
-        tc::fence_proxy_async();
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        const uint32_t taddr = tbase;
-        const uint32_t lane_base = (uint32_t)(lg * 32) << 16;
-        if (tid == 0) {
-#pragma unroll
-            for (int ks = 0; ks < C::KFWD / C::KSTEP; ++ks)
-                tc::mma<FMT>(taddr, tc::make_smem_desc(sAF_u32 + ks * 256, 128, SBO_F),
-                             tc::make_smem_desc(sBf_u32 + (ks % KS_F) * 256, 128, SBO_BF), IDESC_F,
-                             ks > 0 ? 1u : 0u);
-            tc::mma_commit(&bar_f);
-        }
-        uint32_t phase_f = 0, phase_a = 0;
-        bool tc_ok = true;
-
-        // epilogue 2 of block pb: horizontal col2im of S (TMEM) into the H ring
-        auto epi2 = [&](int pb) {
-            const int row = 4 * pb + lg;
-            const int slot = row % HRING;
-            const int a_lo = wg == 0 ? 0 : 4, na = wg == 0 ? 4 : 3;
-            float s8[4][8];
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (j < na) tc::tmem_ld8(taddr + lane_base + (uint32_t)(64 + KS * (a_lo + j)), s8[j]);
-            tc::tmem_ld_wait();
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (j >= na) break;
-                float h = 0.f;
-                if (edge_x) {
-#pragma unroll
-                    for (int bb = 0; bb < KS; ++bb) {
-                        const int src = lane - 3 + bb;
-                        const float v = __shfl_sync(0xffffffffu, s8[j][bb], src & 31);
-                        h += (src >= 0 && src < 32) ? v : 0.0f;
-                    }
-                } else {
-                    // interior tile: lanes 3..28 (the only ones used) have all sources in the warp
-#pragma unroll
-                    for (int bb = 0; bb < KS; ++bb) h += __shfl_sync(0xffffffffu, s8[j][bb], (lane - 3 + bb) & 31);
-                }
-                sH[(slot * KS + a_lo + j) * 32 + lane] = h;
-            }
-        };
-        // vertical col2im of the ext rows whose 7 source rows are complete
-        auto emit = [&](int ty) {
-            if (ty < -3 || ty >= TY + 3) return;
-            float g = 0.f;
-            int s = ((ty % HRING) + HRING) % HRING;
-#pragma unroll
-            for (int aa = 0; aa < KS; ++aa) {
-                const int srow = ty + aa;
-                if (srow >= 0 && srow < R3Y) g += sH[(s * KS + aa) * 32 + lane];
-                s = s + 1 == HRING ? 0 : s + 1;
-            }
-            sG[(ty + 3) * 32 + lane] = g;
-        };
-
-        for (int blk = 0; blk < NBLK; ++blk) {
-            // (a) col2im of the previous block, overlapping MMA_fwd(blk)
-            if (blk > 0) {
-                if (!tc::mbar_wait(&bar_a, phase_a)) tc_ok = false;
-                phase_a ^= 1u;
-                tc::fence_after_sync();
-                epi2(blk - 1);
-                tc::fence_before_sync();
-                __syncthreads();
-                if (tid < 128) emit(4 * (blk - 1) - 6 + (tid >> 5));
-            }
-            // (b) epilogue 1 of this block: rho' -> R (hi | lo), energy terms
-            if (!tc::mbar_wait(&bar_f, phase_f)) tc_ok = false;
-            phase_f ^= 1u;
-            tc::fence_after_sync();
-            {
-                const int row = 4 * blk + lg, col = lane;
-                const bool inimg = all_in || ((unsigned)(y0 - 3 + row) < (unsigned)H && (unsigned)(x0 - 3 + col) < (unsigned)W);
-                const bool owned = row >= 3 + sy && row < 3 + sy + oh && col >= 3 + sx && col < 3 + sx + ow;
-                float z[24];
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    float t8[8];
-                    tc::tmem_ld8(taddr + lane_base + (uint32_t)(24 * wg + 8 * j), t8);
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) z[8 * j + k] = t8[k];
-                }
-                tc::tmem_ld_wait();
-                const float4 *th4 = reinterpret_cast<const float4 *>(sTh + 24 * wg);
-                const float4 *tw4 = reinterpret_cast<const float4 *>(sTh + NF + 24 * wg);
-                float r[24], psum = 0.f;
-#pragma unroll
-                for (int j = 0; j < 6; ++j) {
-                    const float4 t1 = th4[j], t2 = tw4[j];
-                    const float th[4] = {t1.x, t1.y, t1.z, t1.w}, tw[4] = {t2.x, t2.y, t2.z, t2.w};
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const float zz = z[4 * j + k];
-                        const float q = fmaf(zz, zz, 1.0f);
-                        r[4 * j + k] = __fdividef(tw[k] * zz, q);
-                        psum = fmaf(th[k], __log2f(q), psum);
-                    }
-                }
-                if (!inimg) {
-#pragma unroll
-                    for (int i = 0; i < 24; ++i) r[i] = 0.0f;
-                }
-                if (owned) sum2_add(accF, psum * LN2);
-                unsigned char *rowp = sR + tc::kmajor_offset((lg << 5) + lane, 0, KADJ, C::EB);
-#pragma unroll
-                for (int j = 0; j < 24 / C::E; ++j) {
-                    uint4 hi, lo;
-                    hilo_chunk<FMT>(r + j * C::E, hi, lo);
-                    *reinterpret_cast<uint4 *>(rowp + ((24 * wg) / C::E + j) * 128) = hi;
-                    *reinterpret_cast<uint4 *>(rowp + ((NF + 24 * wg) / C::E + j) * 128) = lo;
-                }
-            }
-            tc::fence_before_sync();
-            tc::fence_proxy_async();
-            __syncthreads();
-            if (tid == 0) {
-                tc::fence_after_sync();
-#pragma unroll
-                for (int ks = 0; ks < KADJ / C::KSTEP; ++ks)
-                    tc::mma<FMT>(taddr + 64, tc::make_smem_desc(sR_u32 + ks * 256, 128, SBO_A),
-                                 tc::make_smem_desc(sBa_u32 + (ks % KS_A) * 256, 128, SBO_BA), IDESC_A,
-                                 ks > 0 ? 1u : 0u);
-                tc::mma_commit(&bar_a);
-            }
-            // (c) im2col of the next block, overlapping MMA_adj(blk)
-            if (blk + 1 < NBLK) {
-                im2col<FMT>(sP, sAF, blk + 1, m, part);
-                tc::fence_proxy_async();
-                tc::fence_before_sync();
-                __syncthreads();
-                if (tid == 0) {
-                    tc::fence_after_sync();
-#pragma unroll
-                    for (int ks = 0; ks < C::KFWD / C::KSTEP; ++ks)
-                        tc::mma<FMT>(taddr, tc::make_smem_desc(sAF_u32 + ks * 256, 128, SBO_F),
-                                     tc::make_smem_desc(sBf_u32 + (ks % KS_F) * 256, 128, SBO_BF), IDESC_F,
-                                     ks > 0 ? 1u : 0u);
-                    tc::mma_commit(&bar_f);
-                }
-            }
-        }
-        // last block's col2im, then the ext rows whose missing sources lie off the tile
-        if (!tc::mbar_wait(&bar_a, phase_a)) tc_ok = false;
-        phase_a ^= 1u;
-        tc::fence_after_sync();
-        epi2(NBLK - 1);
-        tc::fence_before_sync();
-        __syncthreads();
-        if (tid < 128) emit(4 * (NBLK - 1) - 6 + (tid >> 5));
-        if (tid >= 128 && tid < 224) emit(4 * (NBLK - 1) - 2 + ((tid - 128) >> 5));  // 58, 59, 60
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        if (warp == 0) tc::tmem_dealloc(taddr, TMEM_COLS);
-
-        // ---- fold the frame, write the owned gradient ------------------------
-        if (MODE != MODE_ENERGY_EXT) {
-            float *gout;
-            if (MODE == MODE_GRAD_EXT)
-                gout = p.g_ext;
-            else if (MODE == MODE_INIT)
-                gout = im.g[0];
-            else
-                gout = im.g[gcur_out];
-            for (int idx = tid; idx < oh * ow; idx += NT) {
-                const int ty = sy + idx / ow, tx = sx + idx % ow;
-                const int y = y0 + ty, x = x0 + tx;
-                float gv = sG[(ty + 3) * 32 + tx + 3];
-                if (y < 3 || y >= H - 3 || x < 3 || x >= W - 3) {
-                    // ext positions the symmetric extension maps onto (y, x): at
-                    // most one per axis (H, W >= 8); scalars, so that nothing is
-                    // indexed dynamically (local memory)
-                    const int oy = ty + 3, ox = tx + 3;
-                    const int qy = y < 3 ? (-y - 1) - y0 + 3 : (y >= H - 3 ? (2 * H - 1 - y) - y0 + 3 : -1);
-                    const int qx = x < 3 ? (-x - 1) - x0 + 3 : (x >= W - 3 ? (2 * W - 1 - x) - x0 + 3 : -1);
-                    if (qx >= 0) gv += sG[oy * 32 + qx];
-                    if (qy >= 0) {
-                        gv += sG[qy * 32 + ox];
-                        if (qx >= 0) gv += sG[qy * 32 + qx];
-                    }
-                }
-                gout[(size_t)y * W + x] = gv;
-            }
-        }
-        if (!tc_ok) {
-            accGD = __int_as_float(0x7fc00000);  // NaN step sum: the image stops (FE_ENONFINITE)
-            if (tid == 0) atomicExch(p.tc_error, 1);
-        }
-        const Sum2 vals[NRED] = {accF, accG, {accGD, 0.f}, {accDD, 0.f}, {accDP, 0.f}};
-        tile_finish<NT>(p, MODE, gtile, img, im, st, vals, sRed, &sLast);
-    }
-    if (MODE == MODE_TRIAL) loop_control(p);
-}
-
-template <int FMT>
-cudaError_t prepare_fmt() {
-    cudaError_t e = cudaSuccess;
-    const int b = (int)Cfg<FMT>::BYTES;
-    if ((e = cudaFuncSetAttribute(tc_tile_kernel<MODE_TRIAL, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)))
-        return e;
-    if ((e = cudaFuncSetAttribute(tc_tile_kernel<MODE_INIT, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)))
-        return e;
-    if ((e = cudaFuncSetAttribute(tc_tile_kernel<MODE_GRAD_EXT, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)))
-        return e;
-    return cudaFuncSetAttribute(tc_tile_kernel<MODE_ENERGY_EXT, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-}
-
-template <int FMT>
-cudaError_t launch_fmt(int mode, const KParams &p, int ngrid, cudaStream_t s) {
-    const size_t b = Cfg<FMT>::BYTES;
-    switch (mode) {
-        case MODE_TRIAL: tc_tile_kernel<MODE_TRIAL, FMT><<<ngrid, NT, b, s>>>(p); break;
-        case MODE_INIT: tc_tile_kernel<MODE_INIT, FMT><<<ngrid, NT, b, s>>>(p); break;
-        case MODE_GRAD_EXT: tc_tile_kernel<MODE_GRAD_EXT, FMT><<<ngrid, NT, b, s>>>(p); break;
-        case MODE_ENERGY_EXT: tc_tile_kernel<MODE_ENERGY_EXT, FMT><<<ngrid, NT, b, s>>>(p); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
 
 // Host rounding of the filter bank: BF16 round-to-nearest-even, TF32
 // round-to-nearest with ties away from zero (as cvt.rna.tf32.f32).
@@ -599,18 +65,17 @@ size_t tc_smem_bytes(int fmt) { return fmt == 1 ? Cfg<1>::BYTES : Cfg<2>::BYTES;
 int tc_threads() { return NT; }
 
 cudaError_t tc_prepare() {
-    cudaError_t e = prepare_fmt<1>();
-    if (e != cudaSuccess) return e;
-    return prepare_fmt<2>();
+    cudaError_t e = prepare_fmt<1, 0>();
+    if (e == cudaSuccess) e = prepare_fmt<2, 0>();
+    if (e == cudaSuccess) e = tcc_prepare();
+    return e;
 }
 
-cudaError_t tc_launch(int mode, int fmt, const KParams &p, int ngrid, cudaStream_t s) {
-    return fmt == 1 ? launch_fmt<1>(mode, p, ngrid, s) : launch_fmt<2>(mode, p, ngrid, s);
+cudaError_t tc_launch(int mode, int fmt, const KParams &p, int ngrid, cudaStream_t s, int model) {
+    if (model == 1) return tcc_launch(mode, fmt, p, ngrid, s);
+    return fmt == 1 ? launch_fmt<1, 0>(mode, p, ngrid, s) : launch_fmt<2, 0>(mode, p, ngrid, s);
 }
 
-const void *tc_trial_entry(int fmt) {
-    return fmt == 1 ? reinterpret_cast<const void *>(&tc_tile_kernel<MODE_TRIAL, 1>)
-                    : reinterpret_cast<const void *>(&tc_tile_kernel<MODE_TRIAL, 2>);
-}
+const void *tc_trial_entry(int fmt, int model) { return model == 1 ? tcc_trial_entry(fmt) : trial_entry<0>(fmt); }
 
 }  // namespace fe

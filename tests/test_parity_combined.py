@@ -194,9 +194,73 @@ def test_solve_to_tolerance_combined(fe, bank):
 def test_combined_model_options(fe, bank):
     k, th = bank
     _, f = _problem(40, 40, seed=1)
-    for bad in (dict(prec="bf16"), dict(prec="tf32"), dict(lam=0.0, lam1=0.0), dict(lam=-1.0),
-                dict(lam1=float("nan"))):
+    for bad in (dict(lam=0.0, lam1=0.0), dict(lam=-1.0), dict(lam1=float("nan")), dict(tile=48)):
         with pytest.raises(fe.FeError):
             _solver(fe, f, k, th, **bad)
     with pytest.raises(fe.FeError):
         fe.Solver([f], k, th, model=7)
+
+
+# ---- tensor-core forms of the combined model --------------------------------
+# The form's model is the bank rounded once to the operand type; the oracle
+# runs with the same rounded bank.  The bound on K^T r at u is the variant
+# forms' (tests/test_parity_tc.py: the hi + lo operand split of u and r);
+# e^w adds the same first-order term as in the FP32 test above.
+TC_GRAD_TOL = {"bf16": 1e-3, "tf32": 2e-5}
+TC_STEP_TOL = {"bf16": 2e-5, "tf32": 1e-5}
+TC_NOISE = {"bf16": 2e-5, "tf32": 4e-6}
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("shape", [(64, 64), (131, 77), (59, 27)])
+def test_tc_gradient_parity_combined(fe, orc, bank, shape, prec):
+    from rounding import ROUND
+    k, th = bank
+    kq = ROUND[prec](k)
+    H, W = shape
+    _, f = _problem(H, W, seed=H + 2 * W)
+    w = np.log(f).astype(np.float32)
+    with _solver(fe, f, k, th, prec=prec) as s:
+        g, Fg = s.gradient(0, w)
+    g_ref, F_ref = orc.gradFw(w, kq, th)
+    u = np.exp(w.astype(np.float64))
+    v_ref = g_ref / u
+    eps = 2.0 ** -24
+    A = np.zeros_like(u)
+    for i in range(kq.shape[0]):
+        ka = np.abs(kq[i]).astype(np.float64)
+        z = orc.K(u, kq[i])
+        A += th[i] * orc.KT(np.abs(2.0 * (1.0 - z * z) / (1.0 + z * z) ** 2) * orc.K(u, ka), ka)
+    bound = u * (TC_GRAD_TOL[prec] * np.max(np.abs(v_ref)) + 4 * eps * A) + 2 * eps * np.abs(g_ref)
+    err = np.abs(g.astype(np.float64) - g_ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    assert Fg == pytest.approx(F_ref, rel=10 * EF_TOL if prec == "bf16" else 2 * EF_TOL)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_tc_single_step_parity_combined(fe, orc, bank, prec):
+    from rounding import ROUND
+    k, th = bank
+    kq = ROUND[prec](k)
+    _, f = _problem(96, 130, seed=11)
+    prm = _oprm(orc, beta=0.8, L0=1.0, eta=2.0, c2=1e-6, max_iter=1)
+    with _solver(fe, f, k, th, prec=prec, beta=0.8, L0=1.0, eta=2.0, c2=1e-6) as s:
+        for nsteps in (0, 4):
+            if nsteps:
+                assert s.step(nsteps) == fe.FE_OK
+            w, wp, _, info = s.get_state(0)
+            assert s.step(1) == fe.FE_OK
+            w1, _, _, info1 = s.get_state(0)
+            K = int(round(np.log(info1["L"] / info["L"]) / np.log(2.0)))
+            ref = None
+            for j in range(K + 1):
+                r = orc.ipiano_fixed(f, kq, th, prm, [info["L"] * 2.0 ** j], w, wp)
+                F1, margin, gd = r["rec"][0, 2], r["rec"][0, 5], r["rec"][0, 6]
+                if j < K:
+                    if np.isfinite(F1):
+                        assert margin <= TC_NOISE[prec] * (abs(F1) + abs(gd))
+                else:
+                    assert np.isfinite(F1) and margin >= -TC_NOISE[prec] * (abs(F1) + abs(gd))
+                    ref = r
+            assert _relmax(w1, ref["u"]) <= TC_STEP_TOL[prec]
+            np.testing.assert_allclose(s.get_u(0), np.exp(w1.astype(np.float64)), rtol=1e-6)
