@@ -188,10 +188,21 @@ def cpu_baseline(fs, k, th, iters_total, seconds, kw=SOLVER_KW):
     out = orc.ipiano(f, k, th, oracle_prm(orc, kw, n))
     dt = time.perf_counter() - t0
     npx = f.size
+    cores = orc.num_threads()
+    # the same oracle on one core (a few iterations of the same image)
+    orc.set_threads(1)
+    try:
+        t1 = time.perf_counter()
+        out1 = orc.ipiano(f, k, th, oracle_prm(orc, kw, 3))
+        dt1 = time.perf_counter() - t1
+    finally:
+        orc.set_threads(cores)
     return {"value": round(npx * out["n"] / dt / 1e6, 4), "unit": "Mpixel*iter/s",
-            "cores": orc.num_threads(), "kind": "oracle",
+            "cores": cores, "kind": "oracle",
             "sample": "FP64 oracle, one %dx%d image of the workload, %d iPiano iterations "
-                      "(%.1f s)" % (f.shape[0], f.shape[1], out["n"], dt)}
+                      "(%.1f s)" % (f.shape[0], f.shape[1], out["n"], dt),
+            "single_core": {"value": round(npx * out1["n"] / dt1 / 1e6, 4), "cores": 1,
+                            "sample": "the same image, %d iterations (%.1f s)" % (out1["n"], dt1)}}
 
 
 def combine_ranks(local_ms, local_units, dist=None, device="cpu"):
