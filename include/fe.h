@@ -97,6 +97,8 @@ typedef enum {
     FE_BF16 = 2             /* filter bank on the tensor cores, BF16 operands */
 } fe_precision;
 
+#define FE_TILE_CLUSTER4 0x100  /* fe_params.tile flag: a 4-CTA cluster per tile */
+
 typedef enum {
     FE_MODEL_VARIANT = 0,   /* Eq. variant in u (all precision forms) */
     FE_MODEL_COMBINED = 1   /* Eq. newmodel in w = log u */
@@ -117,10 +119,14 @@ typedef struct {
     int max_backtrack;      /* rejections allowed per iteration, >= 0 */
     int prec;               /* fe_precision */
     int tile;               /* output tile of the trial kernel: 0 = autotune.  FP32:
-                               0, 32 or 64 (T x T); at 0 fe_init_batch times both
-                               shapes on the context's own images (the initial
-                               gradient kernel, 4 launches each) and keeps the
-                               faster, cached per device and list of image sizes.
+                               0, 64, 32 (T x T), or 32 | FE_TILE_CLUSTER4 (32 x 32
+                               tiles, each split by filter group over a cluster of
+                               4 CTAs that combine through distributed shared
+                               memory: for images too small to fill the GPU); at 0
+                               fe_init_batch times the three on the context's own
+                               images (the initial gradient kernel, 4 launches
+                               each) and keeps the fastest, cached per device and
+                               list of image sizes.
                                Tensor-core forms: 0 only (one shape, 58 rows x
                                26 columns).
                                Other values: FE_EUNSUPPORTED. */
@@ -237,6 +243,10 @@ FE_API fe_status fe_psnr(const float *x, const float *y, long long n, double pea
 /* Output tile (rows x columns) of the context's trial kernel, as chosen by
  * the autotuner or given in fe_params.tile.  FE_EINVAL on NULL arguments. */
 FE_API fe_status fe_tile_size(const fe_ctx *ctx, int *tile_y, int *tile_x);
+
+/* CTAs that work on one tile (1, or 4 for a thread-block cluster per tile);
+ * 0 for a NULL context. */
+FE_API int fe_tile_cluster(const fe_ctx *ctx);
 
 /* Device kernel launches issued by this context since creation (trial,
  * gradient, energy and bookkeeping kernels), for launch accounting. */

@@ -32,6 +32,7 @@ struct fe_ctx {
     std::vector<float> filt, theta;
     int nimg = 0, ntiles = 0, nfp = 0;
     int tile_y = 0, tile_x = 0;  // output tile of the trial kernel (autotuned or given)
+    int cluster = 1;             // CTAs per tile (FP32: 4 = a thread-block cluster per 32 x 32 tile)
     std::vector<int> H, W;
     std::vector<ImgDesc> himg;
     std::vector<TileDesc> htile;
@@ -207,8 +208,9 @@ fe_status validate_params(fe_ctx *c, const fe_params *p) {
         return set_err(c, FE_EINVAL, "unknown precision %d", p->prec);
     if (p->prec != FE_FP32 && p->nf > 48)
         return set_err(c, FE_EUNSUPPORTED, "the tensor-core forms take at most 48 filters (nf=%d)", p->nf);
-    if (p->prec == FE_FP32 && p->tile != 0 && !fp32_tile_supported(p->tile))
-        return set_err(c, FE_EUNSUPPORTED, "FP32 tile %d: use 0 (autotune), 32 or 64", p->tile);
+    if (p->prec == FE_FP32 && p->tile != 0 && !fp32_tile_supported(p->tile) && p->tile != (32 | FE_TILE_CLUSTER4))
+        return set_err(c, FE_EUNSUPPORTED, "FP32 tile %d: use 0 (autotune), 32, 64 or 32 | FE_TILE_CLUSTER4",
+                       p->tile);
     if (p->prec != FE_FP32 && p->tile != 0)
         return set_err(c, FE_EUNSUPPORTED, "the tensor-core forms have one tile shape: tile must be 0");
     return FE_OK;
@@ -216,7 +218,7 @@ fe_status validate_params(fe_ctx *c, const fe_params *p) {
 
 // Launch one tile kernel of the context's precision form.
 cudaError_t launch_tiles(const fe_ctx *c, int mode, const KParams &kp, int grid) {
-    if (c->prm.prec == FE_FP32) return fp32_launch(mode, kp, grid, c->s, c->tile_y, c->prm.model);
+    if (c->prm.prec == FE_FP32) return fp32_launch(mode, kp, grid, c->s, c->tile_y, c->prm.model, c->cluster);
     return tc_launch(mode, c->prm.prec == FE_BF16 ? 1 : 2, kp, grid, c->s, c->prm.model);
 }
 
@@ -243,8 +245,9 @@ void axis_tiles(bool tc, int N, int T, std::vector<int> &o, std::vector<int> &re
     }
 }
 
-// The tile list of every image for a TY x TX tile (host copy only).
-void build_tiles(fe_ctx *c, int TY, int TX) {
+// The tile list of every image for a TY x TX tile (host copy only); cl CTAs
+// work on each tile.
+void build_tiles(fe_ctx *c, int TY, int TX, int cl = 1) {
     const bool tc = c->prm.prec != FE_FP32;
     c->htile.clear();
     for (int j = 0; j < c->nimg; ++j) {
@@ -261,6 +264,13 @@ void build_tiles(fe_ctx *c, int TY, int TX) {
     c->ntiles = (int)c->htile.size();
     c->tile_y = TY;
     c->tile_x = TX;
+    c->cluster = cl;
+}
+
+// FP32 tile candidates: code = T, or T | FE_TILE_CLUSTER4
+void build_tiles_code(fe_ctx *c, int code) {
+    const int T = code & 0xff;
+    build_tiles(c, T, T, (code & FE_TILE_CLUSTER4) ? 4 : 1);
 }
 
 size_t count_tiles(const fe_ctx *c, int TY, int TX) {
@@ -370,8 +380,9 @@ fe_status build_graph(fe_ctx *c) {
     std::memset(&knp, 0, sizeof knp);
     const int fmt = c->prm.prec == FE_BF16 ? 1 : 2;
     const bool tc = c->prm.prec != FE_FP32;
-    knp.func = const_cast<void *>(tc ? tc_trial_entry(fmt, c->prm.model) : fp32_trial_entry(c->tile_y, c->prm.model));
-    knp.gridDim = dim3(c->ntiles);
+    knp.func = const_cast<void *>(tc ? tc_trial_entry(fmt, c->prm.model)
+                                     : fp32_trial_entry(c->tile_y, c->prm.model, c->cluster));
+    knp.gridDim = dim3(c->ntiles * (tc ? 1 : c->cluster));
     knp.blockDim = dim3(tc ? tc_threads() : fp32_threads(c->tile_y));
     knp.sharedMemBytes = (unsigned)(tc ? tc_smem_bytes(fmt) : fp32_smem_bytes(c->tile_y));
     knp.kernelParams = args;
@@ -380,6 +391,18 @@ fe_status build_graph(fe_ctx *c) {
     if (e != cudaSuccess) {
         cudaGraphDestroy(g);
         return set_err(c, FE_ECUDA, "cudaGraphAddKernelNode: %s", cudaGetErrorString(e));
+    }
+    if (!tc && c->cluster > 1) {  // thread-block clusters of c->cluster CTAs
+        cudaKernelNodeAttrValue v;
+        std::memset(&v, 0, sizeof v);
+        v.clusterDim.x = (unsigned)c->cluster;
+        v.clusterDim.y = 1;
+        v.clusterDim.z = 1;
+        e = cudaGraphKernelNodeSetAttribute(kn, cudaKernelNodeAttributeClusterDimension, &v);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return set_err(c, FE_ECUDA, "cluster dimension of the graph node: %s", cudaGetErrorString(e));
+        }
     }
     cudaGraphExec_t ex;
     e = cudaGraphInstantiate(&ex, g, 0);
@@ -478,7 +501,7 @@ fe_status autotune_tile(fe_ctx *c, const std::vector<int> &cand) {
         float best_ms = 0.f;
         fe_status st = FE_OK;
         for (int T : cand) {
-            build_tiles(c, T, T);
+            build_tiles_code(c, T);
             if ((st = upload_tiles(c)) != FE_OK) break;
             KParams kp = c->kp;
             kp.tile0 = 0;
@@ -508,7 +531,7 @@ fe_status autotune_tile(fe_ctx *c, const std::vector<int> &cand) {
         std::lock_guard<std::mutex> lk(mu);
         cache[key] = best;
     }
-    build_tiles(c, best, best);
+    build_tiles_code(c, best);
     return upload_tiles(c);
 }
 
@@ -608,15 +631,15 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
     else if (p->tile != 0)
         cand.push_back(p->tile);
     else
-        cand = {64, 32};
+        cand = {64, 32, 32 | FE_TILE_CLUSTER4};
     size_t max_tiles = 0;
     for (int T : cand)
-        max_tiles = std::max(max_tiles, tc ? count_tiles(c, tc_tile_y, tc_tile_x) : count_tiles(c, T, T));
+        max_tiles = std::max(max_tiles, tc ? count_tiles(c, tc_tile_y, tc_tile_x) : count_tiles(c, T & 0xff, T & 0xff));
     if (max_tiles > (size_t)0x7fffffff) return bail(set_err(c, FE_EINVAL, "too many tiles"));
     if (tc)
         build_tiles(c, tc_tile_y, tc_tile_x);
     else
-        build_tiles(c, cand[0], cand[0]);
+        build_tiles_code(c, cand[0]);
     if (cudaGetDevice(&c->dev) != cudaSuccess) return bail(set_err(c, FE_ECUDA, "no CUDA device"));
 
     if (cudaError_t e = tc ? tc_prepare() : fp32_prepare(); e != cudaSuccess)
@@ -919,6 +942,8 @@ fe_status fe_tile_size(const fe_ctx *c, int *tile_y, int *tile_x) {
     *tile_x = c->tile_x;
     return FE_OK;
 }
+
+int fe_tile_cluster(const fe_ctx *c) { return c ? c->cluster : 0; }
 
 fe_status fe_image_size(const fe_ctx *c, int img, int *H, int *W) {
     if (!c || img < 0 || img >= c->nimg) return FE_EINVAL;

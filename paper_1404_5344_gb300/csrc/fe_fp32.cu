@@ -16,21 +16,25 @@ int fp32_threads(int T) { return T == 32 ? Geo<32>::NT : Geo<64>::NT; }
 cudaError_t fp32_prepare() {
     cudaError_t e = prepare_tile<64, 0>();
     if (e == cudaSuccess) e = prepare_tile<32, 0>();
+    if (e == cudaSuccess) e = prepare_tile<32, 0, 4>();
     if (e == cudaSuccess) e = fp32c_prepare();
     return e;
 }
 
-cudaError_t fp32_launch(int mode, const KParams &p, int ngrid, cudaStream_t s, int T, int model) {
-    if (model == 1) return fp32c_launch(mode, p, ngrid, s, T);
-    if (T == 64) return launch_tile<64, 0>(mode, p, ngrid, s);
-    if (T == 32) return launch_tile<32, 0>(mode, p, ngrid, s);
+cudaError_t fp32_launch(int mode, const KParams &p, int ngrid, cudaStream_t s, int T, int model, int cl) {
+    if (model == 1) return fp32c_launch(mode, p, ngrid, s, T, cl);
+    if (T == 64 && cl == 1) return launch_tile<64, 0>(mode, p, ngrid, s);
+    if (T == 32 && cl == 1) return launch_tile<32, 0>(mode, p, ngrid, s);
+    if (T == 32 && cl == 4) return launch_tile<32, 0, 4>(mode, p, ngrid, s);
     return cudaErrorInvalidValue;
 }
 
-const void *fp32_trial_entry(int T, int model) {
-    if (model == 1) return fp32c_trial_entry(T);
-    return T == 32 ? reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL, 32, 0>)
-                   : reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL, 64, 0>);
+const void *fp32_trial_entry(int T, int model, int cl) {
+    if (model == 1) return fp32c_trial_entry(T, cl);
+    if (T == 32)
+        return cl == 4 ? reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL, 32, 0, 4>)
+                       : reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL, 32, 0, 1>);
+    return reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL, 64, 0, 1>);
 }
 
 }  // namespace fe

@@ -8,18 +8,23 @@ namespace fe {
 
 cudaError_t fp32c_prepare() {
     cudaError_t e = prepare_tile<64, 1>();
-    return e != cudaSuccess ? e : prepare_tile<32, 1>();
+    if (e == cudaSuccess) e = prepare_tile<32, 1>();
+    if (e == cudaSuccess) e = prepare_tile<32, 1, 4>();
+    return e;
 }
 
-cudaError_t fp32c_launch(int mode, const KParams &p, int ngrid, cudaStream_t s, int T) {
-    if (T == 64) return launch_tile<64, 1>(mode, p, ngrid, s);
-    if (T == 32) return launch_tile<32, 1>(mode, p, ngrid, s);
+cudaError_t fp32c_launch(int mode, const KParams &p, int ngrid, cudaStream_t s, int T, int cl) {
+    if (T == 64 && cl == 1) return launch_tile<64, 1>(mode, p, ngrid, s);
+    if (T == 32 && cl == 1) return launch_tile<32, 1>(mode, p, ngrid, s);
+    if (T == 32 && cl == 4) return launch_tile<32, 1, 4>(mode, p, ngrid, s);
     return cudaErrorInvalidValue;
 }
 
-const void *fp32c_trial_entry(int T) {
-    return T == 32 ? reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL, 32, 1>)
-                   : reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL, 64, 1>);
+const void *fp32c_trial_entry(int T, int cl) {
+    if (T == 32)
+        return cl == 4 ? reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL, 32, 1, 4>)
+                       : reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL, 32, 1, 1>);
+    return reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL, 64, 1, 1>);
 }
 
 }  // namespace fe

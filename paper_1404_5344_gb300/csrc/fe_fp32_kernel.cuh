@@ -47,6 +47,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <cooperative_groups.h>
+
 #include "fe_internal.cuh"
 #include "fe_tile_common.cuh"
 
@@ -203,7 +205,14 @@ __device__ __forceinline__ float forward_unit(const float *__restrict__ sU, floa
 // MODEL 0: Eq. variant, iterate u.  MODEL 1: Eq. newmodel, iterate w = log u
 // (the filter bank sees u = e^w; grad_w F = e^w (.) sum_i theta_i K_i^T r_i;
 // the prox is prox_w).
-template <int MODE, int T, int MODEL>
+// CL > 1: the tile is split over a thread-block cluster of CL CTAs by filter
+// group (rank r takes groups r, r + CL, ...), for images too small to fill
+// the GPU otherwise.  Every rank recomputes the prologue (only rank 0 writes
+// u^{n+1} and keeps the step sums); after the groups each rank leaves its
+// partial K^T r, frame values and F sum in its shared memory, rank 0 adds
+// the other ranks' partials in rank order through distributed shared memory
+// and finishes the tile.  Launched with a cluster dimension of CL.
+template <int MODE, int T, int MODEL, int CL>
 __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(const KParams p) {
     using Q = Geo<T>;
     constexpr int TY = Q::TY, TX = Q::TX, NT = Q::NT, R3Y = Q::R3Y, R3X = Q::R3X, R3YA = Q::R3YA;
@@ -217,7 +226,9 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
     __shared__ int sLast;
 
     const int tid = threadIdx.x;
-    const int gtile = p.tile0 + (int)blockIdx.x;
+    int rank = 0;
+    if constexpr (CL > 1) rank = (int)cooperative_groups::this_cluster().block_rank();
+    const int gtile = p.tile0 + (int)blockIdx.x / CL;
     const TileDesc td = p.tiles[gtile];
     const int img = td.img;
     const ImgDesc im = p.imgs[img];
@@ -266,7 +277,7 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
                     const float dprev = u0 - u_1;
                     const float uhat = fmaf(-a, g0, fmaf(b, dprev, u0));
                     v = MODEL == 0 ? prox_g(uhat, f2, tl) : prox_w(uhat, f2, a, l1, l2);
-                    if (inner) {
+                    if (inner && rank == 0) {
                         un[off] = v;
                         const float d = v - u0;
                         accGD = fmaf(g0, d, accGD);
@@ -276,7 +287,7 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
                     }
                 } else {
                     v = __ldg(uc + off);
-                    if (inner) {
+                    if (inner && rank == 0) {
                         const float f2 = __ldg(f2p + off);
                         sum2_add(accG, MODEL == 0 ? v * v - 2.0f * f2 * logf(v) : data_w(v, f2, l1, l2));
                     }
@@ -296,7 +307,7 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
         const int aux = tid % Q::AUX, auy = tid / Q::AUX;  // adjoint unit of this thread
         const bool border = y0 == 0 || x0 == 0 || y0 + TY > H - 3 || x0 + TX > W - 3;
 
-        for (int grp = 0; grp < p.nfp / G; ++grp) {
+        for (int grp = rank; grp < p.nfp / G; grp += CL) {
             __syncthreads();  // sU / weights ready; previous group's sR reads done
             // ---- 3+4: forward bank and potential on tile + 3 -------------
             for (int unit = tid; unit < FWD_UNITS; unit += NT) {
@@ -367,7 +378,39 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
             }
         }
 
-        if (MODE != MODE_ENERGY_EXT) {
+        if constexpr (CL > 1) {
+            // ---- combine the ranks' partials at rank 0 (distributed shared memory)
+            auto cluster = cooperative_groups::this_cluster();
+            __syncthreads();  // this CTA's sR reads are done
+            constexpr int NA = AUR * 4;
+            float *part = sR;  // per thread: NA adjoint sums, RING_PER_T frame values, F (s, c)
+            static_assert(NT * (NA + RING_PER_T + 2) <= (int)SM_R, "partials fit in sR");
+#pragma unroll
+            for (int pp = 0; pp < AUR; ++pp)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) part[tid * NA + pp * 4 + q] = acc[pp][q];
+#pragma unroll
+            for (int k = 0; k < RING_PER_T; ++k) part[NT * NA + tid * RING_PER_T + k] = fr[k];
+            part[NT * (NA + RING_PER_T) + 2 * tid] = accF.s;
+            part[NT * (NA + RING_PER_T) + 2 * tid + 1] = accF.c;
+            cluster.sync();  // every rank's partials are visible in the cluster
+            if (rank == 0) {
+                for (int r = 1; r < CL; ++r) {
+                    const float *rp = cluster.map_shared_rank(part, r);
+#pragma unroll
+                    for (int pp = 0; pp < AUR; ++pp)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[pp][q] += rp[tid * NA + pp * 4 + q];
+#pragma unroll
+                    for (int k = 0; k < RING_PER_T; ++k) fr[k] += rp[NT * NA + tid * RING_PER_T + k];
+                    accF = sum2_merge(accF, Sum2{rp[NT * (NA + RING_PER_T) + 2 * tid],
+                                                rp[NT * (NA + RING_PER_T) + 2 * tid + 1]});
+                }
+            }
+            cluster.sync();  // rank 0 has read the other ranks' shared memory
+        }
+
+        if (MODE != MODE_ENERGY_EXT && rank == 0) {
             // ---- fold the frame back onto the pixels it mirrors ----------
             if (border) {
                 __syncthreads();  // all sR reads done; reuse sR for the ring
@@ -417,42 +460,61 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
         }
 
         // ---- 6: per-tile FP64 partial sums, last-CTA decision -------------
-        const Sum2 vals[NRED] = {accF, accG, {accGD, 0.f}, {accDD, 0.f}, {accDP, 0.f}};
-        tile_finish<NT>(p, MODE, gtile, img, im, st, vals, sRed, &sLast);
+        if (rank == 0) {
+            const Sum2 vals[NRED] = {accF, accG, {accGD, 0.f}, {accDD, 0.f}, {accDP, 0.f}};
+            tile_finish<NT>(p, MODE, gtile, img, im, st, vals, sRed, &sLast);
+        }
     }
 
-    // ---- loop control: the last CTA of the launch --------------------------
-    if (MODE == MODE_TRIAL) loop_control(p);
+    // ---- loop control: the last rank-0 CTA of the launch -------------------
+    if (MODE == MODE_TRIAL && rank == 0) loop_control(p, gridDim.x / CL);
 }
 
-template <int T, int MODEL>
+template <int T, int MODEL, int CL = 1>
 cudaError_t prepare_tile() {
     const int b = (int)Geo<T>::SM_BYTES;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_TRIAL, T, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)) !=
+    if ((e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_TRIAL, T, MODEL, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)) !=
         cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_INIT, T, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)) !=
+    if ((e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_INIT, T, MODEL, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)) !=
         cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_GRAD_EXT, T, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_GRAD_EXT, T, MODEL, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   b)) != cudaSuccess)
         return e;
-    return cudaFuncSetAttribute(fp32_tile_kernel<MODE_ENERGY_EXT, T, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    return cudaFuncSetAttribute(fp32_tile_kernel<MODE_ENERGY_EXT, T, MODEL, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
 }
 
-template <int T, int MODEL>
+// ngrid = tiles; CL CTAs per tile, launched as clusters of CL
+template <int T, int MODEL, int CL = 1>
 cudaError_t launch_tile(int mode, const KParams &p, int ngrid, cudaStream_t s) {
-    const dim3 grid(ngrid), block(Geo<T>::NT);
-    const size_t b = Geo<T>::SM_BYTES;
+    const void *fn;
     switch (mode) {
-        case MODE_TRIAL: fp32_tile_kernel<MODE_TRIAL, T, MODEL><<<grid, block, b, s>>>(p); break;
-        case MODE_INIT: fp32_tile_kernel<MODE_INIT, T, MODEL><<<grid, block, b, s>>>(p); break;
-        case MODE_GRAD_EXT: fp32_tile_kernel<MODE_GRAD_EXT, T, MODEL><<<grid, block, b, s>>>(p); break;
-        case MODE_ENERGY_EXT: fp32_tile_kernel<MODE_ENERGY_EXT, T, MODEL><<<grid, block, b, s>>>(p); break;
+        case MODE_TRIAL: fn = reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL, T, MODEL, CL>); break;
+        case MODE_INIT: fn = reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_INIT, T, MODEL, CL>); break;
+        case MODE_GRAD_EXT: fn = reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_GRAD_EXT, T, MODEL, CL>); break;
+        case MODE_ENERGY_EXT:
+            fn = reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_ENERGY_EXT, T, MODEL, CL>);
+            break;
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ngrid * CL);
+    cfg.blockDim = dim3(Geo<T>::NT);
+    cfg.dynamicSmemBytes = Geo<T>::SM_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    if (CL > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    void *args[] = {const_cast<KParams *>(&p)};
+    return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 

@@ -111,13 +111,15 @@ size_t fp32_smem_bytes(int T = fp32_tile_size);
 int fp32_tile();                                    // the default tile, fp32_tile_size
 int fp32_threads(int T = fp32_tile_size);           // block size of the tile kernel
 cudaError_t fp32_prepare();  // opt in to the large shared-memory carve-out (every tile and model)
-// model: 0 = Eq. variant (iterate u), 1 = combined model (iterate w = log u)
+// model: 0 = Eq. variant (iterate u), 1 = combined model (iterate w = log u);
+// cl: CTAs per tile (1, or 4 = a thread-block cluster per 32 x 32 tile);
+// grid = tiles (the launch multiplies by cl)
 cudaError_t fp32_launch(int mode, const KParams &p, int grid, cudaStream_t s, int T = fp32_tile_size,
-                        int model = 0);
-const void *fp32_trial_entry(int T = fp32_tile_size, int model = 0);
+                        int model = 0, int cl = 1);
+const void *fp32_trial_entry(int T = fp32_tile_size, int model = 0, int cl = 1);
 cudaError_t fp32c_prepare();  // combined-model instantiations (fe_fp32_comb.cu)
-cudaError_t fp32c_launch(int mode, const KParams &p, int grid, cudaStream_t s, int T);
-const void *fp32c_trial_entry(int T);
+cudaError_t fp32c_launch(int mode, const KParams &p, int grid, cudaStream_t s, int T, int cl);
+const void *fp32c_trial_entry(int T, int cl);
 
 // Tensor-core tile kernel (fe_tc.cu); fmt 1 = BF16, 2 = TF32 operands
 constexpr int tc_tile_y = 58, tc_tile_x = 26;  // output tile; tile + 3-pixel halo = 64 x 32

@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
         const Sum2 vals[NRED] = {accF, accG, {accGD, 0.f}, {accDD, 0.f}, {accDP, 0.f}};
         tile_finish<NT>(p, MODE, gtile, img, im, st, vals, sRed, &sLast);
     }
-    if (MODE == MODE_TRIAL) loop_control(p);
+    if (MODE == MODE_TRIAL) loop_control(p, gridDim.x);
 }
 
 template <int FMT, int MODEL>

@@ -246,14 +246,16 @@ __device__ void tile_finish(const KParams &p, int mode, int gtile, int img, cons
     }
 }
 
-// Loop control of a trial launch (thread 0 of every CTA): the last CTA to
-// arrive counts the images still iterating, spends one unit of the trial
-// budget, and sets the while-condition of the CUDA graph.
-__device__ void loop_control(const KParams &p) {
+// Loop control of a trial launch (thread 0 of every participating CTA: all
+// CTAs, or the rank-0 CTA of every cluster): the last of the `participants`
+// to arrive - each after its own tile's reduction and decision - counts the
+// images still iterating, spends one unit of the trial budget, and sets the
+// while-condition of the CUDA graph.
+__device__ void loop_control(const KParams &p, unsigned participants) {
     if (threadIdx.x != 0) return;
     __threadfence();
     const unsigned prev = atomicAdd(&p.loop->grid_arrivals, 1u);
-    if (prev != gridDim.x - 1u) return;
+    if (prev != participants - 1u) return;
     __threadfence();
     LoopCtl *lc = p.loop;
     lc->grid_arrivals = 0u;

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "l
 FE_OK, FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_ENONFINITE = 0, 1, 2, 3, 4
 FE_EBACKTRACK, FE_ETIMEOUT, FE_ENOTCONVERGED, FE_EUNSUPPORTED = 5, 6, 7, 8
 FE_FP32, FE_TF32, FE_BF16 = 0, 1, 2
+FE_TILE_CLUSTER4 = 0x100
 PRECISIONS = {"fp32": FE_FP32, "tf32": FE_TF32, "bf16": FE_BF16}
 
 #: every symbol include/fe.h declares
@@ -29,7 +30,7 @@ EXPORTS = (
     "fe_default_params", "fe_init_batch", "fe_init", "fe_reset", "fe_destroy", "fe_step",
     "fe_solve", "fe_get_info", "fe_get_u", "fe_energy", "fe_gradient", "fe_get_state",
     "fe_set_state", "fe_num_images", "fe_image_size", "fe_launch_count", "fe_set_loop_mode", "fe_tile_size",
-    "fe_ssim", "fe_psnr", "fe_tc_wait_selftest",
+    "fe_ssim", "fe_psnr", "fe_tc_wait_selftest", "fe_tile_cluster",
     "fe_last_error", "fe_status_string", "fe_abi_version", "fe_gradient_noalloc",
     "fe_tc_gemm_selftest", "fe_cnn_create", "fe_cnn_destroy", "fe_cnn_num_params",
     "fe_cnn_last_error", "fe_cnn_set_params", "fe_cnn_get_params", "fe_cnn_forward",
@@ -82,6 +83,7 @@ def _load(path: str = LIB_PATH) -> C.CDLL:
     L.fe_num_images.argtypes = [VP]
     L.fe_image_size.argtypes = [VP, I, P(I), P(I)]
     L.fe_tile_size.argtypes = [VP, P(I), P(I)]
+    L.fe_tile_cluster.argtypes = [VP]
     L.fe_ssim.argtypes = [VP, VP, I, I, D, P(D), VP]
     L.fe_tc_wait_selftest.argtypes = [C.c_uint, P(I)]
     L.fe_psnr.argtypes = [VP, VP, C.c_longlong, D, P(D), VP]
@@ -112,7 +114,7 @@ def _load(path: str = LIB_PATH) -> C.CDLL:
     for name in ("fe_tc_gemm_selftest", "fe_gradient_noalloc", "fe_init_batch","fe_init", "fe_reset", "fe_step", "fe_solve", "fe_get_info",
                  "fe_get_u", "fe_energy", "fe_gradient", "fe_get_state", "fe_set_state",
                  "fe_image_size", "fe_set_loop_mode", "fe_num_images", "fe_abi_version", "fe_tile_size",
-                 "fe_ssim", "fe_psnr", "fe_tc_wait_selftest"):
+                 "fe_ssim", "fe_psnr", "fe_tc_wait_selftest", "fe_tile_cluster"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -236,6 +238,11 @@ class Solver:
         ty, tx = C.c_int(), C.c_int()
         self._check(lib.fe_tile_size(self.ctx, C.byref(ty), C.byref(tx)))
         return ty.value, tx.value
+
+    @property
+    def cluster(self) -> int:
+        """CTAs working on one tile (4: a thread-block cluster per tile)."""
+        return int(lib.fe_tile_cluster(self.ctx))
 
     # -- ABI calls -----------------------------------------------------
     def reset(self, f, u0=None):

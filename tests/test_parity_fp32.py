@@ -54,7 +54,9 @@ def _relmax(a, b):
 SIZES = [(64, 64), (8, 8), (131, 77), (200, 13), (13, 200), (67, 129), (128, 128)]
 
 
-TILES = [64, 32]  # both output-tile shapes of the FP32 kernel
+# the FP32 kernel's tile shapes: 64 x 64, 32 x 32, and 32 x 32 split over a
+# 4-CTA cluster (FE_TILE_CLUSTER4 = 0x100)
+TILES = [64, 32, 32 | 0x100]
 
 
 @pytest.mark.parametrize("tile", TILES)
@@ -64,7 +66,8 @@ def test_gradient_parity(fe, orc, bank, shape, tile):
     H, W = shape
     _, f = _problem(H, W, seed=H * 7 + W)
     with fe.Solver([f], k, th, tile=tile) as s:
-        assert s.tile == (tile, tile)
+        assert s.tile == (tile & 0xff, tile & 0xff)
+        assert s.cluster == (4 if tile & 0x100 else 1)
         g, Fg = s.gradient(0, f)
     g_ref, F_ref = orc.gradF(f, k, th)
     assert _relmax(g, g_ref) <= GRAD_TOL
@@ -185,12 +188,15 @@ def test_trajectory_64x64_100_iterations(fe, orc, bank, tile):
         _check_decisions(orc, f, k, th, prm, u, up, L_start, Ls[n])
 
 
-def test_loop_modes_bit_identical(fe, bank):
+@pytest.mark.parametrize("tile", [0, 32 | 0x100])
+def test_loop_modes_bit_identical(fe, bank, tile):
+    """The CUDA-graph loop (one while node; for clusters the kernel node carries
+    the cluster dimension) and the host loop give the same bits."""
     k, th = bank
     _, f = _problem(100, 90, seed=5)
     outs = []
     for mode in (0, 1):
-        with fe.Solver([f], k, th, L0=1e-2, loop_mode=mode) as s:
+        with fe.Solver([f], k, th, L0=1e-2, loop_mode=mode, tile=tile) as s:
             assert s.step(25) == fe.FE_OK
             outs.append((s.get_u(0), s.info(0)))
     assert np.array_equal(outs[0][0], outs[1][0])
@@ -296,18 +302,24 @@ def test_tile_autotune_and_shapes(fe, bank):
     _, f = _problem(150, 97, seed=31, kind="textured")
     with fe.Solver([f], k, th) as a:
         ta = a.tile
-        assert ta in ((64, 64), (32, 32))
+        assert ta in ((64, 64), (32, 32)) and a.cluster in (1, 4)
         with fe.Solver([f], k, th) as b:
             assert b.tile == ta  # cached
     gs, us = [], []
-    for t in TILES:
+    for t in (64, 32):  # same per-pixel order: bit-identical
         with fe.Solver([f], k, th, L0=1e-2, beta=0.0, tile=t) as s:
-            assert s.tile == (t, t)
+            assert s.tile == (t, t) and s.cluster == 1
             gs.append(s.gradient(0, f)[0])
             assert s.step(1) == fe.FE_OK
             us.append(s.get_u(0))
     assert np.array_equal(gs[0], gs[1])
     assert np.array_equal(us[0], us[1])
-    for bad in (16, 48, 128, -1):
+    # the cluster variant sums each pixel's filters rank by rank: another FP32
+    # summation order, so the two agree within the FP32 gradient bound
+    with fe.Solver([f], k, th, L0=1e-2, beta=0.0, tile=32 | 0x100) as s:
+        assert s.tile == (32, 32) and s.cluster == 4
+        gc = s.gradient(0, f)[0]
+    assert float(np.max(np.abs(gc - gs[0])) / np.max(np.abs(gs[0]))) <= GRAD_TOL
+    for bad in (16, 48, 128, -1, 64 | 0x100, 0x100):
         with pytest.raises(fe.FeError):
             fe.Solver([f], k, th, tile=bad)
