@@ -616,7 +616,7 @@ def main():
     torch.cuda.synchronize()
     kw = model_kw(args)
     solver = fe.Solver(f_dev, k, th, prec=args.prec, stream=stream, loop_mode=args.loop_mode, **kw)
-    tile = solver.tile
+    tile, cluster = solver.tile, solver.cluster
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def one_step():
@@ -719,7 +719,8 @@ def main():
                 "dtype": {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[args.prec], "data": "synthetic",
                 "config": dict(workload_config(args, npix, len(fs)), **{
                            "loop": "cuda-graph while node" if args.loop_mode == 1 else "host chunks",
-                           "tile": "%dx%d (%s)" % (tile + ("autotuned" if args.prec == "fp32" else "fixed",)),
+                           "tile": "%dx%d%s (%s)" % (tile + (" on a 4-CTA cluster" if cluster == 4 else "",
+                                                             "autotuned" if args.prec == "fp32" else "fixed")),
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "256 MiB buffer written between timed steps; state 6 planes x "
                                  "%.0f MB" % (npix * 4 / 1e6)}),

@@ -69,7 +69,7 @@ def _oprm(orc, **kw):
     return orc.params(model=orc.MODEL_COMBINED, **kw)
 
 
-@pytest.mark.parametrize("tile", [64, 32])
+@pytest.mark.parametrize("tile", [64, 32, 32 | 0x100])
 @pytest.mark.parametrize("shape", [(64, 64), (131, 77), (8, 9), (200, 13)])
 def test_gradient_parity_combined(fe, orc, bank, shape, tile):
     k, th = bank
