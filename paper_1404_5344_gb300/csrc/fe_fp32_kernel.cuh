@@ -193,11 +193,11 @@ __device__ __forceinline__ float forward_unit(const float *__restrict__ sU, floa
             const float zz = z[r][i];
             const float q = fmaf(zz, zz, 1.0f);
             if (MODE != MODE_ENERGY_EXT) {
-                float rv = __fdividef(th2[i] * zz, q);
+                float rv = (th2[i] * zz) * rcp_ftz(q);
                 if (MASK && !inimg) rv = 0.0f;
                 sR[(i * R3YA + pr) * SR_LD + c] = rv;
             }
-            psum = fmaf(th[i], __log2f(q), psum);
+            psum = fmaf(th[i], lg2_ftz(q), psum);
         }
         if (inner) fsum += psum;
     }

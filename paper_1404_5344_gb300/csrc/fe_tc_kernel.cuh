@@ -432,8 +432,8 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
                     for (int k = 0; k < 4; ++k) {
                         const float zz = z[4 * j + k];
                         const float q = fmaf(zz, zz, 1.0f);
-                        r[4 * j + k] = __fdividef(tw[k] * zz, q);
-                        psum = fmaf(th[k], __log2f(q), psum);
+                        r[4 * j + k] = (tw[k] * zz) * rcp_ftz(q);
+                        psum = fmaf(th[k], lg2_ftz(q), psum);
                     }
                 }
                 if (!inimg) {

@@ -12,6 +12,22 @@
 namespace fe {
 namespace {
 
+// Approximate reciprocal and base-2 logarithm on the special-function unit
+// with subnormal inputs and results flushed to zero.  The response epilogues
+// apply them to q = 1 + z^2 >= 1, where the flush never triggers, so they give
+// the same values as the non-flushing forms without the extra instructions
+// those spend on subnormal operands.
+__device__ __forceinline__ float rcp_ftz(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_ftz(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Symmetric (half-sample) reflection for j in [-6, n+6) when n >= 6; indices
 // further out only feed responses outside the image and are clamped.
 __device__ __forceinline__ int reflect(int j, int n) {
