@@ -683,12 +683,13 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
         return bail(set_err(c, FE_ECUDA, "cudaMemset failed"));
 
     // weight tables: forward = flipped taps (convolution as correlation),
-    // tap-major; adjoint = taps as stored, filter-major (correlation = K^T)
+    // tap-major; adjoint = taps as stored times 2 theta_i (the factor of
+    // theta_i rho'), filter-major (correlation = K^T)
     std::vector<float> wf((size_t)KT * NFMAX, 0.f), wa((size_t)NFMAX * KT_PAD, 0.f), th(NFMAX, 0.f);
     for (int i = 0; i < p->nf; ++i) {
         for (int t = 0; t < KT; ++t) {
             wf[(size_t)t * NFMAX + i] = p->filters[(size_t)i * KT + (KT - 1 - t)];
-            wa[(size_t)i * KT_PAD + t] = p->filters[(size_t)i * KT + t];
+            wa[(size_t)i * KT_PAD + t] = 2.0f * p->theta[i] * p->filters[(size_t)i * KT + t];
         }
         th[i] = p->theta[i];
     }

@@ -12,9 +12,10 @@
 //      u = (uhat + sqrt(uhat^2 + 4(1+t l) t l f^2)) / (2 (1 + t l)), evaluated
 //      as 2 t l f^2 / (sqrt(D) - uhat) when uhat < 0 (no cancellation)
 //   3. forward filter bank z_i = k_i * u on tile + halo 3, 7x7 taps, FFMA
-//   4. r_i = theta_i rho'(z_i) = theta_i 2 z_i / (1 + z_i^2) (zero outside the
-//      image), and the energy term theta_i log(1 + z_i^2) on the tile
-//   5. adjoint bank g = sum_i K_i^T r_i on the tile (correlation with k_i),
+//   4. s_i = z_i / (1 + z_i^2) (zero outside the image), and the energy term
+//      theta_i log(1 + z_i^2) on the tile; theta_i rho'(z_i) = 2 theta_i s_i,
+//      and the factor 2 theta_i is folded into the adjoint weights
+//   5. adjoint bank g = sum_i (2 theta_i K_i)^T s_i on the tile (correlation),
 //      plus the transpose of the symmetric extension: values of K_i^T r on
 //      the 3-pixel frame outside the image are folded back onto the pixels
 //      they mirror
@@ -139,8 +140,9 @@ __device__ __forceinline__ int pos_to_ring(int pr, int pc) {
 }
 
 // Forward bank of one unit (1 column x FWD_ROWS rows x G filters of group
-// grp) and its epilogue: r_i into sR, theta_i log2(1 + z_i^2) summed over the
-// unit's tile pixels.  MASK: some pixel of the unit lies outside the image (a
+// grp) and its epilogue: s_i = z_i / (1 + z_i^2) into sR (theta_i rho'(z_i) =
+// 2 theta_i s_i; the adjoint weights carry 2 theta_i), theta_i log2(1 + z_i^2)
+// summed over the unit's tile pixels.  MASK: some pixel of the unit lies outside the image (a
 // run-time flag: one inlined copy of this function instead of two keeps the
 // kernel's code small enough for the instruction cache, measured 7 % faster).
 template <int T, int MODE>
@@ -172,12 +174,9 @@ __device__ __forceinline__ float forward_unit(const float *__restrict__ sU, floa
                 for (int i = 0; i < G; ++i) z[r][i] = fmaf(w[i], v[r + aa], z[r][i]);
         }
     }
-    float th[G], th2[G];
+    float th[G];
 #pragma unroll
-    for (int i = 0; i < G; ++i) {
-        th[i] = __ldg(theta + grp * G + i);
-        th2[i] = 2.0f * th[i];
-    }
+    for (int i = 0; i < G; ++i) th[i] = __ldg(theta + grp * G + i);
     const int x = x0 - 3 + c;
     const bool colin = x >= 0 && x < W, colint = c >= 3 && c < 3 + TX;
     float fsum = 0.f;
@@ -193,7 +192,7 @@ __device__ __forceinline__ float forward_unit(const float *__restrict__ sU, floa
             const float zz = z[r][i];
             const float q = fmaf(zz, zz, 1.0f);
             if (MODE != MODE_ENERGY_EXT) {
-                float rv = (th2[i] * zz) * rcp_ftz(q);
+                float rv = zz * rcp_ftz(q);
                 if (MASK && !inimg) rv = 0.0f;
                 sR[(i * R3YA + pr) * SR_LD + c] = rv;
             }
@@ -205,7 +204,7 @@ __device__ __forceinline__ float forward_unit(const float *__restrict__ sU, floa
 }
 
 // MODEL 0: Eq. variant, iterate u.  MODEL 1: Eq. newmodel, iterate w = log u
-// (the filter bank sees u = e^w; grad_w F = e^w (.) sum_i theta_i K_i^T r_i;
+// (the filter bank sees u = e^w; grad_w F = e^w (.) sum_i theta_i K_i^T rho'(z_i);
 // the prox is prox_w).
 // CL > 1: the tile is split over a thread-block cluster of CL CTAs by filter
 // group (rank r takes groups r, r + CL, ...), for images too small to fill
@@ -361,7 +360,7 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
                     int pr, pc, j, jx;
                     ring_to_pos<T>(idx, pr, pc);
                     if (!axis_pos(pr, y0, TY, H, j) || !axis_pos(pc, x0, TX, W, jx)) continue;
-                    // s(j, jx) = sum_i sum_ab k_i[a][b] r_i(j - 3 + a, jx - 3 + b); r_i is
+                    // frame value at (j, jx) = sum_i sum_ab 2 theta_i k_i[a][b] s_i(j - 3 + a, jx - 3 + b); s_i is
                     // zero off-image and the response region covers every on-image row
                     // and column this frame pixel needs, so only those taps are visited
                     const int alo = max(max(0, 3 - j), y0 - j), ahi = min(min(KS, H + 3 - j), R3Y + y0 - j);

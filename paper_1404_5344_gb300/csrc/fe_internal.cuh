@@ -85,7 +85,7 @@ struct KParams {
     unsigned *img_arrivals;  // [nimg]
     LoopCtl *loop;
     const float *wf;     // forward weights, flipped, tap-major: wf[t * NFMAX + i] = k_i[48 - t]
-    const float *wa;     // adjoint weights, filter-major: wa[i * KT_PAD + t] = k_i[t]
+    const float *wa;     // adjoint weights, filter-major: wa[i * KT_PAD + t] = 2 theta_i k_i[t]
     const float *theta;  // [NFMAX], zero beyond nf
     int nfp;             // nf rounded up to the filter-group size
     int nimg, ntiles;

@@ -49,7 +49,8 @@ std::mutex na_mu;
 unsigned char *na_base[NA_MAX_DEV] = {};
 
 // Weight tables in the layout the tile kernel reads (see KParams): forward
-// taps flipped and tap-major, adjoint taps filter-major, zero beyond nf.
+// taps flipped and tap-major, adjoint taps times 2 theta_i filter-major, zero
+// beyond nf.
 // Also writes the image and tile descriptors and clears the counters.
 __global__ void na_setup_kernel(unsigned char *base, const float *filters, const float *theta, int nf,
                                 int H, int W, int tiles_x, int ntiles, const float *u) {
@@ -66,7 +67,7 @@ __global__ void na_setup_kernel(unsigned char *base, const float *filters, const
         }
         if (j < NFMAX * KT_PAD) {
             const int i = j / KT_PAD, t = j % KT_PAD;
-            wa[j] = (i < nf && t < KT) ? filters[i * KT + t] : 0.0f;
+            wa[j] = (i < nf && t < KT) ? 2.0f * theta[i] * filters[i * KT + t] : 0.0f;
         }
         if (j < NFMAX) th[j] = j < nf ? theta[j] : 0.0f;
         if (j < ntiles) tiles[j] = TileDesc{0, (j / tiles_x) * T, (j % tiles_x) * T, 0};
