@@ -37,11 +37,13 @@
 //           GPU with 64 x 64 tiles; forward units of 1 column x 13 rows over
 //           a 39-row (one padding row) x 38-column region (114 units, one
 //           round); adjoint units of 2 x 4 output pixels (one per thread)
-// A forward unit slides its column window over the 7 kernel columns; weight
-// vectors are uniform 128-bit loads from the tap-major table in global
-// memory (L1).  An adjoint unit reads each window row with three LDS.128 and
-// holds each filter's 49 weights in registers while its window rows stream
-// through.
+// The weights of a filter group (forward taps, adjoint taps, theta) are
+// staged in shared memory, double-buffered: asynchronous copies (cp.async)
+// fetch the next group's weights while the current group runs.  A forward
+// unit slides its column window over the 7 kernel columns, reading weight
+// vectors as uniform 128-bit shared loads.  An adjoint unit reads each window
+// row with three LDS.128 and holds each filter's 49 weights in registers
+// while its window rows stream through.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -94,7 +96,11 @@ struct Geo {
     // for the adjoint's 128-bit loads
     static constexpr size_t SM_U = ((size_t)R6Y * SU_LD + 3) / 4 * 4;
     static constexpr size_t SM_R = (size_t)G * R3YA * SR_LD;
-    static constexpr size_t SM_FLOATS = SM_U + SM_R;
+    // one group's weights: forward taps (tap-major, G per tap), adjoint taps
+    // (filter-major, KT_PAD per filter), theta; two buffers
+    static constexpr int WB_F = 0, WB_A = KT * G, WB_T = WB_A + G * KT_PAD, WBUF = WB_T + G;
+    static constexpr size_t SM_W = 2 * (size_t)WBUF;
+    static constexpr size_t SM_FLOATS = SM_U + SM_R + SM_W;
     static constexpr size_t SM_BYTES = SM_FLOATS * 4 + (size_t)NWARP * NRED * 8;
     static_assert(NT == ADJ_UNITS, "one adjoint unit per thread");
     static_assert(SU_LD >= R6X && SR_LD >= R3X, "row pitches hold a region row");
@@ -103,11 +109,39 @@ struct Geo {
     static_assert(SM_U % 4 == 0 && SM_R % 4 == 0 && (SR_LD * R3YA) % 4 == 0,
                   "every plane and row of sR starts on a 16-byte boundary");
     static_assert(SM_FLOATS % 2 == 0, "double scratch alignment");
+    static_assert(WB_A % 4 == 0 && WB_T % 4 == 0 && WBUF % 4 == 0 && (SM_U + SM_R) % 4 == 0,
+                  "weight buffers and their parts start on 16-byte boundaries");
+    static_assert(KT * G / 4 + G * KT_PAD / 4 + 1 <= NT, "one 16-byte copy per thread stages a group");
     static_assert(MINB * (SM_BYTES + 1024) <= 228 * 1024, "MINB CTAs per SM");
     static_assert(RING <= SM_R, "the frame ring reuses sR");
 };
 
 constexpr float LN2 = 0.69314718055994530942f;
+
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Stage the weights of filter group grp in wb (one 16-byte copy per thread):
+// forward taps wf[t * NFMAX + grp G .. + G) -> wb[WB_F + t G ..], adjoint taps
+// wa[(grp G + i) KT_PAD + t] -> wb[WB_A + i KT_PAD + t], theta -> wb[WB_T ..].
+template <int T>
+__device__ __forceinline__ void stage_weights(float *wb, const KParams &p, int grp, int tid) {
+    using Q = Geo<T>;
+    constexpr int NA4 = G * KT_PAD / 4;  // float4 of adjoint taps
+    static_assert(G == 4, "one float4 of forward taps per tap");
+    if (tid < KT)
+        cp_async16(wb + Q::WB_F + tid * G, p.wf + tid * NFMAX + grp * G);
+    else if (tid < KT + NA4)
+        cp_async16(wb + Q::WB_A + (tid - KT) * 4, p.wa + (size_t)grp * G * KT_PAD + (tid - KT) * 4);
+    else if (tid == KT + NA4)
+        cp_async16(wb + Q::WB_T, p.theta + grp * G);
+    cp_async_commit();
+}
 
 template <int T>
 __device__ __forceinline__ void ring_to_pos(int idx, int &pr, int &pc) {
@@ -147,8 +181,8 @@ __device__ __forceinline__ int pos_to_ring(int pr, int pc) {
 // kernel's code small enough for the instruction cache, measured 7 % faster).
 template <int T, int MODE>
 __device__ __forceinline__ float forward_unit(const float *__restrict__ sU, float *__restrict__ sR,
-                                              const float *__restrict__ wf, const float *__restrict__ theta,
-                                              int grp, int c, int rb, int y0, int x0, int H, int W, bool MASK) {
+                                              const float *__restrict__ wb, int c, int rb, int y0, int x0, int H,
+                                              int W, bool MASK) {
     using Q = Geo<T>;
     constexpr int FWD_ROWS = Q::FWD_ROWS, FWD_WIN = Q::FWD_WIN, SU_LD = Q::SU_LD, SR_LD = Q::SR_LD;
     constexpr int TY = Q::TY, TX = Q::TX, R3YA = Q::R3YA;
@@ -158,7 +192,7 @@ __device__ __forceinline__ float forward_unit(const float *__restrict__ sU, floa
 #pragma unroll
         for (int i = 0; i < G; ++i) z[r][i] = 0.f;
     const float *ucol = sU + rb * FWD_ROWS * SU_LD + c;
-    const float *wcol = wf + grp * G;
+    const float *wcol = wb + Q::WB_F;
 #pragma unroll 1
     for (int bb = 0; bb < KS; ++bb) {
         float v[FWD_WIN];
@@ -166,7 +200,7 @@ __device__ __forceinline__ float forward_unit(const float *__restrict__ sU, floa
         for (int r = 0; r < FWD_WIN; ++r) v[r] = ucol[r * SU_LD + bb];
 #pragma unroll
         for (int aa = 0; aa < KS; ++aa) {
-            const float4 w0 = __ldg(reinterpret_cast<const float4 *>(wcol + (aa * KS + bb) * NFMAX));
+            const float4 w0 = *reinterpret_cast<const float4 *>(wcol + (aa * KS + bb) * G);
             const float w[G] = {w0.x, w0.y, w0.z, w0.w};
 #pragma unroll
             for (int r = 0; r < FWD_ROWS; ++r)
@@ -176,7 +210,7 @@ __device__ __forceinline__ float forward_unit(const float *__restrict__ sU, floa
     }
     float th[G];
 #pragma unroll
-    for (int i = 0; i < G; ++i) th[i] = __ldg(theta + grp * G + i);
+    for (int i = 0; i < G; ++i) th[i] = wb[Q::WB_T + i];
     const int x = x0 - 3 + c;
     const bool colin = x >= 0 && x < W, colint = c >= 3 && c < 3 + TX;
     float fsum = 0.f;
@@ -223,7 +257,8 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
     extern __shared__ __align__(16) float smem[];
     float *sU = smem;
     float *sR = sU + SM_U;
-    double *sRed = reinterpret_cast<double *>(sR + SM_R);
+    float *sW = sR + SM_R;  // two weight buffers
+    double *sRed = reinterpret_cast<double *>(sW + Q::SM_W);
     __shared__ int sLast;
 
     const int tid = threadIdx.x;
@@ -308,14 +343,21 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
         const int aux = tid % Q::AUX, auy = tid / Q::AUX;  // adjoint unit of this thread
         const bool border = y0 == 0 || x0 == 0 || y0 + TY > H - 3 || x0 + TX > W - 3;
 
-        for (int grp = rank; grp < p.nfp / G; grp += CL) {
-            __syncthreads();  // sU / weights ready; previous group's sR reads done
+        const int ngrp = p.nfp / G;
+        if (rank < ngrp) stage_weights<T>(sW, p, rank, tid);
+        for (int grp = rank, gi = 0; grp < ngrp; grp += CL, ++gi) {
+            const float *wb = sW + (gi & 1) * Q::WBUF;
+            cp_async_wait_all();  // this thread's copies of the group's weights
+            __syncthreads();      // sU / weights ready; previous group's sR and weight reads done
+            // the next group's weights into the other buffer (its last readers,
+            // the previous group, finished before the barrier above)
+            if (grp + CL < ngrp) stage_weights<T>(sW + ((gi + 1) & 1) * Q::WBUF, p, grp + CL, tid);
             // ---- 3+4: forward bank and potential on tile + 3 -------------
             for (int unit = tid; unit < FWD_UNITS; unit += NT) {
                 const int c = unit % R3X, rb = unit / R3X;
                 const int x = x0 - 3 + c, ylo = y0 - 3 + rb * FWD_ROWS;
                 const bool full = x >= 0 && x < W && ylo >= 0 && ylo + FWD_ROWS <= H;
-                const float fs = forward_unit<T, MODE>(sU, sR, p.wf, p.theta, grp, c, rb, y0, x0, H, W, !full);
+                const float fs = forward_unit<T, MODE>(sU, sR, wb, c, rb, y0, x0, H, W, !full);
                 sum2_add(accF, fs);
             }
             if (MODE == MODE_ENERGY_EXT) continue;
@@ -323,11 +365,11 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
 
             // ---- 5: adjoint bank on the tile (AUR x 4 unit per thread) -----
             for (int i = 0; i < G; ++i) {
-                const float *wrow = p.wa + (grp * G + i) * KT_PAD;
+                const float *wrow = wb + Q::WB_A + i * KT_PAD;
                 float kw[KT_PAD];
 #pragma unroll
                 for (int j = 0; j < KT_PAD / 4; ++j) {
-                    const float4 t = __ldg(reinterpret_cast<const float4 *>(wrow) + j);
+                    const float4 t = reinterpret_cast<const float4 *>(wrow)[j];
                     kw[4 * j] = t.x;
                     kw[4 * j + 1] = t.y;
                     kw[4 * j + 2] = t.z;
@@ -367,11 +409,11 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
                     const int blo = max(max(0, 3 - jx), x0 - jx), bhi = min(min(KS, W + 3 - jx), R3X + x0 - jx);
                     float s = 0.f;
                     for (int i = 0; i < G; ++i) {
-                        const float *wrow = p.wa + (grp * G + i) * KT_PAD;
+                        const float *wrow = wb + Q::WB_A + i * KT_PAD;
                         const float *Ri = sR + (size_t)i * R3YA * SR_LD;
                         for (int aa = alo; aa < ahi; ++aa)
                             for (int bb = blo; bb < bhi; ++bb)
-                                s = fmaf(__ldg(wrow + aa * KS + bb), Ri[(j - y0 + aa) * SR_LD + (jx - x0 + bb)], s);
+                                s = fmaf(wrow[aa * KS + bb], Ri[(j - y0 + aa) * SR_LD + (jx - x0 + bb)], s);
                     }
                     fr[k] += s;
                 }
