@@ -394,15 +394,12 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
         };
 
         for (int blk = 0; blk < NBLK; ++blk) {
-            // (a) col2im of the previous block, overlapping MMA_fwd(blk)
+            // (a) horizontal col2im of the previous block, overlapping MMA_fwd(blk)
             if (blk > 0) {
                 if (!tc::mbar_wait(&bar_a, phase_a)) tc_ok = false;
                 phase_a ^= 1u;
                 tc::fence_after_sync();
                 epi2(blk - 1);
-                tc::fence_before_sync();
-                __syncthreads();
-                if (tid < 128) emit(4 * (blk - 1) - 6 + (tid >> 5));
             }
             // (b) epilogue 1 of this block: rho' -> R (hi | lo), energy terms
             if (!tc::mbar_wait(&bar_f, phase_f)) tc_ok = false;
@@ -450,6 +447,8 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
                     *reinterpret_cast<uint4 *>(rowp + ((NF + 24 * wg) / C::E + j) * 128) = lo;
                 }
             }
+            // one barrier publishes both the H rows of block blk - 1 and the R
+            // operand of block blk (and orders epi2's reads of S before MMA_adj)
             tc::fence_before_sync();
             tc::fence_proxy_async();
             __syncthreads();
@@ -462,6 +461,9 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
                                  ks > 0 ? 1u : 0u);
                 tc::mma_commit(&bar_a);
             }
+            // vertical col2im of the rows whose sources block blk - 1 completed
+            // (the ring slots it reads are rewritten only after the next barrier)
+            if (blk > 0 && tid < 128) emit(4 * (blk - 1) - 6 + (tid >> 5));
             // (c) im2col of the next block, overlapping MMA_adj(blk)
             if (blk + 1 < NBLK) {
                 im2col<FMT>(sP, sAF, blk + 1, m, part);
@@ -480,6 +482,7 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
             }
         }
         // last block's col2im, then the ext rows whose missing sources lie off the tile
+        __syncthreads();  // the emits of block NBLK - 2 are done with the ring slots epi2 rewrites
         if (!tc::mbar_wait(&bar_a, phase_a)) tc_ok = false;
         phase_a ^= 1u;
         tc::fence_after_sync();
