@@ -264,3 +264,35 @@ def test_tc_single_step_parity_combined(fe, orc, bank, prec):
                     ref = r
             assert _relmax(w1, ref["u"]) <= TC_STEP_TOL[prec]
             np.testing.assert_allclose(s.get_u(0), np.exp(w1.astype(np.float64)), rtol=1e-6)
+
+
+@pytest.mark.parametrize("form", [("fp32", 64), ("fp32", 32), ("fp32", 32 | 0x100), ("bf16", 0), ("tf32", 0)])
+def test_gradient_parity_combined_distinct_weights(fe, orc, form):
+    """A bank of 20 filters with distinct weights theta_i (five groups of
+    four on the FP32 path, zero-padded GEMM columns on the tensor-core
+    path): the gradient in w against the oracle, with the bounds above."""
+    from rounding import ROUND
+    from paper_1404_5344_gb300 import synth
+    prec, tile = form
+    k, _ = synth.filter_bank(20, 7, seed=4, theta=0.1)
+    th = np.linspace(0.02, 0.3, 20).astype(np.float32)[::-1].copy()
+    kq = k if prec == "fp32" else ROUND[prec](k)
+    tol = GRAD_TOL if prec == "fp32" else TC_GRAD_TOL[prec]
+    _, f = _problem(96, 80, seed=5)
+    w = np.log(f).astype(np.float32)
+    kw = {"tile": tile} if prec == "fp32" else {"prec": prec}
+    with _solver(fe, f, k, th, **kw) as s:
+        g, Fg = s.gradient(0, w)
+    g_ref, F_ref = orc.gradFw(w, kq, th)
+    u = np.exp(w.astype(np.float64))
+    v_ref = g_ref / u
+    eps = 2.0 ** -24
+    A = np.zeros_like(u)
+    for i in range(kq.shape[0]):
+        ka = np.abs(kq[i]).astype(np.float64)
+        z = orc.K(u, kq[i])
+        A += th[i] * orc.KT(np.abs(2.0 * (1.0 - z * z) / (1.0 + z * z) ** 2) * orc.K(u, ka), ka)
+    bound = u * (tol * np.max(np.abs(v_ref)) + 4 * eps * A) + 2 * eps * np.abs(g_ref)
+    err = np.abs(g.astype(np.float64) - g_ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    assert Fg == pytest.approx(F_ref, rel=EF_TOL if prec != "bf16" else 10 * EF_TOL)

@@ -323,3 +323,29 @@ def test_tile_autotune_and_shapes(fe, bank):
     for bad in (16, 48, 128, -1, 64 | 0x100, 0x100):
         with pytest.raises(fe.FeError):
             fe.Solver([f], k, th, tile=bad)
+
+
+@pytest.mark.parametrize("tile", TILES)
+@pytest.mark.parametrize("nf", [1, 5, 9, 48, 64])
+def test_filter_counts_and_distinct_weights(fe, orc, tile, nf):
+    """Banks of 1..64 filters with distinct weights theta_i (the device pads
+    the bank to a multiple of 8 filters, i.e. 2..16 groups of 4, and stages
+    each group's taps and weights in shared memory; with the cluster tile,
+    ranks without a group exist for nf <= 8): gradient, energy and one step
+    against the oracle."""
+    from paper_1404_5344_gb300 import synth
+    k, _ = synth.filter_bank(nf, 7, seed=nf, theta=0.1)
+    th = np.linspace(0.02, 0.3, nf).astype(np.float32)[::-1].copy()
+    _, f = _problem(96, 80, seed=nf, kind="textured")
+    with fe.Solver([f], k, th, lam=5.0, beta=0.8, L0=1e-2, tile=tile) as s:
+        g, Fg = s.gradient(0, f)
+        assert s.step(2) == fe.FE_OK
+        u, up, _, _ = s.get_state(0)
+        assert s.step(1) == fe.FE_OK
+        u1, L = s.get_u(0), s.info(0)["L"]
+    g_ref, F_ref = orc.gradF(f, k, th)
+    assert _relmax(g, g_ref) <= GRAD_TOL
+    assert Fg == pytest.approx(F_ref, rel=E_TOL)
+    ref = orc.ipiano_fixed(f, k, th, orc.params(lam=5.0, beta=0.8, L0=1e-2, max_iter=1), [L], u, up)
+    assert ref["status"] == 0
+    assert _relmax(u1, ref["u"]) <= STEP_TOL

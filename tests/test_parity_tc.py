@@ -188,3 +188,30 @@ def test_tc_single_tile_shape(fe, bank, prec):
     for bad in (32, 64):
         with pytest.raises(fe.FeError):
             fe.Solver([f], k, th, prec=prec, tile=bad)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("nf", [1, 9, 40, 48])
+def test_tc_filter_counts_and_distinct_weights(fe, orc, prec, nf):
+    """Banks of 1..48 filters with distinct weights theta_i (zero-padded to
+    the GEMMs' 48 columns): gradient and energy against the oracle run with
+    the same rounded bank."""
+    from paper_1404_5344_gb300 import synth
+    k, _ = synth.filter_bank(nf, 7, seed=nf, theta=0.1)
+    th = np.linspace(0.02, 0.3, nf).astype(np.float32)[::-1].copy()
+    kq = ROUND[prec](k)
+    _, f = _problem(96, 80, seed=nf)
+    with fe.Solver([f], k, th, prec=prec) as s:
+        g, Fg = s.gradient(0, f)
+    g_ref, F_ref = orc.gradF(f, kq, th)
+    assert _relmax(g, g_ref) <= GRAD_TOL[prec]
+    assert Fg == pytest.approx(F_ref, rel=E_TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_tc_more_than_48_filters_unsupported(fe, prec):
+    from paper_1404_5344_gb300 import synth
+    k, th = synth.filter_bank(64, 7, seed=1, theta=0.1)
+    _, f = _problem(32, 32, seed=1)
+    with pytest.raises(fe.FeError):
+        fe.Solver([f], k, th, prec=prec)
