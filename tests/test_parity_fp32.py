@@ -344,8 +344,28 @@ def test_filter_counts_and_distinct_weights(fe, orc, tile, nf):
         assert s.step(1) == fe.FE_OK
         u1, L = s.get_u(0), s.info(0)["L"]
     g_ref, F_ref = orc.gradF(f, k, th)
-    assert _relmax(g, g_ref) <= GRAD_TOL
+    err = np.abs(g.astype(np.float64) - g_ref)
+    bound = _grad_bound(orc, f, k, th, g_ref, GRAD_TOL, 2.0 ** -24)
+    assert np.all(err <= bound), float(np.max(err / bound))
     assert Fg == pytest.approx(F_ref, rel=E_TOL)
     ref = orc.ipiano_fixed(f, k, th, orc.params(lam=5.0, beta=0.8, L0=1e-2, max_iter=1), [L], u, up)
     assert ref["status"] == 0
     assert _relmax(u1, ref["u"]) <= STEP_TOL
+
+
+def _grad_bound(orc, u, k, th, g_ref, tol, eps_z):
+    """Per-pixel bound on the gradient error for any bank: tol max|g_ref|
+    (the adjoint's FP32 accumulation, as for the 48-filter bank) plus the
+    rounding of z = k * u carried through rho'': a 49-term FMA chain errs
+    by about sqrt(49) eps_z sum|k||u| in a random-walk model, and
+    |d rho'| = |rho''(z)| |dz|, so the gradient errs by up to
+    7 eps_z A(p), A = sum_i theta_i |K_i|^T (|rho''(z_i)| |K_i| u); 8 is
+    used.  For small banks max|g| is small against A, so a bound relative
+    to max|g| alone does not hold there."""
+    u = np.asarray(u, np.float64)
+    A = np.zeros_like(u)
+    for i in range(k.shape[0]):
+        ka = np.abs(k[i]).astype(np.float64)
+        z = orc.K(u, k[i])
+        A += th[i] * orc.KT(np.abs(2.0 * (1.0 - z * z) / (1.0 + z * z) ** 2) * orc.K(u, ka), ka)
+    return tol * np.max(np.abs(g_ref)) + 8 * eps_z * A + 2.0 ** -23 * np.abs(g_ref)
