@@ -91,7 +91,6 @@ struct Geo {
     static constexpr int AUX = TX / 4;                      // adjoint units per tile row
     static constexpr int ADJ_UNITS = (TY / AUR) * AUX;
     static constexpr int RING = 2 * 3 * R3X + 2 * 3 * TY;   // frame positions
-    static constexpr int RING_PER_T = (RING + NT - 1) / NT;
     // sR follows sU: round sU up to 4 floats so that sR is 16-byte aligned
     // for the adjoint's 128-bit loads
     static constexpr size_t SM_U = ((size_t)R6Y * SU_LD + 3) / 4 * 4;
@@ -114,6 +113,7 @@ struct Geo {
     static_assert(KT * G / 4 + G * KT_PAD / 4 + 1 <= NT, "one 16-byte copy per thread stages a group");
     static_assert(MINB * (SM_BYTES + 1024) <= 228 * 1024, "MINB CTAs per SM");
     static_assert(RING <= SM_R, "the frame ring reuses sR");
+    static_assert(3 * R3Y <= NT && 3 * TX <= NT, "one frame-strip task per thread and strip");
 };
 
 constexpr float LN2 = 0.69314718055994530942f;
@@ -141,27 +141,6 @@ __device__ __forceinline__ void stage_weights(float *wb, const KParams &p, int g
     else if (tid == KT + NA4)
         cp_async16(wb + Q::WB_T, p.theta + grp * G);
     cp_async_commit();
-}
-
-template <int T>
-__device__ __forceinline__ void ring_to_pos(int idx, int &pr, int &pc) {
-    constexpr int TY = T, TX = T, R3X = T + 6;
-    if (idx < 3 * R3X) {
-        pr = idx / R3X;
-        pc = idx % R3X;
-    } else if (idx < 6 * R3X) {
-        idx -= 3 * R3X;
-        pr = TY + 3 + idx / R3X;
-        pc = idx % R3X;
-    } else if (idx < 6 * R3X + 3 * TY) {
-        idx -= 6 * R3X;
-        pr = 3 + idx / 3;
-        pc = idx % 3;
-    } else {
-        idx -= 6 * R3X + 3 * TY;
-        pr = 3 + idx / 3;
-        pc = TX + 3 + idx % 3;
-    }
 }
 
 template <int T>
@@ -252,7 +231,7 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
     using Q = Geo<T>;
     constexpr int TY = Q::TY, TX = Q::TX, NT = Q::NT, R3Y = Q::R3Y, R3X = Q::R3X, R3YA = Q::R3YA;
     constexpr int R6Y = Q::R6Y, R6X = Q::R6X, SU_LD = Q::SU_LD, SR_LD = Q::SR_LD, AUR = Q::AUR;
-    constexpr int FWD_ROWS = Q::FWD_ROWS, FWD_UNITS = Q::FWD_UNITS, RING = Q::RING, RING_PER_T = Q::RING_PER_T;
+    constexpr int FWD_ROWS = Q::FWD_ROWS, FWD_UNITS = Q::FWD_UNITS;
     constexpr size_t SM_U = Q::SM_U, SM_R = Q::SM_R;
     extern __shared__ __align__(16) float smem[];
     float *sU = smem;
@@ -337,11 +316,11 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
         for (int i = 0; i < AUR; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-        float fr[RING_PER_T];
-#pragma unroll
-        for (int k = 0; k < RING_PER_T; ++k) fr[k] = 0.f;
+        // frame values of this thread's strip tasks (left, right, top, bottom)
+        float fr[4] = {0.f, 0.f, 0.f, 0.f};
         const int aux = tid % Q::AUX, auy = tid / Q::AUX;  // adjoint unit of this thread
-        const bool border = y0 == 0 || x0 == 0 || y0 + TY > H - 3 || x0 + TX > W - 3;
+        const bool sLft = x0 == 0, sTop = y0 == 0, sRgt = x0 + TX > W - 3, sBot = y0 + TY > H - 3;
+        const bool border = sLft || sTop || sRgt || sBot;
 
         const int ngrp = p.nfp / G;
         if (rank < ngrp) stage_weights<T>(sW, p, rank, tid);
@@ -393,29 +372,96 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
                     }
                 }
             }
-            // ---- 5b: K^T r on the frame outside the image (border tiles) --
+            // ---- 5b: K^T s on the frame outside the image (border tiles) --
+            // frame value at (j, jx) = sum_i sum_ab 2 theta_i k_i[a][b]
+            // s_i(j - 3 + a, jx - 3 + b), s_i zero off-image, so only the taps
+            // that reach into the image count.  The frame is cut into strips
+            // of depth d = 1..3, one (line, depth) task per thread and strip,
+            // with static tap loops: the left / right strips run over the
+            // ring's rows l in [0, R3Y) (axis_pos maps l to the image row j,
+            // the corner rows included), the top / bottom strips over the
+            // tile's columns.
             if (border) {
+                if (tid < 3 * R3Y && (sLft || sRgt)) {
+                    const int d = 1 + tid / R3Y, l = tid - (d - 1) * R3Y;
+                    int j;
+                    if (axis_pos(l, y0, TY, H, j)) {
+                        // rows of s inside the image and in the response region;
+                        // sR row of tap a: j - y0 + a
+                        const int alo = max(max(0, 3 - j), y0 - j), ahi = min(min(KS, H + 3 - j), R3Y + y0 - j);
+                        const int r0 = j - y0;
+                        if (sLft) {
+                            // frame column -d: taps b >= 3 + d, sR column b - d
+                            float sv = 0.f;
 #pragma unroll
-                for (int k = 0; k < RING_PER_T; ++k) {
-                    const int idx = tid + k * NT;
-                    if (idx >= RING) break;
-                    int pr, pc, j, jx;
-                    ring_to_pos<T>(idx, pr, pc);
-                    if (!axis_pos(pr, y0, TY, H, j) || !axis_pos(pc, x0, TX, W, jx)) continue;
-                    // frame value at (j, jx) = sum_i sum_ab 2 theta_i k_i[a][b] s_i(j - 3 + a, jx - 3 + b); s_i is
-                    // zero off-image and the response region covers every on-image row
-                    // and column this frame pixel needs, so only those taps are visited
-                    const int alo = max(max(0, 3 - j), y0 - j), ahi = min(min(KS, H + 3 - j), R3Y + y0 - j);
-                    const int blo = max(max(0, 3 - jx), x0 - jx), bhi = min(min(KS, W + 3 - jx), R3X + x0 - jx);
-                    float s = 0.f;
-                    for (int i = 0; i < G; ++i) {
-                        const float *wrow = wb + Q::WB_A + i * KT_PAD;
-                        const float *Ri = sR + (size_t)i * R3YA * SR_LD;
-                        for (int aa = alo; aa < ahi; ++aa)
-                            for (int bb = blo; bb < bhi; ++bb)
-                                s = fmaf(wrow[aa * KS + bb], Ri[(j - y0 + aa) * SR_LD + (jx - x0 + bb)], s);
+                            for (int i = 0; i < G; ++i) {
+                                const float *wrow = wb + Q::WB_A + i * KT_PAD;
+                                const float *Ri = sR + (size_t)i * R3YA * SR_LD + r0 * SR_LD - d;
+#pragma unroll
+                                for (int aa = 0; aa < KS; ++aa) {
+                                    if (aa < alo || aa >= ahi) continue;
+#pragma unroll
+                                    for (int bb = 4; bb < KS; ++bb)
+                                        if (bb >= 3 + d) sv = fmaf(wrow[aa * KS + bb], Ri[aa * SR_LD + bb], sv);
+                                }
+                            }
+                            fr[0] += sv;
+                        }
+                        if (sRgt && W - d >= x0 && W - d < x0 + TX) {
+                            // frame column W - 1 + d: taps b <= 3 - d, sR column W - x0 - 1 + d + b
+                            float sv = 0.f;
+#pragma unroll
+                            for (int i = 0; i < G; ++i) {
+                                const float *wrow = wb + Q::WB_A + i * KT_PAD;
+                                const float *Ri = sR + (size_t)i * R3YA * SR_LD + r0 * SR_LD + (W - x0 - 1 + d);
+#pragma unroll
+                                for (int aa = 0; aa < KS; ++aa) {
+                                    if (aa < alo || aa >= ahi) continue;
+#pragma unroll
+                                    for (int bb = 0; bb < 3; ++bb)
+                                        if (bb <= 3 - d) sv = fmaf(wrow[aa * KS + bb], Ri[aa * SR_LD + bb], sv);
+                                }
+                            }
+                            fr[1] += sv;
+                        }
                     }
-                    fr[k] += s;
+                }
+                if (tid < 3 * TX && (sTop || sBot)) {
+                    const int d = 1 + tid / TX, c = tid - (d - 1) * TX;  // image column x0 + c
+                    if (x0 + c < W) {
+                        if (sTop) {
+                            // frame row -d: taps a >= 3 + d, sR row a - d, sR column c + b
+                            float sv = 0.f;
+#pragma unroll
+                            for (int i = 0; i < G; ++i) {
+                                const float *wrow = wb + Q::WB_A + i * KT_PAD;
+                                const float *Ri = sR + (size_t)i * R3YA * SR_LD - d * SR_LD + c;
+#pragma unroll
+                                for (int aa = 4; aa < KS; ++aa) {
+                                    if (aa < 3 + d) continue;
+#pragma unroll
+                                    for (int bb = 0; bb < KS; ++bb) sv = fmaf(wrow[aa * KS + bb], Ri[aa * SR_LD + bb], sv);
+                                }
+                            }
+                            fr[2] += sv;
+                        }
+                        if (sBot && H - d >= y0 && H - d < y0 + TY) {
+                            // frame row H - 1 + d: taps a <= 3 - d, sR row H - y0 - 1 + d + a
+                            float sv = 0.f;
+#pragma unroll
+                            for (int i = 0; i < G; ++i) {
+                                const float *wrow = wb + Q::WB_A + i * KT_PAD;
+                                const float *Ri = sR + (size_t)i * R3YA * SR_LD + (H - y0 - 1 + d) * SR_LD + c;
+#pragma unroll
+                                for (int aa = 0; aa < 3; ++aa) {
+                                    if (aa > 3 - d) continue;
+#pragma unroll
+                                    for (int bb = 0; bb < KS; ++bb) sv = fmaf(wrow[aa * KS + bb], Ri[aa * SR_LD + bb], sv);
+                                }
+                            }
+                            fr[3] += sv;
+                        }
+                    }
                 }
             }
         }
@@ -425,16 +471,17 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
             auto cluster = cooperative_groups::this_cluster();
             __syncthreads();  // this CTA's sR reads are done
             constexpr int NA = AUR * 4;
-            float *part = sR;  // per thread: NA adjoint sums, RING_PER_T frame values, F (s, c)
-            static_assert(NT * (NA + RING_PER_T + 2) <= (int)SM_R, "partials fit in sR");
+            constexpr int NFR = 4;
+            float *part = sR;  // per thread: NA adjoint sums, NFR frame values, F (s, c)
+            static_assert(NT * (NA + NFR + 2) <= (int)SM_R, "partials fit in sR");
 #pragma unroll
             for (int pp = 0; pp < AUR; ++pp)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) part[tid * NA + pp * 4 + q] = acc[pp][q];
 #pragma unroll
-            for (int k = 0; k < RING_PER_T; ++k) part[NT * NA + tid * RING_PER_T + k] = fr[k];
-            part[NT * (NA + RING_PER_T) + 2 * tid] = accF.s;
-            part[NT * (NA + RING_PER_T) + 2 * tid + 1] = accF.c;
+            for (int k = 0; k < NFR; ++k) part[NT * NA + tid * NFR + k] = fr[k];
+            part[NT * (NA + NFR) + 2 * tid] = accF.s;
+            part[NT * (NA + NFR) + 2 * tid + 1] = accF.c;
             cluster.sync();  // every rank's partials are visible in the cluster
             if (rank == 0) {
                 for (int r = 1; r < CL; ++r) {
@@ -444,9 +491,9 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
 #pragma unroll
                         for (int q = 0; q < 4; ++q) acc[pp][q] += rp[tid * NA + pp * 4 + q];
 #pragma unroll
-                    for (int k = 0; k < RING_PER_T; ++k) fr[k] += rp[NT * NA + tid * RING_PER_T + k];
-                    accF = sum2_merge(accF, Sum2{rp[NT * (NA + RING_PER_T) + 2 * tid],
-                                                rp[NT * (NA + RING_PER_T) + 2 * tid + 1]});
+                    for (int k = 0; k < NFR; ++k) fr[k] += rp[NT * NA + tid * NFR + k];
+                    accF = sum2_merge(accF, Sum2{rp[NT * (NA + NFR) + 2 * tid],
+                                                rp[NT * (NA + NFR) + 2 * tid + 1]});
                 }
             }
             cluster.sync();  // rank 0 has read the other ranks' shared memory
@@ -456,10 +503,17 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
             // ---- fold the frame back onto the pixels it mirrors ----------
             if (border) {
                 __syncthreads();  // all sR reads done; reuse sR for the ring
-#pragma unroll
-                for (int k = 0; k < RING_PER_T; ++k) {
-                    const int idx = tid + k * NT;
-                    if (idx < RING) sR[idx] = fr[k];
+                // each ring slot is written by the one task that computed it
+                // (slots of lines outside this tile's frame are never read)
+                if (tid < 3 * R3Y) {
+                    const int d = 1 + tid / R3Y, l = tid - (d - 1) * R3Y;
+                    if (sLft) sR[pos_to_ring<T>(l, 3 - d)] = fr[0];
+                    if (sRgt) sR[pos_to_ring<T>(l, TX + 2 + d)] = fr[1];
+                }
+                if (tid < 3 * TX) {
+                    const int d = 1 + tid / TX, c = tid - (d - 1) * TX;
+                    if (sTop) sR[pos_to_ring<T>(3 - d, c + 3)] = fr[2];
+                    if (sBot) sR[pos_to_ring<T>(TY + 2 + d, c + 3)] = fr[3];
                 }
                 __syncthreads();
             }
