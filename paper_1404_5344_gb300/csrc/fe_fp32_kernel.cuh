@@ -383,7 +383,10 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
             // tile's columns.
             if (border) {
                 if (tid < 3 * R3Y && (sLft || sRgt)) {
-                    const int d = 1 + tid / R3Y, l = tid - (d - 1) * R3Y;
+                    // depth fastest: the lanes of a load read 3 columns of ~11
+                    // rows (a column of 32 rows would hit every bank 8 times:
+                    // SR_LD = 8 mod 32)
+                    const int d = 1 + tid % 3, l = tid / 3;
                     int j;
                     if (axis_pos(l, y0, TY, H, j)) {
                         // rows of s inside the image and in the response region;
@@ -506,7 +509,7 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
                 // each ring slot is written by the one task that computed it
                 // (slots of lines outside this tile's frame are never read)
                 if (tid < 3 * R3Y) {
-                    const int d = 1 + tid / R3Y, l = tid - (d - 1) * R3Y;
+                    const int d = 1 + tid % 3, l = tid / 3;
                     if (sLft) sR[pos_to_ring<T>(l, 3 - d)] = fr[0];
                     if (sRgt) sR[pos_to_ring<T>(l, TX + 2 + d)] = fr[1];
                 }
