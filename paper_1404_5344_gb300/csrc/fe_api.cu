@@ -40,6 +40,8 @@ struct fe_ctx {
     ImgDesc *d_imgs = nullptr;
     ImgState *d_st = nullptr;
     TileDesc *d_tiles = nullptr;
+    int *d_order = nullptr;  // launch order of the tiles (whole-list launches)
+    std::vector<int> horder;
     double *d_part = nullptr;
     unsigned *d_arr = nullptr;
     LoopCtl *d_loop = nullptr;
@@ -265,6 +267,20 @@ void build_tiles(fe_ctx *c, int TY, int TX, int cl = 1) {
     c->tile_y = TY;
     c->tile_x = TX;
     c->cluster = cl;
+    // launch order of the FP32 64 x 64 tiles: tiles with more image borders
+    // first (their frame work makes them the longest), so that the last wave
+    // of a launch holds the shortest tiles; ties keep the list order
+    // (measured +0.9 % on 24 x 512^2 + 24 x 256^2; the split 32 x 32 tiles
+    // on small batches run faster in list order, -2.5 % ordered)
+    auto sides = [&](const TileDesc &t) {
+        const int H = c->H[t.img], W = c->W[t.img];
+        return (t.y0 == 0) + (t.x0 == 0) + (t.y0 + TY > H - 3) + (t.x0 + TX > W - 3);
+    };
+    c->horder.resize(c->ntiles);
+    for (int k = 0; k < c->ntiles; ++k) c->horder[k] = k;
+    if (!tc && TY == 64 && cl == 1)
+        std::stable_sort(c->horder.begin(), c->horder.end(),
+                         [&](int a, int b) { return sides(c->htile[a]) > sides(c->htile[b]); });
 }
 
 // FP32 tile candidates: code = T, or T | FE_TILE_CLUSTER4
@@ -283,6 +299,7 @@ fe_status upload_tiles(fe_ctx *c) {
     FE_CUDA(c, cudaMemcpyAsync(c->d_imgs, c->himg.data(), sizeof(ImgDesc) * c->nimg, cudaMemcpyHostToDevice, c->s));
     FE_CUDA(c, cudaMemcpyAsync(c->d_tiles, c->htile.data(), sizeof(TileDesc) * c->ntiles, cudaMemcpyHostToDevice,
                                c->s));
+    FE_CUDA(c, cudaMemcpyAsync(c->d_order, c->horder.data(), sizeof(int) * c->ntiles, cudaMemcpyHostToDevice, c->s));
     c->kp.ntiles = c->ntiles;
     return FE_OK;
 }
@@ -659,6 +676,7 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
     if ((st = dalloc(c, &c->d_imgs, nimg)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_st, nimg)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_tiles, max_tiles)) != FE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_order, max_tiles)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_part, max_tiles * NRED)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_arr, nimg)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_loop, 1)) != FE_OK) return bail(st);
@@ -698,7 +716,8 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
         cudaMemcpy(c->d_th, th.data(), th.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->d_imgs, c->himg.data(), sizeof(ImgDesc) * nimg, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->d_tiles, c->htile.data(), sizeof(TileDesc) * c->ntiles, cudaMemcpyHostToDevice) !=
-            cudaSuccess)
+            cudaSuccess ||
+        cudaMemcpy(c->d_order, c->horder.data(), sizeof(int) * c->ntiles, cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(set_err(c, FE_ECUDA, "upload of descriptors failed: %s", cudaGetErrorString(cudaGetLastError())));
 
     KParams &kp = c->kp;
@@ -706,6 +725,7 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
     kp.imgs = c->d_imgs;
     kp.st = c->d_st;
     kp.tiles = c->d_tiles;
+    kp.order = c->d_order;
     kp.partials = c->d_part;
     kp.img_arrivals = c->d_arr;
     kp.loop = c->d_loop;
@@ -907,6 +927,7 @@ static fe_status ext_launch(fe_ctx *c, int mode, int img, const float *u, float 
     FE_CUDA(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->s));
     KParams kp = c->kp;
     kp.tile0 = d.tile_begin;
+    kp.order = nullptr;  // one image's tiles in list order
     kp.u_ext = ud;
     kp.g_ext = gd;
     FE_CUDA(c, launch_tiles(c, mode, kp, d.ntiles));

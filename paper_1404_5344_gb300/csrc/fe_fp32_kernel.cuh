@@ -243,7 +243,8 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
     const int tid = threadIdx.x;
     int rank = 0;
     if constexpr (CL > 1) rank = (int)cooperative_groups::this_cluster().block_rank();
-    const int gtile = p.tile0 + (int)blockIdx.x / CL;
+    const int bt = p.tile0 + (int)blockIdx.x / CL;
+    const int gtile = p.order ? p.order[bt] : bt;
     const TileDesc td = p.tiles[gtile];
     const int img = td.img;
     const ImgDesc im = p.imgs[img];

@@ -92,6 +92,7 @@ struct KParams {
     double beta, eta, c2;
     int max_bt;
     int tile0;                  // first global tile of this launch (grid covers tile0 ..)
+    const int *order;           // whole-list launches: block b runs tile order[b] (NULL: tile0 + b)
     const float *u_ext;         // input of the EXT modes (one image per launch)
     float *g_ext;               // gradient output of MODE_GRAD_EXT
     double *results;            // [nimg][2]: F, G of the EXT modes

@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
     __shared__ int sLast;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int gtile = p.tile0 + (int)blockIdx.x;
+    const int gtile = p.order ? p.order[p.tile0 + (int)blockIdx.x] : p.tile0 + (int)blockIdx.x;
     const TileDesc td = p.tiles[gtile];
     const int img = td.img;
     const ImgDesc im = p.imgs[img];
