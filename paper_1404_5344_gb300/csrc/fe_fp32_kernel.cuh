@@ -182,9 +182,9 @@ __device__ __forceinline__ float forward_unit(const float *__restrict__ sU, floa
             const float4 w0 = *reinterpret_cast<const float4 *>(wcol + (aa * KS + bb) * G);
             const float w[G] = {w0.x, w0.y, w0.z, w0.w};
 #pragma unroll
-            for (int r = 0; r < FWD_ROWS; ++r)
+            for (int i = 0; i < G; ++i)
 #pragma unroll
-                for (int i = 0; i < G; ++i) z[r][i] = fmaf(w[i], v[r + aa], z[r][i]);
+                for (int r = 0; r < FWD_ROWS; ++r) z[r][i] = fmaf(w[i], v[r + aa], z[r][i]);
         }
     }
     float th[G];
