@@ -40,9 +40,9 @@ FLOP_PER_PIXEL_TRIAL = 2 * 48 * 49 * 2  # forward + adjoint bank, 2 flop per MAC
 # launch with every image active, per pixel, from one ncu capture of the
 # current kernels on 24 x 512^2 (profiles/*_trial_24x512.md); None where no
 # capture of the current kernel exists
-TRAFFIC_PER_PIXEL = {("fp32", "variant"): 125.478400e6 / 6291456,
-                     ("bf16", "variant"): 127.715328e6 / 6291456,
-                     ("fp32", "combined"): 126.239488e6 / 6291456}
+TRAFFIC_PER_PIXEL = {("fp32", "variant"): 137.742848e6 / 6291456,
+                     ("bf16", "variant"): 128.986880e6 / 6291456,
+                     ("fp32", "combined"): 137.732352e6 / 6291456}
 SMS, FP32_LANES = 152, 128
 METRIC = "Mpixel*iter/s of fused iPiano step"
 
