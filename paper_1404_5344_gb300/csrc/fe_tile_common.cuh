@@ -56,8 +56,13 @@ __device__ __forceinline__ float data_w(float w, float f2, float l1, float l2) {
 // paper's choice, Sec. III-A): the root of phi(w) = w - what + tau g'(w),
 // g'(w) = l1 (1 - f^2 e^{-2w}) + l2 (e^{2w} - f^2).  phi is increasing
 // (phi' = 1 + tau g'' > 0) and g'(log f) = 0, so the root lies between what
-// and log f; a Newton step that leaves that bracket is replaced by
+// and log f; a Newton step that leaves that closed bracket is replaced by
 // bisection.  At most 20 steps; stops once a step is below 2^-22 (1 + |w|).
+// The bracket test is inclusive: near the root a step that rounds onto the
+// bracket end just updated (w itself) must count as converged; a strict
+// test bisects away from the root there, and in FP32 the iteration then
+// bounced until the step limit (every warp ran 20 steps, with errors up to
+// 1e-4 against the FP64 root; inclusive: 4-10 steps, 1e-7).
 __device__ __forceinline__ float prox_w(float what, float f2, float tau, float l1, float l2) {
     const float lf = 0.5f * logf(f2);
     float lo = fminf(what, lf), hi = fmaxf(what, lf);
@@ -72,7 +77,7 @@ __device__ __forceinline__ float prox_w(float what, float f2, float tau, float l
             lo = w;
         const float d2 = fmaf(2.0f * tau, fmaf(l1 * f2, em2, l2 * e2), 1.0f);
         float wn = w - ph / d2;
-        if (!(wn > lo && wn < hi)) wn = 0.5f * (lo + hi);
+        if (!(wn >= lo && wn <= hi)) wn = 0.5f * (lo + hi);
         const float step = fabsf(wn - w);
         w = wn;
         if (step <= 2.4e-7f * (1.0f + fabsf(w))) break;

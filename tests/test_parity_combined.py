@@ -296,3 +296,29 @@ def test_gradient_parity_combined_distinct_weights(fe, orc, form):
     err = np.abs(g.astype(np.float64) - g_ref)
     assert np.all(err <= bound), float(np.max(err / bound))
     assert Fg == pytest.approx(F_ref, rel=EF_TOL if prec != "bf16" else 10 * EF_TOL)
+
+
+@pytest.mark.parametrize("L0", [1e-3, 1.0, 100.0])
+def test_newton_prox_per_pixel(fe, orc, L0):
+    """The Newton prox of the combined model on its own: with theta = 0 the
+    first step is w^1 = prox_{alpha G}(w^0) pixel by pixel (every trial is
+    accepted: F = 0), which must match the FP64 root to FP32 precision:
+    |w - w_ref| <= 1e-6 (1 + |w_ref|) (the FP32 iteration stops at steps
+    below 2^-22 (1 + |w|)).  A Newton safeguard that bisects away from a
+    converged iterate ends anywhere in the bracket and fails this."""
+    from paper_1404_5344_gb300 import synth
+    k, _ = synth.filter_bank(8, 7, seed=2, theta=0.1)
+    th = np.zeros(8, np.float32)
+    _, f = _problem(48, 64, seed=31)
+    rng = np.random.default_rng(5)
+    u0 = (f * np.exp(rng.normal(0.0, 0.3, f.shape))).astype(np.float32)
+    with _solver(fe, f, k, th, u0=u0, L0=L0, beta=0.8) as s:
+        w0 = s.get_state(0)[0].copy()
+        assert s.step(1) == fe.FE_OK
+        w1 = s.get_state(0)[0]
+        alpha = s.info(0)["alpha"]
+    assert alpha == pytest.approx(2 * (1 - 0.8) / (L0 + 2e-6), rel=1e-12)
+    ref = np.array([orc.proxc(float(a), float(b), alpha, L1, L2) for a, b in zip(w0.ravel(), f.ravel())])
+    ref = ref.reshape(w1.shape)
+    err = np.abs(w1.astype(np.float64) - ref) / (1.0 + np.abs(ref))
+    assert float(np.max(err)) <= 1e-6, float(np.max(err))
