@@ -119,11 +119,12 @@ typedef struct {
     int max_backtrack;      /* rejections allowed per iteration, >= 0 */
     int prec;               /* fe_precision */
     int tile;               /* output tile of the trial kernel: 0 = autotune.  FP32:
-                               0, 64, 32 (T x T), or 32 | FE_TILE_CLUSTER4 (32 x 32
-                               tiles, each split by filter group over a cluster of
-                               4 CTAs that combine through distributed shared
-                               memory: for images too small to fill the GPU); at 0
-                               fe_init_batch times the three on the context's own
+                               0, 64, 32 (T x T), or 32 | FE_TILE_CLUSTER4 /
+                               64 | FE_TILE_CLUSTER4 (T x T tiles, each split by
+                               filter group over a cluster of 4 CTAs that combine
+                               through distributed shared memory: for images too
+                               small to fill the GPU); at 0 fe_init_batch times the
+                               four on the context's own
                                images (the initial gradient kernel, 4 launches
                                each) and keeps the fastest, cached per device and
                                list of image sizes.

@@ -210,8 +210,9 @@ fe_status validate_params(fe_ctx *c, const fe_params *p) {
         return set_err(c, FE_EINVAL, "unknown precision %d", p->prec);
     if (p->prec != FE_FP32 && p->nf > 48)
         return set_err(c, FE_EUNSUPPORTED, "the tensor-core forms take at most 48 filters (nf=%d)", p->nf);
-    if (p->prec == FE_FP32 && p->tile != 0 && !fp32_tile_supported(p->tile) && p->tile != (32 | FE_TILE_CLUSTER4))
-        return set_err(c, FE_EUNSUPPORTED, "FP32 tile %d: use 0 (autotune), 32, 64 or 32 | FE_TILE_CLUSTER4",
+    if (p->prec == FE_FP32 && p->tile != 0 && !fp32_tile_supported(p->tile) && p->tile != (32 | FE_TILE_CLUSTER4) &&
+        p->tile != (64 | FE_TILE_CLUSTER4))
+        return set_err(c, FE_EUNSUPPORTED, "FP32 tile %d: use 0 (autotune), 32, 64, 32 | FE_TILE_CLUSTER4 or 64 | FE_TILE_CLUSTER4",
                        p->tile);
     if (p->prec != FE_FP32 && p->tile != 0)
         return set_err(c, FE_EUNSUPPORTED, "the tensor-core forms have one tile shape: tile must be 0");
@@ -641,14 +642,14 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
         c->himg.push_back(d);
     }
     // candidate tile shapes: the tensor-core forms have one; FP32 has 64 and
-    // 32 (autotuned when p->tile == 0)
+    // 32, each also split over a 4-CTA cluster (autotuned when p->tile == 0)
     std::vector<int> cand;
     if (tc)
         cand.push_back(0);
     else if (p->tile != 0)
         cand.push_back(p->tile);
     else
-        cand = {64, 32, 32 | FE_TILE_CLUSTER4};
+        cand = {64, 32, 32 | FE_TILE_CLUSTER4, 64 | FE_TILE_CLUSTER4};
     size_t max_tiles = 0;
     for (int T : cand)
         max_tiles = std::max(max_tiles, tc ? count_tiles(c, tc_tile_y, tc_tile_x) : count_tiles(c, T & 0xff, T & 0xff));

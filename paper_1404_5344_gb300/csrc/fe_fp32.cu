@@ -18,10 +18,12 @@ cudaError_t fp32_prepare() {
     if (e == cudaSuccess) e = prepare_tile<32, 0>();
     if (e == cudaSuccess) e = prepare_tile<32, 0, 4>();
     if (e == cudaSuccess) e = fp32c_prepare();
+    if (e == cudaSuccess) e = fp32cl64_prepare();
     return e;
 }
 
 cudaError_t fp32_launch(int mode, const KParams &p, int ngrid, cudaStream_t s, int T, int model, int cl) {
+    if (T == 64 && cl == 4) return fp32cl64_launch(mode, p, ngrid, s, model);
     if (model == 1) return fp32c_launch(mode, p, ngrid, s, T, cl);
     if (T == 64 && cl == 1) return launch_tile<64, 0>(mode, p, ngrid, s);
     if (T == 32 && cl == 1) return launch_tile<32, 0>(mode, p, ngrid, s);
@@ -30,6 +32,7 @@ cudaError_t fp32_launch(int mode, const KParams &p, int ngrid, cudaStream_t s, i
 }
 
 const void *fp32_trial_entry(int T, int model, int cl) {
+    if (T == 64 && cl == 4) return fp32cl64_trial_entry(model);
     if (model == 1) return fp32c_trial_entry(T, cl);
     if (T == 32)
         return cl == 4 ? reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL, 32, 0, 4>)

@@ -121,6 +121,9 @@ const void *fp32_trial_entry(int T = fp32_tile_size, int model = 0, int cl = 1);
 cudaError_t fp32c_prepare();  // combined-model instantiations (fe_fp32_comb.cu)
 cudaError_t fp32c_launch(int mode, const KParams &p, int grid, cudaStream_t s, int T, int cl);
 const void *fp32c_trial_entry(int T, int cl);
+cudaError_t fp32cl64_prepare();  // 64 x 64 tiles on 4-CTA clusters, both models (fe_fp32_cl64.cu)
+cudaError_t fp32cl64_launch(int mode, const KParams &p, int grid, cudaStream_t s, int model);
+const void *fp32cl64_trial_entry(int model);
 
 // Tensor-core tile kernel (fe_tc.cu); fmt 1 = BF16, 2 = TF32 operands
 constexpr int tc_tile_y = 58, tc_tile_x = 26;  // output tile; tile + 3-pixel halo = 64 x 32

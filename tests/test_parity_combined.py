@@ -69,7 +69,7 @@ def _oprm(orc, **kw):
     return orc.params(model=orc.MODEL_COMBINED, **kw)
 
 
-@pytest.mark.parametrize("tile", [64, 32, 32 | 0x100])
+@pytest.mark.parametrize("tile", [64, 32, 32 | 0x100, 64 | 0x100])
 @pytest.mark.parametrize("shape", [(64, 64), (131, 77), (8, 9), (200, 13)])
 def test_gradient_parity_combined(fe, orc, bank, shape, tile):
     k, th = bank
@@ -266,7 +266,8 @@ def test_tc_single_step_parity_combined(fe, orc, bank, prec):
             np.testing.assert_allclose(s.get_u(0), np.exp(w1.astype(np.float64)), rtol=1e-6)
 
 
-@pytest.mark.parametrize("form", [("fp32", 64), ("fp32", 32), ("fp32", 32 | 0x100), ("bf16", 0), ("tf32", 0)])
+@pytest.mark.parametrize("form", [("fp32", 64), ("fp32", 32), ("fp32", 32 | 0x100), ("fp32", 64 | 0x100), ("bf16", 0),
+                                  ("tf32", 0)])
 def test_gradient_parity_combined_distinct_weights(fe, orc, form):
     """A bank of 20 filters with distinct weights theta_i (five groups of
     four on the FP32 path, zero-padded GEMM columns on the tensor-core

@@ -55,8 +55,8 @@ SIZES = [(64, 64), (8, 8), (131, 77), (200, 13), (13, 200), (67, 129), (128, 128
 
 
 # the FP32 kernel's tile shapes: 64 x 64, 32 x 32, and 32 x 32 split over a
-# 4-CTA cluster (FE_TILE_CLUSTER4 = 0x100)
-TILES = [64, 32, 32 | 0x100]
+# 4-CTA cluster (FE_TILE_CLUSTER4 = 0x100), and 64 x 64 split likewise
+TILES = [64, 32, 32 | 0x100, 64 | 0x100]
 
 
 @pytest.mark.parametrize("tile", TILES)
@@ -295,7 +295,7 @@ def test_gradient_parity_large_sampled(fe, orc, bank, shape):
 
 
 def test_tile_autotune_and_shapes(fe, bank):
-    """tile = 0 picks one of the two shapes and caches the choice per list of
+    """tile = 0 picks one of the four shapes and caches the choice per list of
     image sizes; a forced tile is kept; the per-pixel arithmetic does not
     depend on the tile, so gradients and one step agree bit for bit."""
     k, th = bank
@@ -314,13 +314,17 @@ def test_tile_autotune_and_shapes(fe, bank):
             us.append(s.get_u(0))
     assert np.array_equal(gs[0], gs[1])
     assert np.array_equal(us[0], us[1])
-    # the cluster variant sums each pixel's filters rank by rank: another FP32
-    # summation order, so the two agree within the FP32 gradient bound
-    with fe.Solver([f], k, th, L0=1e-2, beta=0.0, tile=32 | 0x100) as s:
-        assert s.tile == (32, 32) and s.cluster == 4
-        gc = s.gradient(0, f)[0]
-    assert float(np.max(np.abs(gc - gs[0])) / np.max(np.abs(gs[0]))) <= GRAD_TOL
-    for bad in (16, 48, 128, -1, 64 | 0x100, 0x100):
+    # the cluster variants sum each pixel's filters rank by rank: another FP32
+    # summation order, so they agree with the others within the FP32
+    # gradient bound (and with each other bit for bit: same ranks, same order)
+    gcs = []
+    for t in (32, 64):
+        with fe.Solver([f], k, th, L0=1e-2, beta=0.0, tile=t | 0x100) as s:
+            assert s.tile == (t, t) and s.cluster == 4
+            gcs.append(s.gradient(0, f)[0])
+        assert float(np.max(np.abs(gcs[-1] - gs[0])) / np.max(np.abs(gs[0]))) <= GRAD_TOL
+    assert np.array_equal(gcs[0], gcs[1])
+    for bad in (16, 48, 128, -1, 0x100, 16 | 0x100, 0x200 | 64):
         with pytest.raises(fe.FeError):
             fe.Solver([f], k, th, tile=bad)
 
