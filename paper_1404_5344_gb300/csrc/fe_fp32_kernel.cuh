@@ -27,8 +27,9 @@
 // the tile + halo fit in shared memory; the adjoint accumulators stay in
 // registers across groups.
 //
-// Two tile shapes, T x T output pixels per CTA (the autotuner of the host
-// side picks one per context):
+// Two tile shapes, T x T output pixels per CTA, each also split by filter
+// group over a 4-CTA thread-block cluster (CL = 4; the autotuner of the host
+// side picks one of the four per context):
 //   T = 64: 256 threads, two CTAs per SM so that one CTA's barrier waits are
 //           covered by the other; forward units of 1 column x 10 rows x 4
 //           filters over the 70 x 70 response region (490 units, two rounds);
@@ -43,7 +44,9 @@
 // unit slides its column window over the 7 kernel columns, reading weight
 // vectors as uniform 128-bit shared loads.  An adjoint unit reads each window
 // row with three LDS.128 and holds each filter's 49 weights in registers
-// while its window rows stream through.
+// while its window rows stream through.  The frame of the symmetric-boundary
+// transpose (the 3-pixel ring outside the image) is computed per group as
+// strip tasks and folded onto the pixels it mirrors after the last group.
 #pragma once
 
 #include <cuda_runtime.h>
