@@ -42,7 +42,7 @@ FLOP_PER_PIXEL_TRIAL = 2 * 48 * 49 * 2  # forward + adjoint bank, 2 flop per MAC
 # capture of the current kernel exists
 TRAFFIC_PER_PIXEL = {("fp32", "variant"): 137.742848e6 / 6291456,
                      ("bf16", "variant"): 128.986880e6 / 6291456,
-                     ("fp32", "combined"): 137.732352e6 / 6291456}
+                     ("fp32", "combined"): 137.161984e6 / 6291456}
 SMS, FP32_LANES = 152, 128
 METRIC = "Mpixel*iter/s of fused iPiano step"
 
