@@ -403,13 +403,14 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
 #pragma unroll
                             for (int i = 0; i < G; ++i) {
                                 const float *wrow = wb + Q::WB_A + i * KT_PAD;
-                                const float *Ri = sR + (size_t)i * R3YA * SR_LD + r0 * SR_LD - d;
+                                const float *Ri = sR + (size_t)i * R3YA * SR_LD;
 #pragma unroll
                                 for (int aa = 0; aa < KS; ++aa) {
                                     if (aa < alo || aa >= ahi) continue;
 #pragma unroll
                                     for (int bb = 4; bb < KS; ++bb)
-                                        if (bb >= 3 + d) sv = fmaf(wrow[aa * KS + bb], Ri[aa * SR_LD + bb], sv);
+                                        if (bb >= 3 + d)
+                                            sv = fmaf(wrow[aa * KS + bb], Ri[(r0 + aa) * SR_LD + bb - d], sv);
                                 }
                             }
                             fr[0] += sv;
@@ -420,13 +421,13 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
 #pragma unroll
                             for (int i = 0; i < G; ++i) {
                                 const float *wrow = wb + Q::WB_A + i * KT_PAD;
-                                const float *Ri = sR + (size_t)i * R3YA * SR_LD + r0 * SR_LD + (W - x0 - 1 + d);
+                                const float *Ri = sR + (size_t)i * R3YA * SR_LD + (W - x0 - 1 + d);
 #pragma unroll
                                 for (int aa = 0; aa < KS; ++aa) {
                                     if (aa < alo || aa >= ahi) continue;
 #pragma unroll
                                     for (int bb = 0; bb < 3; ++bb)
-                                        if (bb <= 3 - d) sv = fmaf(wrow[aa * KS + bb], Ri[aa * SR_LD + bb], sv);
+                                        if (bb <= 3 - d) sv = fmaf(wrow[aa * KS + bb], Ri[(r0 + aa) * SR_LD + bb], sv);
                                 }
                             }
                             fr[1] += sv;
@@ -442,12 +443,13 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
 #pragma unroll
                             for (int i = 0; i < G; ++i) {
                                 const float *wrow = wb + Q::WB_A + i * KT_PAD;
-                                const float *Ri = sR + (size_t)i * R3YA * SR_LD - d * SR_LD + c;
+                                const float *Ri = sR + (size_t)i * R3YA * SR_LD + c;
 #pragma unroll
                                 for (int aa = 4; aa < KS; ++aa) {
                                     if (aa < 3 + d) continue;
 #pragma unroll
-                                    for (int bb = 0; bb < KS; ++bb) sv = fmaf(wrow[aa * KS + bb], Ri[aa * SR_LD + bb], sv);
+                                    for (int bb = 0; bb < KS; ++bb)
+                                        sv = fmaf(wrow[aa * KS + bb], Ri[(aa - d) * SR_LD + bb], sv);
                                 }
                             }
                             fr[2] += sv;
