@@ -5,7 +5,8 @@ benchmark times, on sampled outputs the FP64 oracle can compute exactly:
   loop): one iPiano step of the whole batch, then for several images and
   crops the oracle steps a window with a 6-pixel margin from the GPU's own
   (u^n, u^{n-1}) at the GPU's accepted L (grad F has a radius of 6 pixels,
-  so the inner crop is exact);
+  so the inner crop is exact) - for the FP32 variant model, the combined
+  model, and the BF16 / TF32 forms (oracle with the same rounded bank);
 * the batch of 64 uneven images (128^2 .. 1536^2): gradients at sampled
   pixels of several images against the oracle's per-pixel gradient;
 * the warm-start network on 512^2 images: outputs on crops with a 5-pixel
@@ -157,3 +158,69 @@ def test_degenerate_cases_on_the_gpu(fe, bank):
         s.solve(500, 1e-12)
         u = s.get_u(0)
     np.testing.assert_allclose(u, f, rtol=1e-5)
+
+
+def _throughput_batch():
+    from paper_1404_5344_gb300 import synth
+    fs = []
+    for j in range(48):
+        s = 512 if j < 24 else 256
+        fs.append(synth.speckle(synth.textured_image(s, s, seed=1000 + j), L=(1.0, 4.0, 8.0)[j % 3], seed=5000 + j))
+    return fs
+
+
+def test_throughput_batch_one_step_crops_combined(fe, orc, bank):
+    """The combined model (Eq. newmodel, lambda1 = 160, lambda2 = 0.004, the
+    bench's --model combined line) on the whole throughput batch in its
+    CUDA-graph loop: one step, then windowed oracle steps from the GPU's own
+    (w^n, w^{n-1}) at the GPU's L, as for the variant model above; 1e-5 of
+    max|w| on the crop."""
+    import torch
+    k, th = bank
+    fs = _throughput_batch()
+    fd = [torch.from_numpy(f).cuda() for f in fs]
+    kw = dict(lam=0.004, beta=0.8, L0=1.0, eta=2.0, c2=1e-6)
+    prm = orc.params(max_iter=1, model=orc.MODEL_COMBINED, lam1=160.0, **kw)
+    with fe.Solver(fd, k, th, model="combined", lam1=160.0, loop_mode=1, **kw) as s:
+        assert s.step(3) == fe.FE_OK
+        picks = [0, 13, 30, 47]
+        states = {j: s.get_state(j) for j in picks}
+        assert s.step(1) == fe.FE_OK
+        after = {j: (s.get_state(j)[0], s.info(j)["L"]) for j in picks}
+    for j in picks:
+        w, wp, _, _ = states[j]
+        w1, L = after[j]
+        S = fs[j].shape[0]
+        for (y, x) in [(0, 0), (S // 2 - 40, S // 3), (S - 64, S - 64)]:
+            ref = _window_step(orc, fs[j], k, th, prm, w, wp, L, y, x, 64, 64)
+            got = w1[y:y + 64, x:x + 64]
+            assert float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))) <= STEP_TOL, (j, y, x)
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16", 2e-5), ("tf32", 1e-5)])
+def test_throughput_batch_one_step_crops_tensor_core(fe, orc, bank, prec, tol):
+    """The tensor-core forms (the bench's --prec lines) on the whole
+    throughput batch in its CUDA-graph loop: one step against the oracle run
+    with the same rounded bank on windowed crops (the single-step tolerances
+    of tests/test_parity_tc.py)."""
+    import torch
+    from rounding import ROUND
+    k, th = bank
+    kq = ROUND[prec](k)
+    fs = _throughput_batch()
+    fd = [torch.from_numpy(f).cuda() for f in fs]
+    prm = orc.params(lam=5.0, beta=0.8, L0=1.0, eta=2.0, c2=1e-6, max_iter=1)
+    with fe.Solver(fd, k, th, lam=5.0, beta=0.8, L0=1.0, prec=prec, loop_mode=1) as s:
+        assert s.step(3) == fe.FE_OK
+        picks = [0, 23, 24, 47]
+        states = {j: s.get_state(j) for j in picks}
+        assert s.step(1) == fe.FE_OK
+        after = {j: (s.get_u(j), s.info(j)["L"]) for j in picks}
+    for j in picks:
+        u, up, _, _ = states[j]
+        u1, L = after[j]
+        S = fs[j].shape[0]
+        for (y, x) in [(0, 0), (S // 2 - 40, S // 3), (S - 64, S - 64)]:
+            ref = _window_step(orc, fs[j], kq, th, prm, u, up, L, y, x, 64, 64)
+            got = u1[y:y + 64, x:x + 64]
+            assert float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))) <= tol, (j, y, x)
