@@ -24,14 +24,15 @@
 // pair of that type (K doubles; the B operand is stored once and the MMAs of
 // the lo half re-read it), so z and S are accurate for the rounded bank and
 // the descent test sees a consistent gradient.  The prologue writes u^{n+1}
-// as hi and lo planes of the operand type (BF16: plus copies shifted by one
-// element, so that every 8-pixel run starts on a 4-byte boundary); the
-// im2col is then a copy of 4-byte words.
+// as hi and lo planes of the operand type; the im2col copies 4-byte words
+// (BF16: an 8-pixel run that starts at an odd column is realigned from five
+// words by funnel shifts).
 //
 // Geometry: 26 x 58 output tile; tile + 3-pixel halo = 32 x 64 pixels = 16
 // GEMM blocks of 4 rows x 32 columns (M = 128); tile + 6 = 38 x 70 for u^{n+1}.
 // 256 threads: the two warpgroups split the epilogues by TMEM column; one
-// thread issues the MMAs.  BF16 fits two CTAs per SM (85 KB of shared memory).
+// thread issues the MMAs.  BF16 fits three CTAs per SM (72 KB of shared memory,
+// 80 registers per thread), TF32 one (118 KB).
 //
 // Waits on the MMA completion barriers are bounded; on a time-out the kernel
 // records tc_error, poisons its partial sums (the image stops with a
@@ -60,7 +61,7 @@ constexpr int NBLK = R3Y / 4;                // 16 GEMM blocks of 128 pixels
 constexpr int NF = 48;                       // N of the forward GEMM
 constexpr int NTAP = 64;                     // N of the adjoint GEMM (49 taps + zeros)
 constexpr int KADJ = 2 * NF;                 // r hi | r lo
-constexpr int HRING = 12;                    // rows of the horizontal-sum ring
+constexpr int HRING = 10;                    // rows of the horizontal-sum ring (the 10 a vertical gather reads)
 constexpr int TMEM_COLS = 128;               // D_fwd at column 0, D_adj at column 64
 static_assert(R3X == 32, "one warp per halo row");
 static_assert(R3Y % 4 == 0, "GEMM blocks of 4 rows");
@@ -74,18 +75,19 @@ struct Cfg {
     static constexpr int E = 16 / EB;                      // elements per 16-byte chunk
     static constexpr int NCH = KPASS / E;                  // chunks per pass
     static constexpr int RCH = 8 / E;                      // chunks per kernel row
-    static constexpr int NPL = FMT == 1 ? 4 : 2;           // planes: hi, (hi shifted,) lo, (lo shifted)
-    // plane stride in 4-byte words; BF16: = 16 (mod 32) so that the even and
-    // odd lanes of the im2col (unshifted / shifted copy) use disjoint banks
-    static constexpr int PL_WORDS = FMT == 1 ? 1424 : R6Y * PP;
+    static constexpr int NPL = 2;                          // planes: hi, lo
+    static constexpr int PL_WORDS = R6Y * PP * EB / 4;     // plane stride in 4-byte words
     static_assert(PL_WORDS * 4 >= R6Y * PP * EB, "plane holds the u region");
     static constexpr size_t AF_BYTES = (size_t)128 * KFWD * EB;
     static constexpr size_t R_BYTES = (size_t)128 * KADJ * EB;
     static constexpr size_t BF_BYTES = (size_t)NF * KPASS * EB;   // one pass: hi and lo MMAs share it
     static constexpr size_t BA_BYTES = (size_t)NTAP * NF * EB;    // likewise for r hi and r lo
+    // one buffer holds the A operand of the forward GEMM (im2col of block b + 1)
+    // and the R operand of the adjoint GEMM (block b) in turn: R is written
+    // after MMA_fwd(b) completed, the im2col after MMA_adj(b) completed
     static constexpr size_t OFF_AF = 0;
-    static constexpr size_t OFF_R = OFF_AF + AF_BYTES;
-    static constexpr size_t OFF_BF = OFF_R + R_BYTES;
+    static constexpr size_t OFF_R = OFF_AF;
+    static constexpr size_t OFF_BF = OFF_AF + (AF_BYTES > R_BYTES ? AF_BYTES : R_BYTES);
     static constexpr size_t OFF_BA = OFF_BF + BF_BYTES;
     static constexpr size_t OFF_U = OFF_BA + BA_BYTES;       // NPL planes of u^{n+1}
     static constexpr size_t OFF_H = OFF_U + (size_t)NPL * PL_WORDS * 4;
@@ -93,12 +95,12 @@ struct Cfg {
     static constexpr size_t OFF_TH = OFF_G + (size_t)R3Y * R3X * 4;
     static constexpr size_t OFF_RED = OFF_TH + (size_t)2 * NF * 4;
     static constexpr size_t BYTES = OFF_RED + (size_t)(NT / 32) * NRED * 8;
-    static_assert(OFF_R % 128 == 0 && OFF_BF % 128 == 0 && OFF_BA % 128 == 0 && OFF_U % 128 == 0,
+    static_assert(OFF_H % 16 == 0 && OFF_BF % 128 == 0 && OFF_BA % 128 == 0 && OFF_U % 128 == 0,
                   "operand alignment");
     static_assert(OFF_U % 16 == 0 && OFF_TH % 16 == 0 && OFF_RED % 8 == 0, "alignment");
     static_assert(BF_BYTES % 16 == 0 && BA_BYTES % 16 == 0, "vector copies");
 };
-static_assert(2 * (Cfg<1>::BYTES + 1024) <= 228 * 1024, "BF16: two CTAs per SM");
+static_assert(3 * (Cfg<1>::BYTES + 1024) <= 228 * 1024, "BF16: three CTAs per SM");
 static_assert(Cfg<2>::BYTES <= 227 * 1024, "TF32: one CTA per SM");
 
 constexpr float LN2 = 0.69314718055994530942f;
@@ -137,34 +139,47 @@ __device__ __forceinline__ void hilo_chunk<2>(const float *v, uint4 &hi, uint4 &
 // m/32, column pc = m%32) gets, for window row a, the 8 values u(4 blk + m/32
 // + a, pc .. pc + 7) as K values 8a .. 8a + 7 (hi part in chunks [0, NCH), lo
 // in [NCH, 2 NCH)).  part 0 copies the hi plane, part 1 the lo plane.  The
-// runs are copied as 4-byte words: BF16 reads the unshifted plane at even pc
-// and the copy shifted by one element at odd pc.
+// runs are copied as 4-byte words; BF16 holds two elements per word, so a run
+// that starts at an odd column is taken from five words shifted by one
+// element (funnel shifts; at an even column the shift is 0).  BF16 K-pads each
+// pass with window row 7, whose chunk is rewritten with zeros here (the
+// buffer held the R operand of the previous block).
 template <int FMT>
 __device__ __forceinline__ void im2col(const uint32_t *__restrict__ sP, unsigned char *__restrict__ sAF, int blk,
                                        int m, int part) {
     using C = Cfg<FMT>;
     const int pr = 4 * blk + (m >> 5), pc = m & 31;
-    const uint32_t *src;
-    if (FMT == 1)
-        src = sP + (2 * part + (pc & 1)) * C::PL_WORDS + pr * (PP / 2) + (pc >> 1);
-    else
-        src = sP + part * C::PL_WORDS + pr * PP + pc;
     constexpr int ROW_WORDS = PP * C::EB / 4;
     unsigned char *row = sAF + tc::kmajor_offset(m, 0, C::KFWD, C::EB) + part * C::NCH * 128;
+    if (FMT == 1) {
+        const uint32_t *src = sP + part * C::PL_WORDS + pr * ROW_WORDS + (pc >> 1);
+        const uint32_t sh = (uint32_t)(pc & 1) * 16u;
 #pragma unroll
-    for (int a = 0; a < KS; ++a)
-#pragma unroll
-        for (int h = 0; h < C::RCH; ++h) {
-            const uint32_t *w = src + a * ROW_WORDS + h * 4;
-            *reinterpret_cast<uint4 *>(row + (a * C::RCH + h) * 128) = make_uint4(w[0], w[1], w[2], w[3]);
+        for (int a = 0; a < KS; ++a) {
+            const uint32_t *w = src + a * ROW_WORDS;  // words pc/2 .. pc/2 + 4: inside the 40-element row
+            const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3], w4 = w[4];
+            *reinterpret_cast<uint4 *>(row + a * 128) =
+                make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh), __funnelshift_r(w2, w3, sh),
+                           __funnelshift_r(w3, w4, sh));
         }
+        *reinterpret_cast<uint4 *>(row + (C::NCH - 1) * 128) = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+        const uint32_t *src = sP + part * C::PL_WORDS + pr * ROW_WORDS + pc;
+#pragma unroll
+        for (int a = 0; a < KS; ++a)
+#pragma unroll
+            for (int h = 0; h < C::RCH; ++h) {
+                const uint32_t *w = src + a * ROW_WORDS + h * 4;
+                *reinterpret_cast<uint4 *>(row + (a * C::RCH + h) * 128) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+    }
 }
 
 // MODEL 0: Eq. variant, iterate u.  MODEL 1: the combined model (Eq. newmodel)
 // in w = log u: the prox is prox_w, the planes hold u = e^w, and the
 // gradient is e^w (.) K^T r.
 template <int MODE, int FMT, int MODEL>
-__global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KParams p) {
+__global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 1) tc_tile_kernel(const KParams p) {
     using C = Cfg<FMT>;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sAF = smem + C::OFF_AF;
@@ -206,12 +221,6 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
                 const float th = __ldg(p.theta + tid);
                 sTh[tid] = th;
                 sTh[NF + tid] = 2.0f * th;
-            }
-            // BF16: the last K chunk of each pass (window row 7) is zero in A
-            if (FMT == 1 && tid < 2 * 128) {
-                const int mm = tid & 127, pt = tid >> 7;
-                *reinterpret_cast<uint4 *>(sAF + tc::kmajor_offset(mm, 0, C::KFWD, C::EB) +
-                                           (pt * C::NCH + C::NCH - 1) * 128) = make_uint4(0u, 0u, 0u, 0u);
             }
             // the padding columns of the planes (read with weight 0) hold zeros
             for (int j = tid; j < C::NPL * R6Y; j += NT) {
@@ -301,14 +310,10 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
                         const __nv_bfloat16 hb = __float2bfloat16_rn(uv);
                         const __nv_bfloat16 lb = __float2bfloat16_rn(uv - __bfloat162float(hb));
                         __nv_bfloat16 *ph = reinterpret_cast<__nv_bfloat16 *>(sP);
-                        __nv_bfloat16 *pl = reinterpret_cast<__nv_bfloat16 *>(sP + 2 * C::PL_WORDS);
+                        __nv_bfloat16 *pl = reinterpret_cast<__nv_bfloat16 *>(sP + C::PL_WORDS);
                         const int e = ry * PP + rx;
                         ph[e] = hb;
                         pl[e] = lb;
-                        if (rx > 0) {  // shifted copies: element rx - 1 holds column rx
-                            ph[2 * C::PL_WORDS + e - 1] = hb;
-                            pl[2 * C::PL_WORDS + e - 1] = lb;
-                        }
                     } else {
                         const float hv = tc::round_tf32(uv);
                         const int e = ry * PP + rx;
@@ -394,13 +399,9 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
         };
 
         for (int blk = 0; blk < NBLK; ++blk) {
-            // (a) horizontal col2im of the previous block, overlapping MMA_fwd(blk)
-            if (blk > 0) {
-                if (!tc::mbar_wait(&bar_a, phase_a)) tc_ok = false;
-                phase_a ^= 1u;
-                tc::fence_after_sync();
-                epi2(blk - 1);
-            }
+            // (a) horizontal col2im of the previous block (its MMA_adj completed
+            // before the im2col of this block), overlapping MMA_fwd(blk)
+            if (blk > 0) epi2(blk - 1);
             // (b) epilogue 1 of this block: rho' -> R (hi | lo), energy terms
             if (!tc::mbar_wait(&bar_f, phase_f)) tc_ok = false;
             phase_f ^= 1u;
@@ -464,8 +465,12 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
             // vertical col2im of the rows whose sources block blk - 1 completed
             // (the ring slots it reads are rewritten only after the next barrier)
             if (blk > 0 && tid < 128) emit(4 * (blk - 1) - 6 + (tid >> 5));
-            // (c) im2col of the next block, overlapping MMA_adj(blk)
+            // (c) im2col of the next block into the operand buffer, once
+            // MMA_adj(blk) has read R from it
             if (blk + 1 < NBLK) {
+                if (!tc::mbar_wait(&bar_a, phase_a)) tc_ok = false;
+                phase_a ^= 1u;
+                tc::fence_after_sync();
                 im2col<FMT>(sP, sAF, blk + 1, m, part);
                 tc::fence_proxy_async();
                 tc::fence_before_sync();
@@ -539,19 +544,20 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 2 : 1) tc_tile_kernel(const KPa
 
 template <int FMT, int MODEL>
 cudaError_t prepare_fmt() {
-    cudaError_t e = cudaSuccess;
+    // the dynamic shared memory of the form, and the largest shared-memory
+    // carveout (BF16 runs three CTAs per SM)
     const int b = (int)Cfg<FMT>::BYTES;
-    if ((e = cudaFuncSetAttribute(tc_tile_kernel<MODE_TRIAL, FMT, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  b)))
-        return e;
-    if ((e = cudaFuncSetAttribute(tc_tile_kernel<MODE_INIT, FMT, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  b)))
-        return e;
-    if ((e = cudaFuncSetAttribute(tc_tile_kernel<MODE_GRAD_EXT, FMT, MODEL>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, b)))
-        return e;
-    return cudaFuncSetAttribute(tc_tile_kernel<MODE_ENERGY_EXT, FMT, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                b);
+    const void *fns[4] = {reinterpret_cast<const void *>(&tc_tile_kernel<MODE_TRIAL, FMT, MODEL>),
+                          reinterpret_cast<const void *>(&tc_tile_kernel<MODE_INIT, FMT, MODEL>),
+                          reinterpret_cast<const void *>(&tc_tile_kernel<MODE_GRAD_EXT, FMT, MODEL>),
+                          reinterpret_cast<const void *>(&tc_tile_kernel<MODE_ENERGY_EXT, FMT, MODEL>)};
+    for (const void *fn : fns) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <int FMT, int MODEL>
