@@ -32,7 +32,8 @@
 // GEMM blocks of 4 rows x 32 columns (M = 128); tile + 6 = 38 x 70 for u^{n+1}.
 // 256 threads: the two warpgroups split the epilogues by TMEM column; one
 // thread issues the MMAs.  BF16 fits three CTAs per SM (72 KB of shared memory,
-// 80 registers per thread), TF32 one (118 KB).
+// 80 registers per thread), TF32 two (111 KB: the gradient rows of the
+// vertical fold only, 128 registers).
 //
 // Waits on the MMA completion barriers are bounded; on a time-out the kernel
 // records tc_error, poisons its partial sums (the image stops with a
@@ -63,6 +64,14 @@ constexpr int NTAP = 64;                     // N of the adjoint GEMM (49 taps +
 constexpr int KADJ = 2 * NF;                 // r hi | r lo
 constexpr int HRING = 10;                    // rows of the horizontal-sum ring (the 10 a vertical gather reads)
 constexpr int TMEM_COLS = 128;               // D_fwd at column 0, D_adj at column 64
+constexpr int NFOLD = 12;                    // gradient rows kept for the vertical fold
+
+// Slot of image row y among the rows the vertical fold needs (the 3 rows at
+// each image border and their 3 mirror rows outside it), -1 for other rows
+// (H >= 8 keeps the two ranges apart).
+__device__ __forceinline__ int fold_slot(int y, int H) {
+    return (y >= -3 && y < 3) ? y + 3 : ((y >= H - 3 && y < H + 3) ? y - H + 9 : -1);
+}
 static_assert(R3X == 32, "one warp per halo row");
 static_assert(R3Y % 4 == 0, "GEMM blocks of 4 rows");
 
@@ -91,8 +100,14 @@ struct Cfg {
     static constexpr size_t OFF_BA = OFF_BF + BF_BYTES;
     static constexpr size_t OFF_U = OFF_BA + BA_BYTES;       // NPL planes of u^{n+1}
     static constexpr size_t OFF_H = OFF_U + (size_t)NPL * PL_WORDS * 4;
+    // gradient rows: BF16 keeps every row of the region (three CTAs per SM
+    // fit either way; the final pass then folds and writes with all warps),
+    // TF32 only the rows of the vertical fold (image rows -3..2, H-3..H+2),
+    // writing the others as they are formed, so that two CTAs fit per SM
+    static constexpr bool FULL_G = FMT == 1;
+    static constexpr int GROWS = FULL_G ? R3Y : NFOLD;
     static constexpr size_t OFF_G = OFF_H + (size_t)HRING * 7 * 32 * 4;
-    static constexpr size_t OFF_TH = OFF_G + (size_t)R3Y * R3X * 4;
+    static constexpr size_t OFF_TH = OFF_G + (size_t)GROWS * R3X * 4;
     static constexpr size_t OFF_RED = OFF_TH + (size_t)2 * NF * 4;
     static constexpr size_t BYTES = OFF_RED + (size_t)(NT / 32) * NRED * 8;
     static_assert(OFF_H % 16 == 0 && OFF_BF % 128 == 0 && OFF_BA % 128 == 0 && OFF_U % 128 == 0,
@@ -101,7 +116,8 @@ struct Cfg {
     static_assert(BF_BYTES % 16 == 0 && BA_BYTES % 16 == 0, "vector copies");
 };
 static_assert(3 * (Cfg<1>::BYTES + 1024) <= 228 * 1024, "BF16: three CTAs per SM");
-static_assert(Cfg<2>::BYTES <= 227 * 1024, "TF32: one CTA per SM");
+static_assert(Cfg<2>::GROWS == NFOLD, "TF32: compact fold rows");
+static_assert(2 * (Cfg<2>::BYTES + 1024) <= 228 * 1024, "TF32: two CTAs per SM");
 
 constexpr float LN2 = 0.69314718055994530942f;
 
@@ -179,7 +195,7 @@ __device__ __forceinline__ void im2col(const uint32_t *__restrict__ sP, unsigned
 // in w = log u: the prox is prox_w, the planes hold u = e^w, and the
 // gradient is e^w (.) K^T r.
 template <int MODE, int FMT, int MODEL>
-__global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 1) tc_tile_kernel(const KParams p) {
+__global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KParams p) {
     using C = Cfg<FMT>;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sAF = smem + C::OFF_AF;
@@ -188,7 +204,7 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 1) tc_tile_kernel(const KPa
     unsigned char *sBa = smem + C::OFF_BA;
     uint32_t *sP = reinterpret_cast<uint32_t *>(smem + C::OFF_U);  // u^{n+1} planes
     float *sH = reinterpret_cast<float *>(smem + C::OFF_H);
-    float *sG = reinterpret_cast<float *>(smem + C::OFF_G);
+    float *sG = reinterpret_cast<float *>(smem + C::OFF_G);  // GROWS rows of 32
     float *sTh = reinterpret_cast<float *>(smem + C::OFF_TH);  // theta_i, then 2 theta_i
     double *sRed = reinterpret_cast<double *>(smem + C::OFF_RED);
     __shared__ uint64_t bar_f, bar_a;
@@ -385,6 +401,11 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 1) tc_tile_kernel(const KPa
             }
         };
         // vertical col2im of the ext rows whose 7 source rows are complete
+        // (one warp per row, lane = column).  BF16: the row goes to sG.  TF32:
+        // a row that the vertical fold needs is kept in sG; any other owned
+        // pixel is written at once, after the horizontal fold: the frame
+        // value of its mirror column comes from that column's lane.
+        float *gout = MODE == MODE_GRAD_EXT ? p.g_ext : (MODE == MODE_INIT ? im.g[0] : im.g[gcur_out]);
         auto emit = [&](int ty) {
             if (ty < -3 || ty >= TY + 3) return;
             float g = 0.f;
@@ -395,7 +416,26 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 1) tc_tile_kernel(const KPa
                 if (srow >= 0 && srow < R3Y) g += sH[(s * KS + aa) * 32 + lane];
                 s = s + 1 == HRING ? 0 : s + 1;
             }
-            sG[(ty + 3) * 32 + lane] = g;
+            if constexpr (C::FULL_G) {
+                sG[(ty + 3) * 32 + lane] = g;
+                return;
+            }
+            const int y = y0 + ty, slot = fold_slot(y, H);  // uniform over the warp
+            if (slot >= 0) {
+                sG[slot * 32 + lane] = g;
+                return;
+            }
+            if (MODE == MODE_ENERGY_EXT) return;
+            const int x = x0 + lane - 3;
+            const int qx = x < 3 ? (-x - 1) - x0 + 3 : (x >= W - 3 ? (2 * W - 1 - x) - x0 + 3 : -1);
+            const float gm = __shfl_sync(0xffffffffu, g, qx & 31);
+            if (ty >= sy && ty < sy + oh && lane - 3 >= sx && lane - 3 < sx + ow) {
+                float gv = g;
+                if (qx >= 0) gv += gm;
+                // combined model: grad_w F = e^w (.) K^T r, e^w as the prologue formed it
+                if (MODEL == 1) gv *= expf(xg[(size_t)y * W + x]);
+                gout[(size_t)y * W + x] = gv;
+            }
         };
 
         for (int blk = 0; blk < NBLK; ++blk) {
@@ -502,14 +542,8 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 1) tc_tile_kernel(const KPa
         if (warp == 0) tc::tmem_dealloc(taddr, TMEM_COLS);
 
         // ---- fold the frame, write the owned gradient ------------------------
-        if (MODE != MODE_ENERGY_EXT) {
-            float *gout;
-            if (MODE == MODE_GRAD_EXT)
-                gout = p.g_ext;
-            else if (MODE == MODE_INIT)
-                gout = im.g[0];
-            else
-                gout = im.g[gcur_out];
+        // (frame columns first, then the frame row, then the corner)
+        if (MODE != MODE_ENERGY_EXT && C::FULL_G) {
             for (int idx = tid; idx < oh * ow; idx += NT) {
                 const int ty = sy + idx / ow, tx = sx + idx % ow;
                 const int y = y0 + ty, x = x0 + tx;
@@ -528,6 +562,28 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 1) tc_tile_kernel(const KPa
                     }
                 }
                 // combined model: grad_w F = e^w (.) K^T r, e^w as the prologue formed it
+                if (MODEL == 1) gv *= expf(xg[(size_t)y * W + x]);
+                gout[(size_t)y * W + x] = gv;
+            }
+        }
+        // TF32: the rows kept for the vertical fold (the others were written
+        // by the vertical col2im)
+        if (MODE != MODE_ENERGY_EXT && !C::FULL_G) {
+            for (int idx = tid; idx < NFOLD * 32; idx += NT) {
+                const int sl = idx >> 5, ln = idx & 31;
+                const int y = sl < 6 ? sl - 3 : H - 9 + sl;  // inverse of fold_slot
+                const int ty = y - y0, tx = ln - 3, x = x0 + tx;
+                if (ty < sy || ty >= sy + oh || tx < sx || tx >= sx + ow) continue;  // owned pixels only
+                float gv = sG[sl * 32 + ln];
+                // ext positions the symmetric extension maps onto (y, x): at
+                // most one per axis (H, W >= 8)
+                const int qx = x < 3 ? (-x - 1) - x0 + 3 : (x >= W - 3 ? (2 * W - 1 - x) - x0 + 3 : -1);
+                const int qs = y < 3 ? fold_slot(-y - 1, H) : (y >= H - 3 ? fold_slot(2 * H - 1 - y, H) : -1);
+                if (qx >= 0) gv += sG[sl * 32 + qx];
+                if (qs >= 0) {
+                    gv += sG[qs * 32 + ln];
+                    if (qx >= 0) gv += sG[qs * 32 + qx];
+                }
                 if (MODEL == 1) gv *= expf(xg[(size_t)y * W + x]);
                 gout[(size_t)y * W + x] = gv;
             }
