@@ -503,8 +503,10 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
                 tc::mma_commit(&bar_a);
             }
             // vertical col2im of the rows whose sources block blk - 1 completed
-            // (the ring slots it reads are rewritten only after the next barrier)
-            if (blk > 0 && tid < 128) emit(4 * (blk - 1) - 6 + (tid >> 5));
+            // (the ring slots it reads are rewritten only after the next
+            // barrier); one row per warp: warps 0, 5, 2, 7, i.e. one per SM
+            // sub-partition and two per warpgroup
+            if (blk > 0 && (warp & 1) == (warp >> 2)) emit(4 * (blk - 1) - 6 + (warp & 3));
             // (c) im2col of the next block into the operand buffer, once
             // MMA_adj(blk) has read R from it
             if (blk + 1 < NBLK) {
