@@ -89,3 +89,33 @@ def test_reference_arm_json_contract():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+@pytest.mark.gpu
+def test_bench_json_contract_gpu():
+    """A short run of the GPU arm prints one JSON line with the contract's
+    keys: roofline of the trial kernel, e2e through the C ABI with host
+    buffers, the clock record of the timed region, launch count."""
+    import json
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--steps", "1", "--warmup", "3",
+                        "--n512", "1", "--n256", "1", "--iters", "5", "--no-cpu-baseline"],
+                       capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr
+    lines = [x for x in r.stdout.strip().splitlines() if x.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "gpu_launches", "clocks"):
+        assert key in d, key
+    assert d["value"] > 0 and d["n_gpus"] == 1 and d["dtype"] == "f32" and d["gpu_launches"] > 0
+    rf = d["roofline"]
+    assert rf["bound"] == "alu" and rf["unit"] == "TFLOP/s" and 0 < rf["frac"] < 1.5
+    assert abs(rf["frac"] - rf["achieved"] / rf["peak"]) < 1e-3
+    e = d["e2e"]
+    assert e["value"] > 0 and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
+    # a timed region this short may end before the 200 ms clock sampler sees
+    # the GPU under load: null, else the median clock and the throttle reasons
+    assert d["clocks"] is None or ("sm_mhz" in d["clocks"] and "reasons" in d["clocks"])
