@@ -111,6 +111,8 @@ def lib():
             L.orc_Gc.argtypes = [_D, _D, C.c_long, C.c_double, C.c_double]
             L.orc_proxc.restype = C.c_double
             L.orc_proxc.argtypes = [C.c_double] * 5
+            L.orc_proxc_iters.restype = C.c_double
+            L.orc_proxc_iters.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_int)]
             L.orc_ipiano.restype = C.c_int
             L.orc_ipiano.argtypes = [_D, C.c_int, C.c_int, _D, _D, C.c_int, C.c_int,
                                      C.POINTER(OrcParams), _D, _D, _D,
@@ -281,6 +283,13 @@ def Gc(w, f, lam1: float, lam2: float):
 def proxc(what, f, tau, lam1, lam2):
     """Prox of tau*G of the combined model at one pixel (Newton's method)."""
     return lib().orc_proxc(float(what), float(f), float(tau), float(lam1), float(lam2))
+
+
+def proxc_iters(what, f, tau, lam1, lam2):
+    """proxc and the number of Newton (or bisection) steps it took."""
+    n = C.c_int(0)
+    w = lib().orc_proxc_iters(float(what), float(f), float(tau), float(lam1), float(lam2), C.byref(n))
+    return w, n.value
 
 
 def params(lam=5.0, beta=0.8, L0=1.0, eta=2.0, c2=1e-6, max_backtrack=30,

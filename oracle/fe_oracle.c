@@ -378,15 +378,19 @@ ORC_API double orc_Gc(const double *w, const double *f, long N, double lambda1, 
 /* Proximal map of tau*G for the combined model, one pixel: the root of
  * phi(w) = w - what + tau g'(w) by Newton's method (Sec. III-A: the prox is
  * solved with Newton's method).  phi is strictly increasing (phi' = 1 +
- * tau g'' > 0) and g'(log f) = 0, so the root lies between what and log f;
- * a Newton step that leaves that bracket is replaced by bisection.
- * Iterates until the step is below 1e-15 (1 + |w|) or 200 iterations. */
-ORC_API double orc_proxc(double what, double f, double tau, double lambda1, double lambda2)
+ * tau g'' > 0) and g'(log f) = 0, so the root lies in the closed interval
+ * between what and log f; a Newton step that leaves that interval is
+ * replaced by bisection (a step onto its end stays a Newton step).
+ * Iterates until the step is below 1e-15 (1 + |w|) or 200 iterations;
+ * *iters (may be NULL) receives the number of steps taken. */
+ORC_API double orc_proxc_iters(double what, double f, double tau, double lambda1, double lambda2, int *iters)
 {
     const double lf = log(f);
     double lo = what < lf ? what : lf, hi = what < lf ? lf : what;
     double w = what;
-    for (int it = 0; it < 200; ++it) {
+    int it = 0;
+    while (it < 200) {
+        ++it;
         const double ph = w - what + tau * gc_d1(w, f, lambda1, lambda2);
         if (ph == 0.0)
             break;
@@ -395,14 +399,21 @@ ORC_API double orc_proxc(double what, double f, double tau, double lambda1, doub
         else
             lo = w;
         double wn = w - ph / (1.0 + tau * gc_d2(w, f, lambda1, lambda2));
-        if (!(wn > lo && wn < hi))
+        if (!(wn >= lo && wn <= hi))
             wn = 0.5 * (lo + hi);
         const double step = fabs(wn - w);
         w = wn;
         if (step <= 1e-15 * (1.0 + fabs(w)))
             break;
     }
+    if (iters)
+        *iters = it;
     return w;
+}
+
+ORC_API double orc_proxc(double what, double f, double tau, double lambda1, double lambda2)
+{
+    return orc_proxc_iters(what, f, tau, lambda1, lambda2, NULL);
 }
 
 /* ----------------------------------------------------------------------- */
