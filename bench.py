@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -84,6 +85,9 @@ def parse():
     ap.add_argument("--lam", type=float, default=0.02,
                     help="data weight of the batch64 workload (at lambda = 5 the tolerance is met in 1-2 steps)")
     ap.add_argument("--max-iter", type=int, default=3000)
+    ap.add_argument("--clocks-csv", default=None,
+                    help="where the nvidia-smi clock samples of the timed region are written "
+                         "(default: a file in the system's temporary directory)")
     return ap.parse_args()
 
 
@@ -637,8 +641,8 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
 
-    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % rank)) \
-        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ClockSampler(local, "/tmp/fe_clocks.csv")
+    clocks = ClockSampler(local, args.clocks_csv or os.path.join(
+        tempfile.gettempdir(), "fe_clocks_%d_rank%d.csv" % (os.getpid(), rank)))
     total_ms, loop_ms = 0.0, 0.0
     lc0 = solver.launch_count()
     pix_iters_done, trials, pix_trials = 0, 0, 0

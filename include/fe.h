@@ -158,7 +158,12 @@ typedef struct {
 typedef struct fe_ctx fe_ctx;
 
 /* Default parameters: nf = 0 and filters = NULL (caller sets them),
- * lambda 5, beta 0.8, L0 1, eta 2, c2 1e-6, max_backtrack 30, FP32. */
+ * lambda 5, beta 0.8, L0 1, eta 2, c2 1e-6, max_backtrack 30, FP32.
+ * Defines: the parameters of the problem of Eq. variant (Sec. II-B: filters
+ * k_i, weights theta_i, lambda) and of iPiano's update rule (Sec. II-C: alpha
+ * from L_n, beta).  The paper gives no values for beta, L0, eta, c2 or the
+ * backtracking cap; these defaults are the readings stated above.
+ * p: host pointer, overwritten in full.  No error: a NULL p is ignored. */
 FE_API void fe_default_params(fe_params *p);
 
 /* Create a context for nimg images of sizes H[j] x W[j] (each >= 8) with
@@ -166,61 +171,100 @@ FE_API void fe_default_params(fe_params *p);
  * optional starting points u0[j] (any pointer, > 0; u0 == NULL or u0[j] ==
  * NULL means u^0 = f).  Allocates the device state, computes grad F(u^0),
  * F(u^0), G(u^0).  stream is a cudaStream_t (NULL = legacy default stream).
+ * Defines: the problem argmin_{u>0} F(u) + G(u) of Eq. variant (Sec. II-B,
+ * with the FoE prior of Eq. FOEmodel and the data term of Eq. dataterm2), or
+ * of Eq. newmodel in w = log u (Sec. III-A), cast as Eq. fplusg (Sec. II-C);
+ * the start u^{-1} = u^0 = f is a reading (the paper states no start).
+ * Ownership: f, u0 and p are read during the call only; the context owns its
+ * device state until fe_destroy.  *out receives the context (NULL on error).
  * Errors: FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_EUNSUPPORTED (*out is NULL). */
 FE_API fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg,
                         const int *H, const int *W,
                         const float *const *f, const float *const *u0, void *stream);
 
-/* Single-image form of fe_init_batch. */
+/* Single-image form of fe_init_batch (same definition, arguments and
+ * errors with nimg = 1). */
 FE_API fe_status fe_init(fe_ctx **out, const fe_params *p, int H, int W,
                   const float *f, const float *u0, void *stream);
 
 /* Restart every image from new observations (and optional starts) of the
- * same sizes, without reallocating.  Same argument rules as fe_init_batch. */
+ * same sizes, without reallocating.  Same argument rules as fe_init_batch.
+ * Defines: the initialisation step of iPiano (Sec. II-C: u^{-1} = u^0, g^0 =
+ * grad F(u^0)) on new data f; the counters n, trials, backtracks restart at 0
+ * and L at fe_params.L0.  Errors: FE_EINVAL, FE_ECUDA. */
 FE_API fe_status fe_reset(fe_ctx *ctx, const float *const *f, const float *const *u0);
 
+/* Free the context and every device buffer it allocated (stream-ordered,
+ * then synchronised).  Resource management: no counterpart in the paper.
+ * ctx == NULL is a no-op.  The context must not be used afterwards. */
 FE_API void fe_destroy(fe_ctx *ctx);
 
-/* Run n accepted iPiano iterations on every image that has no error
- * (Sec. II-C update rule with the backtracking rule above).  The whole loop
+/* Run n accepted iPiano iterations on every image that has no error.
+ * Defines: the basic update rule of iPiano, Sec. II-C,
+ *   u^{n+1} = (I + alpha dG)^{-1}(u^n - alpha grad F(u^n) + beta (u^n - u^{n-1})),
+ * with grad F and the closed-form prox of Eq. variant given there (or the
+ * Newton prox of Eq. newmodel, Sec. III-A), and alpha_n from the backtracking
+ * rule above (a reading: the paper names alpha and beta only).  The whole loop
  * runs on the device: one fused trial kernel per trial, accept/reject decided
- * on the device.  Asynchronous unless worst != NULL, in which case it
- * synchronises and stores the first non-OK per-image status (or FE_OK). */
+ * on the device.  n >= 0 (0 is a no-op).  Asynchronous unless worst != NULL,
+ * in which case it synchronises and stores the first non-OK per-image status
+ * (or FE_OK) in *worst (host pointer).  Errors: FE_EINVAL, FE_ECUDA. */
 FE_API fe_status fe_step(fe_ctx *ctx, int n, fe_status *worst);
 
 /* Iterate until |H^{n+1}-H^n|/|H^{n+1}-G(f)| < rel_tol or max_iter accepted
  * iterations (counted from this call) on every image.  Synchronises.
+ * Defines: the iPiano update rule of Sec. II-C (as fe_step) run to the
+ * stopping rule above, which is a reading (the paper states none): the
+ * relative change of H = F + G of Eq. fplusg, measured above the data-term
+ * floor G(f).  rel_tol >= 0, max_iter >= 0.
  * Returns FE_OK if all images converged, FE_ENOTCONVERGED if some hit
- * max_iter, else the first error status. */
+ * max_iter, else the first error status (FE_EINVAL, FE_ECUDA, or a per-image
+ * FE_ENONFINITE / FE_EBACKTRACK / FE_ETIMEOUT). */
 FE_API fe_status fe_solve(fe_ctx *ctx, int max_iter, double rel_tol);
 
-/* Summary of image img (synchronises). */
+/* Summary of image img (synchronises): n, L_n, alpha_n of the update rule
+ * (Sec. II-C) and F, G, H = F + G of Eq. fplusg at u^n.  out: host pointer.
+ * Errors: FE_EINVAL (NULL, img out of range), FE_ECUDA. */
 FE_API fe_status fe_get_info(fe_ctx *ctx, int img, fe_info *out);
 
-/* Copy u^n of image img to out (any pointer, H*W floats); FE_MODEL_COMBINED:
- * u^n = e^{w^n}. */
+/* Copy u^n of image img to out (any pointer, H*W floats, caller-owned);
+ * FE_MODEL_COMBINED: u^n = e^{w^n}, the change of variables u = e^w of
+ * Eq. original (Sec. II-C).  Synchronises.  Errors: FE_EINVAL, FE_ECUDA. */
 FE_API fe_status fe_get_u(fe_ctx *ctx, int img, float *out);
 
 /* Energies of an arbitrary iterate u (any pointer, H*W floats of image img's
  * size; u > 0 for FE_MODEL_VARIANT, w = log u for FE_MODEL_COMBINED) against
- * image img's f: E = F + G.  Any output pointer may be NULL.  Synchronises. */
+ * image img's f: E = F + G.  Any output pointer may be NULL (host pointers).
+ * Defines: F = E_FoE of Eq. FOEmodel (Sec. II-A, rho(x) = log(1 + x^2)) and G =
+ * the data term of Eq. dataterm2 (Sec. II-B), i.e. the objective of
+ * Eq. variant; FE_MODEL_COMBINED: the objective of Eq. newmodel (Sec. III-A).
+ * Sums in FP64.  Synchronises.  Errors: FE_EINVAL, FE_ECUDA. */
 FE_API fe_status fe_energy(fe_ctx *ctx, int img, const float *u, double *E, double *F, double *G);
 
-/* grad F (Sec. II-C) at an arbitrary iterate (u, or w for FE_MODEL_COMBINED;
- * any pointer) into g (any pointer), both H*W floats of image img's size;
- * F into *F if F != NULL.  Synchronises. */
+/* grad F at an arbitrary iterate (u, or w for FE_MODEL_COMBINED; any
+ * pointer) into g (any pointer, caller-owned), both H*W floats of image img's
+ * size; F into *F (host) if F != NULL.
+ * Defines: grad_u F = sum_i theta_i K_i^T rho'(K_i u) (Sec. II-C, model
+ * Eq. variant); grad_w F = sum_i theta_i W K_i^T rho'(K_i e^w), W = diag(e^w)
+ * (Sec. II-C, models in w).  Synchronises.  Errors: FE_EINVAL, FE_ECUDA. */
 FE_API fe_status fe_gradient(fe_ctx *ctx, int img, const float *u, float *g, double *F);
 
 /* Checkpoint: copy u^n, u^{n-1}, grad F(u^n) (any pointers, H*W floats each;
- * any may be NULL) and the scalar state of image img. */
+ * any may be NULL) and the scalar state of image img.  These are the
+ * quantities the update rule of Sec. II-C reads; the checkpoint itself has no
+ * counterpart in the paper.  Synchronises.  Errors: FE_EINVAL, FE_ECUDA. */
 FE_API fe_status fe_get_state(fe_ctx *ctx, int img, float *u, float *u_prev, float *g, fe_info *info);
 
 /* Restore a checkpoint taken with fe_get_state (same sizes and params):
- * continuing from it reproduces the uninterrupted run bit for bit. */
+ * continuing from it reproduces the uninterrupted run bit for bit.  No
+ * counterpart in the paper (see fe_get_state).  u, u_prev, g: any pointers,
+ * none NULL; info: host pointer.  Errors: FE_EINVAL, FE_ECUDA. */
 FE_API fe_status fe_set_state(fe_ctx *ctx, int img, const float *u, const float *u_prev,
                        const float *g, const fe_info *info);
 
-/* Number of images / size of image img. */
+/* Number of images / size of image img (H, W: host pointers).  Bookkeeping,
+ * no counterpart in the paper.  fe_num_images(NULL) = 0; fe_image_size:
+ * FE_EINVAL on NULL or an index out of range. */
 FE_API int fe_num_images(const fe_ctx *ctx);
 FE_API fe_status fe_image_size(const fe_ctx *ctx, int img, int *H, int *W);
 
@@ -242,20 +286,25 @@ FE_API fe_status fe_ssim(const float *x, const float *y, int H, int W, double pe
 FE_API fe_status fe_psnr(const float *x, const float *y, long long n, double peak, double *out, void *stream);
 
 /* Output tile (rows x columns) of the context's trial kernel, as chosen by
- * the autotuner or given in fe_params.tile.  FE_EINVAL on NULL arguments. */
+ * the autotuner or given in fe_params.tile.  The paper has no counterpart
+ * (a launch parameter of this implementation).  FE_EINVAL on NULL arguments. */
 FE_API fe_status fe_tile_size(const fe_ctx *ctx, int *tile_y, int *tile_x);
 
 /* CTAs that work on one tile (1, or 4 for a thread-block cluster per tile);
- * 0 for a NULL context. */
+ * 0 for a NULL context.  No counterpart in the paper (launch parameter). */
 FE_API int fe_tile_cluster(const fe_ctx *ctx);
 
 /* Device kernel launches issued by this context since creation (trial,
- * gradient, energy and bookkeeping kernels), for launch accounting. */
+ * gradient, energy and bookkeeping kernels), for launch accounting.  No
+ * counterpart in the paper.  Synchronises the context's stream; 0 for NULL,
+ * -1 if reading the device counter failed. */
 FE_API long long fe_launch_count(const fe_ctx *ctx);
 
 /* Select how fe_step/fe_solve drive the device loop: 0 = host loop of
  * kernel launches in chunks, 1 = one CUDA graph with a device-side while
- * node (default when the driver supports it). */
+ * node (default when the driver supports it).  Both run the same iterations
+ * of Sec. II-C; the choice has no counterpart in the paper.  FE_EINVAL for
+ * other modes or a NULL context. */
 FE_API fe_status fe_set_loop_mode(fe_ctx *ctx, int mode);
 
 /* Allocation-free gradient of one image: grad F(u) into g and F(u) into *F,
@@ -279,7 +328,10 @@ FE_API fe_status fe_set_loop_mode(fe_ctx *ctx, int mode);
  * what it reads); calls whose kernels overlap on the GPU race on it and must
  * be serialised by the caller.  The first call on a device does a one-time
  * set-up with that device current (device address of the array, kernel
- * attribute) and should come before any stream capture.
+ * attribute) and should come before any stream capture.  That set-up belongs
+ * to the device's primary context: after cudaDeviceReset the next call must
+ * redo it, which happens by itself when a launch fails (the failed call
+ * returns FE_ECUDA and forgets the set-up), so the call after it succeeds.
  * Errors: FE_EINVAL (NULL pointer, nf outside 1..64, H or W < 8, too many
  * tiles), FE_ECUDA; the message is in fe_last_error(NULL). */
 FE_API fe_status fe_gradient_noalloc(const float *u, float *g, double *F, int H, int W,
@@ -320,7 +372,8 @@ FE_API fe_status fe_cnn_train_step(fe_cnn *net, const float *f, const float *u_t
                                    float lr, double *loss);
 
 /* Diagnostic of the tensor-core building block used by the FE_TF32 / FE_BF16
- * forms: D = A * B^T with A 128 x K, B N x K (row-major float, any pointers)
+ * forms (no counterpart in the paper: it tests the GEMM that the filter banks
+ * k_i * u and K_i^T r of Sec. II-C run on): D = A * B^T with A 128 x K, B N x K (row-major float, any pointers)
  * rounded to the form's operand type (BF16 round-to-nearest-even, TF32
  * round-to-nearest), accumulated in FP32 by tcgen05.mma in tensor memory,
  * D 128 x N row-major float (any pointer).  prec = FE_BF16 (K multiple of 16)
@@ -338,6 +391,12 @@ FE_API fe_status fe_tc_gemm_selftest(int prec, int N, int K, const float *A, con
  * trial kernels' MMA waits take the same bounded path. */
 FE_API fe_status fe_tc_wait_selftest(unsigned max_iter, int *timed_out);
 
+/* Error reporting and versioning (no counterpart in the paper).
+ * fe_last_error: message of the last failure on ctx, or of the last
+ * context-free call (ctx == NULL) on this host thread; the string is owned by
+ * the library and valid until the next call on the same context / thread.
+ * fe_status_string: static name of a status.  fe_abi_version: FE_ABI_VERSION
+ * of the built library. */
 FE_API const char *fe_last_error(const fe_ctx *ctx);
 FE_API const char *fe_status_string(fe_status s);
 FE_API int fe_abi_version(void);

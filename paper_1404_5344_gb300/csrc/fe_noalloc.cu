@@ -20,7 +20,9 @@
 // resolves the device address of the array with cudaGetSymbolAddress (in host
 // code the array's name is only a host-side stand-in, not a device address)
 // and raises the kernel's shared-memory limit.  That first call should come
-// before any stream capture.
+// before any stream capture.  Both belong to the device's primary context:
+// cudaDeviceReset makes them stale, so a call whose launch fails forgets the
+// device's set-up and the next call redoes it.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -121,6 +123,16 @@ fe_status na_device_base(unsigned char **out) {
     return FE_OK;
 }
 
+// After a failed launch (for example once cudaDeviceReset has torn down the
+// context the set-up was made in) the current device's set-up is dropped, so
+// that the next call resolves the array's address and the attribute again.
+void na_forget_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEV) return;
+    std::lock_guard<std::mutex> lock(na_mu);
+    na_base[dev] = nullptr;
+}
+
 }  // namespace
 }  // namespace fe
 
@@ -154,6 +166,7 @@ extern "C" fe_status fe_gradient_noalloc(const float *u, float *g, double *F, in
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     na_setup_kernel<<<16, 256, 0, s>>>(base, filters, theta, nf, H, W, (int)tiles_x, (int)ntiles, u);
     if (cudaGetLastError() != cudaSuccess) {
+        na_forget_device();
         set_global_error("fe_gradient_noalloc: set-up kernel launch failed");
         return FE_ECUDA;
     }
@@ -175,9 +188,12 @@ extern "C" fe_status fe_gradient_noalloc(const float *u, float *g, double *F, in
     kp.g_ext = g;
     kp.results = reinterpret_cast<double *>(base + NA_OFF_RES);
     if (fp32_launch(MODE_GRAD_EXT, kp, (int)ntiles, s) != cudaSuccess) {
+        na_forget_device();
         set_global_error("fe_gradient_noalloc: gradient kernel launch failed");
         return FE_ECUDA;
     }
+    // results[0] is F; results[1] (the data term) is computed from the
+    // stand-in f = u set up above, can be NaN for u <= 0, and is never returned
     if (F && cudaMemcpyAsync(F, base + NA_OFF_RES, sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
         set_global_error("fe_gradient_noalloc: copy of F failed");
         return FE_ECUDA;

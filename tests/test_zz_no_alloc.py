@@ -3,23 +3,48 @@
 Some callers may not allocate device memory where they evaluate the prior's
 gradient (a plugin held to a host framework's fixed memory pool, a real-time
 loop that forbids allocation calls).  This entry point takes only caller
-buffers and keeps its scratch in a static device array.  The test calls it
+buffers and keeps its scratch in a static device array.  The GPU test calls it
 through the C ABI twice in a row (different images and sizes, so the second
 call runs on the first call's leftover scratch) and compares each result with
-the context-based fe_gradient, within the gradient tolerance of the parity
-tests.  This file is named to be collected last.
+the context-based fe_gradient and with the FP64 oracle's grad F, within the
+gradient tolerance of the parity tests; a third call of the same size must
+leave the device's free memory and torch's allocation unchanged.  A CPU test
+checks that the entry point's translation unit names no allocating call.  This
+file is named to be collected last.
 """
 import ctypes as C
+import os
+import re
 
 import numpy as np
 import pytest
 
-pytestmark = pytest.mark.gpu
+GRAD_TOL = 1e-5  # same bound as the FP32 gradient parity tests (of max|g_ref|)
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                   "paper_1404_5344_gb300", "csrc", "fe_noalloc.cu")
 
-GRAD_TOL = 1e-5  # same bound as the FP32 gradient parity tests
+
+def test_noalloc_source_calls_no_allocator():
+    """The translation unit of the entry point calls no allocating routine
+    (comments aside): a later edit that adds one fails here on CPU."""
+    code = open(SRC).read()
+    code = re.sub(r"//[^\n]*", "", code)
+    code = re.sub(r"/\*.*?\*/", "", code, flags=re.S)
+    for name in ("cudaMalloc", "cudaMallocAsync", "cudaMallocManaged", "cudaMallocHost", "cudaFree",
+                 "cudaFreeAsync", "cudaHostAlloc", "cuMemAlloc", "cuMemCreate", "malloc(", "new "):
+        assert name not in code, name
+    assert "static __device__ __align__(256)" in code
 
 
-def test_noalloc_gradient_matches_context_gradient_twice():
+def _noalloc(fe, ud, gd, Fd, H, W, kd, thd, nf, stream):
+    return fe.lib.fe_gradient_noalloc(C.c_void_p(ud.data_ptr()), C.c_void_p(gd.data_ptr()),
+                                      C.c_void_p(Fd.data_ptr()), H, W,
+                                      C.c_void_p(kd.data_ptr()), C.c_void_p(thd.data_ptr()),
+                                      nf, C.c_void_p(stream.cuda_stream))
+
+
+@pytest.mark.gpu
+def test_noalloc_gradient_matches_context_gradient_and_oracle_twice(orc):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -37,24 +62,45 @@ def test_noalloc_gradient_matches_context_gradient_twice():
         gd = torch.full((H, W), float("nan"), device="cuda")
         Fd = torch.zeros(1, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
-        st = fe.lib.fe_gradient_noalloc(C.c_void_p(ud.data_ptr()), C.c_void_p(gd.data_ptr()),
-                                        C.c_void_p(Fd.data_ptr()), H, W,
-                                        C.c_void_p(kd.data_ptr()), C.c_void_p(thd.data_ptr()),
-                                        48, C.c_void_p(stream.cuda_stream))
+        st = _noalloc(fe, ud, gd, Fd, H, W, kd, thd, 48, stream)
         assert st == fe.FE_OK, fe.lib.fe_last_error(None)
         stream.synchronize()
-        g_na, F_na = gd.cpu().numpy(), float(Fd.item())
+        g_na, F_na = gd.cpu().numpy().astype(np.float64), float(Fd.item())
+        # against the context-based entry point
         with fe.Solver([u], k, th) as s:
-            g_ref, F_ref = s.gradient(0, u)
-        err = np.max(np.abs(g_na.astype(np.float64) - g_ref)) / np.max(np.abs(g_ref))
+            g_ctx, F_ctx = s.gradient(0, u)
+        err = np.max(np.abs(g_na - g_ctx)) / np.max(np.abs(g_ctx))
+        assert err <= GRAD_TOL, err
+        assert F_na == pytest.approx(F_ctx, rel=2e-6)
+        # against the FP64 oracle (Sec. II-C: grad F = sum_i theta_i K_i^T rho'(K_i u))
+        g_ref, F_ref = orc.gradF(u, k, th)
+        err = np.max(np.abs(g_na - g_ref)) / np.max(np.abs(g_ref))
         assert err <= GRAD_TOL, err
         assert F_na == pytest.approx(F_ref, rel=2e-6)
 
+    # a third call of the last size allocates nothing: torch's allocator does
+    # not move and the device's free memory does not shrink (it may grow if a
+    # memory pool released earlier frees meanwhile)
+    torch.cuda.synchronize()
+    alloc0 = torch.cuda.memory_allocated()
+    free0, _ = torch.cuda.mem_get_info()
+    st = _noalloc(fe, ud, gd, Fd, H, W, kd, thd, 48, stream)
+    assert st == fe.FE_OK, fe.lib.fe_last_error(None)
+    stream.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert free1 >= free0, (free0, free1)
+    err = np.max(np.abs(gd.cpu().numpy().astype(np.float64) - g_ref)) / np.max(np.abs(g_ref))
+    assert err <= GRAD_TOL, err
 
+
+@pytest.mark.gpu
 def test_noalloc_rejects_oversize_image():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
+    from paper_1404_5344_gb300 import build
+    build.build()
     from paper_1404_5344_gb300 import fe
     d = torch.zeros(16, device="cuda")
     p = C.c_void_p(d.data_ptr())
