@@ -13,9 +13,18 @@ value  : sum of pixels x accepted iterations / device time of the K steps
          (CUDA events on the solver's stream), inputs resident in HBM.
 e2e    : same metric through the C ABI with HOST (pinned) buffers: every
          step copies f in, solves, copies u out.
-roofline: the fused trial kernel is bound by FP32 FMA issue: peak =
-         152 SMs x 128 lanes x 2 flop x SM clock; algorithmic work is
-         2 x 48 x 49 MACs = 9408 flop per pixel per trial.
+roofline: the fused trial kernel is bound by FP32 FMA issue: peak = the
+         FP32 FMA rate measured by the library's own microbenchmark
+         (fe_peak), beside the rate derived from the device's SM count x 128
+         lanes x 2 flop x SM clock; algorithmic work is 2 x 48 x 49 MACs =
+         9408 flop per pixel per trial.  The tensor-core forms take the
+         measured dense BF16 peak (TF32: x 1.1 / 2.25), beside this library's
+         own tcgen05 stream rate.
+peaks  : measured rates of FP32 FMA (scalar and packed), FP64 FMA, the
+         special-function unit (rcp, lg2) and the tensor cores (BF16, TF32).
+forms  : the TF32 and BF16 forms and the combined model on the same
+         workload, and the batching form's time to tolerance (64 uneven
+         images, FP32 and BF16, against 64 sequential FP32 solves).
 
 ``--impl reference`` times the FP64 CPU oracle (the only reference that
 exists: the paper ships no code) on a bounded sample of the same workload.
@@ -45,7 +54,6 @@ TRAFFIC_PER_PIXEL = {("fp32", "variant"): 137.742848e6 / 6291456,
                      ("bf16", "variant"): 128.764928e6 / 6291456,
                      ("tf32", "variant"): 128.206592e6 / 6291456,
                      ("fp32", "combined"): 137.161984e6 / 6291456}
-SMS, FP32_LANES = 152, 128
 METRIC = "Mpixel*iter/s of fused iPiano step"
 
 
@@ -64,6 +72,9 @@ def parse():
                          "(lambda1 = 160, lambda2 = 0.004, FP32 form)")
     ap.add_argument("--loop-mode", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the other forms (TF32, BF16, combined model, batch of 64) in the default line")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the peak-rate microbenchmarks")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="paper",
                     choices=["paper", "batch64", "warmstart", "precision", "quality"],
@@ -273,6 +284,69 @@ def run_reference(args):
     return 0
 
 
+def batch64_inputs():
+    """The batching form's workload: 64 textured images, sides log-uniform in
+    [128, 1536] (seed 7), L alternating 1 / 4, the seeded bank."""
+    from paper_1404_5344_gb300 import synth
+    sizes = synth.uneven_sizes(64, 128, 1536, seed=7)
+    fs = []
+    for j, s in enumerate(sizes):
+        u = synth.textured_image(s, s, seed=2000 + j)
+        fs.append(synth.speckle(u, L=1.0 if j % 2 == 0 else 4.0, seed=6000 + j))
+    k, th = synth.filter_bank(48, 7, seed=0, theta=0.1)
+    return sizes, fs, k, th
+
+
+def _event_timer(torch, stream):
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), out
+    return timed
+
+
+def batch64_batched(fe, torch, f_dev, k, th, prec, kw, steps, warmup, tol, max_iter, stream):
+    """Time to tolerance of the whole batch in ONE context (one CUDA-graph
+    launch drives every image's device-side loop); includes the restart from
+    f, excludes context creation.  Returns (best ms, per-image infos, tile)."""
+    timed = _event_timer(torch, stream)
+    batch = fe.Solver(f_dev, k, th, prec=prec, stream=stream, **kw)
+    tile = batch.tile
+    for _ in range(max(1, warmup)):
+        batch.reset(f_dev)
+        batch.solve(max_iter, tol)
+    t = []
+    st = None
+    for _ in range(max(1, steps)):
+        batch.reset(f_dev)
+        ms, st = timed(lambda: batch.solve(max_iter, tol))
+        t.append(ms)
+    infos = [batch.info(i) for i in range(len(f_dev))]
+    batch.close()
+    return min(t), infos, tile, st
+
+
+def batch64_sequential(fe, torch, f_dev, k, th, kw, tol, max_iter, stream):
+    """64 sequential single-image FP32 solves at the same tolerance (each
+    context autotunes its own tile); the sum of their event times."""
+    timed = _event_timer(torch, stream)
+    singles = [fe.Solver([f], k, th, prec="fp32", stream=stream, **kw) for f in f_dev]
+    for j in range(min(4, len(singles))):
+        singles[j].reset([f_dev[j]])
+        singles[j].solve(max_iter, tol)
+    t_seq, its = 0.0, []
+    for j, s in enumerate(singles):
+        s.reset([f_dev[j]])
+        ms, _ = timed(lambda: s.solve(max_iter, tol))
+        t_seq += ms
+        its.append(s.info(0)["n"])
+        s.close()
+    return t_seq, its
+
+
 def run_batch64(args):
     """Batching form: 64 textured images, sides log-uniform in [128, 1536]
     (seeded), L alternating 1 / 4, solved to |H^{n+1} - H^n| / |H^{n+1} - G(f)| < tol
@@ -282,58 +356,21 @@ def run_batch64(args):
     include the restart from f (initial gradient) and exclude context
     creation; CUDA events on the solvers' stream."""
     import torch
-    from paper_1404_5344_gb300 import build, synth
+    from paper_1404_5344_gb300 import build
     build.build()
     from paper_1404_5344_gb300 import fe
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    sizes = synth.uneven_sizes(64, 128, 1536, seed=7)
-    fs = []
-    for j, s in enumerate(sizes):
-        u = synth.textured_image(s, s, seed=2000 + j)
-        fs.append(synth.speckle(u, L=1.0 if j % 2 == 0 else 4.0, seed=6000 + j))
-    k, th = synth.filter_bank(48, 7, seed=0, theta=0.1)
+    sizes, fs, k, th = batch64_inputs()
     npix = sum(s * s for s in sizes)
     stream = torch.cuda.Stream()
     f_dev = [torch.from_numpy(f).cuda() for f in fs]
     torch.cuda.synchronize()
-
-    def timed(fn):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        out = fn()
-        e1.record(stream)
-        e1.synchronize()
-        return e0.elapsed_time(e1), out
-
     kw = dict(SOLVER_KW, lam=args.lam)
-    batch = fe.Solver(f_dev, k, th, prec=args.prec, stream=stream, **kw)
-    tile = batch.tile
-    for _ in range(max(1, args.warmup)):
-        batch.reset(f_dev)
-        batch.solve(args.max_iter, args.tol)
-    t_batch = []
-    for _ in range(args.steps):
-        batch.reset(f_dev)
-        ms, st = timed(lambda: batch.solve(args.max_iter, args.tol))
-        t_batch.append(ms)
-    infos = [batch.info(i) for i in range(len(fs))]
+    tb, infos, tile, st = batch64_batched(fe, torch, f_dev, k, th, args.prec, kw, args.steps, args.warmup,
+                                          args.tol, args.max_iter, stream)
     its = [x["n"] for x in infos]
     trials = [x["trials"] for x in infos]
-    batch.close()
-
-    singles = [fe.Solver([f], k, th, prec="fp32", stream=stream, **kw) for f in f_dev]
-    for j in range(min(4, len(singles))):
-        singles[j].reset([f_dev[j]])
-        singles[j].solve(args.max_iter, args.tol)
-    t_seq = 0.0
-    its_seq = []
-    for j, s in enumerate(singles):
-        s.reset([f_dev[j]])
-        ms, _ = timed(lambda: s.solve(args.max_iter, args.tol))
-        t_seq += ms
-        its_seq.append(s.info(0)["n"])
-        s.close()
-    tb = min(t_batch)
+    t_seq, its_seq = batch64_sequential(fe, torch, f_dev, k, th, kw, args.tol, args.max_iter, stream)
     line = {"metric": "time to |dH|/|H - G(f)| < %g (s)" % args.tol, "value": round(tb / 1e3, 4), "unit": "s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[args.prec],
@@ -342,7 +379,7 @@ def run_batch64(args):
                                    "48x7x7 seeded bank, lambda=%g, tol=%g on |dH|/|H - G(f)|, max_iter=%d" % (
                                        args.lam, args.tol, args.max_iter),
                        "pixels": npix, "precision": args.prec, "loop": "one CUDA-graph launch per solve",
-                       "tile": "%dx%d (autotuned for the batch; each sequential solve autotunes its own)" % tile},
+                       "tile": "%s (autotuned for the batch; each sequential solve autotunes its own)" % (tile,)},
             "sequential_fp32_s": round(t_seq / 1e3, 4),
             "speedup_vs_sequential_fp32": round(t_seq / tb, 3),
             "iterations": {"batched_min": min(its), "batched_max": max(its), "batched_mean": round(sum(its) / len(its), 2),
@@ -588,6 +625,128 @@ def run_quality(args):
     return 0
 
 
+PEAK_KINDS = ("ffma", "ffma2", "dfma", "mufu_rcp", "mufu_lg2", "tc_bf16", "tc_tf32")
+
+
+def measure_peaks(fe, local):
+    """Measured rates of the units the kernels are bound by (fe_peak: CUDA
+    events, each kind timed in isolation, best of 5 launches of ~20 ms), with
+    the SM clocks sampled meanwhile.  FMA and tensor kinds in TFLOP/s, MUFU
+    kinds in Tinstr/s."""
+    clocks = ClockSampler(local, os.path.join(tempfile.gettempdir(), "fe_peak_clocks_%d.csv" % os.getpid()))
+    out = {}
+    try:
+        for kind in PEAK_KINDS:
+            r = fe.peak(kind, target_ms=20.0, reps=5)
+            out[kind] = round(r["rate"] / 1e12, 3)
+    finally:
+        clk = clocks.stop()
+    out["unit"] = "TFLOP/s (fma, tensor kinds); Tinstr/s (mufu kinds)"
+    out["sms"] = fe.device_sms()
+    out["clocks"] = clk
+    out["method"] = ("fe_peak: CUDA-core kinds on every SM at full occupancy, 8 independent chains per "
+                     "thread; tensor kinds one CTA per SM issuing M128xN256 tcgen05.mma (K 16 BF16, 8 TF32) "
+                     "into one TMEM accumulator; best of 5 launches of ~20 ms after a warm-up")
+    return out
+
+
+def measure_throughput(fe, torch, args, f_dev, k, th, shapes, prec, model, steps, warmup, stream, flush,
+                       clock_path=None, dist=None, local=0):
+    """One throughput measurement of the workload: `warmup` untimed steps,
+    then `steps` timed steps (each: restart every image from f + args.iters
+    iPiano iterations of the whole batch through the C ABI), a 256 MiB buffer
+    written before each step (L2 flush), CUDA events on the solver's stream."""
+    kw = COMBINED_KW if model == "combined" else SOLVER_KW
+    solver = fe.Solver(f_dev, k, th, prec=prec, stream=stream, loop_mode=args.loop_mode, **kw)
+    tile, cluster = solver.tile, solver.cluster
+
+    def one_step():
+        solver.reset(f_dev)
+        ev_l0 = torch.cuda.Event(enable_timing=True)
+        ev_l0.record(stream)
+        solver.step(args.iters, sync=False)
+        return ev_l0
+
+    for _ in range(warmup):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        one_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local, clock_path) if clock_path else None
+    total_ms, loop_ms = 0.0, 0.0
+    lc0 = solver.launch_count()
+    pix_iters, trials, pix_trials = 0, 0, 0
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        el = one_step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        loop_ms += el.elapsed_time(e1)
+        # fe_reset restarts the counters: n = accepted iterations of this step
+        infos = [solver.info(i) for i in range(len(f_dev))]
+        pix_iters += sum(x["n"] * h * w for x, (h, w) in zip(infos, shapes))
+        trials += sum(x["trials"] for x in infos)
+        pix_trials += sum(x["trials"] * h * w for x, (h, w) in zip(infos, shapes))
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    launches = solver.launch_count() - lc0
+    statuses = sorted({x["status"] for x in infos})
+    solver.close()
+    return {"total_ms": total_ms, "loop_ms": loop_ms, "pix_iters": pix_iters, "trials": trials,
+            "pix_trials": pix_trials, "launches": launches, "statuses": statuses, "tile": tile,
+            "cluster": cluster, "clocks": clk, "steps": steps}
+
+
+def roofline_of(prec, model, r, npix, peaks, sm_mhz_max):
+    """Roofline object of the trial kernel: algorithmic work (9408 flop per
+    pixel per trial, every image-trial that ran) over the device time of the
+    iteration loop, against the measured peak of the unit that bounds it."""
+    achieved = FLOP_PER_PIXEL_TRIAL * r["pix_trials"] / (r["loop_ms"] / 1e3) / 1e12
+    sms = peaks.get("sms") or 0
+    # time of one trial launch over the whole batch, from the work-weighted
+    # average: loop time / (pixel-trials / pixels); late launches of a step
+    # cover only the images still iterating, so a plain average per launch
+    # would not be a full-batch time
+    full_ms = r["loop_ms"] / (r["pix_trials"] / npix)
+    if prec == "fp32":
+        derived = sms * 128 * 2 * sm_mhz_max * 1e6 / 1e12
+        peak = peaks.get("ffma") or derived
+        rl = {"bound": "alu", "kernel": "fp32_tile_kernel<MODE_TRIAL>",
+              "peak_basis": ("measured FP32 FMA rate (fe_peak ffma, %d SMs at full occupancy)" % sms
+                             if peaks.get("ffma") else "FP32 FMA from unit counts"),
+              "peak_derived": round(derived, 3),
+              "peak_derived_basis": "%d SMs (from the device) x 128 FP32 lanes x 2 flop x %.0f MHz (max SM "
+                                    "clock)" % (sms, sm_mhz_max)}
+    else:
+        bf16_sust, src = measured_bf16_sustained()
+        ratio = 1.0 if prec == "bf16" else 1.1 / 2.25
+        peak = bf16_sust * ratio
+        rl = {"bound": "tensor", "kernel": "tc_tile_kernel<MODE_TRIAL, %s>" % prec.upper(),
+              "peak_basis": "dense %s tensor peak = %.1f TFLOP/s sustained BF16 (%s) x %.3f" % (
+                  prec.upper(), bf16_sust, src, ratio),
+              "peak_measured_tcgen05": peaks.get("tc_" + prec),
+              "peak_measured_tcgen05_basis": "fe_peak tc_%s: this library's own M128xN256 tcgen05.mma stream, "
+                                             "burst" % prec}
+    rl.update({"achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+               "frac": round(achieved / peak, 4),
+               "traffic": (round(TRAFFIC_PER_PIXEL[(prec, model)] * npix) if (prec, model) in TRAFFIC_PER_PIXEL
+                           else None),
+               "traffic_basis": "ncu DRAM bytes of one trial launch of 24x512^2 with all images active, scaled "
+                                "to this workload's full-batch launch by pixels",
+               "work": "9408 flop (2 x 48 x 49 MAC) per pixel per trial, every image-trial",
+               "ms_per_full_batch_trial": round(full_ms, 4)})
+    if prec == "fp32":
+        rl["frac_of_derived"] = round(achieved / rl["peak_derived"], 4)
+    return rl
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -620,80 +779,20 @@ def main():
     stream = torch.cuda.Stream()
     f_dev = [torch.from_numpy(f).cuda() for f in fs]
     torch.cuda.synchronize()
-    kw = model_kw(args)
-    solver = fe.Solver(f_dev, k, th, prec=args.prec, stream=stream, loop_mode=args.loop_mode, **kw)
-    tile, cluster = solver.tile, solver.cluster
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def one_step():
-        solver.reset(f_dev)
-        ev_l0 = torch.cuda.Event(enable_timing=True)
-        ev_l0.record(stream)
-        st = solver.step(args.iters, sync=False)
-        return st, ev_l0
-
-    for _ in range(args.warmup):
-        with torch.cuda.stream(stream):
-            flush.fill_(1.0)
-        one_step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-
-    clocks = ClockSampler(local, args.clocks_csv or os.path.join(
-        tempfile.gettempdir(), "fe_clocks_%d_rank%d.csv" % (os.getpid(), rank)))
-    total_ms, loop_ms = 0.0, 0.0
-    lc0 = solver.launch_count()
-    pix_iters_done, trials, pix_trials = 0, 0, 0
-    for _ in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        _, el = one_step()
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
-        loop_ms += el.elapsed_time(e1)
-        # fe_reset restarts the counters: n = accepted iterations of this step
-        infos = [solver.info(i) for i in range(len(fs))]
-        pix_iters_done += sum(x["n"] * h * w for x, (h, w) in zip(infos, shapes))
-        trials += sum(x["trials"] for x in infos)
-        pix_trials += sum(x["trials"] * h * w for x, (h, w) in zip(infos, shapes))
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    launches = solver.launch_count() - lc0
-    statuses = sorted({x["status"] for x in infos})
-
-    T_ms, units = combine_ranks(total_ms, pix_iters_done, dist, device="cuda")
+    r = measure_throughput(fe, torch, args, f_dev, k, th, shapes, args.prec, args.model, args.steps,
+                           args.warmup, stream, flush, clock_path=args.clocks_csv or os.path.join(
+                               tempfile.gettempdir(), "fe_clocks_%d_rank%d.csv" % (os.getpid(), rank)),
+                           dist=dist, local=local)
+    clk = r["clocks"]
+    T_ms, units = combine_ranks(r["total_ms"], r["pix_iters"], dist, device="cuda")
     value = units / (T_ms / 1e3) / 1e6
-
-    # Trial-kernel rate: algorithmic work of every image-trial that ran
-    # (9408 flop per pixel, accepted and rejected trials alike) over the
-    # device time of the iteration loop (trial launches + one loop-begin
-    # kernel per step; the per-step restart is outside this window).  A
-    # launch late in a step covers only the images still iterating, so work
-    # is counted per image-trial, not per launch.
+    launches = r["launches"]
     trial_launches = max(1, launches - args.steps * (len(fs) + 2))
-    per_launch_ms = loop_ms / trial_launches
-    achieved_tflops = FLOP_PER_PIXEL_TRIAL * pix_trials / (loop_ms / 1e3) / 1e12
-    sm_mhz_max = (clk or {}).get("sm_max_mhz") or 2070.0
-    if args.prec == "fp32":
-        bound, kernel = "alu", "fp32_tile_kernel<MODE_TRIAL>"
-        peak_tflops = SMS * FP32_LANES * 2 * sm_mhz_max * 1e6 / 1e12
-        basis = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" % sm_mhz_max
-    else:
-        # the trial kernel runs inside a seconds-long loop: sustained dense
-        # BF16 peak (measured); TF32 at the nominal TF32/BF16 ratio 1.1/2.25
-        bf16_sust, src = measured_bf16_sustained()
-        ratio = 1.0 if args.prec == "bf16" else 1.1 / 2.25
-        bound, kernel = "tensor", "tc_tile_kernel<MODE_TRIAL, %s>" % args.prec.upper()
-        peak_tflops = bf16_sust * ratio
-        basis = "dense %s tensor peak = %.1f TFLOP/s sustained BF16 (%s) x %.3f" % (
-            args.prec.upper(), bf16_sust, src, ratio)
 
     # e2e through the C ABI with host buffers
+    kw = model_kw(args)
     f_host = [torch.from_numpy(f).pin_memory() for f in fs]
     u_host = [torch.empty(f.shape, dtype=torch.float32).pin_memory() for f in fs]
     e2e_solver = fe.Solver([x.numpy() for x in f_host], k, th, prec=args.prec, stream=stream,
@@ -716,6 +815,18 @@ def main():
     e2e_value = e2e_units / (e2e_T / 1e3) / 1e6
     e2e_solver.close()
 
+    # measured peaks (outside the timed region) and the roofline against them
+    peaks = measure_peaks(fe, local) if not args.no_peaks else {"sms": fe.device_sms()}
+    sm_mhz_max = (clk or {}).get("sm_max_mhz") or 2070.0
+    rl = roofline_of(args.prec, args.model, r, npix, peaks, sm_mhz_max)
+
+    # the other forms on the same workload (and the batching form), so that
+    # one run carries every form's number under the same clock record
+    forms = None
+    if not args.no_forms and world == 1:
+        forms = measure_forms(fe, torch, args, f_dev, k, th, shapes, npix, stream, flush, peaks, sm_mhz_max,
+                              local)
+
     line = None
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 2), "unit": "Mpixel*iter/s",
@@ -725,37 +836,74 @@ def main():
                 "dtype": {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[args.prec], "data": "synthetic",
                 "config": dict(workload_config(args, npix, len(fs)), **{
                            "loop": "cuda-graph while node" if args.loop_mode == 1 else "host chunks",
-                           "tile": "%dx%d%s (%s)" % (tile + (" on a 4-CTA cluster" if cluster == 4 else "",
-                                                             "autotuned" if args.prec == "fp32" else "fixed")),
+                           "tile": "%dx%d%s (%s)" % (r["tile"] + (" on a 4-CTA cluster" if r["cluster"] == 4 else "",
+                                                                  "autotuned" if args.prec == "fp32" else "fixed")),
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "256 MiB buffer written between timed steps; state 6 planes x "
                                  "%.0f MB" % (npix * 4 / 1e6)}),
                 "e2e": {"value": round(e2e_value, 2), "unit": "Mpixel*iter/s",
                         "h2d_bytes_per_step": int(npix * 4), "d2h_bytes_per_step": int(npix * 4)},
                 "gpu_launches": int(launches), "trial_kernel_launches": int(trial_launches),
-                "trials": int(trials), "statuses": statuses,
-                "roofline": {"bound": bound, "achieved": round(achieved_tflops, 3),
-                             "peak": round(peak_tflops, 3), "unit": "TFLOP/s",
-                             "frac": round(achieved_tflops / peak_tflops, 4),
-                             "traffic": (round(TRAFFIC_PER_PIXEL[(args.prec, args.model)] * npix)
-                                         if (args.prec, args.model) in TRAFFIC_PER_PIXEL else None),
-                             "traffic_basis": "ncu DRAM bytes of one trial launch of 24x512^2 with all images "
-                                              "active, scaled to this workload's full-batch launch by pixels",
-                             "kernel": kernel, "peak_basis": basis,
-                             "work": "9408 flop (2 x 48 x 49 MAC) per pixel per trial, every image-trial",
-                             "per_launch_ms": round(per_launch_ms, 4)},
-                "clocks": clk}
-        if clk and clk.get("sm_mhz") and args.prec == "fp32":
-            line["roofline"]["frac_at_observed_clock"] = round(
-                achieved_tflops / (SMS * FP32_LANES * 2 * clk["sm_mhz"] * 1e6 / 1e12), 4)
+                "trials": int(r["trials"]), "statuses": r["statuses"],
+                "roofline": rl, "clocks": clk, "peaks": peaks}
+        if clk and clk.get("sm_mhz") and args.prec == "fp32" and peaks.get("sms"):
+            line["roofline"]["frac_of_derived_at_observed_clock"] = round(
+                rl["achieved"] / (peaks["sms"] * 128 * 2 * clk["sm_mhz"] * 1e6 / 1e12), 4)
+        if forms is not None:
+            line["forms"] = forms
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(fs, k, th, args.iters, args.cpu_seconds, kw)
         print(json.dumps(line), flush=True)
-    solver.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def measure_forms(fe, torch, args, f_dev, k, th, shapes, npix, stream, flush, peaks, sm_mhz_max, local):
+    """The precision forms (TF32, BF16) and the combined model on the same
+    throughput workload, and the batching form's time to tolerance (FP32 and
+    BF16 in one context against 64 sequential FP32 solves), each under its
+    own clock record.  Fewer steps than the headline: these are reported
+    beside it, not in its place."""
+    out = {}
+    steps, warmup = max(1, min(args.steps, 5)), max(3, min(args.warmup, 3))
+    for name, prec, model in (("bf16", "bf16", args.model), ("tf32", "tf32", args.model),
+                              ("combined_fp32", "fp32", "combined"), ("combined_bf16", "bf16", "combined")):
+        if prec == args.prec and model == args.model:
+            continue
+        r = measure_throughput(fe, torch, args, f_dev, k, th, shapes, prec, model, steps, warmup, stream, flush,
+                               clock_path=os.path.join(tempfile.gettempdir(), "fe_clocks_%d_%s.csv" % (
+                                   os.getpid(), name)), local=local)
+        out[name] = {"value": round(r["pix_iters"] / (r["total_ms"] / 1e3) / 1e6, 2), "unit": "Mpixel*iter/s",
+                     "precision": prec, "model": model, "steps": steps, "warmup": warmup,
+                     "ms_per_step": round(r["total_ms"] / steps, 3), "statuses": r["statuses"],
+                     "tile": "%dx%d" % r["tile"], "roofline": roofline_of(prec, model, r, npix, peaks, sm_mhz_max),
+                     "clocks": r["clocks"]}
+    # batching form: time to tolerance of 64 uneven images
+    sizes, bfs, bk, bth = batch64_inputs()
+    bf_dev = [torch.from_numpy(f).cuda() for f in bfs]
+    torch.cuda.synchronize()
+    kw = dict(SOLVER_KW, lam=args.lam)
+    clocks = ClockSampler(local, os.path.join(tempfile.gettempdir(), "fe_clocks_%d_batch64.csv" % os.getpid()))
+    res = {}
+    for prec in ("fp32", "bf16"):
+        tb, infos, tile, st = batch64_batched(fe, torch, bf_dev, bk, bth, prec, kw, 2, 1, args.tol, args.max_iter,
+                                              stream)
+        its = [x["n"] for x in infos]
+        res[prec] = {"s": round(tb / 1e3, 4), "status": st, "tile": str(tile), "iterations_max": max(its),
+                     "iterations_mean": round(sum(its) / len(its), 1)}
+    t_seq, its_seq = batch64_sequential(fe, torch, bf_dev, bk, bth, kw, args.tol, args.max_iter, stream)
+    clk = clocks.stop()
+    for prec in res:
+        res[prec]["speedup_vs_sequential_fp32"] = round(t_seq / 1e3 / res[prec]["s"], 3)
+    out["batch64"] = {"metric": "time to |dH|/|H - G(f)| < %g (s), lower is better" % args.tol,
+                      "workload": "64 textured images, sides log-uniform in [128, 1536] (seed 7, %d pixels), "
+                                  "L in {1, 4}, lambda=%g, max_iter=%d" % (sum(s * s for s in sizes), args.lam,
+                                                                           args.max_iter),
+                      "batched": res, "sequential_fp32_s": round(t_seq / 1e3, 4),
+                      "sequential_iterations_mean": round(sum(its_seq) / len(its_seq), 1), "clocks": clk}
+    return out
 
 
 if __name__ == "__main__":

@@ -391,6 +391,37 @@ FE_API fe_status fe_tc_gemm_selftest(int prec, int N, int K, const float *A, con
  * trial kernels' MMA waits take the same bounded path. */
 FE_API fe_status fe_tc_wait_selftest(unsigned max_iter, int *timed_out);
 
+/* ---- Peak-rate microbenchmarks ---------------------------------------------
+ * Measured roofline denominators (no counterpart in the paper): the rate of
+ * the units the solver's kernels are bound by, on the current device, each
+ * timed in isolation (one warm-up launch that scales the work to about
+ * target_ms, then the best of reps launches; CUDA events on a private stream,
+ * synchronised).  CUDA-core kinds run every SM at full occupancy with 8
+ * independent dependency chains per thread; tensor-core kinds run one CTA per
+ * SM issuing a stream of M 128 x N 256 MMAs into one tensor-memory
+ * accumulator (operands in shared memory).
+ * *rate: operations per second of the whole device - flop for the FMA and
+ * tensor kinds (2 per FMA, 4 per packed FMA, 2 M N K per MMA), instructions
+ * (per thread) for the MUFU kinds.  *best_ms (may be NULL): the best launch
+ * time; *sms (may be NULL): multiprocessors of the device.  Allocates no
+ * device memory.  Errors: FE_EINVAL (kind outside the enum, reps outside
+ * 1..100, target_ms outside (0, 2000], rate NULL), FE_ECUDA, FE_ETIMEOUT (a
+ * tensor-core completion wait gave up; bounded by about 4e9 SM clocks). */
+typedef enum {
+    FE_PEAK_FFMA = 0,       /* fma.rn.f32 */
+    FE_PEAK_FFMA2 = 1,      /* fma.rn.f32x2 (two FP32 FMAs per instruction) */
+    FE_PEAK_DFMA = 2,       /* fma.rn.f64 */
+    FE_PEAK_MUFU_RCP = 3,   /* rcp.approx.ftz.f32 */
+    FE_PEAK_MUFU_LG2 = 4,   /* lg2.approx.ftz.f32 */
+    FE_PEAK_TC_BF16 = 5,    /* tcgen05.mma kind::f16, BF16 operands, FP32 accumulation */
+    FE_PEAK_TC_TF32 = 6     /* tcgen05.mma kind::tf32 */
+} fe_peak_kind;
+FE_API fe_status fe_peak(int kind, double target_ms, int reps, double *rate, double *best_ms, int *sms);
+
+/* Multiprocessor count of the current device (cudaDevAttrMultiProcessorCount)
+ * into *sms.  Errors: FE_EINVAL (NULL), FE_ECUDA. */
+FE_API fe_status fe_device_sms(int *sms);
+
 /* Error reporting and versioning (no counterpart in the paper).
  * fe_last_error: message of the last failure on ctx, or of the last
  * context-free call (ctx == NULL) on this host thread; the string is owned by

@@ -34,7 +34,7 @@ EXPORTS = (
     "fe_last_error", "fe_status_string", "fe_abi_version", "fe_gradient_noalloc",
     "fe_tc_gemm_selftest", "fe_cnn_create", "fe_cnn_destroy", "fe_cnn_num_params",
     "fe_cnn_last_error", "fe_cnn_set_params", "fe_cnn_get_params", "fe_cnn_forward",
-    "fe_cnn_loss_grad", "fe_cnn_train_step",
+    "fe_cnn_loss_grad", "fe_cnn_train_step", "fe_peak", "fe_device_sms",
 )
 
 
@@ -108,13 +108,16 @@ def _load(path: str = LIB_PATH) -> C.CDLL:
     L.fe_cnn_forward.argtypes = [VP, VP, I, I, I, VP, VP]
     L.fe_cnn_loss_grad.argtypes = [VP, VP, VP, I, I, I, P(D), VP]
     L.fe_cnn_train_step.argtypes = [VP, VP, VP, I, I, I, C.c_float, P(D)]
+    L.fe_peak.argtypes = [I, D, I, P(D), P(D), P(I)]
+    L.fe_device_sms.argtypes = [P(I)]
     for name in ("fe_cnn_create", "fe_cnn_num_params", "fe_cnn_set_params", "fe_cnn_get_params",
                  "fe_cnn_forward", "fe_cnn_loss_grad", "fe_cnn_train_step"):
         getattr(L, name).restype = C.c_int
     for name in ("fe_tc_gemm_selftest", "fe_gradient_noalloc", "fe_init_batch","fe_init", "fe_reset", "fe_step", "fe_solve", "fe_get_info",
                  "fe_get_u", "fe_energy", "fe_gradient", "fe_get_state", "fe_set_state",
                  "fe_image_size", "fe_set_loop_mode", "fe_num_images", "fe_abi_version", "fe_tile_size",
-                 "fe_ssim", "fe_psnr", "fe_tc_wait_selftest", "fe_tile_cluster"):
+                 "fe_ssim", "fe_psnr", "fe_tc_wait_selftest", "fe_tile_cluster", "fe_peak",
+                 "fe_device_sms"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -336,6 +339,28 @@ def psnr(x, y, peak: float = 255.0, stream=None) -> float:
     if st != FE_OK:
         raise FeError(st, lib.fe_last_error(None).decode())
     return out.value
+
+
+PEAK_KINDS = {"ffma": 0, "ffma2": 1, "dfma": 2, "mufu_rcp": 3, "mufu_lg2": 4, "tc_bf16": 5, "tc_tf32": 6}
+
+
+def peak(kind: str, target_ms: float = 20.0, reps: int = 5) -> dict:
+    """fe_peak: measured rate of one unit of the current device (flop/s for
+    the FMA and tensor kinds, instructions/s for the MUFU kinds)."""
+    rate, ms, sms = C.c_double(), C.c_double(), C.c_int()
+    st = lib.fe_peak(PEAK_KINDS[kind], float(target_ms), int(reps), C.byref(rate), C.byref(ms), C.byref(sms))
+    if st != FE_OK:
+        raise FeError(st, lib.fe_last_error(None).decode())
+    return {"rate": rate.value, "ms": ms.value, "sms": sms.value}
+
+
+def device_sms() -> int:
+    """fe_device_sms: multiprocessor count of the current device."""
+    n = C.c_int()
+    st = lib.fe_device_sms(C.byref(n))
+    if st != FE_OK:
+        raise FeError(st, lib.fe_last_error(None).decode())
+    return n.value
 
 
 class CNN:

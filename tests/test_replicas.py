@@ -101,7 +101,7 @@ def test_bench_json_contract_gpu():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--steps", "1", "--warmup", "3",
-                        "--n512", "1", "--n256", "1", "--iters", "5", "--no-cpu-baseline"],
+                        "--n512", "1", "--n256", "1", "--iters", "5", "--no-cpu-baseline", "--no-forms"],
                        capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stderr
     lines = [x for x in r.stdout.strip().splitlines() if x.strip()]
@@ -114,6 +114,12 @@ def test_bench_json_contract_gpu():
     rf = d["roofline"]
     assert rf["bound"] == "alu" and rf["unit"] == "TFLOP/s" and 0 < rf["frac"] < 1.5
     assert abs(rf["frac"] - rf["achieved"] / rf["peak"]) < 1e-3
+    # the FP32 peak is the measured FMA rate; the SM count comes from the device
+    pk = d["peaks"]
+    assert pk["sms"] > 0 and pk["ffma"] > 0 and rf["peak"] == pytest.approx(pk["ffma"], rel=1e-3)
+    # derived peak = SMs x 128 lanes x 2 flop x a clock between 1 and 2.1 GHz
+    assert 1.0e3 <= rf["peak_derived"] * 1e6 / (pk["sms"] * 256) <= 2.1e3
+    assert 0.5 < pk["ffma"] / rf["peak_derived"] < 1.05
     e = d["e2e"]
     assert e["value"] > 0 and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     # a timed region this short may end before the 200 ms clock sampler sees
