@@ -9,6 +9,8 @@
 // graph whose while-node re-launches the trial kernel until the kernel's
 // last CTA clears the condition.  Both are bounded by a device-side trial
 // budget, so neither can spin forever.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -51,6 +53,7 @@ struct fe_ctx {
     int *d_tc_error = nullptr;
     double *d_gpart = nullptr;  // partial sums of the data-term floor G(f)
     unsigned char *d_tcw_fwd = nullptr, *d_tcw_adj = nullptr;
+    CUtensorMap *d_tmaps = nullptr;  // tensor-core forms: 6 TMA maps per image (u0..2, g0..1, f2)
     float *d_scratch = nullptr;  // 2 planes of the largest image (host-pointer staging)
     size_t max_plane = 0;
     KParams kp{};
@@ -216,6 +219,56 @@ fe_status validate_params(fe_ctx *c, const fe_params *p) {
                        p->tile);
     if (p->prec != FE_FP32 && p->tile != 0)
         return set_err(c, FE_EUNSUPPORTED, "the tensor-core forms have one tile shape: tile must be 0");
+    return FE_OK;
+}
+
+// cuTensorMapEncodeTiled from the driver, through the runtime's entry-point
+// query (the library links only the runtime); NULL when unavailable, in which
+// case the trial kernels read their inputs with plain loads.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *q = nullptr;
+        cudaDriverEntryPointQueryResult r;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &q, 12000, cudaEnableDefault, &r) ==
+                cudaSuccess &&
+            r == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(q);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// TMA maps of every plane of every image whose row pitch is a multiple of 16
+// bytes (W % 4 == 0): FP32 elements, dims {W, H}, box {tc_box_x, tc_box_y},
+// zero fill outside the plane.  Other images keep tmap = NULL (plain loads).
+fe_status build_tensor_maps(fe_ctx *c) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return FE_OK;
+    std::vector<CUtensorMap> maps((size_t)c->nimg * 6);
+    std::vector<int> ok(c->nimg, 0);
+    for (int j = 0; j < c->nimg; ++j) {
+        const ImgDesc &d = c->himg[j];
+        if (d.W % 4 != 0) continue;
+        float *planes[6] = {d.u[0], d.u[1], d.u[2], d.g[0], d.g[1], d.f2};
+        bool good = true;
+        for (int k = 0; k < 6 && good; ++k) {
+            const cuuint64_t dims[2] = {(cuuint64_t)d.W, (cuuint64_t)d.H};
+            const cuuint64_t strides[1] = {(cuuint64_t)d.W * 4};
+            const cuuint32_t box[2] = {(cuuint32_t)tc_box_x, (cuuint32_t)tc_box_y};
+            const cuuint32_t es[2] = {1, 1};
+            good = enc(&maps[(size_t)j * 6 + k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, planes[k], dims, strides, box,
+                       es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        }
+        ok[j] = good;
+    }
+    fe_status st = dalloc(c, &c->d_tmaps, maps.size());
+    if (st != FE_OK) return st;
+    FE_CUDA(c, cudaMemcpy(c->d_tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    for (int j = 0; j < c->nimg; ++j) c->himg[j].tmap = ok[j] ? c->d_tmaps + (size_t)j * 6 : nullptr;
     return FE_OK;
 }
 
@@ -700,6 +753,7 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
     }
     if (cudaMemset(c->d_tc_error, 0, sizeof(int)) != cudaSuccess)
         return bail(set_err(c, FE_ECUDA, "cudaMemset failed"));
+    if (tc && (st = build_tensor_maps(c)) != FE_OK) return bail(st);
 
     // weight tables: forward = flipped taps (convolution as correlation),
     // tap-major; adjoint = taps as stored times 2 theta_i (the factor of

@@ -48,6 +48,11 @@ struct ImgDesc {
     double lambda1;  // combined model: weight of the log-domain term
     double gscale;   // factor applied to the summed data-term partials (variant: lambda/2;
                      // combined: 1, the kernel sums the full per-pixel value)
+    // tensor-core forms: six TMA tensor maps (CUtensorMap, 128 bytes each) of
+    // the planes u[0], u[1], u[2], g[0], g[1], f2 in device memory, for the
+    // trial's box loads of tile + 6-pixel halo; NULL where the plane pitch is
+    // not a multiple of 16 bytes (W % 4 != 0): those images use plain loads
+    const void *tmap;
 };
 
 struct ImgState {
@@ -127,6 +132,9 @@ const void *fp32cl64_trial_entry(int model);
 
 // Tensor-core tile kernel (fe_tc.cu); fmt 1 = BF16, 2 = TF32 operands
 constexpr int tc_tile_y = 58, tc_tile_x = 26;  // output tile; tile + 3-pixel halo = 64 x 32
+// TMA box of the trial's inputs: the tile + 6-pixel halo (70 rows x 38
+// columns) from a start column rounded down to a multiple of 4 (16 bytes)
+constexpr int tc_box_x = 44, tc_box_y = 70;
 size_t tc_smem_bytes(int fmt);
 int tc_threads();
 cudaError_t tc_prepare();  // every format and model

@@ -86,6 +86,7 @@ __global__ void na_setup_kernel(unsigned char *base, const float *filters, const
         d.lambda = 1.0;
         d.lambda1 = 0.0;
         d.gscale = 0.5;
+        d.tmap = nullptr;
         *reinterpret_cast<ImgDesc *>(base + NA_OFF_IMG) = d;
         *reinterpret_cast<unsigned *>(base + NA_OFF_ARR) = 0u;
         reinterpret_cast<double *>(base + NA_OFF_RES)[0] = 0.0;

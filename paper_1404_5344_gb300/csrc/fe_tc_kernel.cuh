@@ -96,10 +96,7 @@ struct Cfg {
     // after MMA_fwd(b) completed, the im2col after MMA_adj(b) completed
     static constexpr size_t OFF_AF = 0;
     static constexpr size_t OFF_R = OFF_AF;
-    static constexpr size_t OFF_BF = OFF_AF + (AF_BYTES > R_BYTES ? AF_BYTES : R_BYTES);
-    static constexpr size_t OFF_BA = OFF_BF + BF_BYTES;
-    static constexpr size_t OFF_U = OFF_BA + BA_BYTES;       // NPL planes of u^{n+1}
-    static constexpr size_t OFF_H = OFF_U + (size_t)NPL * PL_WORDS * 4;
+    static constexpr size_t OFF_H = OFF_AF + (AF_BYTES > R_BYTES ? AF_BYTES : R_BYTES);
     // gradient rows: BF16 keeps every row of the region (three CTAs per SM
     // fit either way; the final pass then folds and writes with all warps),
     // TF32 only the rows of the vertical fold (image rows -3..2, H-3..H+2),
@@ -107,12 +104,21 @@ struct Cfg {
     static constexpr bool FULL_G = FMT == 1;
     static constexpr int GROWS = FULL_G ? R3Y : NFOLD;
     static constexpr size_t OFF_G = OFF_H + (size_t)HRING * 7 * 32 * 4;
-    static constexpr size_t OFF_TH = OFF_G + (size_t)GROWS * R3X * 4;
+    static constexpr size_t OFF_BF = (OFF_G + (size_t)GROWS * R3X * 4 + 127) / 128 * 128;
+    static constexpr size_t OFF_BA = OFF_BF + BF_BYTES;
+    static constexpr size_t OFF_U = OFF_BA + BA_BYTES;       // NPL planes of u^{n+1}
+    static constexpr size_t OFF_TH = OFF_U + (size_t)NPL * PL_WORDS * 4;
     static constexpr size_t OFF_RED = OFF_TH + (size_t)2 * NF * 4;
     static constexpr size_t BYTES = OFF_RED + (size_t)(NT / 32) * NRED * 8;
+    // TMA staging of the trial's four input planes (u^n, u^{n-1}, g^n, f^2 on
+    // the tile + 6 box): overlays the operand buffer, the H ring and the
+    // gradient rows, none of which is live before the first im2col
+    static constexpr size_t STAGE_PLANE = ((size_t)tc_box_y * tc_box_x * 4 + 127) / 128 * 128;
+    static constexpr size_t OFF_STAGE = 0;
+    static_assert(OFF_STAGE + 4 * STAGE_PLANE <= OFF_BF, "the staging planes end before the B operands");
     static_assert(OFF_H % 16 == 0 && OFF_BF % 128 == 0 && OFF_BA % 128 == 0 && OFF_U % 128 == 0,
                   "operand alignment");
-    static_assert(OFF_U % 16 == 0 && OFF_TH % 16 == 0 && OFF_RED % 8 == 0, "alignment");
+    static_assert(OFF_U % 16 == 0 && OFF_TH % 16 == 0 && OFF_RED % 8 == 0 && OFF_G % 16 == 0, "alignment");
     static_assert(BF_BYTES % 16 == 0 && BA_BYTES % 16 == 0, "vector copies");
 };
 static_assert(3 * (Cfg<1>::BYTES + 1024) <= 228 * 1024, "BF16: three CTAs per SM");
@@ -120,6 +126,17 @@ static_assert(Cfg<2>::GROWS == NFOLD, "TF32: compact fold rows");
 static_assert(2 * (Cfg<2>::BYTES + 1024) <= 228 * 1024, "TF32: two CTAs per SM");
 
 constexpr float LN2 = 0.69314718055994530942f;
+
+// Closed-form prox of t*G (Sec. II-C) as prox_g computes it, with the square
+// root and the division on the special-function unit (approximate forms; the
+// tensor-core forms are approximations of the model to begin with):
+// c4 = 4 (1 + tl) tl, inv2 = 1 / (2 (1 + tl)), tl2 = 2 tl.
+__device__ __forceinline__ float prox_g_sfu(float uhat, float f2, float c4, float inv2, float tl2) {
+    const float D = fmaf(uhat, uhat, c4 * f2);
+    float sD;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sD) : "f"(D));
+    return uhat >= 0.0f ? (uhat + sD) * inv2 : (tl2 * f2) * rcp_ftz(sD - uhat);
+}
 
 // hi = x rounded to the operand type, lo = (x - hi) rounded, for one 16-byte
 // chunk of E consecutive K values.
@@ -146,6 +163,43 @@ __device__ __forceinline__ void hilo_chunk<2>(const float *v, uint4 &hi, uint4 &
         const float hv = tc::round_tf32(v[j]);
         h[j] = __float_as_uint(hv);
         l[j] = __float_as_uint(tc::round_tf32(v[j] - hv));
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// The same split for E consecutive K values held as E/2 packed FP32 pairs:
+// the residual x - hi of both elements in one packed subtraction.
+template <int FMT>
+__device__ __forceinline__ void hilo_chunk2(const uint64_t *v2, uint4 &hi, uint4 &lo);
+template <>
+__device__ __forceinline__ void hilo_chunk2<1>(const uint64_t *v2, uint4 &hi, uint4 &lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float a, b;
+        tc::f2_unpack(v2[j], a, b);
+        h[j] = tc::bf16x2_rn(a, b);
+        const uint64_t hp = tc::f2_pack(__uint_as_float(h[j] << 16), __uint_as_float(h[j] & 0xffff0000u));
+        tc::f2_unpack(tc::f2_sub(v2[j], hp), a, b);
+        l[j] = tc::bf16x2_rn(a, b);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+template <>
+__device__ __forceinline__ void hilo_chunk2<2>(const uint64_t *v2, uint4 &hi, uint4 &lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        float a, b;
+        tc::f2_unpack(v2[j], a, b);
+        const float ha = tc::round_tf32(a), hb = tc::round_tf32(b);
+        h[2 * j] = __float_as_uint(ha);
+        h[2 * j + 1] = __float_as_uint(hb);
+        tc::f2_unpack(tc::f2_sub(v2[j], tc::f2_pack(ha, hb)), a, b);
+        l[2 * j] = __float_as_uint(tc::round_tf32(a));
+        l[2 * j + 1] = __float_as_uint(tc::round_tf32(b));
     }
     hi = make_uint4(h[0], h[1], h[2], h[3]);
     lo = make_uint4(l[0], l[1], l[2], l[3]);
@@ -207,7 +261,7 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
     float *sG = reinterpret_cast<float *>(smem + C::OFF_G);  // GROWS rows of 32
     float *sTh = reinterpret_cast<float *>(smem + C::OFF_TH);  // theta_i, then 2 theta_i
     double *sRed = reinterpret_cast<double *>(smem + C::OFF_RED);
-    __shared__ uint64_t bar_f, bar_a;
+    __shared__ uint64_t bar_f, bar_a, bar_ld;
     __shared__ uint32_t tbase;
     __shared__ int sLast;
 
@@ -227,6 +281,31 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
     }
 
     if (active) {
+        int cur = 0, gcur = 0;
+        if (MODE == MODE_TRIAL) {
+            cur = st->cur;
+            gcur = st->gcur;
+        }
+        // ---- TMA box loads of the trial's inputs (tile + 6 halo) -----------
+        // The box starts at (x0 - 6) rounded down to a multiple of 4 columns
+        // (16 bytes); it may reach outside the image, where it reads zeros.
+        // The symmetric extension is applied afterwards, by indexing the
+        // staged box at reflected coordinates (all of which lie in the box).
+        constexpr int SP = (int)(C::STAGE_PLANE / 4);  // staging plane stride (floats)
+        const bool use_tma = MODE == MODE_TRIAL && im.tmap != nullptr;
+        const int ys = y0 - 6, xs = ((x0 - 6) >> 2) << 2;  // arithmetic shift: floor
+        const float *stg = reinterpret_cast<const float *>(smem + C::OFF_STAGE);
+        if (use_tma && tid == 0) {
+            tc::mbar_init(&bar_ld, 1);
+            tc::mbar_arrive_expect_tx(&bar_ld, 4u * (uint32_t)(tc_box_y * tc_box_x * 4));
+            const unsigned char *tm = static_cast<const unsigned char *>(im.tmap);
+            float *dst = reinterpret_cast<float *>(smem + C::OFF_STAGE);
+            tc::tma_load_2d(dst, tm + 128 * cur, xs, ys, &bar_ld);                   // u^n
+            tc::tma_load_2d(dst + SP, tm + 128 * ((cur + 2) % 3), xs, ys, &bar_ld);  // u^{n-1}
+            tc::tma_load_2d(dst + 2 * SP, tm + 128 * (3 + gcur), xs, ys, &bar_ld);   // g^n
+            tc::tma_load_2d(dst + 3 * SP, tm + 128 * 5, xs, ys, &bar_ld);            // f^2
+        }
+        bool tc_ok = true;
         // ---- rounded filter bank (B operands) and theta into shared memory --
         {
             const uint4 *gf = reinterpret_cast<const uint4 *>(p.tcw_fwd);
@@ -259,10 +338,9 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
         // FP32 for the small step-test terms
         Sum2 accF{0.f, 0.f}, accG{0.f, 0.f};
         float accGD = 0.f, accDD = 0.f, accDP = 0.f;
-        int cur = 0, gcur = 0;
-        if (MODE == MODE_TRIAL) {
-            cur = st->cur;
-            gcur = st->gcur;
+        if (use_tma && !tc::mbar_wait(&bar_ld, 0)) {
+            tc_ok = false;                // the tile's sums are poisoned below
+            (void)tc::mbar_wait(&bar_ld, 0);  // a second bounded chance for copies in flight
         }
         const float *uc = (MODE == MODE_TRIAL || MODE == MODE_INIT) ? im.u[cur] : p.u_ext;
         float *un = im.u[(cur + 1) % 3];
@@ -280,6 +358,9 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
             const float *upv = im.u[(cur + 2) % 3];
             const float *gc = im.g[gcur];
             const float *f2p = im.f2;
+            const float c4 = 4.0f * (1.0f + tl) * tl, inv2 = 1.0f / (2.0f * (1.0f + tl)), tl2 = 2.0f * tl;
+            // tile + 6 inside the image: no reflection
+            const bool in6 = y0 >= 6 && y0 + TY + 6 <= H && x0 >= 6 && x0 + TX + 6 <= W;
             constexpr int NPIX = R6Y * R6X, UNR = 4;
             for (int base = 0; base < NPIX; base += UNR * NT) {
                 size_t off[UNR];
@@ -290,13 +371,23 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
                     const int idx = base + k * NT + tid;
                     inb[k] = idx < NPIX;
                     const int ry = inb[k] ? idx / R6X : 0, rx = inb[k] ? idx - ry * R6X : 0;
-                    off[k] = (size_t)reflect(y0 - 6 + ry, H) * W + reflect(x0 - 6 + rx, W);
+                    const int yr = in6 ? y0 - 6 + ry : reflect(y0 - 6 + ry, H);
+                    const int xr = in6 ? x0 - 6 + rx : reflect(x0 - 6 + rx, W);
+                    off[k] = (size_t)yr * W + xr;
                     owned[k] = inb[k] && ry >= 6 + sy && ry < 6 + sy + oh && rx >= 6 + sx && rx < 6 + sx + ow;
-                    u0[k] = __ldg(uc + off[k]);
-                    f2[k] = (MODE == MODE_TRIAL || owned[k]) ? __ldg(f2p + off[k]) : 1.0f;
-                    if (MODE == MODE_TRIAL) {
-                        u_1[k] = __ldg(upv + off[k]);
-                        g0[k] = __ldg(gc + off[k]);
+                    if (use_tma) {
+                        const int si = (yr - ys) * tc_box_x + (xr - xs);
+                        u0[k] = stg[si];
+                        u_1[k] = stg[SP + si];
+                        g0[k] = stg[2 * SP + si];
+                        f2[k] = stg[3 * SP + si];
+                    } else {
+                        u0[k] = __ldg(uc + off[k]);
+                        f2[k] = (MODE == MODE_TRIAL || owned[k]) ? __ldg(f2p + off[k]) : 1.0f;
+                        if (MODE == MODE_TRIAL) {
+                            u_1[k] = __ldg(upv + off[k]);
+                            g0[k] = __ldg(gc + off[k]);
+                        }
                     }
                 }
 #pragma unroll
@@ -306,7 +397,7 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
                     if (MODE == MODE_TRIAL) {
                         const float dprev = u0[k] - u_1[k];
                         const float uhat = fmaf(-a, g0[k], fmaf(b, dprev, u0[k]));
-                        v = MODEL == 0 ? prox_g(uhat, f2[k], tl) : prox_w(uhat, f2[k], a, l1, l2);
+                        v = MODEL == 0 ? prox_g_sfu(uhat, f2[k], c4, inv2, tl2) : prox_w(uhat, f2[k], a, l1, l2);
                         if (owned[k]) {
                             un[off[k]] = v;
                             const float d = v - u0[k];
@@ -317,8 +408,10 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
                     } else {
                         v = u0[k];
                     }
+                    // data term (variant: u^2 - 2 f^2 log u, the log on the special-function unit)
                     if (owned[k])
-                        sum2_add(accG, MODEL == 0 ? v * v - 2.0f * f2[k] * logf(v) : data_w(v, f2[k], l1, l2));
+                        sum2_add(accG, MODEL == 0 ? fmaf(v, v, (-2.0f * LN2) * f2[k] * lg2_ftz(v))
+                                                  : data_w(v, f2[k], l1, l2));
                     // hi / lo planes of the operand type (the bank sees u)
                     const float uv = MODEL == 0 ? v : expf(v);
                     const int idx = base + k * NT + tid, ry = idx / R6X, rx = idx - ry * R6X;
@@ -352,6 +445,10 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
         const bool full_y = y0 >= 3 && y0 + TY + 3 <= H, full_x = x0 >= 3 && x0 + TX + 3 <= W;
         const bool all_in = full_y && full_x;  // every halo pixel lies in the image
 
+        // every plane element is written, and every staged value read,
+        // before the im2col of block 0 reads the planes and overwrites the
+        // staging area
+        __syncthreads();
         // block 0: im2col and forward MMA
         im2col<FMT>(sP, sAF, 0, m, part);
         tc::fence_proxy_async();
@@ -369,7 +466,6 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
             tc::mma_commit(&bar_f);
         }
         uint32_t phase_f = 0, phase_a = 0;
-        bool tc_ok = true;
 
         // epilogue 2 of block pb: horizontal col2im of S (TMEM) into the H ring
         auto epi2 = [&](int pb) {
@@ -381,23 +477,27 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
             for (int j = 0; j < 4; ++j)
                 if (j < na) tc::tmem_ld8(taddr + lane_base + (uint32_t)(64 + KS * (a_lo + j)), s8[j]);
             tc::tmem_ld_wait();
+            // two window rows at a time: the 7 shuffled values of rows j and
+            // j + 1 are summed as packed pairs (the sum order per row is that
+            // of the scalar loop)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < 4; j += 2) {
                 if (j >= na) break;
-                float h = 0.f;
-                if (edge_x) {
+                const bool two = j + 1 < na;  // warpgroup 1 has 3 rows
+                uint64_t h2 = 0ull;
 #pragma unroll
-                    for (int bb = 0; bb < KS; ++bb) {
-                        const int src = lane - 3 + bb;
-                        const float v = __shfl_sync(0xffffffffu, s8[j][bb], src & 31);
-                        h += (src >= 0 && src < 32) ? v : 0.0f;
-                    }
-                } else {
+                for (int bb = 0; bb < KS; ++bb) {
+                    const int src = lane - 3 + bb;
+                    float v0 = __shfl_sync(0xffffffffu, s8[j][bb], src & 31);
+                    float v1 = two ? __shfl_sync(0xffffffffu, s8[j + 1][bb], src & 31) : 0.0f;
                     // interior tile: lanes 3..28 (the only ones used) have all sources in the warp
-#pragma unroll
-                    for (int bb = 0; bb < KS; ++bb) h += __shfl_sync(0xffffffffu, s8[j][bb], (lane - 3 + bb) & 31);
+                    if (edge_x && !(src >= 0 && src < 32)) v0 = v1 = 0.0f;
+                    h2 = tc::f2_add(h2, tc::f2_pack(v0, v1));
                 }
-                sH[(slot * KS + a_lo + j) * 32 + lane] = h;
+                float h0, h1;
+                tc::f2_unpack(h2, h0, h1);
+                sH[(slot * KS + a_lo + j) * 32 + lane] = h0;
+                if (two) sH[(slot * KS + a_lo + j + 1) * 32 + lane] = h1;
             }
         };
         // vertical col2im of the ext rows whose 7 source rows are complete
@@ -459,31 +559,40 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
                     for (int k = 0; k < 8; ++k) z[8 * j + k] = t8[k];
                 }
                 tc::tmem_ld_wait();
+                // pairs of filters in packed FP32 (one instruction per pair for
+                // q = 1 + z^2, 2 theta z, r = 2 theta z / q and the F sum; the
+                // reciprocal and log2 stay scalar on the special-function unit)
                 const float4 *th4 = reinterpret_cast<const float4 *>(sTh + 24 * wg);
                 const float4 *tw4 = reinterpret_cast<const float4 *>(sTh + NF + 24 * wg);
-                float r[24], psum = 0.f;
+                const uint64_t one2 = tc::f2_pack(1.0f, 1.0f);
+                uint64_t r2[12], ps2 = 0ull;  // ps2 = (0, 0)
 #pragma unroll
                 for (int j = 0; j < 6; ++j) {
                     const float4 t1 = th4[j], t2 = tw4[j];
-                    const float th[4] = {t1.x, t1.y, t1.z, t1.w}, tw[4] = {t2.x, t2.y, t2.z, t2.w};
+                    const uint64_t thp[2] = {tc::f2_pack(t1.x, t1.y), tc::f2_pack(t1.z, t1.w)};
+                    const uint64_t twp[2] = {tc::f2_pack(t2.x, t2.y), tc::f2_pack(t2.z, t2.w)};
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const float zz = z[4 * j + k];
-                        const float q = fmaf(zz, zz, 1.0f);
-                        r[4 * j + k] = (tw[k] * zz) * rcp_ftz(q);
-                        psum = fmaf(th[k], lg2_ftz(q), psum);
+                    for (int k = 0; k < 2; ++k) {
+                        const uint64_t zp = tc::f2_pack(z[4 * j + 2 * k], z[4 * j + 2 * k + 1]);
+                        const uint64_t qp = tc::f2_fma(zp, zp, one2);
+                        float q0, q1;
+                        tc::f2_unpack(qp, q0, q1);
+                        r2[2 * j + k] = tc::f2_mul(tc::f2_mul(twp[k], zp), tc::f2_pack(rcp_ftz(q0), rcp_ftz(q1)));
+                        ps2 = tc::f2_fma(thp[k], tc::f2_pack(lg2_ftz(q0), lg2_ftz(q1)), ps2);
                     }
                 }
                 if (!inimg) {
 #pragma unroll
-                    for (int i = 0; i < 24; ++i) r[i] = 0.0f;
+                    for (int i = 0; i < 12; ++i) r2[i] = 0ull;
                 }
-                if (owned) sum2_add(accF, psum * LN2);
+                float pa, pb;
+                tc::f2_unpack(ps2, pa, pb);
+                if (owned) sum2_add(accF, (pa + pb) * LN2);
                 unsigned char *rowp = sR + tc::kmajor_offset((lg << 5) + lane, 0, KADJ, C::EB);
 #pragma unroll
                 for (int j = 0; j < 24 / C::E; ++j) {
                     uint4 hi, lo;
-                    hilo_chunk<FMT>(r + j * C::E, hi, lo);
+                    hilo_chunk2<FMT>(r2 + j * (C::E / 2), hi, lo);
                     *reinterpret_cast<uint4 *>(rowp + ((24 * wg) / C::E + j) * 128) = hi;
                     *reinterpret_cast<uint4 *>(rowp + ((NF + 24 * wg) / C::E + j) * 128) = lo;
                 }
