@@ -169,12 +169,47 @@ __device__ __forceinline__ float forward_unit(const float *__restrict__ sU, floa
     constexpr int FWD_ROWS = Q::FWD_ROWS, FWD_WIN = Q::FWD_WIN, SU_LD = Q::SU_LD, SR_LD = Q::SR_LD;
     constexpr int TY = Q::TY, TX = Q::TX, R3YA = Q::R3YA;
     float z[FWD_ROWS][G];
+    const float *ucol = sU + rb * FWD_ROWS * SU_LD + c;
+    const float *wcol = wb + Q::WB_F;
+    if constexpr (FWD_ROWS <= 10) {
+    // accumulators of filter pairs (0, 1) and (2, 3) as packed FP32 pairs:
+    // one fma.rn.f32x2 updates both filters of a pair at a row (each element
+    // rounded as the scalar FMA, in the same order), with the window value
+    // duplicated into both halves of its operand; half the FMA instructions
+    // of the scalar form (the 13-row units of the 32 x 32 tile keep the
+    // scalar form: their packed window does not fit the register budget)
+    static_assert(G == 4, "two filter pairs per group");
+    uint64_t z2[FWD_ROWS][2];
+#pragma unroll
+    for (int r = 0; r < FWD_ROWS; ++r) z2[r][0] = z2[r][1] = 0ull;
+#pragma unroll 1
+    for (int bb = 0; bb < KS; ++bb) {
+        uint64_t vd[FWD_WIN];
+#pragma unroll
+        for (int r = 0; r < FWD_WIN; ++r) {
+            const float v = ucol[r * SU_LD + bb];
+            vd[r] = f2_pack(v, v);
+        }
+#pragma unroll
+        for (int aa = 0; aa < KS; ++aa) {
+            const float4 w0 = *reinterpret_cast<const float4 *>(wcol + (aa * KS + bb) * G);
+            const uint64_t w01 = f2_pack(w0.x, w0.y), w23 = f2_pack(w0.z, w0.w);
+#pragma unroll
+            for (int r = 0; r < FWD_ROWS; ++r) z2[r][0] = f2_fma(w01, vd[r + aa], z2[r][0]);
+#pragma unroll
+            for (int r = 0; r < FWD_ROWS; ++r) z2[r][1] = f2_fma(w23, vd[r + aa], z2[r][1]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < FWD_ROWS; ++r) {
+        f2_unpack(z2[r][0], z[r][0], z[r][1]);
+        f2_unpack(z2[r][1], z[r][2], z[r][3]);
+    }
+    } else {
 #pragma unroll
     for (int r = 0; r < FWD_ROWS; ++r)
 #pragma unroll
         for (int i = 0; i < G; ++i) z[r][i] = 0.f;
-    const float *ucol = sU + rb * FWD_ROWS * SU_LD + c;
-    const float *wcol = wb + Q::WB_F;
 #pragma unroll 1
     for (int bb = 0; bb < KS; ++bb) {
         float v[FWD_WIN];
@@ -189,6 +224,7 @@ __device__ __forceinline__ float forward_unit(const float *__restrict__ sU, floa
 #pragma unroll
                 for (int r = 0; r < FWD_ROWS; ++r) z[r][i] = fmaf(w[i], v[r + aa], z[r][i]);
         }
+    }
     }
     float th[G];
 #pragma unroll

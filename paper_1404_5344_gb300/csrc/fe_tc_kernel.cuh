@@ -178,11 +178,11 @@ __device__ __forceinline__ void hilo_chunk2<1>(const uint64_t *v2, uint4 &hi, ui
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         float a, b;
-        tc::f2_unpack(v2[j], a, b);
-        h[j] = tc::bf16x2_rn(a, b);
-        const uint64_t hp = tc::f2_pack(__uint_as_float(h[j] << 16), __uint_as_float(h[j] & 0xffff0000u));
-        tc::f2_unpack(tc::f2_sub(v2[j], hp), a, b);
-        l[j] = tc::bf16x2_rn(a, b);
+        f2_unpack(v2[j], a, b);
+        h[j] = bf16x2_rn(a, b);
+        const uint64_t hp = f2_pack(__uint_as_float(h[j] << 16), __uint_as_float(h[j] & 0xffff0000u));
+        f2_unpack(f2_sub(v2[j], hp), a, b);
+        l[j] = bf16x2_rn(a, b);
     }
     hi = make_uint4(h[0], h[1], h[2], h[3]);
     lo = make_uint4(l[0], l[1], l[2], l[3]);
@@ -193,11 +193,11 @@ __device__ __forceinline__ void hilo_chunk2<2>(const uint64_t *v2, uint4 &hi, ui
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
         float a, b;
-        tc::f2_unpack(v2[j], a, b);
+        f2_unpack(v2[j], a, b);
         const float ha = tc::round_tf32(a), hb = tc::round_tf32(b);
         h[2 * j] = __float_as_uint(ha);
         h[2 * j + 1] = __float_as_uint(hb);
-        tc::f2_unpack(tc::f2_sub(v2[j], tc::f2_pack(ha, hb)), a, b);
+        f2_unpack(f2_sub(v2[j], f2_pack(ha, hb)), a, b);
         l[2 * j] = __float_as_uint(tc::round_tf32(a));
         l[2 * j + 1] = __float_as_uint(tc::round_tf32(b));
     }
@@ -492,10 +492,10 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
                     float v1 = two ? __shfl_sync(0xffffffffu, s8[j + 1][bb], src & 31) : 0.0f;
                     // interior tile: lanes 3..28 (the only ones used) have all sources in the warp
                     if (edge_x && !(src >= 0 && src < 32)) v0 = v1 = 0.0f;
-                    h2 = tc::f2_add(h2, tc::f2_pack(v0, v1));
+                    h2 = f2_add(h2, f2_pack(v0, v1));
                 }
                 float h0, h1;
-                tc::f2_unpack(h2, h0, h1);
+                f2_unpack(h2, h0, h1);
                 sH[(slot * KS + a_lo + j) * 32 + lane] = h0;
                 if (two) sH[(slot * KS + a_lo + j + 1) * 32 + lane] = h1;
             }
@@ -564,21 +564,21 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
                 // reciprocal and log2 stay scalar on the special-function unit)
                 const float4 *th4 = reinterpret_cast<const float4 *>(sTh + 24 * wg);
                 const float4 *tw4 = reinterpret_cast<const float4 *>(sTh + NF + 24 * wg);
-                const uint64_t one2 = tc::f2_pack(1.0f, 1.0f);
+                const uint64_t one2 = f2_pack(1.0f, 1.0f);
                 uint64_t r2[12], ps2 = 0ull;  // ps2 = (0, 0)
 #pragma unroll
                 for (int j = 0; j < 6; ++j) {
                     const float4 t1 = th4[j], t2 = tw4[j];
-                    const uint64_t thp[2] = {tc::f2_pack(t1.x, t1.y), tc::f2_pack(t1.z, t1.w)};
-                    const uint64_t twp[2] = {tc::f2_pack(t2.x, t2.y), tc::f2_pack(t2.z, t2.w)};
+                    const uint64_t thp[2] = {f2_pack(t1.x, t1.y), f2_pack(t1.z, t1.w)};
+                    const uint64_t twp[2] = {f2_pack(t2.x, t2.y), f2_pack(t2.z, t2.w)};
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
-                        const uint64_t zp = tc::f2_pack(z[4 * j + 2 * k], z[4 * j + 2 * k + 1]);
-                        const uint64_t qp = tc::f2_fma(zp, zp, one2);
+                        const uint64_t zp = f2_pack(z[4 * j + 2 * k], z[4 * j + 2 * k + 1]);
+                        const uint64_t qp = f2_fma(zp, zp, one2);
                         float q0, q1;
-                        tc::f2_unpack(qp, q0, q1);
-                        r2[2 * j + k] = tc::f2_mul(tc::f2_mul(twp[k], zp), tc::f2_pack(rcp_ftz(q0), rcp_ftz(q1)));
-                        ps2 = tc::f2_fma(thp[k], tc::f2_pack(lg2_ftz(q0), lg2_ftz(q1)), ps2);
+                        f2_unpack(qp, q0, q1);
+                        r2[2 * j + k] = f2_mul(f2_mul(twp[k], zp), f2_pack(rcp_ftz(q0), rcp_ftz(q1)));
+                        ps2 = f2_fma(thp[k], f2_pack(lg2_ftz(q0), lg2_ftz(q1)), ps2);
                     }
                 }
                 if (!inimg) {
@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
                     for (int i = 0; i < 12; ++i) r2[i] = 0ull;
                 }
                 float pa, pb;
-                tc::f2_unpack(ps2, pa, pb);
+                f2_unpack(ps2, pa, pb);
                 if (owned) sum2_add(accF, (pa + pb) * LN2);
                 unsigned char *rowp = sR + tc::kmajor_offset((lg << 5) + lane, 0, KADJ, C::EB);
 #pragma unroll
