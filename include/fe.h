@@ -222,6 +222,17 @@ FE_API fe_status fe_step(fe_ctx *ctx, int n, fe_status *worst);
  * FE_ENONFINITE / FE_EBACKTRACK / FE_ETIMEOUT). */
 FE_API fe_status fe_solve(fe_ctx *ctx, int max_iter, double rel_tol);
 
+/* fe_solve with an energy target per image: image j also stops at the first
+ * accepted iterate whose energy H = F + G (Eq. fplusg, Sec. II-C) is <=
+ * H_target[j] (a stopping reading of this library; the paper states no
+ * stopping rule).  H_target: host array of nimg doubles (-inf disables the
+ * target of an image; NaN is rejected), or NULL (fe_solve).  rel_tol = 0
+ * disables the relative-change rule.  It compares runs from different
+ * starting points at the same energy (the learned warm start against plain
+ * iPiano).  Returns as fe_solve: FE_OK when every image met a stopping rule,
+ * FE_ENOTCONVERGED when some hit max_iter first, else the first error. */
+FE_API fe_status fe_solve_to_energy(fe_ctx *ctx, int max_iter, double rel_tol, const double *H_target);
+
 /* Summary of image img (synchronises): n, L_n, alpha_n of the update rule
  * (Sec. II-C) and F, G, H = F + G of Eq. fplusg at u^n.  out: host pointer.
  * Errors: FE_EINVAL (NULL, img out of range), FE_ECUDA. */

@@ -52,6 +52,7 @@ struct fe_ctx {
     int *d_flag = nullptr;
     int *d_tc_error = nullptr;
     double *d_gpart = nullptr;  // partial sums of the data-term floor G(f)
+    double *d_htarget = nullptr;  // per-image energy targets of fe_solve_to_energy
     unsigned char *d_tcw_fwd = nullptr, *d_tcw_adj = nullptr;
     CUtensorMap *d_tmaps = nullptr;  // tensor-core forms: 6 TMA maps per image (u0..2, g0..1, f2)
     float *d_scratch = nullptr;  // 2 planes of the largest image (host-pointer staging)
@@ -142,10 +143,11 @@ __global__ void gfloor_kernel(const float *f2, size_t N, int model, double lam, 
 }
 
 __global__ void begin_kernel(ImgState *st, int nimg, long long n, double tol, LoopCtl *lc,
-                             long long budget) {
+                             long long budget, const double *H_target) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int nact = 0;
     for (int j = 0; j < nimg; ++j) {
+        st[j].H_target = H_target ? H_target[j] : -INFINITY;
         if (st[j].status == FE_OK) {
             st[j].done = 0;
             st[j].converged = 0;
@@ -741,6 +743,7 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
     if ((st = dalloc(c, &c->d_flag, 4)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_tc_error, 1)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_gpart, (size_t)nimg * GF_BLOCKS)) != FE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_htarget, (size_t)nimg)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_scratch, 2 * c->max_plane)) != FE_OK) return bail(st);
     if (tc) {
         std::vector<unsigned char> bf, ba;
@@ -832,7 +835,7 @@ fe_status fe_step(fe_ctx *c, int n, fe_status *worst) {
     if (n < 0) return set_err(c, FE_EINVAL, "n must be >= 0");
     if (n > 0) {
         const long long budget = (long long)n * (c->prm.max_backtrack + 1) + 1;
-        begin_kernel<<<1, 32, 0, c->s>>>(c->d_st, c->nimg, n, 0.0, c->d_loop, budget);
+        begin_kernel<<<1, 32, 0, c->s>>>(c->d_st, c->nimg, n, 0.0, c->d_loop, budget, nullptr);
         FE_CUDA(c, cudaGetLastError());
         ++c->host_launches;
         fe_status st = run_loop(c, n, budget, worst != nullptr);
@@ -852,11 +855,20 @@ fe_status fe_step(fe_ctx *c, int n, fe_status *worst) {
     return FE_OK;
 }
 
-fe_status fe_solve(fe_ctx *c, int max_iter, double rel_tol) {
+fe_status fe_solve(fe_ctx *c, int max_iter, double rel_tol) { return fe_solve_to_energy(c, max_iter, rel_tol, nullptr); }
+
+fe_status fe_solve_to_energy(fe_ctx *c, int max_iter, double rel_tol, const double *H_target) {
     if (!c) return FE_EINVAL;
     if (max_iter < 0 || !(rel_tol >= 0.0)) return set_err(c, FE_EINVAL, "max_iter >= 0 and rel_tol >= 0 required");
     const long long budget = (long long)max_iter * (c->prm.max_backtrack + 1) + 1;
-    begin_kernel<<<1, 32, 0, c->s>>>(c->d_st, c->nimg, max_iter, rel_tol, c->d_loop, budget);
+    const double *d_target = nullptr;
+    if (H_target) {
+        for (int j = 0; j < c->nimg; ++j)
+            if (std::isnan(H_target[j])) return set_err(c, FE_EINVAL, "H_target[%d] is NaN", j);
+        FE_CUDA(c, cudaMemcpyAsync(c->d_htarget, H_target, sizeof(double) * c->nimg, cudaMemcpyHostToDevice, c->s));
+        d_target = c->d_htarget;
+    }
+    begin_kernel<<<1, 32, 0, c->s>>>(c->d_st, c->nimg, max_iter, rel_tol, c->d_loop, budget, d_target);
     FE_CUDA(c, cudaGetLastError());
     ++c->host_launches;
     fe_status st = run_loop(c, std::min(max_iter, 32), budget, true);

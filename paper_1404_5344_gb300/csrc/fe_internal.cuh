@@ -60,6 +60,7 @@ struct ImgState {
     double L, alpha;
     double rel_change, last_gd, last_dd, last_dp;
     double tol;
+    double H_target;  // stop once an accepted H <= H_target (-inf: no energy target)
     double Gf;  // min of the data term: at u = f (variant), at w = log f (combined)
     long long n, trials, backtracks, target;
     int cur, gcur, bt, status, done, converged;

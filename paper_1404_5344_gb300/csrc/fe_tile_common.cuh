@@ -222,7 +222,7 @@ __device__ void decide(const KParams &p, ImgState *st, const double *t, int mode
         st->gcur ^= 1;
         st->n += 1;
         st->bt = 0;
-        if (st->tol > 0.0 && st->rel_change < st->tol) {
+        if ((st->tol > 0.0 && st->rel_change < st->tol) || H1 <= st->H_target) {
             st->converged = 1;
             st->done = 1;
         }

@@ -34,7 +34,7 @@ EXPORTS = (
     "fe_last_error", "fe_status_string", "fe_abi_version", "fe_gradient_noalloc",
     "fe_tc_gemm_selftest", "fe_cnn_create", "fe_cnn_destroy", "fe_cnn_num_params",
     "fe_cnn_last_error", "fe_cnn_set_params", "fe_cnn_get_params", "fe_cnn_forward",
-    "fe_cnn_loss_grad", "fe_cnn_train_step", "fe_peak", "fe_device_sms",
+    "fe_cnn_loss_grad", "fe_cnn_train_step", "fe_peak", "fe_device_sms", "fe_solve_to_energy",
 )
 
 
@@ -74,6 +74,7 @@ def _load(path: str = LIB_PATH) -> C.CDLL:
     L.fe_destroy.restype = None
     L.fe_step.argtypes = [VP, I, P(I)]
     L.fe_solve.argtypes = [VP, I, D]
+    L.fe_solve_to_energy.argtypes = [VP, I, D, VP]
     L.fe_get_info.argtypes = [VP, I, P(FeInfo)]
     L.fe_get_u.argtypes = [VP, I, VP]
     L.fe_energy.argtypes = [VP, I, VP, P(D), P(D), P(D)]
@@ -117,7 +118,7 @@ def _load(path: str = LIB_PATH) -> C.CDLL:
                  "fe_get_u", "fe_energy", "fe_gradient", "fe_get_state", "fe_set_state",
                  "fe_image_size", "fe_set_loop_mode", "fe_num_images", "fe_abi_version", "fe_tile_size",
                  "fe_ssim", "fe_psnr", "fe_tc_wait_selftest", "fe_tile_cluster", "fe_peak",
-                 "fe_device_sms"):
+                 "fe_device_sms", "fe_solve_to_energy"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -269,6 +270,14 @@ class Solver:
 
     def solve(self, max_iter: int, rel_tol: float) -> int:
         st = lib.fe_solve(self.ctx, int(max_iter), float(rel_tol))
+        if st not in (FE_OK, FE_ENOTCONVERGED):
+            self._check(st)
+        return st
+
+    def solve_to_energy(self, max_iter: int, H_target, rel_tol: float = 0.0) -> int:
+        """fe_solve_to_energy: also stop image j once an accepted H <= H_target[j]."""
+        t = np.ascontiguousarray(np.broadcast_to(np.asarray(H_target, np.float64), (self.nimg,)))
+        st = lib.fe_solve_to_energy(self.ctx, int(max_iter), float(rel_tol), t.ctypes.data)
         if st not in (FE_OK, FE_ENOTCONVERGED):
             self._check(st)
         return st

@@ -11,9 +11,14 @@ buffers and cuts crops):
    count).
 3. ``train``: Adam on random crops, loss mean (d - (log u* - log f))^2.
 4. ``evaluate``: for held-out images, iterations and device time of plain
-   iPiano from f versus iPiano from u0 = CNN(f), both to the same tolerance.
-   The energy H(u0) is checked first: if it is not below H(f), the solve
-   starts from f (plain iPiano stays the fallback and the judge).
+   iPiano from f versus iPiano from u0 = CNN(f) to the SAME ENERGY: plain
+   iPiano first runs to the relative energy tolerance (its energy H_plain
+   there defines the target), then both runs start over and stop at the
+   first accepted iterate with H <= H* = H_plain + eps (H(f) - H_plain)
+   (fe_solve_to_energy).  The energy H(u0) is checked first: if it is not
+   below H(f), the solve starts from f (plain iPiano stays the fallback and
+   the judge).  Runs that stop on the relative-change rule alone are also
+   reported (their energies can differ).
 """
 from __future__ import annotations
 
@@ -117,10 +122,15 @@ def train(cnn, F, Ut, steps, batch=32, crop=64, lr=1e-3, seed=0, log_every=0, de
     return losses
 
 
-def evaluate(cnn, fs, filters, theta, tol=1e-6, max_iter=3000, prec="fp32", stream=None, solver_kw=None):
+def evaluate(cnn, fs, filters, theta, tol=1e-6, max_iter=3000, prec="fp32", stream=None, solver_kw=None,
+             eps=1e-3):
     """Plain iPiano from f vs iPiano from the CNN prediction, per image (fs:
-    list of torch CUDA tensors [H, W]).  Times are CUDA-event device times
-    of the solves (the CNN inference is timed separately)."""
+    list of torch CUDA tensors [H, W]), at equal energy: the target is H* =
+    H_plain + eps (H(f) - H_plain), H_plain the energy where plain iPiano
+    meets the relative tolerance tol; both runs stop at the first accepted
+    iterate with H <= H* (max_iter at most).  Times are CUDA-event device
+    times of the solves (the CNN inference is timed separately).  Also
+    returned: both runs stopped by the relative-change rule alone."""
     import torch
     kw = dict(SOLVER_KW if solver_kw is None else solver_kw)
     st = stream if stream is not None else torch.cuda.current_stream()
@@ -139,17 +149,32 @@ def evaluate(cnn, fs, filters, theta, tol=1e-6, max_iter=3000, prec="fp32", stre
             t_plain, _ = timed(lambda: plain.solve(max_iter, tol))
             ip = plain.info(0)
             H_f = plain.energy(0, f)[0]
+            H_star = ip["H"] + eps * (H_f - ip["H"])
+            plain.reset([f])
+            t_plain_eq, _ = timed(lambda: plain.solve_to_energy(max_iter, H_star))
+            ipe = plain.info(0)
         u0 = torch.empty_like(f)
         t_cnn, _ = timed(lambda: cnn.forward(f, u0=u0))
         with Solver([f], filters, theta, prec=prec, stream=stream, u0=u0, **kw) as warm:
             H_u0 = warm.energy(0, u0)[0]
             used = H_u0 < H_f
-            if not used:
-                warm.reset([f])
+            start = [u0] if used else None
+
+            def restart():
+                warm.reset([f], u0=start)
+
+            restart()
+            t_warm_eq, _ = timed(lambda: warm.solve_to_energy(max_iter, H_star))
+            iwe = warm.info(0)
+            restart()
             t_warm, _ = timed(lambda: warm.solve(max_iter, tol))
             iw = warm.info(0)
         out.append(dict(iters_plain=int(ip["n"]), iters_warm=int(iw["n"]), ms_plain=t_plain,
                         ms_warm=t_warm, ms_cnn=t_cnn, H_plain=ip["H"], H_warm=iw["H"],
                         H_f=H_f, H_u0=H_u0, used_cnn=bool(used),
-                        converged_plain=bool(ip["converged"]), converged_warm=bool(iw["converged"])))
+                        converged_plain=bool(ip["converged"]), converged_warm=bool(iw["converged"]),
+                        H_target=H_star, iters_plain_eq=int(ipe["n"]), iters_warm_eq=int(iwe["n"]),
+                        ms_plain_eq=t_plain_eq, ms_warm_eq=t_warm_eq,
+                        H_plain_eq=ipe["H"], H_warm_eq=iwe["H"],
+                        reached_plain_eq=bool(ipe["H"] <= H_star), reached_warm_eq=bool(iwe["H"] <= H_star)))
     return out

@@ -80,6 +80,28 @@ def test_loss_and_gradient_parity(fe):
         off += nw + co
 
 
+def test_loss_and_gradient_parity_128(fe):
+    """The same at training size: a batch of 2 x 128 x 128 (sums over 32768
+    pixels per weight), every parameter's gradient within 1e-3 of the largest
+    and each layer's own gradient within 2e-3 of that layer's largest."""
+    from oracle import cnn
+    net = fe.CNN(seed=11)
+    rng = np.random.default_rng(12)
+    p = (rng.standard_normal(net.num_params) * 0.12).astype(np.float32)
+    net.set_params(p)
+    f, u = _batch(2, 128, 128, 13)
+    loss, g = net.loss_grad(f, u)
+    lr_, gr = cnn.loss_grad(_bf16_weights(p.astype(np.float64)), f, u)
+    assert loss == pytest.approx(lr_, rel=1e-4)
+    assert np.max(np.abs(g - gr)) <= 1e-3 * np.max(np.abs(gr))
+    off = 0
+    for co, ci in cnn.layer_shapes():
+        n = co * ci * 9 + co
+        gl, grl = g[off:off + n], gr[off:off + n]
+        assert np.max(np.abs(gl - grl)) <= 2e-3 * np.max(np.abs(grl)), (co, ci)
+        off += n
+
+
 def test_params_roundtrip_and_training_reduces_loss(fe):
     import torch
     net = fe.CNN(seed=7)
@@ -97,12 +119,12 @@ def test_params_roundtrip_and_training_reduces_loss(fe):
 
 def test_warm_start_gain(fe):
     """Train on solver-generated pairs (96 observations of 96x96, lambda =
-    0.02), then solve 4 held-out 256x256 observations to the same relative
-    energy tolerance from f and from the CNN start.  The warm start must
-    save iterations in total, be taken (H(u0) < H(f)) on at least half of
-    the images, and end at an energy within 1% of the decrease plain iPiano
-    achieves from f (both runs stop on the same relative-change rule, so
-    neither is exactly at the minimum)."""
+    0.02), then solve 4 held-out 256x256 observations from f and from the
+    CNN start to the SAME ENERGY: H* = H_plain + 1e-3 (H(f) - H_plain), with
+    H_plain where plain iPiano meets the relative tolerance 1e-6.  Both runs
+    must reach H* on every image; the warm start must be taken (H(u0) <
+    H(f)) on at least half of the images and need fewer iterations in total
+    (an image that fell back to f runs the same solve as plain)."""
     import torch
     from paper_1404_5344_gb300 import synth, warmstart
     k, th = synth.filter_bank(48, 7, seed=0, theta=0.1)
@@ -116,9 +138,10 @@ def test_warm_start_gain(fe):
     Ft, _ = warmstart.make_observations(4, 256, seed=9000)
     res = warmstart.evaluate(net, [torch.from_numpy(x).cuda() for x in Ft], k, th, tol=1e-6)
     for r in res:
-        assert r["converged_plain"] and r["converged_warm"], r
-        assert r["H_warm"] - r["H_plain"] <= 0.01 * (r["H_f"] - r["H_plain"]), r
+        assert r["converged_plain"], r
+        assert r["reached_plain_eq"] and r["reached_warm_eq"], r
+        assert r["H_plain_eq"] <= r["H_target"] and r["H_warm_eq"] <= r["H_target"], r
         if not r["used_cnn"]:
-            assert r["iters_warm"] == r["iters_plain"], r  # fell back to f: the same solve
+            assert r["iters_warm_eq"] == r["iters_plain_eq"], r  # fell back to f: the same solve
     assert sum(r["used_cnn"] for r in res) >= 2, res
-    assert sum(r["iters_warm"] for r in res) < 0.85 * sum(r["iters_plain"] for r in res), res
+    assert sum(r["iters_warm_eq"] for r in res) < 0.85 * sum(r["iters_plain_eq"] for r in res), res

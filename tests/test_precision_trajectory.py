@@ -1,0 +1,75 @@
+"""Trajectory error of every precision form against the FP64 oracle.
+
+A 128 x 128 textured image (L = 1 speckle) is solved for 150 iPiano
+iterations with lambda = 0.02 (the regime where the filter bank, not the data
+term, shapes the result) by the FP32, TF32 and BF16 forms.  The GPU's accepted
+L_n of every iteration are replayed in the oracle's fixed-L iteration (the
+update rule of Sec. II-C), once with the form's rounded bank (the form's own
+model: the implementation's error) and once with the unrounded FP32 bank (the
+error a user of the form gets against the model with the stated filters).
+Reported and asserted per form: max |u - u_ref| / max |u_ref|, mean |u -
+u_ref| / mean |u_ref|, and the PSNR (peak 255, against the clean image) minus
+the oracle's.  The bounds are those of the single-step parity tests carried
+over 150 iterations (rounded bank), and the model change of rounding the bank
+(unrounded bank), each with a margin over the observed values recorded in
+the design notes.
+"""
+import numpy as np
+import pytest
+
+from rounding import ROUND
+
+pytestmark = pytest.mark.gpu
+
+N_IT = 150
+# (rounded bank: max, mean), (unrounded bank: max, mean), |PSNR delta| dB vs the unrounded oracle
+BOUNDS = {"fp32": ((1e-4, 2e-5), (1e-4, 2e-5), 1e-3),
+          "tf32": ((1e-4, 2e-5), (2e-3, 1e-3), 2e-2),
+          "bf16": ((2e-4, 5e-5), (1e-2, 1e-2), 1e-1)}
+
+
+@pytest.fixture(scope="module")
+def fe():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1404_5344_gb300 import build
+    build.build()
+    from paper_1404_5344_gb300 import fe as fe_mod
+    return fe_mod
+
+
+def _psnr(u, clean):
+    mse = float(np.mean((np.asarray(u, np.float64) - clean) ** 2))
+    return 10.0 * np.log10(255.0 ** 2 / mse)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
+def test_trajectory_against_fp64_oracle(fe, orc, bank48, prec):
+    from paper_1404_5344_gb300 import synth
+    k, th = bank48
+    clean = synth.textured_image(128, 128, seed=41)
+    f = synth.speckle(clean, L=1.0, seed=42)
+    kw = dict(lam=0.02, beta=0.8, L0=1.0, eta=2.0, c2=1e-6, max_backtrack=30)
+    Ls = []
+    with fe.Solver([f], k, th, prec=prec, **kw) as s:
+        for _ in range(N_IT):
+            assert s.step(1) == fe.FE_OK
+            Ls.append(s.info(0)["L"])
+        ug = s.get_u(0).astype(np.float64)
+    prm = orc.params(lam=kw["lam"], beta=kw["beta"], L0=kw["L0"], eta=kw["eta"], c2=kw["c2"], max_iter=1)
+    kq = k if prec == "fp32" else ROUND[prec](k)
+    res = {}
+    for name, bank_ in (("rounded", kq), ("unrounded", k)):
+        ref = orc.ipiano_fixed(f, bank_, th, prm, Ls, f)
+        assert ref["status"] == 0
+        u_ref = ref["u"]
+        res[name] = (float(np.max(np.abs(ug - u_ref)) / np.max(np.abs(u_ref))),
+                     float(np.mean(np.abs(ug - u_ref)) / np.mean(np.abs(u_ref))),
+                     _psnr(ug, clean) - _psnr(u_ref, clean))
+    print("trajectory %s: rounded bank max %.3e mean %.3e dPSNR %.2e; unrounded bank max %.3e mean %.3e "
+          "dPSNR %.2e" % ((prec,) + res["rounded"] + res["unrounded"]))
+    (rmax, rmean), (umax, umean), dps = BOUNDS[prec]
+    assert res["rounded"][0] <= rmax and res["rounded"][1] <= rmean, res
+    assert res["unrounded"][0] <= umax and res["unrounded"][1] <= umean, res
+    assert abs(res["unrounded"][2]) <= dps, res
