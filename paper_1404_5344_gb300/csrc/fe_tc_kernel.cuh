@@ -471,34 +471,47 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
         auto epi2 = [&](int pb) {
             const int row = 4 * pb + lg;
             const int slot = row % HRING;
-            const int a_lo = wg == 0 ? 0 : 4, na = wg == 0 ? 4 : 3;
+            const int a_lo = wg == 0 ? 0 : 4;
             float s8[4][8];
+            // warpgroup 1 has 3 window rows; it loads a 4th (columns 64 + 49
+            // .. 64 + 56: the zero taps of the padded bank, S = 0 there) so
+            // that both warpgroups run the same unconditional pair loop
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (j < na) tc::tmem_ld8(taddr + lane_base + (uint32_t)(64 + KS * (a_lo + j)), s8[j]);
+            for (int j = 0; j < 4; ++j) tc::tmem_ld8(taddr + lane_base + (uint32_t)(64 + KS * (a_lo + j)), s8[j]);
             tc::tmem_ld_wait();
             // two window rows at a time: the 7 shuffled values of rows j and
             // j + 1 are summed as packed pairs (the sum order per row is that
-            // of the scalar loop)
+            // of a scalar loop)
+            uint64_t h2[2] = {0ull, 0ull};
+            if (edge_x) {
+                // border tile: a source lane outside the warp contributes 0
 #pragma unroll
-            for (int j = 0; j < 4; j += 2) {
-                if (j >= na) break;
-                const bool two = j + 1 < na;  // warpgroup 1 has 3 rows
-                uint64_t h2 = 0ull;
+                for (int j = 0; j < 4; j += 2)
 #pragma unroll
-                for (int bb = 0; bb < KS; ++bb) {
-                    const int src = lane - 3 + bb;
-                    float v0 = __shfl_sync(0xffffffffu, s8[j][bb], src & 31);
-                    float v1 = two ? __shfl_sync(0xffffffffu, s8[j + 1][bb], src & 31) : 0.0f;
-                    // interior tile: lanes 3..28 (the only ones used) have all sources in the warp
-                    if (edge_x && !(src >= 0 && src < 32)) v0 = v1 = 0.0f;
-                    h2 = f2_add(h2, f2_pack(v0, v1));
-                }
-                float h0, h1;
-                f2_unpack(h2, h0, h1);
-                sH[(slot * KS + a_lo + j) * 32 + lane] = h0;
-                if (two) sH[(slot * KS + a_lo + j + 1) * 32 + lane] = h1;
+                    for (int bb = 0; bb < KS; ++bb) {
+                        const int src = lane - 3 + bb;
+                        const bool ok = src >= 0 && src < 32;
+                        const float v0 = __shfl_sync(0xffffffffu, s8[j][bb], src & 31);
+                        const float v1 = __shfl_sync(0xffffffffu, s8[j + 1][bb], src & 31);
+                        h2[j >> 1] = f2_add(h2[j >> 1], f2_pack(ok ? v0 : 0.0f, ok ? v1 : 0.0f));
+                    }
+            } else {
+                // interior tile: lanes 3..28 (the only ones used) have all sources in the warp
+#pragma unroll
+                for (int j = 0; j < 4; j += 2)
+#pragma unroll
+                    for (int bb = 0; bb < KS; ++bb)
+                        h2[j >> 1] = f2_add(h2[j >> 1], f2_pack(__shfl_sync(0xffffffffu, s8[j][bb], (lane - 3 + bb) & 31),
+                                                                __shfl_sync(0xffffffffu, s8[j + 1][bb], (lane - 3 + bb) & 31)));
             }
+            float h[4];
+            f2_unpack(h2[0], h[0], h[1]);
+            f2_unpack(h2[1], h[2], h[3]);
+            float *hrow = sH + (slot * KS + a_lo) * 32 + lane;
+            hrow[0] = h[0];
+            hrow[32] = h[1];
+            hrow[64] = h[2];
+            if (wg == 0) hrow[96] = h[3];
         };
         // vertical col2im of the ext rows whose 7 source rows are complete
         // (one warp per row, lane = column).  BF16: the row goes to sG.  TF32:
@@ -509,12 +522,20 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
         auto emit = [&](int ty) {
             if (ty < -3 || ty >= TY + 3) return;
             float g = 0.f;
-            int s = ((ty % HRING) + HRING) % HRING;
+            int s = (ty + HRING) % HRING;  // ty >= -3
+            if (ty >= 0 && ty + KS <= R3Y) {  // all 7 source rows in the region (warp-uniform)
 #pragma unroll
-            for (int aa = 0; aa < KS; ++aa) {
-                const int srow = ty + aa;
-                if (srow >= 0 && srow < R3Y) g += sH[(s * KS + aa) * 32 + lane];
-                s = s + 1 == HRING ? 0 : s + 1;
+                for (int aa = 0; aa < KS; ++aa) {
+                    g += sH[(s * KS + aa) * 32 + lane];
+                    s = s + 1 == HRING ? 0 : s + 1;
+                }
+            } else {
+#pragma unroll
+                for (int aa = 0; aa < KS; ++aa) {
+                    const int srow = ty + aa;
+                    if (srow >= 0 && srow < R3Y) g += sH[(s * KS + aa) * 32 + lane];
+                    s = s + 1 == HRING ? 0 : s + 1;
+                }
             }
             if constexpr (C::FULL_G) {
                 sG[(ty + 3) * 32 + lane] = g;
@@ -581,9 +602,11 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
                         ps2 = f2_fma(thp[k], f2_pack(lg2_ftz(q0), lg2_ftz(q1)), ps2);
                     }
                 }
-                if (!inimg) {
+                if (!all_in) {  // tile-uniform: only border tiles have halo pixels off the image
+                    if (!inimg) {
 #pragma unroll
-                    for (int i = 0; i < 12; ++i) r2[i] = 0ull;
+                        for (int i = 0; i < 12; ++i) r2[i] = 0ull;
+                    }
                 }
                 float pa, pb;
                 f2_unpack(ps2, pa, pb);
