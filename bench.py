@@ -50,10 +50,8 @@ FLOP_PER_PIXEL_TRIAL = 2 * 48 * 49 * 2  # forward + adjoint bank, 2 flop per MAC
 # launch with every image active, per pixel, from one ncu capture of the
 # current kernels on 24 x 512^2 (profiles/*_trial_24x512.md); None where no
 # capture of the current kernel exists
-TRAFFIC_PER_PIXEL = {("fp32", "variant"): 137.742848e6 / 6291456,
-                     ("bf16", "variant"): 128.764928e6 / 6291456,
-                     ("tf32", "variant"): 128.206592e6 / 6291456,
-                     ("fp32", "combined"): 137.161984e6 / 6291456}
+TRAFFIC_PER_PIXEL = {("fp32", "variant"): 137.891584e6 / 6291456,
+                     ("bf16", "variant"): 129.373440e6 / 6291456}
 METRIC = "Mpixel*iter/s of fused iPiano step"
 
 
