@@ -51,7 +51,9 @@ FLOP_PER_PIXEL_TRIAL = 2 * 48 * 49 * 2  # forward + adjoint bank, 2 flop per MAC
 # current kernels on 24 x 512^2 (profiles/*_trial_24x512.md); None where no
 # capture of the current kernel exists
 TRAFFIC_PER_PIXEL = {("fp32", "variant"): 137.891584e6 / 6291456,
-                     ("bf16", "variant"): 129.373440e6 / 6291456}
+                     ("bf16", "variant"): 129.373440e6 / 6291456,
+                     ("tf32", "variant"): 127.864576e6 / 6291456,
+                     ("fp32", "combined"): 137.784832e6 / 6291456}
 METRIC = "Mpixel*iter/s of fused iPiano step"
 
 
