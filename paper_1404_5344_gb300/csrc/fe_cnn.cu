@@ -14,6 +14,21 @@
 // the input it also serves as the data gradient, given transposed and
 // flipped weights), weight/bias gradient with per-block partial sums and a
 // fixed-order reduction (deterministic), loss + output gradient, Adam.
+//
+// The 32 -> 32 convolutions (three in the forward pass, three data
+// gradients in the backward pass) run on the tensor cores as implicit GEMMs
+// (conv32_tc_kernel): a CTA computes 16 x 8 output pixels (M = 128) times
+// 32 output channels (N = 32) in tensor memory; K = 9 taps x 32 input
+// channels, each activation carried as a BF16 hi + lo pair (K doubles), so
+// the products of the BF16 weights with the FP32 activations keep about 16
+// bits and the sums are FP32.  No im2col copy is made: the 18 x 10 halo
+// tile is stored channel-chunk-major in shared memory (chunk of 8 channels,
+// then pixel, 16 bytes per pixel and chunk), so the A operand of tap (dy,
+// dx) is the same tile read from a descriptor start shifted by (dy x 10 +
+// dx) pixels, its 8-pixel core-matrix groups (one output row each) 160
+// bytes apart and its two channel chunks of one MMA 2880 bytes apart.  The
+// 1 -> 32 and 32 -> 1 layers (K = 9 or N = 1) stay on the CUDA cores, as
+// do the weight gradients.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -25,6 +40,8 @@
 #include <vector>
 
 #include "fe_internal.cuh"
+#include "fe_tile_common.cuh"
+#include "tc_ptx.cuh"
 
 namespace fe {
 namespace {
@@ -82,6 +99,166 @@ __global__ void __launch_bounds__(NT) conv3x3_kernel(const float *__restrict__ x
         for (int o = 0; o < COUT; ++o)
             y[((size_t)b * COUT + o) * plane + (size_t)yy * W + xx] = RELU ? fmaxf(acc[o], 0.f) : acc[o];
     }
+}
+
+// ---- tensor-core 3x3 convolution, 32 -> 32 channels --------------------------
+constexpr int TC_OY = 16, TC_OX = 8;                  // output tile: 128 pixels (M)
+constexpr int TC_IY = TC_OY + 2, TC_IX = TC_OX + 2;   // 18 x 10 halo tile
+constexpr int TC_NPX = TC_IY * TC_IX;                 // 180 pixels
+constexpr int TC_CHUNK = TC_NPX * 16;                 // one 8-channel chunk of the tile: 2880 bytes
+constexpr int TC_PLANE = 4 * TC_CHUNK;                // 32 channels (hi or lo): 11520 bytes
+constexpr int TC_A_BYTES = 2 * TC_PLANE;              // hi, lo
+constexpr int TC_B_TAP = CW * CW * 2;                 // one tap's B operand: N 32 x K 32 BF16
+constexpr int TC_B_BYTES = 9 * TC_B_TAP;
+constexpr int TC_SMEM = TC_A_BYTES + TC_B_BYTES;      // 41472 bytes
+static_assert(TC_A_BYTES % 128 == 0, "B operand alignment");
+
+// B operands of the nine taps in the K-major core-matrix byte layout:
+// (tap t, output channel n, input channel k) at t * 2048 + (n / 8) * 512 +
+// (k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2, from a [CIN][9][COUT] weight
+// array of BF16-valued floats (the forward layout, or the transposed and
+// flipped one of the data gradient).
+__global__ void cnn_tc_weights_kernel(const float *__restrict__ w, unsigned short *__restrict__ wq) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= CW * 9 * CW) return;
+    const int k = e / (9 * CW), t = (e / CW) % 9, n = e % CW;
+    const int off = t * TC_B_TAP + (n >> 3) * 512 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+    wq[off / 2] = (unsigned short)(__float_as_uint(w[e]) >> 16);  // exact: w is BF16-valued
+}
+
+// y[b][o][p] = act(bias[o] + sum_c sum_tap w[c][tap][o] x'[b][c][p + off(tap)]),
+// x' = x or x * (mask > 0), zero padding; the convolution of conv3x3_kernel
+// for CIN = COUT = 32, on the tensor cores.  Persistent: a CTA loads the B
+// operands and allocates tensor memory once, then runs the 16 x 8 output
+// tiles blockIdx.x, blockIdx.x + gridDim.x, ... of all B images.  128
+// threads: thread m holds output pixel (m / 8, m % 8) of a tile in TMEM lane
+// m.  A completion wait that runs out sets *err and the CTA stops.
+template <bool RELU>
+__global__ void __launch_bounds__(128) conv32_tc_kernel(const float *__restrict__ x, const float *__restrict__ mask,
+                                                        const unsigned short *__restrict__ wq,
+                                                        const float *__restrict__ bias, float *__restrict__ y, int B,
+                                                        int H, int W, int *err) {
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    unsigned char *sA = tsm;                // [hi | lo][chunk][pixel][8 channels] BF16
+    unsigned char *sB = tsm + TC_A_BYTES;   // [tap] B operands
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tbase;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const size_t plane = (size_t)H * W;
+    const int tiles_x = (W + TC_OX - 1) / TC_OX, tiles_img = tiles_x * ((H + TC_OY - 1) / TC_OY);
+    const int ntiles = tiles_img * B;
+    for (int j = tid; j < TC_B_BYTES / 16; j += 128)
+        reinterpret_cast<uint4 *>(sB)[j] = __ldg(reinterpret_cast<const uint4 *>(wq) + j);
+    if (tid == 0) tc::mbar_init(&bar, 1);
+    if (warp == 0) tc::tmem_alloc(&tbase, 32);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = tbase;
+    float bv[CW];
+#pragma unroll
+    for (int o = 0; o < CW; ++o) bv[o] = bias ? __ldg(bias + o) : 0.f;
+    uint32_t phase = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int b = tile / tiles_img, tr = tile - b * tiles_img;
+        const int ty0 = (tr / tiles_x) * TC_OY, tx0 = (tr % tiles_x) * TC_OX;
+        // halo tile: one task per (pixel, chunk of 8 channels): hi and lo runs;
+        // a thread's (up to) 6 tasks issue all their global loads first, so
+        // that their latencies overlap, then convert and store
+        constexpr int NTASK = (4 * TC_NPX + 127) / 128;
+        float v[NTASK][8];
+#pragma unroll
+        for (int k = 0; k < NTASK; ++k) {
+            const int task = tid + 128 * k;
+            const int q = task / TC_NPX, px = task - q * TC_NPX;
+            const int iy = px / TC_IX, ix = px - iy * TC_IX;
+            const int yy = ty0 - 1 + iy, xx = tx0 - 1 + ix;
+            const bool in = task < 4 * TC_NPX && yy >= 0 && yy < H && xx >= 0 && xx < W;
+            const size_t o0 = ((size_t)b * CW + q * 8) * plane + (size_t)yy * W + xx;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) v[k][c] = in ? __ldg(x + o0 + c * plane) : 0.f;
+            if (mask) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (in && !(__ldg(mask + o0 + c * plane) > 0.f)) v[k][c] = 0.f;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NTASK; ++k) {
+            const int task = tid + 128 * k;
+            if (task >= 4 * TC_NPX) break;
+            const int q = task / TC_NPX, px = task - q * TC_NPX;
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                h[j] = bf16x2_rn(v[k][2 * j], v[k][2 * j + 1]);
+                l[j] = bf16x2_rn(v[k][2 * j] - __uint_as_float(h[j] << 16),
+                                 v[k][2 * j + 1] - __uint_as_float(h[j] & 0xffff0000u));
+            }
+            unsigned char *dst = sA + q * TC_CHUNK + px * 16;
+            *reinterpret_cast<uint4 *>(dst) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4 *>(dst + TC_PLANE) = make_uint4(l[0], l[1], l[2], l[3]);
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {
+            constexpr uint32_t idesc = tc::make_idesc(1, 128, CW);
+            const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+            uint32_t acc = 0u;
+#pragma unroll 1
+            for (int t = 0; t < 9; ++t) {
+                const uint32_t shift = (uint32_t)(((t / 3) * TC_IX + (t % 3)) * 16);
+#pragma unroll
+                for (int pl = 0; pl < 2; ++pl)
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint64_t ad =
+                            tc::make_smem_desc(a0 + pl * TC_PLANE + 2 * ks * TC_CHUNK + shift, TC_CHUNK, TC_IX * 16);
+                        const uint64_t bd = tc::make_smem_desc(b0 + t * TC_B_TAP + ks * 256, 128, 512);
+                        tc::mma<1>(taddr, ad, bd, idesc, acc);
+                        acc = 1u;
+                    }
+            }
+            tc::mma_commit(&bar);
+        }
+        bool ok = tc::mbar_wait(&bar, phase);
+        if (!ok) {
+            if (tid == 0) atomicExch(err, 1);
+            ok = tc::mbar_wait(&bar, phase);  // a second bounded chance for MMAs in flight
+        }
+        phase ^= 1u;
+        tc::fence_after_sync();
+        const bool wok = __all_sync(0xffffffffu, ok);
+        if (wok) {
+            float a[CW];
+#pragma unroll
+            for (int j = 0; j < CW / 8; ++j) {
+                float t8[8];
+                tc::tmem_ld8(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(8 * j), t8);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) a[8 * j + k] = t8[k];
+            }
+            tc::tmem_ld_wait();
+            const int oy = ty0 + tid / TC_OX, ox = tx0 + tid % TC_OX;
+            if (oy < H && ox < W) {
+#pragma unroll
+                for (int o = 0; o < CW; ++o) {
+                    const float r = a[o] + bv[o];
+                    y[((size_t)b * CW + o) * plane + (size_t)oy * W + ox] = RELU ? fmaxf(r, 0.f) : r;
+                }
+            }
+        }
+        // the next tile rewrites the operands and the accumulator
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (!__syncthreads_and(ok)) break;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, 32);
 }
 
 // Per-block partial sums of the weight and bias gradients of one layer:
@@ -200,6 +377,10 @@ struct fe_cnn {
     float *p = nullptr, *pq = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
     unsigned char *is_w = nullptr;
     float *wl[DEPTH] = {}, *wt[DEPTH] = {};  // conv layouts [CIN][9][COUT] and transposed-flipped [COUT][9][CIN]
+    // tensor-core B operands of the 32 -> 32 layers (1..3): forward and data gradient
+    unsigned short *wqf[DEPTH] = {}, *wqt[DEPTH] = {};
+    int *tc_err = nullptr;  // set when a tensor-core completion wait runs out
+    int sms = 1;            // multiprocessors of the device (grid of the persistent convolutions)
     float *act = nullptr, *dact = nullptr, *part = nullptr, *tmp = nullptr;
     double *lpart = nullptr;
     size_t cap_pix = 0, cap_part = 0;
@@ -238,8 +419,32 @@ fe_status refresh_layouts(fe_cnn *n) {
         const int ne = cin_of(l) * cout_of(l) * 9;
         layout_kernel<<<(ne + 255) / 256, 256, 0, n->s>>>(n->pq, n->woff[l], cin_of(l), cout_of(l), n->wl[l], n->wt[l]);
         CNN_CUDA(n, cudaGetLastError());
+        if (cin_of(l) == CW && cout_of(l) == CW) {
+            cnn_tc_weights_kernel<<<(CW * 9 * CW + 255) / 256, 256, 0, n->s>>>(n->wl[l], n->wqf[l]);
+            cnn_tc_weights_kernel<<<(CW * 9 * CW + 255) / 256, 256, 0, n->s>>>(n->wt[l], n->wqt[l]);
+            CNN_CUDA(n, cudaGetLastError());
+        }
     }
     return FE_OK;
+}
+
+// A 32 -> 32 convolution on the tensor cores (conv32_tc_kernel).
+template <bool RELU>
+void conv32(const fe_cnn *n, const float *x, const float *mask, const unsigned short *wq, const float *bias, float *y,
+            int B, int H, int W) {
+    // persistent: four CTAs per SM (41.5 KB of shared memory each), every
+    // CTA several tiles
+    const int tiles = ((W + TC_OX - 1) / TC_OX) * ((H + TC_OY - 1) / TC_OY) * B;
+    const int grid = std::min(tiles, 4 * n->sms);
+    conv32_tc_kernel<RELU><<<grid, 128, TC_SMEM, n->s>>>(x, mask, wq, bias, y, B, H, W, n->tc_err);
+}
+
+// FE_ETIMEOUT if a tensor-core completion wait ran out since creation
+// (the stream has been synchronised by the caller).
+fe_status check_tc(fe_cnn *n) {
+    int e = 0;
+    CNN_CUDA(n, cudaMemcpy(&e, n->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    return e ? cnn_err(n, FE_ETIMEOUT, "a tensor-core completion wait of the CNN ran out") : FE_OK;
 }
 
 fe_status ensure_capacity(fe_cnn *n, size_t pix, size_t parts) {
@@ -285,6 +490,8 @@ cudaError_t cnn_prepare() {
     FE_SMEM((wgrad_kernel<CW, 1, false>), (wgrad_smem<CW, 1>()));
     FE_SMEM((wgrad_kernel<CW, CW, true>), (wgrad_smem<CW, CW>()));
     FE_SMEM((wgrad_kernel<1, CW, true>), (wgrad_smem<1, CW>()));
+    FE_SMEM((conv32_tc_kernel<true>), TC_SMEM);
+    FE_SMEM((conv32_tc_kernel<false>), TC_SMEM);
 #undef FE_SMEM
     return e;
 }
@@ -299,9 +506,9 @@ fe_status forward(fe_cnn *n, const float *f_dev, int B, int H, int W) {
     const size_t pix = (size_t)B * H * W;
     prep_input_kernel<<<(unsigned)std::min<size_t>((pix + 255) / 256, 4096), 256, 0, n->s>>>(f_dev, act_ptr(n, -1, pix), pix);
     conv<1, CW, true>(n, act_ptr(n, -1, pix), nullptr, n->wl[0], n->pq + n->boff[0], act_ptr(n, 0, pix), B, H, W);
-    conv<CW, CW, true>(n, act_ptr(n, 0, pix), nullptr, n->wl[1], n->pq + n->boff[1], act_ptr(n, 1, pix), B, H, W);
-    conv<CW, CW, true>(n, act_ptr(n, 1, pix), nullptr, n->wl[2], n->pq + n->boff[2], act_ptr(n, 2, pix), B, H, W);
-    conv<CW, CW, true>(n, act_ptr(n, 2, pix), nullptr, n->wl[3], n->pq + n->boff[3], act_ptr(n, 3, pix), B, H, W);
+    conv32<true>(n, act_ptr(n, 0, pix), nullptr, n->wqf[1], n->pq + n->boff[1], act_ptr(n, 1, pix), B, H, W);
+    conv32<true>(n, act_ptr(n, 1, pix), nullptr, n->wqf[2], n->pq + n->boff[2], act_ptr(n, 2, pix), B, H, W);
+    conv32<true>(n, act_ptr(n, 2, pix), nullptr, n->wqf[3], n->pq + n->boff[3], act_ptr(n, 3, pix), B, H, W);
     conv<CW, 1, false>(n, act_ptr(n, 3, pix), nullptr, n->wl[4], n->pq + n->boff[4], act_ptr(n, 4, pix), B, H, W);
     CNN_CUDA(n, cudaGetLastError());
     return FE_OK;
@@ -337,13 +544,13 @@ fe_status loss_grad(fe_cnn *n, const float *f_dev, const float *ut_dev, int B, i
     std::swap(g_in, g_out);
     // g_in = d loss / d act3 (post-ReLU)
     if ((st = wgrad<CW, CW, true>(n, act_ptr(n, 2, pix), g_in, act_ptr(n, 3, pix), B, H, W, 3)) != FE_OK) return st;
-    conv<CW, CW, false>(n, g_in, act_ptr(n, 3, pix), n->wt[3], nullptr, g_out, B, H, W);
+    conv32<false>(n, g_in, act_ptr(n, 3, pix), n->wqt[3], nullptr, g_out, B, H, W);
     std::swap(g_in, g_out);
     if ((st = wgrad<CW, CW, true>(n, act_ptr(n, 1, pix), g_in, act_ptr(n, 2, pix), B, H, W, 2)) != FE_OK) return st;
-    conv<CW, CW, false>(n, g_in, act_ptr(n, 2, pix), n->wt[2], nullptr, g_out, B, H, W);
+    conv32<false>(n, g_in, act_ptr(n, 2, pix), n->wqt[2], nullptr, g_out, B, H, W);
     std::swap(g_in, g_out);
     if ((st = wgrad<CW, CW, true>(n, act_ptr(n, 0, pix), g_in, act_ptr(n, 1, pix), B, H, W, 1)) != FE_OK) return st;
-    conv<CW, CW, false>(n, g_in, act_ptr(n, 1, pix), n->wt[1], nullptr, g_out, B, H, W);
+    conv32<false>(n, g_in, act_ptr(n, 1, pix), n->wqt[1], nullptr, g_out, B, H, W);
     std::swap(g_in, g_out);
     if ((st = wgrad<1, CW, true>(n, act_ptr(n, -1, pix), g_in, act_ptr(n, 0, pix), B, H, W, 0)) != FE_OK) return st;
     CNN_CUDA(n, cudaGetLastError());
@@ -353,7 +560,7 @@ fe_status loss_grad(fe_cnn *n, const float *f_dev, const float *ut_dev, int B, i
     double s = 0.0;
     for (double v : lp) s += v;
     if (loss) *loss = s / (double)pix;
-    return FE_OK;
+    return check_tc(n);
 }
 
 const float *stage(fe_cnn *n, const float *src, size_t count, int slot, fe_status *st) {
@@ -411,8 +618,18 @@ fe_status fe_cnn_create(fe_cnn **out, unsigned long long seed, void *stream) {
     for (int l = 0; l < DEPTH; ++l) {
         const size_t ne = (size_t)cin_of(l) * cout_of(l) * 9;
         if (cudaMalloc(&n->wl[l], sizeof(float) * ne) || cudaMalloc(&n->wt[l], sizeof(float) * ne)) return fail(FE_ENOMEM);
+        if (cin_of(l) == CW && cout_of(l) == CW &&
+            (cudaMalloc(&n->wqf[l], TC_B_BYTES) || cudaMalloc(&n->wqt[l], TC_B_BYTES)))
+            return fail(FE_ENOMEM);
     }
-    if (cudaMemcpy(n->is_w, isw.data(), off, cudaMemcpyHostToDevice) || cudaMemset(n->m, 0, sizeof(float) * off) ||
+    if (cudaMalloc(&n->tc_err, sizeof(int))) return fail(FE_ENOMEM);
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&n->sms, cudaDevAttrMultiProcessorCount, dev))
+            return fail(FE_ECUDA);
+    }
+    if (cudaMemset(n->tc_err, 0, sizeof(int)) ||
+        cudaMemcpy(n->is_w, isw.data(), off, cudaMemcpyHostToDevice) || cudaMemset(n->m, 0, sizeof(float) * off) ||
         cudaMemset(n->v, 0, sizeof(float) * off) || cudaMemset(n->g, 0, sizeof(float) * off))
         return fail(FE_ECUDA);
     *out = n;
@@ -436,12 +653,15 @@ void fe_cnn_destroy(fe_cnn *n) {
     for (int l = 0; l < DEPTH; ++l) {
         cudaFree(n->wl[l]);
         cudaFree(n->wt[l]);
+        cudaFree(n->wqf[l]);
+        cudaFree(n->wqt[l]);
     }
     cudaFree(n->act);
     cudaFree(n->dact);
     cudaFree(n->part);
     cudaFree(n->tmp);
     cudaFree(n->lpart);
+    cudaFree(n->tc_err);
     delete n;
 }
 
@@ -488,7 +708,7 @@ fe_status fe_cnn_forward(fe_cnn *n, const float *f, int B, int H, int W, float *
     }
     if (d) CNN_CUDA(n, cudaMemcpyAsync(d, dout, sizeof(float) * pix, cudaMemcpyDefault, n->s));
     CNN_CUDA(n, cudaStreamSynchronize(n->s));
-    return FE_OK;
+    return check_tc(n);
 }
 
 fe_status fe_cnn_loss_grad(fe_cnn *n, const float *f, const float *u_target, int B, int H, int W, double *loss,

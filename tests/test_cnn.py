@@ -3,8 +3,11 @@ the FP64 reference (oracle/cnn.py) given the same BF16-rounded weights, and
 what the trained network gains over plain iPiano.
 
 Tolerances: each activation is an FP32 sum of at most 288 products of BF16
-weights and FP32 values, so the network output differs from the FP64
-reference by ~1e-6 relative per layer; 1e-4 of max|d| covers five layers.
+weights and activations; the 32 -> 32 layers run on the tensor cores with
+each activation carried as a BF16 hi + lo pair (about 2^-17 relative), so
+the network output differs from the FP64 reference by ~1e-5 relative per
+layer; 1e-4 of max|d| covers five layers, and u0 = f e^d inherits that
+absolute error of d as a relative error.
 Gradients are FP32 sums over all pixels of the batch (per-block partials
 reduced in FP64): 1e-3 of max|grad| covers the accumulation-order
 differences of sums of ~1e3 terms of both signs.
@@ -58,7 +61,7 @@ def test_forward_parity(fe):
     for b in range(2):
         dr, _ = cnn.forward(pr, f[b])
         assert np.max(np.abs(d[b] - dr)) <= 1e-4 * np.max(np.abs(dr))
-        np.testing.assert_allclose(u0[b], f[b] * np.exp(dr), rtol=2e-5)
+        np.testing.assert_allclose(u0[b], f[b] * np.exp(dr), rtol=1e-4 * np.max(np.abs(dr)) + 1e-6)
 
 
 def test_loss_and_gradient_parity(fe):
