@@ -77,13 +77,14 @@ def parse():
     ap.add_argument("--no-peaks", action="store_true", help="skip the peak-rate microbenchmarks")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="paper",
-                    choices=["paper", "batch64", "warmstart", "precision", "quality"],
+                    choices=["paper", "batch64", "warmstart", "precision", "quality", "cnn"],
                     help="paper: the Mpixel*iter/s workload above; batch64: time to the energy "
                          "tolerance of 64 uneven images in one context vs 64 sequential FP32 solves; "
                          "warmstart: solver-generated pairs, CNN training, then time to tolerance "
                          "from the CNN start vs from f on 512x512 images; precision: one 4096x4096 L=1 "
                          "image in FP32, TF32 and BF16, errors against FP32 and the FP64 oracle; quality: "
-                         "PSNR / SSIM of despeckled images over a sweep of the data weights")
+                         "PSNR / SSIM of despeckled images over a sweep of the data weights; cnn: inference "
+                         "and training-step time of the warm-start network")
     ap.add_argument("--prec-size", type=int, default=4096, help="precision: image side")
     ap.add_argument("--prec-iters", type=int, default=200, help="precision: iterations per form")
     ap.add_argument("--ws-pairs", type=int, default=20000, help="warmstart: 256x256 training pairs")
@@ -610,6 +611,50 @@ def precision_trajectory(fe, orc, stream, args, S=512, n_it=200):
     return out
 
 
+def run_cnn(args):
+    """The warm-start network alone (fe_cnn_*): inference u0 = f exp(CNN(log f))
+    on one 512x512 observation and one Adam training step on 32 crops of
+    128x128, each the mean of args.steps calls after args.warmup, CUDA events
+    on the network's stream.  Seeded observations in [15, 240]; the targets of
+    the training step are 1.01 f (the step's cost does not depend on them)."""
+    import torch
+    from paper_1404_5344_gb300 import build
+    build.build()
+    from paper_1404_5344_gb300 import fe
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.Stream()
+    net = fe.CNN(seed=1, stream=stream)
+    rng = np.random.default_rng(0)
+    f = torch.from_numpy(rng.uniform(15, 240, (512, 512)).astype(np.float32)).cuda()
+    fb = torch.from_numpy(rng.uniform(15, 240, (32, 128, 128)).astype(np.float32)).cuda()
+    ub = fb * 1.01
+    u0 = torch.empty_like(f)
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    with torch.cuda.stream(stream):
+        t_inf = timed(lambda: net.forward(f, u0=u0))
+        t_train = timed(lambda: net.train_step(fb, ub, 1e-4))
+    line = {"metric": "warm-start CNN inference time per 512x512 observation", "value": round(t_inf, 4), "unit": "ms",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "vs_baseline": None, "dtype": "bf16 weights, f32 activations", "data": "synthetic",
+            "config": {"workload": "5-layer 3x3 CNN 1-32-32-32-32-1; inference on one 512x512 observation, one "
+                                   "Adam step on 32 crops of 128x128"},
+            "train_step_ms": round(t_train, 4)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # the paper's (lambda1, lambda2) of the combined model per number of looks (Sec. III-B)
 PAPER_LAMBDAS = {1: (160.0, 0.004), 3: (310.0, 0.008), 8: (550.0, 0.02)}
 
@@ -807,6 +852,8 @@ def main():
         return run_precision(args)
     if args.workload == "quality":
         return run_quality(args)
+    if args.workload == "cnn":
+        return run_cnn(args)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))

@@ -308,6 +308,81 @@ __global__ void __launch_bounds__(NT) wgrad_kernel(const float *__restrict__ x, 
     }
 }
 
+// The same partial sums for CIN = COUT = 32, register-blocked: 288 threads,
+// each accumulating 2 blocks of 4 output x 4 input channels of one tap over
+// the tile's 256 pixels (8 shared loads per 16 FMAs instead of 2 per FMA);
+// the input planes are padded to 325 floats so that the 8 input-channel
+// blocks a warp reads fall on different banks.  Output layout as above.
+constexpr int WG32_NT = 288, WG32_PL = (TS + 2) * (TS + 2) + 1;
+template <bool RELU>
+__global__ void __launch_bounds__(WG32_NT) wgrad32_kernel(const float *__restrict__ x, const float *__restrict__ dy,
+                                                          const float *__restrict__ yout, float *__restrict__ part,
+                                                          int H, int W) {
+    extern __shared__ __align__(16) float wsm[];
+    float *sg = wsm;                    // [32][256]
+    float *sx = wsm + CW * TS * TS;     // [32][WG32_PL]
+    const int b = blockIdx.z, tx0 = blockIdx.x * TS, ty0 = blockIdx.y * TS;
+    const int tid = threadIdx.x;
+    const size_t plane = (size_t)H * W;
+    for (int j = tid; j < CW * (TS + 2) * (TS + 2); j += WG32_NT) {
+        const int c = j / ((TS + 2) * (TS + 2)), r = j % ((TS + 2) * (TS + 2));
+        const int yy = ty0 - 1 + r / (TS + 2), xx = tx0 - 1 + r % (TS + 2);
+        sx[c * WG32_PL + r] =
+            (yy >= 0 && yy < H && xx >= 0 && xx < W) ? x[((size_t)b * CW + c) * plane + (size_t)yy * W + xx] : 0.f;
+    }
+    for (int j = tid; j < CW * TS * TS; j += WG32_NT) {
+        const int o = j / (TS * TS), r = j % (TS * TS);
+        const int yy = ty0 + r / TS, xx = tx0 + r % TS;
+        float g = 0.f;
+        if (yy < H && xx < W) {
+            const size_t idx = ((size_t)b * CW + o) * plane + (size_t)yy * W + xx;
+            g = dy[idx];
+            if (RELU && !(yout[idx] > 0.f)) g = 0.f;
+        }
+        sg[j] = g;
+    }
+    __syncthreads();
+    constexpr int nw = CW * CW * 9;
+    float *out = part + (size_t)((blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (nw + CW);
+#pragma unroll 1
+    for (int task = tid; task < 9 * 64; task += WG32_NT) {
+        const int t = task >> 6, ob = (task >> 3) & 7, cb = task & 7;
+        const int dy0 = t / 3, dx0 = t % 3;
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+        const float *gp = sg + (ob * 4) * (TS * TS);
+        const float *xp = sx + (cb * 4) * WG32_PL + dy0 * (TS + 2) + dx0;
+#pragma unroll 1
+        for (int ry = 0; ry < TS; ++ry) {
+#pragma unroll 4
+            for (int rx = 0; rx < TS; ++rx) {
+                const int r = ry * TS + rx, q = ry * (TS + 2) + rx;
+                float gv[4], xv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) gv[i] = gp[i * (TS * TS) + r];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) xv[j] = xp[j * WG32_PL + q];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(gv[i], xv[j], acc[i][j]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) out[(ob * 4 + i) * CW * 9 + (cb * 4 + j) * 9 + t] = acc[i][j];
+    }
+    if (tid < CW) {
+        float sb = 0.f;
+        for (int r = 0; r < TS * TS; ++r) sb += sg[tid * (TS * TS) + r];
+        out[nw + tid] = sb;
+    }
+}
+
 // Fixed-order reduction of per-block partials: out[e] = sum_k part[k][e].
 __global__ void reduce_parts_kernel(const float *__restrict__ part, int nblocks, int n, float *__restrict__ out) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -471,6 +546,8 @@ constexpr size_t conv_smem() { return sizeof(float) * ((size_t)CIN * 9 * COUT + 
 template <int CIN, int COUT>
 constexpr size_t wgrad_smem() { return sizeof(float) * ((size_t)COUT * TS * TS + (size_t)CIN * (TS + 2) * (TS + 2)); }
 
+constexpr size_t wgrad32_smem() { return sizeof(float) * ((size_t)CW * TS * TS + (size_t)CW * WG32_PL); }
+
 template <int CIN, int COUT, bool RELU>
 void conv(const fe_cnn *n, const float *x, const float *mask, const float *w, const float *bias, float *y, int B, int H,
           int W) {
@@ -491,6 +568,7 @@ cudaError_t cnn_prepare() {
     FE_SMEM((wgrad_kernel<CW, CW, true>), (wgrad_smem<CW, CW>()));
     FE_SMEM((wgrad_kernel<1, CW, true>), (wgrad_smem<1, CW>()));
     FE_SMEM((conv32_tc_kernel<true>), TC_SMEM);
+    FE_SMEM((wgrad32_kernel<true>), wgrad32_smem());
     FE_SMEM((conv32_tc_kernel<false>), TC_SMEM);
 #undef FE_SMEM
     return e;
@@ -518,7 +596,10 @@ template <int CIN, int COUT, bool RELU>
 fe_status wgrad(fe_cnn *n, const float *x, const float *dy, const float *y, int B, int H, int W, int layer) {
     const dim3 grid((W + TS - 1) / TS, (H + TS - 1) / TS, B);
     const int nb = grid.x * grid.y * grid.z, ne = COUT * CIN * 9 + COUT;
-    wgrad_kernel<CIN, COUT, RELU><<<grid, NT, wgrad_smem<CIN, COUT>(), n->s>>>(x, dy, y, n->part, H, W);
+    if constexpr (CIN == CW && COUT == CW)
+        wgrad32_kernel<RELU><<<grid, WG32_NT, wgrad32_smem(), n->s>>>(x, dy, y, n->part, H, W);
+    else
+        wgrad_kernel<CIN, COUT, RELU><<<grid, NT, wgrad_smem<CIN, COUT>(), n->s>>>(x, dy, y, n->part, H, W);
     // weights then bias of this layer are contiguous in the parameter vector
     reduce_parts_kernel<<<(ne + 255) / 256, 256, 0, n->s>>>(n->part, nb, ne, n->g + n->woff[layer]);
     CNN_CUDA(n, cudaGetLastError());
