@@ -677,9 +677,10 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
 
         // ---- fold the frame, write the owned gradient ------------------------
         // (frame columns first, then the frame row, then the corner)
-        if (MODE != MODE_ENERGY_EXT && C::FULL_G) {
-            for (int idx = tid; idx < oh * ow; idx += NT) {
-                const int ty = sy + idx / ow, tx = sx + idx % ow;
+        // one warp per owned row, lane = owned column (no index division)
+        if (MODE != MODE_ENERGY_EXT && C::FULL_G && lane < ow) {
+            for (int r = warp; r < oh; r += NT / 32) {
+                const int ty = sy + r, tx = sx + lane;
                 const int y = y0 + ty, x = x0 + tx;
                 float gv = sG[(ty + 3) * 32 + tx + 3];
                 if (y < 3 || y >= H - 3 || x < 3 || x >= W - 3) {
