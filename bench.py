@@ -377,7 +377,7 @@ def run_batch64(args):
     t_seq, its_seq = batch64_sequential(fe, torch, f_dev, k, th, kw, args.tol, args.max_iter, stream)
     line = {"metric": "time to |dH|/|H - G(f)| < %g (s)" % args.tol, "value": round(tb / 1e3, 4), "unit": "s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[args.prec],
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "bf16r": "bf16", "tf32": "tf32"}[args.prec],
             "data": "synthetic",
             "config": {"workload": "64 textured images, sides log-uniform in [128, 1536] (seed 7), L in {1, 4}, "
                                    "48x7x7 seeded bank, lambda=%g, tol=%g on |dH|/|H - G(f)|, max_iter=%d" % (
@@ -486,7 +486,7 @@ def _round_bank(k, prec):
     if prec == "fp32":
         return np.asarray(k, np.float32)
     b = np.ascontiguousarray(k, np.float32).view(np.uint32).astype(np.uint64)
-    if prec == "bf16":
+    if prec in ("bf16", "bf16r"):
         b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
     else:
         b = (b + 0x1000) & 0xFFFFE000
@@ -518,7 +518,7 @@ def run_precision(args):
     crops = [(0, 0), (S // 2 - 256, S // 2 - 256), (S - 512, S - 512)]
     checkpoints = [0, n_it // 2, n_it - 1]
     res, u_fp32 = {}, None
-    for prec in ("fp32", "tf32", "bf16"):
+    for prec in ("fp32", "tf32", "bf16", "bf16r"):
         kq = _round_bank(k, prec).astype(np.float64)
         prm = orc.params(lam=kw["lam"], beta=kw["beta"], L0=kw["L0"], eta=kw["eta"], c2=kw["c2"], max_iter=1)
         step_err = 0.0
@@ -591,7 +591,7 @@ def precision_trajectory(fe, orc, stream, args, S=512, n_it=200):
     out = {"workload": "%dx%d textured image (seed 43), L=1 speckle (seed 44), lambda=%g, %d iterations; oracle "
                        "with the GPU's L_n replayed" % (S, S, args.lam, n_it)}
     cache = {}
-    for prec in ("fp32", "tf32", "bf16"):
+    for prec in ("fp32", "tf32", "bf16", "bf16r"):
         Ls = []
         with fe.Solver([f], k, th, prec=prec, stream=stream, **kw) as s:
             for _ in range(n_it):
@@ -819,12 +819,12 @@ def roofline_of(prec, model, r, npix, peaks, sm_mhz_max):
                                     "clock)" % (sms, sm_mhz_max)}
     else:
         bf16_sust, src = measured_bf16_sustained()
-        ratio = 1.0 if prec == "bf16" else 1.1 / 2.25
+        ratio = 1.0 if prec in ("bf16", "bf16r") else 1.1 / 2.25
         peak = bf16_sust * ratio
         rl = {"bound": "tensor", "kernel": "tc_tile_kernel<MODE_TRIAL, %s>" % prec.upper(),
               "peak_basis": "dense %s tensor peak = %.1f TFLOP/s sustained BF16 (%s) x %.3f" % (
                   prec.upper(), bf16_sust, src, ratio),
-              "peak_measured_tcgen05": peaks.get("tc_" + prec),
+              "peak_measured_tcgen05": peaks.get("tc_" + prec[:4]),
               "peak_measured_tcgen05_basis": "fe_peak tc_%s: this library's own M128xN256 tcgen05.mma stream, "
                                              "burst" % prec}
     rl.update({"achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
@@ -928,7 +928,7 @@ def main():
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(T_ms / args.steps, 3), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": {"fp32": "f32", "bf16": "bf16", "tf32": "tf32"}[args.prec], "data": "synthetic",
+                "dtype": {"fp32": "f32", "bf16": "bf16", "bf16r": "bf16", "tf32": "tf32"}[args.prec], "data": "synthetic",
                 "config": dict(workload_config(args, npix, len(fs)), **{
                            "loop": "cuda-graph while node" if args.loop_mode == 1 else "host chunks",
                            "tile": "%dx%d%s (%s)" % (r["tile"] + (" on a 4-CTA cluster" if r["cluster"] == 4 else "",
@@ -963,7 +963,7 @@ def measure_forms(fe, torch, args, f_dev, k, th, shapes, npix, stream, flush, pe
     beside it, not in its place."""
     out = {}
     steps, warmup = max(1, min(args.steps, 5)), max(3, min(args.warmup, 3))
-    for name, prec, model in (("bf16", "bf16", args.model), ("tf32", "tf32", args.model),
+    for name, prec, model in (("bf16", "bf16", args.model), ("bf16r", "bf16r", args.model), ("tf32", "tf32", args.model),
                               ("combined_fp32", "fp32", "combined"), ("combined_bf16", "bf16", "combined")):
         if prec == args.prec and model == args.model:
             continue

@@ -94,7 +94,12 @@ typedef enum {
 typedef enum {
     FE_FP32 = 0,            /* filter bank in FP32 FFMA (parity-grade) */
     FE_TF32 = 1,            /* filter bank on the tensor cores, TF32 operands */
-    FE_BF16 = 2             /* filter bank on the tensor cores, BF16 operands */
+    FE_BF16 = 2,            /* filter bank on the tensor cores, BF16 operands */
+    FE_BF16R = 3            /* as FE_BF16, but the response r_i = theta_i rho'(z_i) enters
+                               the adjoint bank rounded once to BF16 (no lo part: half
+                               the adjoint GEMM's K); the energy is that of FE_BF16 and
+                               grad F carries the rounding of r (about 2^-9 relative
+                               per response), a stated-bound variant of the form */
 } fe_precision;
 
 #define FE_TILE_CLUSTER4 0x100  /* fe_params.tile flag: a 4-CTA cluster per tile */

@@ -211,7 +211,7 @@ fe_status validate_params(fe_ctx *c, const fe_params *p) {
     if (!(p->eta > 1.0) || !std::isfinite(p->eta)) return set_err(c, FE_EINVAL, "eta must be > 1");
     if (!(p->c2 >= 0.0) || !std::isfinite(p->c2)) return set_err(c, FE_EINVAL, "c2 must be >= 0");
     if (p->max_backtrack < 0) return set_err(c, FE_EINVAL, "max_backtrack must be >= 0");
-    if (p->prec != FE_FP32 && p->prec != FE_TF32 && p->prec != FE_BF16)
+    if (p->prec != FE_FP32 && p->prec != FE_TF32 && p->prec != FE_BF16 && p->prec != FE_BF16R)
         return set_err(c, FE_EINVAL, "unknown precision %d", p->prec);
     if (p->prec != FE_FP32 && p->nf > 48)
         return set_err(c, FE_EUNSUPPORTED, "the tensor-core forms take at most 48 filters (nf=%d)", p->nf);
@@ -274,10 +274,14 @@ fe_status build_tensor_maps(fe_ctx *c) {
     return FE_OK;
 }
 
+// Tensor-core kernel format of a precision form: 1 = BF16, 2 = TF32, 3 = BF16
+// with r carried as a single BF16 operand.
+int tc_format(int prec) { return prec == FE_BF16 ? 1 : (prec == FE_BF16R ? 3 : 2); }
+
 // Launch one tile kernel of the context's precision form.
 cudaError_t launch_tiles(const fe_ctx *c, int mode, const KParams &kp, int grid) {
     if (c->prm.prec == FE_FP32) return fp32_launch(mode, kp, grid, c->s, c->tile_y, c->prm.model, c->cluster);
-    return tc_launch(mode, c->prm.prec == FE_BF16 ? 1 : 2, kp, grid, c->s, c->prm.model);
+    return tc_launch(mode, tc_format(c->prm.prec), kp, grid, c->s, c->prm.model);
 }
 
 // Tile origins and owned extents along one axis of length N with tile T.
@@ -451,7 +455,7 @@ fe_status build_graph(fe_ctx *c) {
     void *args[] = {&kp};
     cudaKernelNodeParams knp;
     std::memset(&knp, 0, sizeof knp);
-    const int fmt = c->prm.prec == FE_BF16 ? 1 : 2;
+    const int fmt = tc_format(c->prm.prec);
     const bool tc = c->prm.prec != FE_FP32;
     knp.func = const_cast<void *>(tc ? tc_trial_entry(fmt, c->prm.model)
                                      : fp32_trial_entry(c->tile_y, c->prm.model, c->cluster));
@@ -747,7 +751,7 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
     if ((st = dalloc(c, &c->d_scratch, 2 * c->max_plane)) != FE_OK) return bail(st);
     if (tc) {
         std::vector<unsigned char> bf, ba;
-        tc_build_weights(p->prec == FE_BF16 ? 1 : 2, p->filters, p->nf, bf, ba);
+        tc_build_weights(tc_format(p->prec), p->filters, p->nf, bf, ba);
         if ((st = dalloc(c, &c->d_tcw_fwd, bf.size())) != FE_OK) return bail(st);
         if ((st = dalloc(c, &c->d_tcw_adj, ba.size())) != FE_OK) return bail(st);
         if (cudaMemcpy(c->d_tcw_fwd, bf.data(), bf.size(), cudaMemcpyHostToDevice) != cudaSuccess ||

@@ -27,7 +27,7 @@ float u2f(uint32_t u) {
 
 float tc_round(int fmt, float x) {
     uint32_t u = f2u(x);
-    if (fmt == 1) {
+    if (fmt != 2) {  // BF16 (forms 1 and 3)
         u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
     } else {
         u = (u + 0x1000u) & 0xFFFFE000u;
@@ -37,7 +37,7 @@ float tc_round(int fmt, float x) {
 
 void tc_build_weights(int fmt, const float *filters, int nf, std::vector<unsigned char> &fwd,
                       std::vector<unsigned char> &adj) {
-    const int eb = fmt == 1 ? 2 : 4, kpass = fmt == 1 ? 64 : 56;
+    const int eb = fmt != 2 ? 2 : 4, kpass = fmt != 2 ? 64 : 56;
     fwd.assign((size_t)NF * kpass * eb, 0);
     adj.assign((size_t)NTAP * NF * eb, 0);
     auto put = [&](std::vector<unsigned char> &buf, int r, int k, int K, float v) {
@@ -61,19 +61,21 @@ void tc_build_weights(int fmt, const float *filters, int nf, std::vector<unsigne
         }
 }
 
-size_t tc_smem_bytes(int fmt) { return fmt == 1 ? Cfg<1>::BYTES : Cfg<2>::BYTES; }
+size_t tc_smem_bytes(int fmt) { return fmt == 1 ? Cfg<1>::BYTES : (fmt == 3 ? Cfg<3>::BYTES : Cfg<2>::BYTES); }
 int tc_threads() { return NT; }
 
 cudaError_t tc_prepare() {
     cudaError_t e = prepare_fmt<1, 0>();
     if (e == cudaSuccess) e = prepare_fmt<2, 0>();
+    if (e == cudaSuccess) e = prepare_fmt<3, 0>();
     if (e == cudaSuccess) e = tcc_prepare();
     return e;
 }
 
 cudaError_t tc_launch(int mode, int fmt, const KParams &p, int ngrid, cudaStream_t s, int model) {
     if (model == 1) return tcc_launch(mode, fmt, p, ngrid, s);
-    return fmt == 1 ? launch_fmt<1, 0>(mode, p, ngrid, s) : launch_fmt<2, 0>(mode, p, ngrid, s);
+    return fmt == 1 ? launch_fmt<1, 0>(mode, p, ngrid, s)
+                    : (fmt == 3 ? launch_fmt<3, 0>(mode, p, ngrid, s) : launch_fmt<2, 0>(mode, p, ngrid, s));
 }
 
 const void *tc_trial_entry(int fmt, int model) { return model == 1 ? tcc_trial_entry(fmt) : trial_entry<0>(fmt); }

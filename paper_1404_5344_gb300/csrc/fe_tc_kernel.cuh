@@ -61,7 +61,6 @@ constexpr int PP = 40;  // plane pitch (elements): R6X + 2 zero columns read by 
 constexpr int NBLK = R3Y / 4;                // 16 GEMM blocks of 128 pixels
 constexpr int NF = 48;                       // N of the forward GEMM
 constexpr int NTAP = 64;                     // N of the adjoint GEMM (49 taps + zeros)
-constexpr int KADJ = 2 * NF;                 // r hi | r lo
 constexpr int HRING = 10;                    // rows of the horizontal-sum ring (the 10 a vertical gather reads)
 constexpr int TMEM_COLS = 128;               // D_fwd at column 0, D_adj at column 64
 constexpr int NFOLD = 12;                    // gradient rows kept for the vertical fold
@@ -77,9 +76,15 @@ static_assert(R3Y % 4 == 0, "GEMM blocks of 4 rows");
 
 template <int FMT>
 struct Cfg {
-    static constexpr int EB = FMT == 1 ? 2 : 4;            // operand bytes
-    static constexpr int KSTEP = FMT == 1 ? 16 : 8;        // K per MMA
-    static constexpr int KPASS = FMT == 1 ? 64 : 56;       // 7 rows x 8 taps, padded to KSTEP
+    // FMT 1: BF16 operands; 2: TF32; 3: BF16 with the response r carried as a
+    // single BF16 operand (no lo part: half the adjoint K and no split)
+    static constexpr bool BF = FMT != 2;                   // BF16 operands
+    static constexpr int OPF = BF ? 1 : 2;                 // operand format of the instruction descriptor
+    static constexpr bool RLO = FMT != 3;                  // r carried as hi + lo
+    static constexpr int KADJ = RLO ? 2 * NF : NF;         // adjoint K: r hi | r lo, or r
+    static constexpr int EB = BF ? 2 : 4;                  // operand bytes
+    static constexpr int KSTEP = BF ? 16 : 8;              // K per MMA
+    static constexpr int KPASS = BF ? 64 : 56;             // 7 rows x 8 taps, padded to KSTEP
     static constexpr int KFWD = 2 * KPASS;                 // u hi | u lo
     static constexpr int E = 16 / EB;                      // elements per 16-byte chunk
     static constexpr int NCH = KPASS / E;                  // chunks per pass
@@ -101,7 +106,7 @@ struct Cfg {
     // fit either way; the final pass then folds and writes with all warps),
     // TF32 only the rows of the vertical fold (image rows -3..2, H-3..H+2),
     // writing the others as they are formed, so that two CTAs fit per SM
-    static constexpr bool FULL_G = FMT == 1;
+    static constexpr bool FULL_G = BF;
     static constexpr int GROWS = FULL_G ? R3Y : NFOLD;
     static constexpr size_t OFF_G = OFF_H + (size_t)HRING * 7 * 32 * 4;
     static constexpr size_t OFF_BF = (OFF_G + (size_t)GROWS * R3X * 4 + 127) / 128 * 128;
@@ -122,6 +127,7 @@ struct Cfg {
     static_assert(BF_BYTES % 16 == 0 && BA_BYTES % 16 == 0, "vector copies");
 };
 static_assert(3 * (Cfg<1>::BYTES + 1024) <= 228 * 1024, "BF16: three CTAs per SM");
+static_assert(3 * (Cfg<3>::BYTES + 1024) <= 228 * 1024, "BF16, single r: three CTAs per SM");
 static_assert(Cfg<2>::GROWS == NFOLD, "TF32: compact fold rows");
 static_assert(2 * (Cfg<2>::BYTES + 1024) <= 228 * 1024, "TF32: two CTAs per SM");
 
@@ -221,7 +227,7 @@ __device__ __forceinline__ void im2col(const uint32_t *__restrict__ sP, unsigned
     const int pr = 4 * blk + (m >> 5), pc = m & 31;
     constexpr int ROW_WORDS = PP * C::EB / 4;
     unsigned char *row = sAF + tc::kmajor_offset(m, 0, C::KFWD, C::EB) + part * C::NCH * 128;
-    if (FMT == 1) {
+    if (C::BF) {
         const uint32_t *src = sP + part * C::PL_WORDS + pr * ROW_WORDS + (pc >> 1);
         const uint32_t sh = (uint32_t)(pc & 1) * 16u;
 #pragma unroll
@@ -249,7 +255,7 @@ __device__ __forceinline__ void im2col(const uint32_t *__restrict__ sP, unsigned
 // in w = log u: the prox is prox_w, the planes hold u = e^w, and the
 // gradient is e^w (.) K^T r.
 template <int MODE, int FMT, int MODEL>
-__global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KParams p) {
+__global__ void __launch_bounds__(NT, FMT != 2 ? 3 : 2) tc_tile_kernel(const KParams p) {
     using C = Cfg<FMT>;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sAF = smem + C::OFF_AF;
@@ -320,7 +326,7 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
             // the padding columns of the planes (read with weight 0) hold zeros
             for (int j = tid; j < C::NPL * R6Y; j += NT) {
                 uint32_t *rowp = sP + (j / R6Y) * C::PL_WORDS + (j % R6Y) * (PP * C::EB / 4);
-                if (FMT == 1)
+                if (C::BF)
                     rowp[(PP / 2) - 2] = rowp[(PP / 2) - 1] = 0u;  // elements 36..39 (the writes below fill 36, 37)
                 else
                     rowp[PP - 2] = rowp[PP - 1] = 0u;
@@ -415,7 +421,7 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
                     // hi / lo planes of the operand type (the bank sees u)
                     const float uv = MODEL == 0 ? v : expf(v);
                     const int idx = base + k * NT + tid, ry = idx / R6X, rx = idx - ry * R6X;
-                    if (FMT == 1) {
+                    if (C::BF) {
                         const __nv_bfloat16 hb = __float2bfloat16_rn(uv);
                         const __nv_bfloat16 lb = __float2bfloat16_rn(uv - __bfloat162float(hb));
                         __nv_bfloat16 *ph = reinterpret_cast<__nv_bfloat16 *>(sP);
@@ -435,10 +441,10 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
 
         const uint32_t sAF_u32 = tc::smem_u32(sAF), sR_u32 = tc::smem_u32(sR);
         const uint32_t sBf_u32 = tc::smem_u32(sBf), sBa_u32 = tc::smem_u32(sBa);
-        constexpr uint32_t SBO_F = (uint32_t)(C::KFWD / C::E) * 128, SBO_A = (uint32_t)(KADJ / C::E) * 128;
+        constexpr uint32_t SBO_F = (uint32_t)(C::KFWD / C::E) * 128, SBO_A = (uint32_t)(C::KADJ / C::E) * 128;
         constexpr uint32_t SBO_BF = (uint32_t)(C::KPASS / C::E) * 128, SBO_BA = (uint32_t)(NF / C::E) * 128;
         constexpr int KS_F = C::KPASS / C::KSTEP, KS_A = NF / C::KSTEP;  // K steps of one pass
-        constexpr uint32_t IDESC_F = tc::make_idesc(FMT, 128, NF), IDESC_A = tc::make_idesc(FMT, 128, NTAP);
+        constexpr uint32_t IDESC_F = tc::make_idesc(C::OPF, 128, NF), IDESC_A = tc::make_idesc(C::OPF, 128, NTAP);
         const int m = tid & 127, part = tid >> 7;  // im2col: pixel, chunk parity
         const int wg = warp >> 2, lg = warp & 3;   // epilogues: column half, TMEM lane group
         const bool edge_x = x0 == 0 || x0 + TX >= W;
@@ -460,7 +466,7 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
         if (tid == 0) {
 #pragma unroll
             for (int ks = 0; ks < C::KFWD / C::KSTEP; ++ks)
-                tc::mma<FMT>(taddr, tc::make_smem_desc(sAF_u32 + ks * 256, 128, SBO_F),
+                tc::mma<C::OPF>(taddr, tc::make_smem_desc(sAF_u32 + ks * 256, 128, SBO_F),
                              tc::make_smem_desc(sBf_u32 + (ks % KS_F) * 256, 128, SBO_BF), IDESC_F,
                              ks > 0 ? 1u : 0u);
             tc::mma_commit(&bar_f);
@@ -611,13 +617,24 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
                 float pa, pb;
                 f2_unpack(ps2, pa, pb);
                 if (owned) sum2_add(accF, (pa + pb) * LN2);
-                unsigned char *rowp = sR + tc::kmajor_offset((lg << 5) + lane, 0, KADJ, C::EB);
+                unsigned char *rowp = sR + tc::kmajor_offset((lg << 5) + lane, 0, C::KADJ, C::EB);
 #pragma unroll
                 for (int j = 0; j < 24 / C::E; ++j) {
                     uint4 hi, lo;
-                    hilo_chunk2<FMT>(r2 + j * (C::E / 2), hi, lo);
+                    if constexpr (C::RLO) {
+                        hilo_chunk2<C::OPF>(r2 + j * (C::E / 2), hi, lo);
+                        *reinterpret_cast<uint4 *>(rowp + ((NF + 24 * wg) / C::E + j) * 128) = lo;
+                    } else {  // r rounded once to BF16
+                        uint32_t h[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            float x0, x1;
+                            f2_unpack(r2[j * (C::E / 2) + q], x0, x1);
+                            h[q] = bf16x2_rn(x0, x1);
+                        }
+                        hi = make_uint4(h[0], h[1], h[2], h[3]);
+                    }
                     *reinterpret_cast<uint4 *>(rowp + ((24 * wg) / C::E + j) * 128) = hi;
-                    *reinterpret_cast<uint4 *>(rowp + ((NF + 24 * wg) / C::E + j) * 128) = lo;
                 }
             }
             // one barrier publishes both the H rows of block blk - 1 and the R
@@ -628,8 +645,8 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
             if (tid == 0) {
                 tc::fence_after_sync();
 #pragma unroll
-                for (int ks = 0; ks < KADJ / C::KSTEP; ++ks)
-                    tc::mma<FMT>(taddr + 64, tc::make_smem_desc(sR_u32 + ks * 256, 128, SBO_A),
+                for (int ks = 0; ks < C::KADJ / C::KSTEP; ++ks)
+                    tc::mma<C::OPF>(taddr + 64, tc::make_smem_desc(sR_u32 + ks * 256, 128, SBO_A),
                                  tc::make_smem_desc(sBa_u32 + (ks % KS_A) * 256, 128, SBO_BA), IDESC_A,
                                  ks > 0 ? 1u : 0u);
                 tc::mma_commit(&bar_a);
@@ -653,7 +670,7 @@ __global__ void __launch_bounds__(NT, FMT == 1 ? 3 : 2) tc_tile_kernel(const KPa
                     tc::fence_after_sync();
 #pragma unroll
                     for (int ks = 0; ks < C::KFWD / C::KSTEP; ++ks)
-                        tc::mma<FMT>(taddr, tc::make_smem_desc(sAF_u32 + ks * 256, 128, SBO_F),
+                        tc::mma<C::OPF>(taddr, tc::make_smem_desc(sAF_u32 + ks * 256, 128, SBO_F),
                                      tc::make_smem_desc(sBf_u32 + (ks % KS_F) * 256, 128, SBO_BF), IDESC_F,
                                      ks > 0 ? 1u : 0u);
                     tc::mma_commit(&bar_f);
@@ -766,8 +783,9 @@ cudaError_t launch_fmt(int mode, const KParams &p, int ngrid, cudaStream_t s) {
 
 template <int MODEL>
 const void *trial_entry(int fmt) {
-    return fmt == 1 ? reinterpret_cast<const void *>(&tc_tile_kernel<MODE_TRIAL, 1, MODEL>)
-                    : reinterpret_cast<const void *>(&tc_tile_kernel<MODE_TRIAL, 2, MODEL>);
+    return fmt == 1   ? reinterpret_cast<const void *>(&tc_tile_kernel<MODE_TRIAL, 1, MODEL>)
+           : fmt == 3 ? reinterpret_cast<const void *>(&tc_tile_kernel<MODE_TRIAL, 3, MODEL>)
+                      : reinterpret_cast<const void *>(&tc_tile_kernel<MODE_TRIAL, 2, MODEL>);
 }
 
 }  // namespace

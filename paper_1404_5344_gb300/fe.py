@@ -21,9 +21,9 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "l
 
 FE_OK, FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_ENONFINITE = 0, 1, 2, 3, 4
 FE_EBACKTRACK, FE_ETIMEOUT, FE_ENOTCONVERGED, FE_EUNSUPPORTED = 5, 6, 7, 8
-FE_FP32, FE_TF32, FE_BF16 = 0, 1, 2
+FE_FP32, FE_TF32, FE_BF16, FE_BF16R = 0, 1, 2, 3
 FE_TILE_CLUSTER4 = 0x100
-PRECISIONS = {"fp32": FE_FP32, "tf32": FE_TF32, "bf16": FE_BF16}
+PRECISIONS = {"fp32": FE_FP32, "tf32": FE_TF32, "bf16": FE_BF16, "bf16r": FE_BF16R}
 
 #: every symbol include/fe.h declares
 EXPORTS = (

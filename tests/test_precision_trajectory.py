@@ -25,7 +25,10 @@ N_IT = 150
 # (rounded bank: max, mean), (unrounded bank: max, mean), |PSNR delta| dB vs the unrounded oracle
 BOUNDS = {"fp32": ((1e-4, 2e-5), (1e-4, 2e-5), 1e-3),
           "tf32": ((1e-4, 2e-5), (2e-3, 1e-3), 2e-2),
-          "bf16": ((2e-4, 5e-5), (1e-2, 1e-2), 1e-1)}
+          "bf16": ((2e-4, 5e-5), (1e-2, 1e-2), 1e-1),
+          # r rounded to BF16: its gradient error (2^-9 per response) is part of
+          # the form, so the rounded-bank oracle is not its exact reference
+          "bf16r": ((2e-4, 1e-4), (1e-2, 1e-2), 1e-1)}
 
 
 @pytest.fixture(scope="module")
@@ -44,7 +47,7 @@ def _psnr(u, clean):
     return 10.0 * np.log10(255.0 ** 2 / mse)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16", "bf16r"])
 def test_trajectory_against_fp64_oracle(fe, orc, bank48, prec):
     from paper_1404_5344_gb300 import synth
     k, th = bank48
@@ -58,7 +61,7 @@ def test_trajectory_against_fp64_oracle(fe, orc, bank48, prec):
             Ls.append(s.info(0)["L"])
         ug = s.get_u(0).astype(np.float64)
     prm = orc.params(lam=kw["lam"], beta=kw["beta"], L0=kw["L0"], eta=kw["eta"], c2=kw["c2"], max_iter=1)
-    kq = k if prec == "fp32" else ROUND[prec](k)
+    kq = k if prec == "fp32" else ROUND[prec[:4]](k)
     res = {}
     for name, bank_ in (("rounded", kq), ("unrounded", k)):
         ref = orc.ipiano_fixed(f, bank_, th, prm, Ls, f)
