@@ -70,7 +70,9 @@ def parse():
     ap.add_argument("--model", default="variant", choices=["variant", "combined"],
                     help="variant: Eq. variant in u (lambda = 5); combined: Eq. newmodel in w = log u "
                          "(lambda1 = 160, lambda2 = 0.004, FP32 form)")
-    ap.add_argument("--loop-mode", type=int, default=1)
+    ap.add_argument("--loop-mode", type=int, default=2,
+                    help="0 host chunks of per-trial launches, 1 graph while node of per-trial launches, "
+                         "2 one persistent launch per step (default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the other forms (TF32, BF16, combined model, batch of 64) in the default line")
@@ -743,6 +745,11 @@ def measure_peaks(fe, local):
     return out
 
 
+LOOP_NAMES = {0: "host chunks of per-trial launches",
+              1: "cuda-graph while node of per-trial launches",
+              2: "one persistent launch per step (cuda graph)"}
+
+
 def measure_throughput(fe, torch, args, f_dev, k, th, shapes, prec, model, steps, warmup, stream, flush,
                        clock_path=None, dist=None, local=0):
     """One throughput measurement of the workload: `warmup` untimed steps,
@@ -884,7 +891,10 @@ def main():
     T_ms, units = combine_ranks(r["total_ms"], r["pix_iters"], dist, device="cuda")
     value = units / (T_ms / 1e3) / 1e6
     launches = r["launches"]
-    trial_launches = max(1, launches - args.steps * (len(fs) + 2))
+    # fe_reset launches two kernels per image (prep, data-term floor) and the
+    # initial-gradient kernel; fe_step one begin kernel; the rest are trial
+    # launches (one per step when the loop is persistent)
+    trial_launches = max(1, launches - args.steps * (2 * len(fs) + 2))
 
     # e2e through the C ABI with host buffers
     kw = model_kw(args)
@@ -930,7 +940,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp32": "f32", "bf16": "bf16", "bf16r": "bf16", "tf32": "tf32"}[args.prec], "data": "synthetic",
                 "config": dict(workload_config(args, npix, len(fs)), **{
-                           "loop": "cuda-graph while node" if args.loop_mode == 1 else "host chunks",
+                           "loop": LOOP_NAMES.get(args.loop_mode, str(args.loop_mode)),
                            "tile": "%dx%d%s (%s)" % (r["tile"] + (" on a 4-CTA cluster" if r["cluster"] == 4 else "",
                                                                   "autotuned" if args.prec == "fp32" else "fixed")),
                            "parallelism": "replicas" if world > 1 else "single GPU",

@@ -316,10 +316,21 @@ FE_API int fe_tile_cluster(const fe_ctx *ctx);
  * -1 if reading the device counter failed. */
 FE_API long long fe_launch_count(const fe_ctx *ctx);
 
-/* Select how fe_step/fe_solve drive the device loop: 0 = host loop of
- * kernel launches in chunks, 1 = one CUDA graph with a device-side while
- * node (default when the driver supports it).  Both run the same iterations
- * of Sec. II-C; the choice has no counterpart in the paper.  FE_EINVAL for
+/* Select how fe_step/fe_solve drive the device loop of Sec. II-C's
+ * iterations: 0 = host loop of per-trial kernel launches in chunks; 1 = one
+ * CUDA graph whose device-side while node repeats a per-trial launch over
+ * every tile of every active image; 2 (the default) = one CUDA graph holding
+ * ONE persistent launch that runs every trial of every image: its CTAs take
+ * tiles from per-image counters, and the block that decides an image's
+ * trial releases the tiles of that image's next trial at once, so images
+ * advance independently instead of in lockstep.  Mode 2 applies to the FP32
+ * tiles that run on one CTA (not the thread-block cluster tiles) and runs
+ * as mode 1 otherwise; modes 1 and 2 run as
+ * mode 0 on a driver without conditional graph nodes.  All modes compute
+ * the same iterates, energies and decisions bit for bit (each image's trials
+ * and each trial's reduction order are the same).  A persistent launch in
+ * which no trial is decided for 4 s stops; the images it left unfinished get
+ * FE_ETIMEOUT.  The choice has no counterpart in the paper.  FE_EINVAL for
  * other modes or a NULL context. */
 FE_API fe_status fe_set_loop_mode(fe_ctx *ctx, int mode);
 

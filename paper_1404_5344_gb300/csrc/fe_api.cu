@@ -44,6 +44,9 @@ struct fe_ctx {
     TileDesc *d_tiles = nullptr;
     int *d_order = nullptr;  // launch order of the tiles (whole-list launches)
     std::vector<int> horder;
+    int *d_porder = nullptr;  // persistent launches: each image's tiles in the order they are taken
+    std::vector<int> hporder;
+    int *d_sched = nullptr;   // persistent launches: per-image tile counters
     double *d_part = nullptr;
     unsigned *d_arr = nullptr;
     LoopCtl *d_loop = nullptr;
@@ -60,10 +63,12 @@ struct fe_ctx {
     KParams kp{};
     long long host_launches = 0;
     std::string err;
-    int loop_mode = 1;
-    bool graph_built = false;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
+    int loop_mode = 2;
+    // CUDA graphs of the device loop: [0] a while node around per-trial
+    // launches, [1] the persistent trial launch
+    bool graph_built[2] = {false, false};
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -142,26 +147,35 @@ __global__ void gfloor_kernel(const float *f2, size_t N, int model, double lam, 
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
+// Start of fe_step / fe_solve: per-image targets, the trial budget (per
+// launch for per-trial launches, per image for the persistent launch) and
+// the persistent launch's tile counters (0: the first trial's tiles are
+// available; images that do not iterate never offer tiles).
 __global__ void begin_kernel(ImgState *st, int nimg, long long n, double tol, LoopCtl *lc,
-                             long long budget, const double *H_target) {
+                             long long budget, const double *H_target, int *sched) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int nact = 0;
     for (int j = 0; j < nimg; ++j) {
         st[j].H_target = H_target ? H_target[j] : -INFINITY;
+        bool act = false;
         if (st[j].status == FE_OK) {
             st[j].done = 0;
             st[j].converged = 0;
             st[j].bt = 0;
             st[j].target = st[j].n + n;
             st[j].tol = tol;
-            ++nact;
+            st[j].trial_limit = st[j].trials + budget;
+            act = n > 0;
         } else {
             st[j].done = 1;
         }
+        nact += act;
+        sched[j] = act ? 0 : 0x40000000;
     }
     lc->grid_arrivals = 0u;
     lc->active = nact;
     lc->budget = budget;
+    lc->abort = 0;
 }
 
 bool is_device_ptr(const void *p) {
@@ -341,6 +355,15 @@ void build_tiles(fe_ctx *c, int TY, int TX, int cl = 1) {
     if (!tc && TY == 64 && cl == 1)
         std::stable_sort(c->horder.begin(), c->horder.end(),
                          [&](int a, int b) { return sides(c->htile[a]) > sides(c->htile[b]); });
+    // persistent launches take an image's tiles in the same longest-first
+    // order, per image (the order the tiles of one trial become available)
+    c->hporder.resize(c->ntiles);
+    for (int k = 0; k < c->ntiles; ++k) c->hporder[k] = k;
+    for (int j = 0; j < c->nimg; ++j) {
+        auto b = c->hporder.begin() + c->himg[j].tile_begin;
+        std::stable_sort(b, b + c->himg[j].ntiles,
+                         [&](int a, int bb) { return sides(c->htile[a]) > sides(c->htile[bb]); });
+    }
 }
 
 // FP32 tile candidates: code = T, or T | FE_TILE_CLUSTER4
@@ -360,6 +383,8 @@ fe_status upload_tiles(fe_ctx *c) {
     FE_CUDA(c, cudaMemcpyAsync(c->d_tiles, c->htile.data(), sizeof(TileDesc) * c->ntiles, cudaMemcpyHostToDevice,
                                c->s));
     FE_CUDA(c, cudaMemcpyAsync(c->d_order, c->horder.data(), sizeof(int) * c->ntiles, cudaMemcpyHostToDevice, c->s));
+    FE_CUDA(c, cudaMemcpyAsync(c->d_porder, c->hporder.data(), sizeof(int) * c->ntiles, cudaMemcpyHostToDevice,
+                               c->s));
     c->kp.ntiles = c->ntiles;
     return FE_OK;
 }
@@ -422,8 +447,35 @@ fe_status load_inputs(fe_ctx *c, const float *const *f, const float *const *u0) 
     return FE_OK;
 }
 
-fe_status build_graph(fe_ctx *c) {
-    if (c->graph_built) return FE_OK;
+// Whether this context's trial kernel runs as one persistent launch: the
+// FP32 tiles that one CTA works on alone (not the thread-block cluster
+// tiles).  The tensor-core forms keep per-trial launches: their persistent
+// kernel is correct (bit for bit) but measured slower.
+bool persist_supported(const fe_ctx *c) { return c->prm.prec == FE_FP32 && c->cluster == 1; }
+
+// CUDA graph of the device loop: a while node whose body is one trial kernel
+// node.  Per-trial launches (persist false): one launch per trial of every
+// image, the last CTA sets the while condition.  Persistent (persist true):
+// the body is one launch of as many CTAs as fit on the GPU at once (at most
+// one per tile), which runs every trial of every image and ends the loop.
+fe_status build_graph(fe_ctx *c, bool persist) {
+    const int gi = persist ? 1 : 0;
+    if (c->graph_built[gi]) return FE_OK;
+    const int fmt = tc_format(c->prm.prec);
+    const bool tc = c->prm.prec != FE_FP32;
+    const void *fn = persist ? (tc ? tc_ptrial_entry(fmt, c->prm.model) : fp32_ptrial_entry(c->tile_y, c->prm.model))
+                             : (tc ? tc_trial_entry(fmt, c->prm.model)
+                                   : fp32_trial_entry(c->tile_y, c->prm.model, c->cluster));
+    const int threads = tc ? tc_threads() : fp32_threads(c->tile_y);
+    const size_t smem = tc ? tc_smem_bytes(fmt) : fp32_smem_bytes(c->tile_y);
+    int grid = c->ntiles * (tc ? 1 : c->cluster);
+    if (persist) {
+        int per_sm = 0, sms = 0;
+        FE_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
+        FE_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
+        if (per_sm < 1) return set_err(c, FE_EUNSUPPORTED, "persistent launch: no CTA fits on an SM");
+        grid = std::max(1, std::min(c->ntiles, per_sm * sms));
+    }
     cudaGraph_t g = nullptr;
     FE_CUDA(c, cudaGraphCreate(&g, 0));
     cudaGraphConditionalHandle h;
@@ -455,13 +507,10 @@ fe_status build_graph(fe_ctx *c) {
     void *args[] = {&kp};
     cudaKernelNodeParams knp;
     std::memset(&knp, 0, sizeof knp);
-    const int fmt = tc_format(c->prm.prec);
-    const bool tc = c->prm.prec != FE_FP32;
-    knp.func = const_cast<void *>(tc ? tc_trial_entry(fmt, c->prm.model)
-                                     : fp32_trial_entry(c->tile_y, c->prm.model, c->cluster));
-    knp.gridDim = dim3(c->ntiles * (tc ? 1 : c->cluster));
-    knp.blockDim = dim3(tc ? tc_threads() : fp32_threads(c->tile_y));
-    knp.sharedMemBytes = (unsigned)(tc ? tc_smem_bytes(fmt) : fp32_smem_bytes(c->tile_y));
+    knp.func = const_cast<void *>(fn);
+    knp.gridDim = dim3((unsigned)grid);
+    knp.blockDim = dim3((unsigned)threads);
+    knp.sharedMemBytes = (unsigned)smem;
     knp.kernelParams = args;
     cudaGraphNode_t kn;
     e = cudaGraphAddKernelNode(&kn, body, nullptr, 0, &knp);
@@ -487,19 +536,32 @@ fe_status build_graph(fe_ctx *c) {
         cudaGraphDestroy(g);
         return set_err(c, FE_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
     }
-    c->graph = g;
-    c->gexec = ex;
-    c->graph_built = true;
+    c->graph[gi] = g;
+    c->gexec[gi] = ex;
+    c->graph_built[gi] = true;
     return FE_OK;
 }
 
 // Run trial launches until no image is active (or the budget is spent).
+// Loop mode 2 runs the persistent launch where the tile allows it (else as
+// mode 1), mode 1 the graph of per-trial launches, mode 0 (or a driver
+// without conditional graph nodes) host-side chunks of per-trial launches.
 fe_status run_loop(fe_ctx *c, long long n_hint, long long budget, bool sync) {
-    if (c->loop_mode == 1) {
-        fe_status st = build_graph(c);
+    if (c->loop_mode >= 1) {
+        const bool persist = c->loop_mode == 2 && persist_supported(c);
+        fe_status st = build_graph(c, persist);
         if (st == FE_OK) {
-            FE_CUDA(c, cudaGraphLaunch(c->gexec, c->s));
-            if (sync) FE_CUDA(c, cudaStreamSynchronize(c->s));
+            FE_CUDA(c, cudaGraphLaunch(c->gexec[persist ? 1 : 0], c->s));
+            if (sync) {
+                FE_CUDA(c, cudaStreamSynchronize(c->s));
+                if (persist) {
+                    LoopCtl lc;
+                    FE_CUDA(c, cudaMemcpy(&lc, c->d_loop, sizeof lc, cudaMemcpyDeviceToHost));
+                    if (lc.abort)
+                        set_err(c, FE_ETIMEOUT, "persistent launch stopped: no trial was decided for %.0f s",
+                                1e-9 * (double)PERSIST_STALL_NS);
+                }
+            }
             return FE_OK;
         }
         if (st != FE_EUNSUPPORTED) return st;
@@ -656,8 +718,10 @@ void fe_default_params(fe_params *p) {
 void fe_destroy(fe_ctx *c) {
     if (!c) return;
     if (c->s) cudaStreamSynchronize(c->s);
-    if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    if (c->graph) cudaGraphDestroy(c->graph);
+    for (int k = 0; k < 2; ++k) {
+        if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
+        if (c->graph[k]) cudaGraphDestroy(c->graph[k]);
+    }
     for (void *p : c->allocs) cudaFree(p);
     delete c;
 }
@@ -737,6 +801,8 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
     if ((st = dalloc(c, &c->d_st, nimg)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_tiles, max_tiles)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_order, max_tiles)) != FE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_porder, max_tiles)) != FE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_sched, nimg)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_part, max_tiles * NRED)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_arr, nimg)) != FE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_loop, 1)) != FE_OK) return bail(st);
@@ -779,7 +845,8 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
         cudaMemcpy(c->d_imgs, c->himg.data(), sizeof(ImgDesc) * nimg, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->d_tiles, c->htile.data(), sizeof(TileDesc) * c->ntiles, cudaMemcpyHostToDevice) !=
             cudaSuccess ||
-        cudaMemcpy(c->d_order, c->horder.data(), sizeof(int) * c->ntiles, cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(c->d_order, c->horder.data(), sizeof(int) * c->ntiles, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_porder, c->hporder.data(), sizeof(int) * c->ntiles, cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(set_err(c, FE_ECUDA, "upload of descriptors failed: %s", cudaGetErrorString(cudaGetLastError())));
 
     KParams &kp = c->kp;
@@ -805,6 +872,8 @@ fe_status fe_init_batch(fe_ctx **out, const fe_params *p, int nimg, const int *H
     kp.tcw_fwd = c->d_tcw_fwd;
     kp.tcw_adj = c->d_tcw_adj;
     kp.tc_error = c->d_tc_error;
+    kp.sched = c->d_sched;
+    kp.porder = c->d_porder;
 
     if (cudaMemset(c->d_loop, 0, sizeof(LoopCtl)) != cudaSuccess)
         return bail(set_err(c, FE_ECUDA, "cudaMemset: %s", cudaGetErrorString(cudaGetLastError())));
@@ -829,7 +898,7 @@ fe_status fe_reset(fe_ctx *c, const float *const *f, const float *const *u0) {
 }
 
 fe_status fe_set_loop_mode(fe_ctx *c, int mode) {
-    if (!c || (mode != 0 && mode != 1)) return FE_EINVAL;
+    if (!c || mode < 0 || mode > 2) return FE_EINVAL;
     c->loop_mode = mode;
     return FE_OK;
 }
@@ -839,7 +908,7 @@ fe_status fe_step(fe_ctx *c, int n, fe_status *worst) {
     if (n < 0) return set_err(c, FE_EINVAL, "n must be >= 0");
     if (n > 0) {
         const long long budget = (long long)n * (c->prm.max_backtrack + 1) + 1;
-        begin_kernel<<<1, 32, 0, c->s>>>(c->d_st, c->nimg, n, 0.0, c->d_loop, budget, nullptr);
+        begin_kernel<<<1, 32, 0, c->s>>>(c->d_st, c->nimg, n, 0.0, c->d_loop, budget, nullptr, c->d_sched);
         FE_CUDA(c, cudaGetLastError());
         ++c->host_launches;
         fe_status st = run_loop(c, n, budget, worst != nullptr);
@@ -872,7 +941,8 @@ fe_status fe_solve_to_energy(fe_ctx *c, int max_iter, double rel_tol, const doub
         FE_CUDA(c, cudaMemcpyAsync(c->d_htarget, H_target, sizeof(double) * c->nimg, cudaMemcpyHostToDevice, c->s));
         d_target = c->d_htarget;
     }
-    begin_kernel<<<1, 32, 0, c->s>>>(c->d_st, c->nimg, max_iter, rel_tol, c->d_loop, budget, d_target);
+    begin_kernel<<<1, 32, 0, c->s>>>(c->d_st, c->nimg, max_iter, rel_tol, c->d_loop, budget, d_target,
+                                     c->d_sched);
     FE_CUDA(c, cudaGetLastError());
     ++c->host_launches;
     fe_status st = run_loop(c, std::min(max_iter, 32), budget, true);

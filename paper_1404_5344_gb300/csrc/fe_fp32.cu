@@ -40,4 +40,10 @@ const void *fp32_trial_entry(int T, int model, int cl) {
     return reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL, 64, 0, 1>);
 }
 
+const void *fp32_ptrial_entry(int T, int model) {
+    if (model == 1) return fp32c_ptrial_entry(T);
+    return T == 32 ? reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_PTRIAL, 32, 0, 1>)
+                   : reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_PTRIAL, 64, 0, 1>);
+}
+
 }  // namespace fe

@@ -27,4 +27,9 @@ const void *fp32c_trial_entry(int T, int cl) {
     return reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_TRIAL, 64, 1, 1>);
 }
 
+const void *fp32c_ptrial_entry(int T) {
+    return T == 32 ? reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_PTRIAL, 32, 1, 1>)
+                   : reinterpret_cast<const void *>(&fp32_tile_kernel<MODE_PTRIAL, 64, 1, 1>);
+}
+
 }  // namespace fe

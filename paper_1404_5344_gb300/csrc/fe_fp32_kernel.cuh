@@ -282,332 +282,359 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
     const int tid = threadIdx.x;
     int rank = 0;
     if constexpr (CL > 1) rank = (int)cooperative_groups::this_cluster().block_rank();
-    const int bt = p.tile0 + (int)blockIdx.x / CL;
-    const int gtile = p.order ? p.order[bt] : bt;
-    const TileDesc td = p.tiles[gtile];
-    const int img = td.img;
-    const ImgDesc im = p.imgs[img];
-    ImgState *st = p.st + img;
-    const int H = im.H, W = im.W, y0 = td.y0, x0 = td.x0;
-
-    bool active = true;
-    int gcur_out = 0;
-    if (MODE == MODE_TRIAL) {
-        active = (st->done == 0) && (st->n < st->target);
-        gcur_out = st->gcur ^ 1;
-    }
-
-    if (active) {
-        // ---- 1+2: inertial step and prox on tile + 6 ---------------------
-        // per-thread sums: compensated FP32 for F and G (large terms), plain
-        // FP32 for the small step-test terms
-        Sum2 accF{0.f, 0.f}, accG{0.f, 0.f};
-        float accGD = 0.f, accDD = 0.f, accDP = 0.f;
-        {
-            int cur = 0, gcur = 0;
-            float a = 0.f, b = 0.f, tl = 0.f;
-            const float l1 = (float)im.lambda1, l2 = (float)im.lambda;  // combined model
-            if (MODE == MODE_TRIAL) {
-                cur = st->cur;
-                gcur = st->gcur;
-                const double alpha = st->alpha;
-                a = (float)alpha;
-                b = (float)p.beta;
-                tl = (float)(alpha * im.lambda);
+    // persistent launches (MODE_PTRIAL, one CTA per tile): the CTA runs tiles
+    // until every image has stopped, taking each from the per-image counters;
+    // otherwise the launch's block index names the one tile
+    constexpr bool PERSIST = MODE == MODE_PTRIAL;
+    constexpr bool TRIAL = MODE == MODE_TRIAL || PERSIST;
+    static_assert(!PERSIST || CL == 1, "persistent launches run tiles of one CTA");
+    __shared__ int sTask;
+    int pref = p.nimg > 0 ? (int)blockIdx.x % p.nimg : 0;  // image of the last tile taken
+    for (;;) {
+        int gtile;
+        if constexpr (PERSIST) {
+            __syncthreads();  // the previous tile is done with shared memory and sTask
+            if (tid < 32) {
+                const int t = persist_grab(p, pref);
+                if (tid == 0) sTask = t;
             }
-            const float *uc = (MODE == MODE_TRIAL || MODE == MODE_INIT) ? im.u[cur] : p.u_ext;
-            const float *upv = im.u[(cur + 2) % 3];
-            const float *gc = im.g[gcur];
-            float *un = im.u[(cur + 1) % 3];
-            const float *f2p = im.f2;
-            for (int idx = tid; idx < R6Y * R6X; idx += NT) {
-                const int ry = idx / R6X, rx = idx - ry * R6X;
-                const int y = y0 - 6 + ry, x = x0 - 6 + rx;
-                const size_t off = (size_t)reflect(y, H) * W + reflect(x, W);
-                const bool inner = ry >= 6 && ry < 6 + TY && rx >= 6 && rx < 6 + TX && y < H && x < W;
-                float v;
-                if (MODE == MODE_TRIAL) {
-                    const float u0 = __ldg(uc + off), u_1 = __ldg(upv + off), g0 = __ldg(gc + off);
-                    const float f2 = __ldg(f2p + off);
-                    const float dprev = u0 - u_1;
-                    const float uhat = fmaf(-a, g0, fmaf(b, dprev, u0));
-                    v = MODEL == 0 ? prox_g(uhat, f2, tl) : prox_w(uhat, f2, a, l1, l2);
-                    if (inner && rank == 0) {
-                        un[off] = v;
-                        const float d = v - u0;
-                        accGD = fmaf(g0, d, accGD);
-                        accDD = fmaf(d, d, accDD);
-                        accDP = fmaf(d, dprev, accDP);
-                        sum2_add(accG, MODEL == 0 ? v * v - 2.0f * f2 * logf(v) : data_w(v, f2, l1, l2));
-                    }
-                } else {
-                    v = __ldg(uc + off);
-                    if (inner && rank == 0) {
-                        const float f2 = __ldg(f2p + off);
-                        sum2_add(accG, MODEL == 0 ? v * v - 2.0f * f2 * logf(v) : data_w(v, f2, l1, l2));
-                    }
-                }
-                sU[ry * SU_LD + rx] = MODEL == 0 ? v : expf(v);  // the bank sees u
-            }
+            __syncthreads();
+            gtile = sTask;
+            if (gtile < 0) break;
+            // acquire: the decision and the planes of the image's previous trial
+            __threadfence();
+        } else {
+            const int bt = p.tile0 + (int)blockIdx.x / CL;
+            gtile = p.order ? p.order[bt] : bt;
+        }
+        const TileDesc td = p.tiles[gtile];
+        const int img = td.img;
+        const ImgDesc im = p.imgs[img];
+        ImgState *st = p.st + img;
+        const int H = im.H, W = im.W, y0 = td.y0, x0 = td.x0;
+
+        bool active = true;
+        int gcur_out = 0;
+        if (TRIAL) {
+            active = (st->done == 0) && (st->n < st->target);
+            gcur_out = st->gcur ^ 1;
         }
 
-        float acc[AUR][4];
-#pragma unroll
-        for (int i = 0; i < AUR; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-        // frame values of this thread's strip tasks (left, right, top, bottom)
-        float fr[4] = {0.f, 0.f, 0.f, 0.f};
-        const int aux = tid % Q::AUX, auy = tid / Q::AUX;  // adjoint unit of this thread
-        const bool sLft = x0 == 0, sTop = y0 == 0, sRgt = x0 + TX > W - 3, sBot = y0 + TY > H - 3;
-        const bool border = sLft || sTop || sRgt || sBot;
-
-        const int ngrp = p.nfp / G;
-        if (rank < ngrp) stage_weights<T>(sW, p, rank, tid);
-        for (int grp = rank, gi = 0; grp < ngrp; grp += CL, ++gi) {
-            const float *wb = sW + (gi & 1) * Q::WBUF;
-            cp_async_wait_all();  // this thread's copies of the group's weights
-            __syncthreads();      // sU / weights ready; previous group's sR and weight reads done
-            // the next group's weights into the other buffer (its last readers,
-            // the previous group, finished before the barrier above)
-            if (grp + CL < ngrp) stage_weights<T>(sW + ((gi + 1) & 1) * Q::WBUF, p, grp + CL, tid);
-            // ---- 3+4: forward bank and potential on tile + 3 -------------
-            for (int unit = tid; unit < FWD_UNITS; unit += NT) {
-                const int c = unit % R3X, rb = unit / R3X;
-                const int x = x0 - 3 + c, ylo = y0 - 3 + rb * FWD_ROWS;
-                const bool full = x >= 0 && x < W && ylo >= 0 && ylo + FWD_ROWS <= H;
-                const float fs = forward_unit<T, MODE>(sU, sR, wb, c, rb, y0, x0, H, W, !full);
-                sum2_add(accF, fs);
-            }
-            if (MODE == MODE_ENERGY_EXT) continue;
-            __syncthreads();  // sR complete
-
-            // ---- 5: adjoint bank on the tile (AUR x 4 unit per thread) -----
-            for (int i = 0; i < G; ++i) {
-                const float *wrow = wb + Q::WB_A + i * KT_PAD;
-                float kw[KT_PAD];
-#pragma unroll
-                for (int j = 0; j < KT_PAD / 4; ++j) {
-                    const float4 t = reinterpret_cast<const float4 *>(wrow)[j];
-                    kw[4 * j] = t.x;
-                    kw[4 * j + 1] = t.y;
-                    kw[4 * j + 2] = t.z;
-                    kw[4 * j + 3] = t.w;
-                }
-                const float *Ri = sR + (size_t)i * R3YA * SR_LD + (AUR * auy) * SR_LD + 4 * aux;
-#pragma unroll
-                for (int rr = 0; rr < AUR + KS - 1; ++rr) {
-                    const float4 a0 = *reinterpret_cast<const float4 *>(Ri + rr * SR_LD);
-                    const float4 a1 = *reinterpret_cast<const float4 *>(Ri + rr * SR_LD + 4);
-                    const float4 a2 = *reinterpret_cast<const float4 *>(Ri + rr * SR_LD + 8);
-                    const float v[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
-#pragma unroll
-                    for (int pp = 0; pp < AUR; ++pp) {
-                        const int aa = rr - pp;
-                        if (aa < 0 || aa >= KS) continue;
-#pragma unroll
-                        for (int bb = 0; bb < KS; ++bb)
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) acc[pp][q] = fmaf(kw[aa * KS + bb], v[q + bb], acc[pp][q]);
-                    }
-                }
-            }
-            // ---- 5b: K^T s on the frame outside the image (border tiles) --
-            // frame value at (j, jx) = sum_i sum_ab 2 theta_i k_i[a][b]
-            // s_i(j - 3 + a, jx - 3 + b), s_i zero off-image, so only the taps
-            // that reach into the image count.  The frame is cut into strips
-            // of depth d = 1..3, one (line, depth) task per thread and strip,
-            // with static tap loops: the left / right strips run over the
-            // ring's rows l in [0, R3Y) (axis_pos maps l to the image row j,
-            // the corner rows included), the top / bottom strips over the
-            // tile's columns.
-            if (border) {
-                if (tid < 3 * R3Y && (sLft || sRgt)) {
-                    // depth fastest: the lanes of a load read 3 columns of ~11
-                    // rows (a column of 32 rows would hit every bank 8 times:
-                    // SR_LD = 8 mod 32)
-                    const int d = 1 + tid % 3, l = tid / 3;
-                    int j;
-                    if (axis_pos(l, y0, TY, H, j)) {
-                        // rows of s inside the image and in the response region;
-                        // sR row of tap a: j - y0 + a
-                        const int alo = max(max(0, 3 - j), y0 - j), ahi = min(min(KS, H + 3 - j), R3Y + y0 - j);
-                        const int r0 = j - y0;
-                        if (sLft) {
-                            // frame column -d: taps b >= 3 + d, sR column b - d
-                            float sv = 0.f;
-#pragma unroll
-                            for (int i = 0; i < G; ++i) {
-                                const float *wrow = wb + Q::WB_A + i * KT_PAD;
-                                const float *Ri = sR + (size_t)i * R3YA * SR_LD;
-#pragma unroll
-                                for (int aa = 0; aa < KS; ++aa) {
-                                    if (aa < alo || aa >= ahi) continue;
-#pragma unroll
-                                    for (int bb = 4; bb < KS; ++bb)
-                                        if (bb >= 3 + d)
-                                            sv = fmaf(wrow[aa * KS + bb], Ri[(r0 + aa) * SR_LD + bb - d], sv);
-                                }
-                            }
-                            fr[0] += sv;
-                        }
-                        if (sRgt && W - d >= x0 && W - d < x0 + TX) {
-                            // frame column W - 1 + d: taps b <= 3 - d, sR column W - x0 - 1 + d + b
-                            float sv = 0.f;
-#pragma unroll
-                            for (int i = 0; i < G; ++i) {
-                                const float *wrow = wb + Q::WB_A + i * KT_PAD;
-                                const float *Ri = sR + (size_t)i * R3YA * SR_LD + (W - x0 - 1 + d);
-#pragma unroll
-                                for (int aa = 0; aa < KS; ++aa) {
-                                    if (aa < alo || aa >= ahi) continue;
-#pragma unroll
-                                    for (int bb = 0; bb < 3; ++bb)
-                                        if (bb <= 3 - d) sv = fmaf(wrow[aa * KS + bb], Ri[(r0 + aa) * SR_LD + bb], sv);
-                                }
-                            }
-                            fr[1] += sv;
-                        }
-                    }
-                }
-                if (tid < 3 * TX && (sTop || sBot)) {
-                    const int d = 1 + tid / TX, c = tid - (d - 1) * TX;  // image column x0 + c
-                    if (x0 + c < W) {
-                        if (sTop) {
-                            // frame row -d: taps a >= 3 + d, sR row a - d, sR column c + b
-                            float sv = 0.f;
-#pragma unroll
-                            for (int i = 0; i < G; ++i) {
-                                const float *wrow = wb + Q::WB_A + i * KT_PAD;
-                                const float *Ri = sR + (size_t)i * R3YA * SR_LD + c;
-#pragma unroll
-                                for (int aa = 4; aa < KS; ++aa) {
-                                    if (aa < 3 + d) continue;
-#pragma unroll
-                                    for (int bb = 0; bb < KS; ++bb)
-                                        sv = fmaf(wrow[aa * KS + bb], Ri[(aa - d) * SR_LD + bb], sv);
-                                }
-                            }
-                            fr[2] += sv;
-                        }
-                        if (sBot && H - d >= y0 && H - d < y0 + TY) {
-                            // frame row H - 1 + d: taps a <= 3 - d, sR row H - y0 - 1 + d + a
-                            float sv = 0.f;
-#pragma unroll
-                            for (int i = 0; i < G; ++i) {
-                                const float *wrow = wb + Q::WB_A + i * KT_PAD;
-                                const float *Ri = sR + (size_t)i * R3YA * SR_LD + (H - y0 - 1 + d) * SR_LD + c;
-#pragma unroll
-                                for (int aa = 0; aa < 3; ++aa) {
-                                    if (aa > 3 - d) continue;
-#pragma unroll
-                                    for (int bb = 0; bb < KS; ++bb) sv = fmaf(wrow[aa * KS + bb], Ri[aa * SR_LD + bb], sv);
-                                }
-                            }
-                            fr[3] += sv;
-                        }
-                    }
-                }
-            }
-        }
-
-        if constexpr (CL > 1) {
-            // ---- combine the ranks' partials at rank 0 (distributed shared memory)
-            auto cluster = cooperative_groups::this_cluster();
-            __syncthreads();  // this CTA's sR reads are done
-            constexpr int NA = AUR * 4;
-            constexpr int NFR = 4;
-            float *part = sR;  // per thread: NA adjoint sums, NFR frame values, F (s, c)
-            static_assert(NT * (NA + NFR + 2) <= (int)SM_R, "partials fit in sR");
-#pragma unroll
-            for (int pp = 0; pp < AUR; ++pp)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) part[tid * NA + pp * 4 + q] = acc[pp][q];
-#pragma unroll
-            for (int k = 0; k < NFR; ++k) part[NT * NA + tid * NFR + k] = fr[k];
-            part[NT * (NA + NFR) + 2 * tid] = accF.s;
-            part[NT * (NA + NFR) + 2 * tid + 1] = accF.c;
-            cluster.sync();  // every rank's partials are visible in the cluster
-            if (rank == 0) {
-                for (int r = 1; r < CL; ++r) {
-                    const float *rp = cluster.map_shared_rank(part, r);
-#pragma unroll
-                    for (int pp = 0; pp < AUR; ++pp)
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) acc[pp][q] += rp[tid * NA + pp * 4 + q];
-#pragma unroll
-                    for (int k = 0; k < NFR; ++k) fr[k] += rp[NT * NA + tid * NFR + k];
-                    accF = sum2_merge(accF, Sum2{rp[NT * (NA + NFR) + 2 * tid],
-                                                rp[NT * (NA + NFR) + 2 * tid + 1]});
-                }
-            }
-            cluster.sync();  // rank 0 has read the other ranks' shared memory
-        }
-
-        if (MODE != MODE_ENERGY_EXT && rank == 0) {
-            // ---- fold the frame back onto the pixels it mirrors ----------
-            if (border) {
-                __syncthreads();  // all sR reads done; reuse sR for the ring
-                // each ring slot is written by the one task that computed it
-                // (slots of lines outside this tile's frame are never read)
-                if (tid < 3 * R3Y) {
-                    const int d = 1 + tid % 3, l = tid / 3;
-                    if (sLft) sR[pos_to_ring<T>(l, 3 - d)] = fr[0];
-                    if (sRgt) sR[pos_to_ring<T>(l, TX + 2 + d)] = fr[1];
-                }
-                if (tid < 3 * TX) {
-                    const int d = 1 + tid / TX, c = tid - (d - 1) * TX;
-                    if (sTop) sR[pos_to_ring<T>(3 - d, c + 3)] = fr[2];
-                    if (sBot) sR[pos_to_ring<T>(TY + 2 + d, c + 3)] = fr[3];
-                }
-                __syncthreads();
-            }
+        if (active) {
+            // ---- 1+2: inertial step and prox on tile + 6 ---------------------
+            // per-thread sums: compensated FP32 for F and G (large terms), plain
+            // FP32 for the small step-test terms
+            Sum2 accF{0.f, 0.f}, accG{0.f, 0.f};
+            float accGD = 0.f, accDD = 0.f, accDP = 0.f;
             {
-                float *gout;
-                if (MODE == MODE_GRAD_EXT)
-                    gout = p.g_ext;
-                else if (MODE == MODE_INIT)
-                    gout = im.g[0];
-                else
-                    gout = im.g[gcur_out];
-#pragma unroll
-                for (int pp = 0; pp < AUR; ++pp) {
-                    const int y = y0 + AUR * auy + pp;
-                    if (y >= H) continue;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int x = x0 + 4 * aux + q;
-                        if (x >= W) continue;
-                        float gv = acc[pp][q];  // (K^T r)(y, x); the fold follows
-                        if (border && (y < 3 || y >= H - 3 || x < 3 || x >= W - 3)) {
-                            // frame positions that the symmetric extension maps onto
-                            // (y, x): at most one per axis (H, W >= 8); scalars, so
-                            // that nothing is indexed dynamically (local memory)
-                            const int oy = y - y0 + 3, ox = x - x0 + 3;
-                            const int qy = y < 3 ? 2 - y : (y >= H - 3 ? TY + 2 + H - y : -1);  // j = -y-1 | 2H-1-y
-                            const int qx = x < 3 ? 2 - x : (x >= W - 3 ? TX + 2 + W - x : -1);
-                            if (qx >= 0) gv += sR[pos_to_ring<T>(oy, qx)];
-                            if (qy >= 0) {
-                                gv += sR[pos_to_ring<T>(qy, ox)];
-                                if (qx >= 0) gv += sR[pos_to_ring<T>(qy, qx)];
+                int cur = 0, gcur = 0;
+                float a = 0.f, b = 0.f, tl = 0.f;
+                const float l1 = (float)im.lambda1, l2 = (float)im.lambda;  // combined model
+                if (TRIAL) {
+                    cur = st->cur;
+                    gcur = st->gcur;
+                    const double alpha = st->alpha;
+                    a = (float)alpha;
+                    b = (float)p.beta;
+                    tl = (float)(alpha * im.lambda);
+                }
+                const float *uc = (TRIAL || MODE == MODE_INIT) ? im.u[cur] : p.u_ext;
+                const float *upv = im.u[(cur + 2) % 3];
+                const float *gc = im.g[gcur];
+                float *un = im.u[(cur + 1) % 3];
+                const float *f2p = im.f2;
+                for (int idx = tid; idx < R6Y * R6X; idx += NT) {
+                    const int ry = idx / R6X, rx = idx - ry * R6X;
+                    const int y = y0 - 6 + ry, x = x0 - 6 + rx;
+                    const size_t off = (size_t)reflect(y, H) * W + reflect(x, W);
+                    const bool inner = ry >= 6 && ry < 6 + TY && rx >= 6 && rx < 6 + TX && y < H && x < W;
+                    float v;
+                    if (TRIAL) {
+                        // L2 loads: a persistent launch rewrites these planes while it runs
+                        const float u0 = __ldcg(uc + off), u_1 = __ldcg(upv + off), g0 = __ldcg(gc + off);
+                        const float f2 = __ldg(f2p + off);
+                        const float dprev = u0 - u_1;
+                        const float uhat = fmaf(-a, g0, fmaf(b, dprev, u0));
+                        v = MODEL == 0 ? prox_g(uhat, f2, tl) : prox_w(uhat, f2, a, l1, l2);
+                        if (inner && rank == 0) {
+                            un[off] = v;
+                            const float d = v - u0;
+                            accGD = fmaf(g0, d, accGD);
+                            accDD = fmaf(d, d, accDD);
+                            accDP = fmaf(d, dprev, accDP);
+                            sum2_add(accG, MODEL == 0 ? v * v - 2.0f * f2 * logf(v) : data_w(v, f2, l1, l2));
+                        }
+                    } else {
+                        v = __ldg(uc + off);
+                        if (inner && rank == 0) {
+                            const float f2 = __ldg(f2p + off);
+                            sum2_add(accG, MODEL == 0 ? v * v - 2.0f * f2 * logf(v) : data_w(v, f2, l1, l2));
+                        }
+                    }
+                    sU[ry * SU_LD + rx] = MODEL == 0 ? v : expf(v);  // the bank sees u
+                }
+            }
+
+            float acc[AUR][4];
+    #pragma unroll
+            for (int i = 0; i < AUR; ++i)
+    #pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+            // frame values of this thread's strip tasks (left, right, top, bottom)
+            float fr[4] = {0.f, 0.f, 0.f, 0.f};
+            const int aux = tid % Q::AUX, auy = tid / Q::AUX;  // adjoint unit of this thread
+            const bool sLft = x0 == 0, sTop = y0 == 0, sRgt = x0 + TX > W - 3, sBot = y0 + TY > H - 3;
+            const bool border = sLft || sTop || sRgt || sBot;
+
+            const int ngrp = p.nfp / G;
+            if (rank < ngrp) stage_weights<T>(sW, p, rank, tid);
+            for (int grp = rank, gi = 0; grp < ngrp; grp += CL, ++gi) {
+                const float *wb = sW + (gi & 1) * Q::WBUF;
+                cp_async_wait_all();  // this thread's copies of the group's weights
+                __syncthreads();      // sU / weights ready; previous group's sR and weight reads done
+                // the next group's weights into the other buffer (its last readers,
+                // the previous group, finished before the barrier above)
+                if (grp + CL < ngrp) stage_weights<T>(sW + ((gi + 1) & 1) * Q::WBUF, p, grp + CL, tid);
+                // ---- 3+4: forward bank and potential on tile + 3 -------------
+                for (int unit = tid; unit < FWD_UNITS; unit += NT) {
+                    const int c = unit % R3X, rb = unit / R3X;
+                    const int x = x0 - 3 + c, ylo = y0 - 3 + rb * FWD_ROWS;
+                    const bool full = x >= 0 && x < W && ylo >= 0 && ylo + FWD_ROWS <= H;
+                    const float fs = forward_unit<T, MODE>(sU, sR, wb, c, rb, y0, x0, H, W, !full);
+                    sum2_add(accF, fs);
+                }
+                if (MODE == MODE_ENERGY_EXT) continue;
+                __syncthreads();  // sR complete
+
+                // ---- 5: adjoint bank on the tile (AUR x 4 unit per thread) -----
+                for (int i = 0; i < G; ++i) {
+                    const float *wrow = wb + Q::WB_A + i * KT_PAD;
+                    float kw[KT_PAD];
+    #pragma unroll
+                    for (int j = 0; j < KT_PAD / 4; ++j) {
+                        const float4 t = reinterpret_cast<const float4 *>(wrow)[j];
+                        kw[4 * j] = t.x;
+                        kw[4 * j + 1] = t.y;
+                        kw[4 * j + 2] = t.z;
+                        kw[4 * j + 3] = t.w;
+                    }
+                    const float *Ri = sR + (size_t)i * R3YA * SR_LD + (AUR * auy) * SR_LD + 4 * aux;
+    #pragma unroll
+                    for (int rr = 0; rr < AUR + KS - 1; ++rr) {
+                        const float4 a0 = *reinterpret_cast<const float4 *>(Ri + rr * SR_LD);
+                        const float4 a1 = *reinterpret_cast<const float4 *>(Ri + rr * SR_LD + 4);
+                        const float4 a2 = *reinterpret_cast<const float4 *>(Ri + rr * SR_LD + 8);
+                        const float v[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
+    #pragma unroll
+                        for (int pp = 0; pp < AUR; ++pp) {
+                            const int aa = rr - pp;
+                            if (aa < 0 || aa >= KS) continue;
+    #pragma unroll
+                            for (int bb = 0; bb < KS; ++bb)
+    #pragma unroll
+                                for (int q = 0; q < 4; ++q) acc[pp][q] = fmaf(kw[aa * KS + bb], v[q + bb], acc[pp][q]);
+                        }
+                    }
+                }
+                // ---- 5b: K^T s on the frame outside the image (border tiles) --
+                // frame value at (j, jx) = sum_i sum_ab 2 theta_i k_i[a][b]
+                // s_i(j - 3 + a, jx - 3 + b), s_i zero off-image, so only the taps
+                // that reach into the image count.  The frame is cut into strips
+                // of depth d = 1..3, one (line, depth) task per thread and strip,
+                // with static tap loops: the left / right strips run over the
+                // ring's rows l in [0, R3Y) (axis_pos maps l to the image row j,
+                // the corner rows included), the top / bottom strips over the
+                // tile's columns.
+                if (border) {
+                    if (tid < 3 * R3Y && (sLft || sRgt)) {
+                        // depth fastest: the lanes of a load read 3 columns of ~11
+                        // rows (a column of 32 rows would hit every bank 8 times:
+                        // SR_LD = 8 mod 32)
+                        const int d = 1 + tid % 3, l = tid / 3;
+                        int j;
+                        if (axis_pos(l, y0, TY, H, j)) {
+                            // rows of s inside the image and in the response region;
+                            // sR row of tap a: j - y0 + a
+                            const int alo = max(max(0, 3 - j), y0 - j), ahi = min(min(KS, H + 3 - j), R3Y + y0 - j);
+                            const int r0 = j - y0;
+                            if (sLft) {
+                                // frame column -d: taps b >= 3 + d, sR column b - d
+                                float sv = 0.f;
+    #pragma unroll
+                                for (int i = 0; i < G; ++i) {
+                                    const float *wrow = wb + Q::WB_A + i * KT_PAD;
+                                    const float *Ri = sR + (size_t)i * R3YA * SR_LD;
+    #pragma unroll
+                                    for (int aa = 0; aa < KS; ++aa) {
+                                        if (aa < alo || aa >= ahi) continue;
+    #pragma unroll
+                                        for (int bb = 4; bb < KS; ++bb)
+                                            if (bb >= 3 + d)
+                                                sv = fmaf(wrow[aa * KS + bb], Ri[(r0 + aa) * SR_LD + bb - d], sv);
+                                    }
+                                }
+                                fr[0] += sv;
+                            }
+                            if (sRgt && W - d >= x0 && W - d < x0 + TX) {
+                                // frame column W - 1 + d: taps b <= 3 - d, sR column W - x0 - 1 + d + b
+                                float sv = 0.f;
+    #pragma unroll
+                                for (int i = 0; i < G; ++i) {
+                                    const float *wrow = wb + Q::WB_A + i * KT_PAD;
+                                    const float *Ri = sR + (size_t)i * R3YA * SR_LD + (W - x0 - 1 + d);
+    #pragma unroll
+                                    for (int aa = 0; aa < KS; ++aa) {
+                                        if (aa < alo || aa >= ahi) continue;
+    #pragma unroll
+                                        for (int bb = 0; bb < 3; ++bb)
+                                            if (bb <= 3 - d) sv = fmaf(wrow[aa * KS + bb], Ri[(r0 + aa) * SR_LD + bb], sv);
+                                    }
+                                }
+                                fr[1] += sv;
                             }
                         }
-                        // combined model: grad_w F = e^w (.) K^T r, u = e^w from sU
-                        if (MODEL == 1) gv *= sU[(y - y0 + 6) * SU_LD + (x - x0 + 6)];
-                        gout[(size_t)y * W + x] = gv;
+                    }
+                    if (tid < 3 * TX && (sTop || sBot)) {
+                        const int d = 1 + tid / TX, c = tid - (d - 1) * TX;  // image column x0 + c
+                        if (x0 + c < W) {
+                            if (sTop) {
+                                // frame row -d: taps a >= 3 + d, sR row a - d, sR column c + b
+                                float sv = 0.f;
+    #pragma unroll
+                                for (int i = 0; i < G; ++i) {
+                                    const float *wrow = wb + Q::WB_A + i * KT_PAD;
+                                    const float *Ri = sR + (size_t)i * R3YA * SR_LD + c;
+    #pragma unroll
+                                    for (int aa = 4; aa < KS; ++aa) {
+                                        if (aa < 3 + d) continue;
+    #pragma unroll
+                                        for (int bb = 0; bb < KS; ++bb)
+                                            sv = fmaf(wrow[aa * KS + bb], Ri[(aa - d) * SR_LD + bb], sv);
+                                    }
+                                }
+                                fr[2] += sv;
+                            }
+                            if (sBot && H - d >= y0 && H - d < y0 + TY) {
+                                // frame row H - 1 + d: taps a <= 3 - d, sR row H - y0 - 1 + d + a
+                                float sv = 0.f;
+    #pragma unroll
+                                for (int i = 0; i < G; ++i) {
+                                    const float *wrow = wb + Q::WB_A + i * KT_PAD;
+                                    const float *Ri = sR + (size_t)i * R3YA * SR_LD + (H - y0 - 1 + d) * SR_LD + c;
+    #pragma unroll
+                                    for (int aa = 0; aa < 3; ++aa) {
+                                        if (aa > 3 - d) continue;
+    #pragma unroll
+                                        for (int bb = 0; bb < KS; ++bb) sv = fmaf(wrow[aa * KS + bb], Ri[aa * SR_LD + bb], sv);
+                                    }
+                                }
+                                fr[3] += sv;
+                            }
+                        }
                     }
                 }
             }
-        }
 
-        // ---- 6: per-tile FP64 partial sums, last-CTA decision -------------
-        if (rank == 0) {
-            const Sum2 vals[NRED] = {accF, accG, {accGD, 0.f}, {accDD, 0.f}, {accDP, 0.f}};
-            tile_finish<NT>(p, MODE, gtile, img, im, st, vals, sRed, &sLast);
+            if constexpr (CL > 1) {
+                // ---- combine the ranks' partials at rank 0 (distributed shared memory)
+                auto cluster = cooperative_groups::this_cluster();
+                __syncthreads();  // this CTA's sR reads are done
+                constexpr int NA = AUR * 4;
+                constexpr int NFR = 4;
+                float *part = sR;  // per thread: NA adjoint sums, NFR frame values, F (s, c)
+                static_assert(NT * (NA + NFR + 2) <= (int)SM_R, "partials fit in sR");
+    #pragma unroll
+                for (int pp = 0; pp < AUR; ++pp)
+    #pragma unroll
+                    for (int q = 0; q < 4; ++q) part[tid * NA + pp * 4 + q] = acc[pp][q];
+    #pragma unroll
+                for (int k = 0; k < NFR; ++k) part[NT * NA + tid * NFR + k] = fr[k];
+                part[NT * (NA + NFR) + 2 * tid] = accF.s;
+                part[NT * (NA + NFR) + 2 * tid + 1] = accF.c;
+                cluster.sync();  // every rank's partials are visible in the cluster
+                if (rank == 0) {
+                    for (int r = 1; r < CL; ++r) {
+                        const float *rp = cluster.map_shared_rank(part, r);
+    #pragma unroll
+                        for (int pp = 0; pp < AUR; ++pp)
+    #pragma unroll
+                            for (int q = 0; q < 4; ++q) acc[pp][q] += rp[tid * NA + pp * 4 + q];
+    #pragma unroll
+                        for (int k = 0; k < NFR; ++k) fr[k] += rp[NT * NA + tid * NFR + k];
+                        accF = sum2_merge(accF, Sum2{rp[NT * (NA + NFR) + 2 * tid],
+                                                    rp[NT * (NA + NFR) + 2 * tid + 1]});
+                    }
+                }
+                cluster.sync();  // rank 0 has read the other ranks' shared memory
+            }
+
+            if (MODE != MODE_ENERGY_EXT && rank == 0) {
+                // ---- fold the frame back onto the pixels it mirrors ----------
+                if (border) {
+                    __syncthreads();  // all sR reads done; reuse sR for the ring
+                    // each ring slot is written by the one task that computed it
+                    // (slots of lines outside this tile's frame are never read)
+                    if (tid < 3 * R3Y) {
+                        const int d = 1 + tid % 3, l = tid / 3;
+                        if (sLft) sR[pos_to_ring<T>(l, 3 - d)] = fr[0];
+                        if (sRgt) sR[pos_to_ring<T>(l, TX + 2 + d)] = fr[1];
+                    }
+                    if (tid < 3 * TX) {
+                        const int d = 1 + tid / TX, c = tid - (d - 1) * TX;
+                        if (sTop) sR[pos_to_ring<T>(3 - d, c + 3)] = fr[2];
+                        if (sBot) sR[pos_to_ring<T>(TY + 2 + d, c + 3)] = fr[3];
+                    }
+                    __syncthreads();
+                }
+                {
+                    float *gout;
+                    if (MODE == MODE_GRAD_EXT)
+                        gout = p.g_ext;
+                    else if (MODE == MODE_INIT)
+                        gout = im.g[0];
+                    else
+                        gout = im.g[gcur_out];
+    #pragma unroll
+                    for (int pp = 0; pp < AUR; ++pp) {
+                        const int y = y0 + AUR * auy + pp;
+                        if (y >= H) continue;
+    #pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int x = x0 + 4 * aux + q;
+                            if (x >= W) continue;
+                            float gv = acc[pp][q];  // (K^T r)(y, x); the fold follows
+                            if (border && (y < 3 || y >= H - 3 || x < 3 || x >= W - 3)) {
+                                // frame positions that the symmetric extension maps onto
+                                // (y, x): at most one per axis (H, W >= 8); scalars, so
+                                // that nothing is indexed dynamically (local memory)
+                                const int oy = y - y0 + 3, ox = x - x0 + 3;
+                                const int qy = y < 3 ? 2 - y : (y >= H - 3 ? TY + 2 + H - y : -1);  // j = -y-1 | 2H-1-y
+                                const int qx = x < 3 ? 2 - x : (x >= W - 3 ? TX + 2 + W - x : -1);
+                                if (qx >= 0) gv += sR[pos_to_ring<T>(oy, qx)];
+                                if (qy >= 0) {
+                                    gv += sR[pos_to_ring<T>(qy, ox)];
+                                    if (qx >= 0) gv += sR[pos_to_ring<T>(qy, qx)];
+                                }
+                            }
+                            // combined model: grad_w F = e^w (.) K^T r, u = e^w from sU
+                            if (MODEL == 1) gv *= sU[(y - y0 + 6) * SU_LD + (x - x0 + 6)];
+                            gout[(size_t)y * W + x] = gv;
+                        }
+                    }
+                }
+            }
+
+            // ---- 6: per-tile FP64 partial sums, last-CTA decision -------------
+            if (rank == 0) {
+                const Sum2 vals[NRED] = {accF, accG, {accGD, 0.f}, {accDD, 0.f}, {accDP, 0.f}};
+                tile_finish<NT>(p, MODE, gtile, img, im, st, vals, sRed, &sLast);
+            }
         }
+        if constexpr (!PERSIST) break;
     }
 
     // ---- loop control: the last rank-0 CTA of the launch -------------------
+    if constexpr (PERSIST) persist_exit(p, gridDim.x);
     if (MODE == MODE_TRIAL && rank == 0) loop_control(p, gridDim.x / CL);
 }
 
@@ -618,6 +645,10 @@ cudaError_t prepare_tile() {
     if ((e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_TRIAL, T, MODEL, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)) !=
         cudaSuccess)
         return e;
+    if constexpr (CL == 1)
+        if ((e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_PTRIAL, T, MODEL, 1>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, b)) != cudaSuccess)
+            return e;
     if ((e = cudaFuncSetAttribute(fp32_tile_kernel<MODE_INIT, T, MODEL, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)) !=
         cudaSuccess)
         return e;

@@ -14,6 +14,14 @@
 // backtracking rule on the device; the last block of the grid updates the
 // device-side loop control (count of active images, trial budget, and the
 // while-condition of the CUDA graph when the loop runs as a graph).
+//
+// Persistent trial launches (MODE_PTRIAL): one launch runs every trial of
+// every image.  Its CTAs (as many as fit on the GPU at once) take tiles from
+// per-image counters sched[j]: the block that decides image j's trial resets
+// sched[j] to 0 when the image goes on, so that the tiles of its next trial
+// become available at once, while other images' trials still run.  Each
+// image's trials, and each trial's arithmetic and reduction order, are those
+// of the per-trial launches: the results are the same bit for bit.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -36,6 +44,7 @@ enum Mode : int {
     MODE_INIT = 1,        // g = grad F(u[0]) into g[0]; F, G; initialise the state
     MODE_GRAD_EXT = 2,    // g_ext = grad F(u_ext); F, G into results
     MODE_ENERGY_EXT = 3,  // F(u_ext), G(u_ext) into results
+    MODE_PTRIAL = 4,      // persistent: one launch runs every trial of every image
 };
 
 struct ImgDesc {
@@ -63,6 +72,7 @@ struct ImgState {
     double H_target;  // stop once an accepted H <= H_target (-inf: no energy target)
     double Gf;  // min of the data term: at u = f (variant), at w = log f (combined)
     long long n, trials, backtracks, target;
+    long long trial_limit;  // persistent launches: trials allowed before FE_ETIMEOUT
     int cur, gcur, bt, status, done, converged;
 };
 
@@ -81,7 +91,16 @@ struct LoopCtl {
     int active;              // images still iterating after the last launch
     long long budget;        // trial launches left before FE_ETIMEOUT
     long long launches;      // trial launches executed (for launch accounting)
+    unsigned long long decisions;  // persistent launches: trial decisions taken (progress)
+    int abort;               // persistent launches: a wait for work ran out
+    int pad;
 };
+
+// A persistent launch's wait for work gives up when no trial of any image has
+// been decided for this long (one trial of the largest image takes
+// milliseconds): the launch then stops with LoopCtl::abort set instead of
+// spinning on.
+constexpr unsigned long long PERSIST_STALL_NS = 4000000000ull;
 
 struct KParams {
     const ImgDesc *imgs;
@@ -109,6 +128,11 @@ struct KParams {
     const void *tcw_fwd;
     const void *tcw_adj;
     int *tc_error;              // set when a tensor-core wait runs out
+    // persistent trial launches: per-image tile counters ([nimg]; the tiles
+    // of image j's current trial are sched[j] .. ntiles - 1 still to take)
+    // and each image's tiles in the order they are taken (global indices)
+    int *sched;
+    const int *porder;
 };
 
 // FP32 fused tile kernel (fe_fp32.cu)
@@ -124,9 +148,11 @@ cudaError_t fp32_prepare();  // opt in to the large shared-memory carve-out (eve
 cudaError_t fp32_launch(int mode, const KParams &p, int grid, cudaStream_t s, int T = fp32_tile_size,
                         int model = 0, int cl = 1);
 const void *fp32_trial_entry(int T = fp32_tile_size, int model = 0, int cl = 1);
+const void *fp32_ptrial_entry(int T, int model);  // persistent trial kernel (one CTA per tile)
 cudaError_t fp32c_prepare();  // combined-model instantiations (fe_fp32_comb.cu)
 cudaError_t fp32c_launch(int mode, const KParams &p, int grid, cudaStream_t s, int T, int cl);
 const void *fp32c_trial_entry(int T, int cl);
+const void *fp32c_ptrial_entry(int T);
 cudaError_t fp32cl64_prepare();  // 64 x 64 tiles on 4-CTA clusters, both models (fe_fp32_cl64.cu)
 cudaError_t fp32cl64_launch(int mode, const KParams &p, int grid, cudaStream_t s, int model);
 const void *fp32cl64_trial_entry(int model);
@@ -142,9 +168,11 @@ cudaError_t tc_prepare();  // every format and model
 // model: 0 = Eq. variant (iterate u), 1 = combined model (iterate w = log u)
 cudaError_t tc_launch(int mode, int fmt, const KParams &p, int grid, cudaStream_t s, int model = 0);
 const void *tc_trial_entry(int fmt, int model = 0);
+const void *tc_ptrial_entry(int fmt, int model = 0);  // persistent trial kernel
 cudaError_t tcc_prepare();  // combined-model instantiations (fe_tc_comb.cu)
 cudaError_t tcc_launch(int mode, int fmt, const KParams &p, int grid, cudaStream_t s);
 const void *tcc_trial_entry(int fmt);
+const void *tcc_ptrial_entry(int fmt);
 // Host: filter bank rounded to the operand type (BF16 round-to-nearest-even,
 // TF32 round-to-nearest-away) in the byte layout of the two GEMM B operands.
 void tc_build_weights(int fmt, const float *filters, int nf, std::vector<unsigned char> &fwd,

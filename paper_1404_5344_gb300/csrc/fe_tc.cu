@@ -79,5 +79,6 @@ cudaError_t tc_launch(int mode, int fmt, const KParams &p, int ngrid, cudaStream
 }
 
 const void *tc_trial_entry(int fmt, int model) { return model == 1 ? tcc_trial_entry(fmt) : trial_entry<0>(fmt); }
+const void *tc_ptrial_entry(int fmt, int model) { return model == 1 ? tcc_ptrial_entry(fmt) : ptrial_entry<0>(fmt); }
 
 }  // namespace fe

@@ -16,5 +16,6 @@ cudaError_t tcc_launch(int mode, int fmt, const KParams &p, int ngrid, cudaStrea
 }
 
 const void *tcc_trial_entry(int fmt) { return trial_entry<1>(fmt); }
+const void *tcc_ptrial_entry(int fmt) { return ptrial_entry<1>(fmt); }
 
 }  // namespace fe

@@ -272,481 +272,536 @@ __global__ void __launch_bounds__(NT, FMT != 2 ? 3 : 2) tc_tile_kernel(const KPa
     __shared__ int sLast;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int gtile = p.order ? p.order[p.tile0 + (int)blockIdx.x] : p.tile0 + (int)blockIdx.x;
-    const TileDesc td = p.tiles[gtile];
-    const int img = td.img;
-    const ImgDesc im = p.imgs[img];
-    ImgState *st = p.st + img;
-    const int H = im.H, W = im.W, y0 = td.y0, x0 = td.x0, oh = td.oh, ow = td.ow, sy = td.sy, sx = td.sx;
-
-    bool active = true;
-    int gcur_out = 0;
-    if (MODE == MODE_TRIAL) {
-        active = (st->done == 0) && (st->n < st->target);
-        gcur_out = st->gcur ^ 1;
-    }
-
-    if (active) {
-        int cur = 0, gcur = 0;
-        if (MODE == MODE_TRIAL) {
-            cur = st->cur;
-            gcur = st->gcur;
-        }
-        // ---- TMA box loads of the trial's inputs (tile + 6 halo) -----------
-        // The box starts at (x0 - 6) rounded down to a multiple of 4 columns
-        // (16 bytes); it may reach outside the image, where it reads zeros.
-        // The symmetric extension is applied afterwards, by indexing the
-        // staged box at reflected coordinates (all of which lie in the box).
-        constexpr int SP = (int)(C::STAGE_PLANE / 4);  // staging plane stride (floats)
-        const bool use_tma = MODE == MODE_TRIAL && im.tmap != nullptr;
-        const int ys = y0 - 6, xs = ((x0 - 6) >> 2) << 2;  // arithmetic shift: floor
-        const float *stg = reinterpret_cast<const float *>(smem + C::OFF_STAGE);
-        if (use_tma && tid == 0) {
-            tc::mbar_init(&bar_ld, 1);
-            tc::mbar_arrive_expect_tx(&bar_ld, 4u * (uint32_t)(tc_box_y * tc_box_x * 4));
-            const unsigned char *tm = static_cast<const unsigned char *>(im.tmap);
-            float *dst = reinterpret_cast<float *>(smem + C::OFF_STAGE);
-            tc::tma_load_2d(dst, tm + 128 * cur, xs, ys, &bar_ld);                   // u^n
-            tc::tma_load_2d(dst + SP, tm + 128 * ((cur + 2) % 3), xs, ys, &bar_ld);  // u^{n-1}
-            tc::tma_load_2d(dst + 2 * SP, tm + 128 * (3 + gcur), xs, ys, &bar_ld);   // g^n
-            tc::tma_load_2d(dst + 3 * SP, tm + 128 * 5, xs, ys, &bar_ld);            // f^2
-        }
-        bool tc_ok = true;
-        // ---- rounded filter bank (B operands) and theta into shared memory --
-        {
-            const uint4 *gf = reinterpret_cast<const uint4 *>(p.tcw_fwd);
-            const uint4 *ga = reinterpret_cast<const uint4 *>(p.tcw_adj);
-            for (int j = tid; j < (int)(C::BF_BYTES / 16); j += NT) reinterpret_cast<uint4 *>(sBf)[j] = __ldg(gf + j);
-            for (int j = tid; j < (int)(C::BA_BYTES / 16); j += NT) reinterpret_cast<uint4 *>(sBa)[j] = __ldg(ga + j);
-            if (tid < NF) {
-                const float th = __ldg(p.theta + tid);
-                sTh[tid] = th;
-                sTh[NF + tid] = 2.0f * th;
+    // persistent launches (MODE_PTRIAL): the CTA runs tiles until every image
+    // has stopped, taking each from the per-image counters, and does the
+    // set-up below (B operands, barriers, tensor memory) once; otherwise the
+    // launch's block index names the one tile
+    constexpr bool PERSIST = MODE == MODE_PTRIAL;
+    constexpr bool TRIAL = MODE == MODE_TRIAL || PERSIST;
+    __shared__ int sTask;
+    int pref = p.nimg > 0 ? (int)blockIdx.x % p.nimg : 0;  // image of the last tile taken
+    bool setup = false;     // the CTA's one-time set-up is done (uniform over the CTA)
+    uint32_t ld_phase = 0;  // parity of bar_ld's current phase (one phase per tile with TMA)
+    for (;;) {
+        int gtile;
+        if constexpr (PERSIST) {
+            __syncthreads();  // the previous tile is done with shared memory and sTask
+            if (warp == 0) {
+                const int t = persist_grab(p, pref);
+                if (lane == 0) sTask = t;
             }
-            // the padding columns of the planes (read with weight 0) hold zeros
-            for (int j = tid; j < C::NPL * R6Y; j += NT) {
-                uint32_t *rowp = sP + (j / R6Y) * C::PL_WORDS + (j % R6Y) * (PP * C::EB / 4);
-                if (C::BF)
-                    rowp[(PP / 2) - 2] = rowp[(PP / 2) - 1] = 0u;  // elements 36..39 (the writes below fill 36, 37)
-                else
-                    rowp[PP - 2] = rowp[PP - 1] = 0u;
-            }
-        }
-        __syncthreads();  // pad zeros before the plane writes of the prologue
-        if (tid == 0) {
-            tc::mbar_init(&bar_f, 1);
-            tc::mbar_init(&bar_a, 1);
-        }
-        if (warp == 0) tc::tmem_alloc(&tbase, TMEM_COLS);
-
-        // ---- inertial step and prox on tile + 6 (owned pixels: sums) -------
-        // per-thread sums: compensated FP32 for F and G (large terms), plain
-        // FP32 for the small step-test terms
-        Sum2 accF{0.f, 0.f}, accG{0.f, 0.f};
-        float accGD = 0.f, accDD = 0.f, accDP = 0.f;
-        if (use_tma && !tc::mbar_wait(&bar_ld, 0)) {
-            tc_ok = false;                // the tile's sums are poisoned below
-            (void)tc::mbar_wait(&bar_ld, 0);  // a second bounded chance for copies in flight
-        }
-        const float *uc = (MODE == MODE_TRIAL || MODE == MODE_INIT) ? im.u[cur] : p.u_ext;
-        float *un = im.u[(cur + 1) % 3];
-        // the iterate at which the gradient is taken (combined model: w, to form e^w at the output)
-        const float *xg = MODE == MODE_TRIAL ? un : uc;
-        {
-            float a = 0.f, b = 0.f, tl = 0.f;
-            const float l1 = (float)im.lambda1, l2 = (float)im.lambda;  // combined model
-            if (MODE == MODE_TRIAL) {
-                const double alpha = st->alpha;
-                a = (float)alpha;
-                b = (float)p.beta;
-                tl = (float)(alpha * im.lambda);
-            }
-            const float *upv = im.u[(cur + 2) % 3];
-            const float *gc = im.g[gcur];
-            const float *f2p = im.f2;
-            const float c4 = 4.0f * (1.0f + tl) * tl, inv2 = 1.0f / (2.0f * (1.0f + tl)), tl2 = 2.0f * tl;
-            // tile + 6 inside the image: no reflection
-            const bool in6 = y0 >= 6 && y0 + TY + 6 <= H && x0 >= 6 && x0 + TX + 6 <= W;
-            constexpr int NPIX = R6Y * R6X, UNR = 4;
-            for (int base = 0; base < NPIX; base += UNR * NT) {
-                size_t off[UNR];
-                bool inb[UNR], owned[UNR];
-                float u0[UNR], u_1[UNR], g0[UNR], f2[UNR];
-#pragma unroll
-                for (int k = 0; k < UNR; ++k) {
-                    const int idx = base + k * NT + tid;
-                    inb[k] = idx < NPIX;
-                    const int ry = inb[k] ? idx / R6X : 0, rx = inb[k] ? idx - ry * R6X : 0;
-                    const int yr = in6 ? y0 - 6 + ry : reflect(y0 - 6 + ry, H);
-                    const int xr = in6 ? x0 - 6 + rx : reflect(x0 - 6 + rx, W);
-                    off[k] = (size_t)yr * W + xr;
-                    owned[k] = inb[k] && ry >= 6 + sy && ry < 6 + sy + oh && rx >= 6 + sx && rx < 6 + sx + ow;
-                    if (use_tma) {
-                        const int si = (yr - ys) * tc_box_x + (xr - xs);
-                        u0[k] = stg[si];
-                        u_1[k] = stg[SP + si];
-                        g0[k] = stg[2 * SP + si];
-                        f2[k] = stg[3 * SP + si];
-                    } else {
-                        u0[k] = __ldg(uc + off[k]);
-                        f2[k] = (MODE == MODE_TRIAL || owned[k]) ? __ldg(f2p + off[k]) : 1.0f;
-                        if (MODE == MODE_TRIAL) {
-                            u_1[k] = __ldg(upv + off[k]);
-                            g0[k] = __ldg(gc + off[k]);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < UNR; ++k) {
-                    if (!inb[k]) continue;
-                    float v;
-                    if (MODE == MODE_TRIAL) {
-                        const float dprev = u0[k] - u_1[k];
-                        const float uhat = fmaf(-a, g0[k], fmaf(b, dprev, u0[k]));
-                        v = MODEL == 0 ? prox_g_sfu(uhat, f2[k], c4, inv2, tl2) : prox_w(uhat, f2[k], a, l1, l2);
-                        if (owned[k]) {
-                            un[off[k]] = v;
-                            const float d = v - u0[k];
-                            accGD = fmaf(g0[k], d, accGD);
-                            accDD = fmaf(d, d, accDD);
-                            accDP = fmaf(d, dprev, accDP);
-                        }
-                    } else {
-                        v = u0[k];
-                    }
-                    // data term (variant: u^2 - 2 f^2 log u, the log on the special-function unit)
-                    if (owned[k])
-                        sum2_add(accG, MODEL == 0 ? fmaf(v, v, (-2.0f * LN2) * f2[k] * lg2_ftz(v))
-                                                  : data_w(v, f2[k], l1, l2));
-                    // hi / lo planes of the operand type (the bank sees u)
-                    const float uv = MODEL == 0 ? v : expf(v);
-                    const int idx = base + k * NT + tid, ry = idx / R6X, rx = idx - ry * R6X;
-                    if (C::BF) {
-                        const __nv_bfloat16 hb = __float2bfloat16_rn(uv);
-                        const __nv_bfloat16 lb = __float2bfloat16_rn(uv - __bfloat162float(hb));
-                        __nv_bfloat16 *ph = reinterpret_cast<__nv_bfloat16 *>(sP);
-                        __nv_bfloat16 *pl = reinterpret_cast<__nv_bfloat16 *>(sP + C::PL_WORDS);
-                        const int e = ry * PP + rx;
-                        ph[e] = hb;
-                        pl[e] = lb;
-                    } else {
-                        const float hv = tc::round_tf32(uv);
-                        const int e = ry * PP + rx;
-                        sP[e] = __float_as_uint(hv);
-                        sP[C::PL_WORDS + e] = __float_as_uint(tc::round_tf32(uv - hv));
-                    }
-                }
-            }
-        }
-
-        const uint32_t sAF_u32 = tc::smem_u32(sAF), sR_u32 = tc::smem_u32(sR);
-        const uint32_t sBf_u32 = tc::smem_u32(sBf), sBa_u32 = tc::smem_u32(sBa);
-        constexpr uint32_t SBO_F = (uint32_t)(C::KFWD / C::E) * 128, SBO_A = (uint32_t)(C::KADJ / C::E) * 128;
-        constexpr uint32_t SBO_BF = (uint32_t)(C::KPASS / C::E) * 128, SBO_BA = (uint32_t)(NF / C::E) * 128;
-        constexpr int KS_F = C::KPASS / C::KSTEP, KS_A = NF / C::KSTEP;  // K steps of one pass
-        constexpr uint32_t IDESC_F = tc::make_idesc(C::OPF, 128, NF), IDESC_A = tc::make_idesc(C::OPF, 128, NTAP);
-        const int m = tid & 127, part = tid >> 7;  // im2col: pixel, chunk parity
-        const int wg = warp >> 2, lg = warp & 3;   // epilogues: column half, TMEM lane group
-        const bool edge_x = x0 == 0 || x0 + TX >= W;
-        const bool full_y = y0 >= 3 && y0 + TY + 3 <= H, full_x = x0 >= 3 && x0 + TX + 3 <= W;
-        const bool all_in = full_y && full_x;  // every halo pixel lies in the image
-
-        // every plane element is written, and every staged value read,
-        // before the im2col of block 0 reads the planes and overwrites the
-        // staging area
-        __syncthreads();
-        // block 0: im2col and forward MMA
-        im2col<FMT>(sP, sAF, 0, m, part);
-        tc::fence_proxy_async();
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        const uint32_t taddr = tbase;
-        const uint32_t lane_base = (uint32_t)(lg * 32) << 16;
-        if (tid == 0) {
-#pragma unroll
-            for (int ks = 0; ks < C::KFWD / C::KSTEP; ++ks)
-                tc::mma<C::OPF>(taddr, tc::make_smem_desc(sAF_u32 + ks * 256, 128, SBO_F),
-                             tc::make_smem_desc(sBf_u32 + (ks % KS_F) * 256, 128, SBO_BF), IDESC_F,
-                             ks > 0 ? 1u : 0u);
-            tc::mma_commit(&bar_f);
-        }
-        uint32_t phase_f = 0, phase_a = 0;
-
-        // epilogue 2 of block pb: horizontal col2im of S (TMEM) into the H ring
-        auto epi2 = [&](int pb) {
-            const int row = 4 * pb + lg;
-            const int slot = row % HRING;
-            const int a_lo = wg == 0 ? 0 : 4;
-            float s8[4][8];
-            // warpgroup 1 has 3 window rows; it loads a 4th (columns 64 + 49
-            // .. 64 + 56: the zero taps of the padded bank, S = 0 there) so
-            // that both warpgroups run the same unconditional pair loop
-#pragma unroll
-            for (int j = 0; j < 4; ++j) tc::tmem_ld8(taddr + lane_base + (uint32_t)(64 + KS * (a_lo + j)), s8[j]);
-            tc::tmem_ld_wait();
-            // two window rows at a time: the 7 shuffled values of rows j and
-            // j + 1 are summed as packed pairs (the sum order per row is that
-            // of a scalar loop)
-            uint64_t h2[2] = {0ull, 0ull};
-            if (edge_x) {
-                // border tile: a source lane outside the warp contributes 0
-#pragma unroll
-                for (int j = 0; j < 4; j += 2)
-#pragma unroll
-                    for (int bb = 0; bb < KS; ++bb) {
-                        const int src = lane - 3 + bb;
-                        const bool ok = src >= 0 && src < 32;
-                        const float v0 = __shfl_sync(0xffffffffu, s8[j][bb], src & 31);
-                        const float v1 = __shfl_sync(0xffffffffu, s8[j + 1][bb], src & 31);
-                        h2[j >> 1] = f2_add(h2[j >> 1], f2_pack(ok ? v0 : 0.0f, ok ? v1 : 0.0f));
-                    }
-            } else {
-                // interior tile: lanes 3..28 (the only ones used) have all sources in the warp
-#pragma unroll
-                for (int j = 0; j < 4; j += 2)
-#pragma unroll
-                    for (int bb = 0; bb < KS; ++bb)
-                        h2[j >> 1] = f2_add(h2[j >> 1], f2_pack(__shfl_sync(0xffffffffu, s8[j][bb], (lane - 3 + bb) & 31),
-                                                                __shfl_sync(0xffffffffu, s8[j + 1][bb], (lane - 3 + bb) & 31)));
-            }
-            float h[4];
-            f2_unpack(h2[0], h[0], h[1]);
-            f2_unpack(h2[1], h[2], h[3]);
-            float *hrow = sH + (slot * KS + a_lo) * 32 + lane;
-            hrow[0] = h[0];
-            hrow[32] = h[1];
-            hrow[64] = h[2];
-            if (wg == 0) hrow[96] = h[3];
-        };
-        // vertical col2im of the ext rows whose 7 source rows are complete
-        // (one warp per row, lane = column).  BF16: the row goes to sG.  TF32:
-        // a row that the vertical fold needs is kept in sG; any other owned
-        // pixel is written at once, after the horizontal fold: the frame
-        // value of its mirror column comes from that column's lane.
-        float *gout = MODE == MODE_GRAD_EXT ? p.g_ext : (MODE == MODE_INIT ? im.g[0] : im.g[gcur_out]);
-        auto emit = [&](int ty) {
-            if (ty < -3 || ty >= TY + 3) return;
-            float g = 0.f;
-            int s = (ty + HRING) % HRING;  // ty >= -3
-            if (ty >= 0 && ty + KS <= R3Y) {  // all 7 source rows in the region (warp-uniform)
-#pragma unroll
-                for (int aa = 0; aa < KS; ++aa) {
-                    g += sH[(s * KS + aa) * 32 + lane];
-                    s = s + 1 == HRING ? 0 : s + 1;
-                }
-            } else {
-#pragma unroll
-                for (int aa = 0; aa < KS; ++aa) {
-                    const int srow = ty + aa;
-                    if (srow >= 0 && srow < R3Y) g += sH[(s * KS + aa) * 32 + lane];
-                    s = s + 1 == HRING ? 0 : s + 1;
-                }
-            }
-            if constexpr (C::FULL_G) {
-                sG[(ty + 3) * 32 + lane] = g;
-                return;
-            }
-            const int y = y0 + ty, slot = fold_slot(y, H);  // uniform over the warp
-            if (slot >= 0) {
-                sG[slot * 32 + lane] = g;
-                return;
-            }
-            if (MODE == MODE_ENERGY_EXT) return;
-            const int x = x0 + lane - 3;
-            const int qx = x < 3 ? (-x - 1) - x0 + 3 : (x >= W - 3 ? (2 * W - 1 - x) - x0 + 3 : -1);
-            const float gm = __shfl_sync(0xffffffffu, g, qx & 31);
-            if (ty >= sy && ty < sy + oh && lane - 3 >= sx && lane - 3 < sx + ow) {
-                float gv = g;
-                if (qx >= 0) gv += gm;
-                // combined model: grad_w F = e^w (.) K^T r, e^w as the prologue formed it
-                if (MODEL == 1) gv *= expf(xg[(size_t)y * W + x]);
-                gout[(size_t)y * W + x] = gv;
-            }
-        };
-
-        for (int blk = 0; blk < NBLK; ++blk) {
-            // (a) horizontal col2im of the previous block (its MMA_adj completed
-            // before the im2col of this block), overlapping MMA_fwd(blk)
-            if (blk > 0) epi2(blk - 1);
-            // (b) epilogue 1 of this block: rho' -> R (hi | lo), energy terms
-            if (!tc::mbar_wait(&bar_f, phase_f)) tc_ok = false;
-            phase_f ^= 1u;
-            tc::fence_after_sync();
-            {
-                const int row = 4 * blk + lg, col = lane;
-                const bool inimg = all_in || ((unsigned)(y0 - 3 + row) < (unsigned)H && (unsigned)(x0 - 3 + col) < (unsigned)W);
-                const bool owned = row >= 3 + sy && row < 3 + sy + oh && col >= 3 + sx && col < 3 + sx + ow;
-                float z[24];
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    float t8[8];
-                    tc::tmem_ld8(taddr + lane_base + (uint32_t)(24 * wg + 8 * j), t8);
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) z[8 * j + k] = t8[k];
-                }
-                tc::tmem_ld_wait();
-                // pairs of filters in packed FP32 (one instruction per pair for
-                // q = 1 + z^2, 2 theta z, r = 2 theta z / q and the F sum; the
-                // reciprocal and log2 stay scalar on the special-function unit)
-                const float4 *th4 = reinterpret_cast<const float4 *>(sTh + 24 * wg);
-                const float4 *tw4 = reinterpret_cast<const float4 *>(sTh + NF + 24 * wg);
-                const uint64_t one2 = f2_pack(1.0f, 1.0f);
-                uint64_t r2[12], ps2 = 0ull;  // ps2 = (0, 0)
-#pragma unroll
-                for (int j = 0; j < 6; ++j) {
-                    const float4 t1 = th4[j], t2 = tw4[j];
-                    const uint64_t thp[2] = {f2_pack(t1.x, t1.y), f2_pack(t1.z, t1.w)};
-                    const uint64_t twp[2] = {f2_pack(t2.x, t2.y), f2_pack(t2.z, t2.w)};
-#pragma unroll
-                    for (int k = 0; k < 2; ++k) {
-                        const uint64_t zp = f2_pack(z[4 * j + 2 * k], z[4 * j + 2 * k + 1]);
-                        const uint64_t qp = f2_fma(zp, zp, one2);
-                        float q0, q1;
-                        f2_unpack(qp, q0, q1);
-                        r2[2 * j + k] = f2_mul(f2_mul(twp[k], zp), f2_pack(rcp_ftz(q0), rcp_ftz(q1)));
-                        ps2 = f2_fma(thp[k], f2_pack(lg2_ftz(q0), lg2_ftz(q1)), ps2);
-                    }
-                }
-                if (!all_in) {  // tile-uniform: only border tiles have halo pixels off the image
-                    if (!inimg) {
-#pragma unroll
-                        for (int i = 0; i < 12; ++i) r2[i] = 0ull;
-                    }
-                }
-                float pa, pb;
-                f2_unpack(ps2, pa, pb);
-                if (owned) sum2_add(accF, (pa + pb) * LN2);
-                unsigned char *rowp = sR + tc::kmajor_offset((lg << 5) + lane, 0, C::KADJ, C::EB);
-#pragma unroll
-                for (int j = 0; j < 24 / C::E; ++j) {
-                    uint4 hi, lo;
-                    if constexpr (C::RLO) {
-                        hilo_chunk2<C::OPF>(r2 + j * (C::E / 2), hi, lo);
-                        *reinterpret_cast<uint4 *>(rowp + ((NF + 24 * wg) / C::E + j) * 128) = lo;
-                    } else {  // r rounded once to BF16
-                        uint32_t h[4];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            float x0, x1;
-                            f2_unpack(r2[j * (C::E / 2) + q], x0, x1);
-                            h[q] = bf16x2_rn(x0, x1);
-                        }
-                        hi = make_uint4(h[0], h[1], h[2], h[3]);
-                    }
-                    *reinterpret_cast<uint4 *>(rowp + ((24 * wg) / C::E + j) * 128) = hi;
-                }
-            }
-            // one barrier publishes both the H rows of block blk - 1 and the R
-            // operand of block blk (and orders epi2's reads of S before MMA_adj)
-            tc::fence_before_sync();
-            tc::fence_proxy_async();
             __syncthreads();
-            if (tid == 0) {
-                tc::fence_after_sync();
-#pragma unroll
-                for (int ks = 0; ks < C::KADJ / C::KSTEP; ++ks)
-                    tc::mma<C::OPF>(taddr + 64, tc::make_smem_desc(sR_u32 + ks * 256, 128, SBO_A),
-                                 tc::make_smem_desc(sBa_u32 + (ks % KS_A) * 256, 128, SBO_BA), IDESC_A,
-                                 ks > 0 ? 1u : 0u);
-                tc::mma_commit(&bar_a);
+            gtile = sTask;
+            if (gtile < 0) break;
+            // acquire: the decision and the planes of the image's previous trial
+            __threadfence();
+        } else {
+            gtile = p.order ? p.order[p.tile0 + (int)blockIdx.x] : p.tile0 + (int)blockIdx.x;
+        }
+        const TileDesc td = p.tiles[gtile];
+        const int img = td.img;
+        const ImgDesc im = p.imgs[img];
+        ImgState *st = p.st + img;
+        const int H = im.H, W = im.W, y0 = td.y0, x0 = td.x0, oh = td.oh, ow = td.ow, sy = td.sy, sx = td.sx;
+
+        bool active = true;
+        int gcur_out = 0;
+        if (TRIAL) {
+            active = (st->done == 0) && (st->n < st->target);
+            gcur_out = st->gcur ^ 1;
+        }
+
+        if (active) {
+            int cur = 0, gcur = 0;
+            if (TRIAL) {
+                cur = st->cur;
+                gcur = st->gcur;
             }
-            // vertical col2im of the rows whose sources block blk - 1 completed
-            // (the ring slots it reads are rewritten only after the next
-            // barrier); one row per warp: warps 0, 5, 2, 7, i.e. one per SM
-            // sub-partition and two per warpgroup
-            if (blk > 0 && (warp & 1) == (warp >> 2)) emit(4 * (blk - 1) - 6 + (warp & 3));
-            // (c) im2col of the next block into the operand buffer, once
-            // MMA_adj(blk) has read R from it
-            if (blk + 1 < NBLK) {
-                if (!tc::mbar_wait(&bar_a, phase_a)) tc_ok = false;
-                phase_a ^= 1u;
-                tc::fence_after_sync();
-                im2col<FMT>(sP, sAF, blk + 1, m, part);
+            // ---- TMA box loads of the trial's inputs (tile + 6 halo) -----------
+            // The box starts at (x0 - 6) rounded down to a multiple of 4 columns
+            // (16 bytes); it may reach outside the image, where it reads zeros.
+            // The symmetric extension is applied afterwards, by indexing the
+            // staged box at reflected coordinates (all of which lie in the box).
+            constexpr int SP = (int)(C::STAGE_PLANE / 4);  // staging plane stride (floats)
+            const bool use_tma = TRIAL && im.tmap != nullptr;
+            const int ys = y0 - 6, xs = ((x0 - 6) >> 2) << 2;  // arithmetic shift: floor
+            const float *stg = reinterpret_cast<const float *>(smem + C::OFF_STAGE);
+            // the copies' barrier is initialised with the CTA's first tile,
+            // whether or not that tile's plane pitch allows TMA loads (a later
+            // tile's may: persistent CTAs run tiles of several images)
+            if (!setup && tid == 0) tc::mbar_init(&bar_ld, 1);
+            if (use_tma && tid == 0) {
+                // the previous tile's generic accesses of the staging area, and
+                // the other CTAs' plane writes acquired above, before the copies
                 tc::fence_proxy_async();
+                tc::fence_proxy_async_global();
+                tc::mbar_arrive_expect_tx(&bar_ld, 4u * (uint32_t)(tc_box_y * tc_box_x * 4));
+                const unsigned char *tm = static_cast<const unsigned char *>(im.tmap);
+                float *dst = reinterpret_cast<float *>(smem + C::OFF_STAGE);
+                tc::tma_load_2d(dst, tm + 128 * cur, xs, ys, &bar_ld);                   // u^n
+                tc::tma_load_2d(dst + SP, tm + 128 * ((cur + 2) % 3), xs, ys, &bar_ld);  // u^{n-1}
+                tc::tma_load_2d(dst + 2 * SP, tm + 128 * (3 + gcur), xs, ys, &bar_ld);   // g^n
+                tc::tma_load_2d(dst + 3 * SP, tm + 128 * 5, xs, ys, &bar_ld);            // f^2
+            }
+            bool tc_ok = true;
+            // ---- rounded filter bank (B operands) and theta into shared memory --
+            if (!setup) {
+                const uint4 *gf = reinterpret_cast<const uint4 *>(p.tcw_fwd);
+                const uint4 *ga = reinterpret_cast<const uint4 *>(p.tcw_adj);
+                for (int j = tid; j < (int)(C::BF_BYTES / 16); j += NT) reinterpret_cast<uint4 *>(sBf)[j] = __ldg(gf + j);
+                for (int j = tid; j < (int)(C::BA_BYTES / 16); j += NT) reinterpret_cast<uint4 *>(sBa)[j] = __ldg(ga + j);
+                if (tid < NF) {
+                    const float th = __ldg(p.theta + tid);
+                    sTh[tid] = th;
+                    sTh[NF + tid] = 2.0f * th;
+                }
+                // the padding columns of the planes (read with weight 0) hold zeros
+                for (int j = tid; j < C::NPL * R6Y; j += NT) {
+                    uint32_t *rowp = sP + (j / R6Y) * C::PL_WORDS + (j % R6Y) * (PP * C::EB / 4);
+                    if (C::BF)
+                        rowp[(PP / 2) - 2] = rowp[(PP / 2) - 1] = 0u;  // elements 36..39 (the writes below fill 36, 37)
+                    else
+                        rowp[PP - 2] = rowp[PP - 1] = 0u;
+                }
+                __syncthreads();  // pad zeros before the plane writes of the prologue
+                if (tid == 0) {
+                    tc::mbar_init(&bar_f, 1);
+                    tc::mbar_init(&bar_a, 1);
+                }
+                if (warp == 0) tc::tmem_alloc(&tbase, TMEM_COLS);
+                setup = true;
+            }
+
+            // ---- inertial step and prox on tile + 6 (owned pixels: sums) -------
+            // per-thread sums: compensated FP32 for F and G (large terms), plain
+            // FP32 for the small step-test terms
+            Sum2 accF{0.f, 0.f}, accG{0.f, 0.f};
+            float accGD = 0.f, accDD = 0.f, accDP = 0.f;
+            if (use_tma) {
+                if (!tc::mbar_wait(&bar_ld, ld_phase)) {
+                    tc_ok = false;                           // the tile's sums are poisoned below
+                    (void)tc::mbar_wait(&bar_ld, ld_phase);  // a second bounded chance for copies in flight
+                }
+                ld_phase ^= 1u;
+            }
+            const float *uc = (TRIAL || MODE == MODE_INIT) ? im.u[cur] : p.u_ext;
+            float *un = im.u[(cur + 1) % 3];
+            // the iterate at which the gradient is taken (combined model: w, to form e^w at the output)
+            const float *xg = TRIAL ? un : uc;
+            {
+                float a = 0.f, b = 0.f, tl = 0.f;
+                const float l1 = (float)im.lambda1, l2 = (float)im.lambda;  // combined model
+                if (TRIAL) {
+                    const double alpha = st->alpha;
+                    a = (float)alpha;
+                    b = (float)p.beta;
+                    tl = (float)(alpha * im.lambda);
+                }
+                const float *upv = im.u[(cur + 2) % 3];
+                const float *gc = im.g[gcur];
+                const float *f2p = im.f2;
+                const float c4 = 4.0f * (1.0f + tl) * tl, inv2 = 1.0f / (2.0f * (1.0f + tl)), tl2 = 2.0f * tl;
+                // tile + 6 inside the image: no reflection
+                const bool in6 = y0 >= 6 && y0 + TY + 6 <= H && x0 >= 6 && x0 + TX + 6 <= W;
+                constexpr int NPIX = R6Y * R6X, UNR = 4;
+                for (int base = 0; base < NPIX; base += UNR * NT) {
+                    size_t off[UNR];
+                    bool inb[UNR], owned[UNR];
+                    float u0[UNR], u_1[UNR], g0[UNR], f2[UNR];
+    #pragma unroll
+                    for (int k = 0; k < UNR; ++k) {
+                        const int idx = base + k * NT + tid;
+                        inb[k] = idx < NPIX;
+                        const int ry = inb[k] ? idx / R6X : 0, rx = inb[k] ? idx - ry * R6X : 0;
+                        const int yr = in6 ? y0 - 6 + ry : reflect(y0 - 6 + ry, H);
+                        const int xr = in6 ? x0 - 6 + rx : reflect(x0 - 6 + rx, W);
+                        off[k] = (size_t)yr * W + xr;
+                        owned[k] = inb[k] && ry >= 6 + sy && ry < 6 + sy + oh && rx >= 6 + sx && rx < 6 + sx + ow;
+                        if (use_tma) {
+                            const int si = (yr - ys) * tc_box_x + (xr - xs);
+                            u0[k] = stg[si];
+                            u_1[k] = stg[SP + si];
+                            g0[k] = stg[2 * SP + si];
+                            f2[k] = stg[3 * SP + si];
+                        } else {
+                            // L2 loads: a persistent launch rewrites these planes while it runs
+                            u0[k] = __ldcg(uc + off[k]);
+                            f2[k] = (TRIAL || owned[k]) ? __ldg(f2p + off[k]) : 1.0f;
+                            if (TRIAL) {
+                                u_1[k] = __ldcg(upv + off[k]);
+                                g0[k] = __ldcg(gc + off[k]);
+                            }
+                        }
+                    }
+    #pragma unroll
+                    for (int k = 0; k < UNR; ++k) {
+                        if (!inb[k]) continue;
+                        float v;
+                        if (TRIAL) {
+                            const float dprev = u0[k] - u_1[k];
+                            const float uhat = fmaf(-a, g0[k], fmaf(b, dprev, u0[k]));
+                            v = MODEL == 0 ? prox_g_sfu(uhat, f2[k], c4, inv2, tl2) : prox_w(uhat, f2[k], a, l1, l2);
+                            if (owned[k]) {
+                                un[off[k]] = v;
+                                const float d = v - u0[k];
+                                accGD = fmaf(g0[k], d, accGD);
+                                accDD = fmaf(d, d, accDD);
+                                accDP = fmaf(d, dprev, accDP);
+                            }
+                        } else {
+                            v = u0[k];
+                        }
+                        // data term (variant: u^2 - 2 f^2 log u, the log on the special-function unit)
+                        if (owned[k])
+                            sum2_add(accG, MODEL == 0 ? fmaf(v, v, (-2.0f * LN2) * f2[k] * lg2_ftz(v))
+                                                      : data_w(v, f2[k], l1, l2));
+                        // hi / lo planes of the operand type (the bank sees u)
+                        const float uv = MODEL == 0 ? v : expf(v);
+                        const int idx = base + k * NT + tid, ry = idx / R6X, rx = idx - ry * R6X;
+                        if (C::BF) {
+                            const __nv_bfloat16 hb = __float2bfloat16_rn(uv);
+                            const __nv_bfloat16 lb = __float2bfloat16_rn(uv - __bfloat162float(hb));
+                            __nv_bfloat16 *ph = reinterpret_cast<__nv_bfloat16 *>(sP);
+                            __nv_bfloat16 *pl = reinterpret_cast<__nv_bfloat16 *>(sP + C::PL_WORDS);
+                            const int e = ry * PP + rx;
+                            ph[e] = hb;
+                            pl[e] = lb;
+                        } else {
+                            const float hv = tc::round_tf32(uv);
+                            const int e = ry * PP + rx;
+                            sP[e] = __float_as_uint(hv);
+                            sP[C::PL_WORDS + e] = __float_as_uint(tc::round_tf32(uv - hv));
+                        }
+                    }
+                }
+            }
+
+            const uint32_t sAF_u32 = tc::smem_u32(sAF), sR_u32 = tc::smem_u32(sR);
+            const uint32_t sBf_u32 = tc::smem_u32(sBf), sBa_u32 = tc::smem_u32(sBa);
+            constexpr uint32_t SBO_F = (uint32_t)(C::KFWD / C::E) * 128, SBO_A = (uint32_t)(C::KADJ / C::E) * 128;
+            constexpr uint32_t SBO_BF = (uint32_t)(C::KPASS / C::E) * 128, SBO_BA = (uint32_t)(NF / C::E) * 128;
+            constexpr int KS_F = C::KPASS / C::KSTEP, KS_A = NF / C::KSTEP;  // K steps of one pass
+            constexpr uint32_t IDESC_F = tc::make_idesc(C::OPF, 128, NF), IDESC_A = tc::make_idesc(C::OPF, 128, NTAP);
+            const int m = tid & 127, part = tid >> 7;  // im2col: pixel, chunk parity
+            const int wg = warp >> 2, lg = warp & 3;   // epilogues: column half, TMEM lane group
+            const bool edge_x = x0 == 0 || x0 + TX >= W;
+            const bool full_y = y0 >= 3 && y0 + TY + 3 <= H, full_x = x0 >= 3 && x0 + TX + 3 <= W;
+            const bool all_in = full_y && full_x;  // every halo pixel lies in the image
+
+            // every plane element is written, and every staged value read,
+            // before the im2col of block 0 reads the planes and overwrites the
+            // staging area
+            __syncthreads();
+            // block 0: im2col and forward MMA
+            im2col<FMT>(sP, sAF, 0, m, part);
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            const uint32_t taddr = tbase;
+            const uint32_t lane_base = (uint32_t)(lg * 32) << 16;
+            if (tid == 0) {
+    #pragma unroll
+                for (int ks = 0; ks < C::KFWD / C::KSTEP; ++ks)
+                    tc::mma<C::OPF>(taddr, tc::make_smem_desc(sAF_u32 + ks * 256, 128, SBO_F),
+                                 tc::make_smem_desc(sBf_u32 + (ks % KS_F) * 256, 128, SBO_BF), IDESC_F,
+                                 ks > 0 ? 1u : 0u);
+                tc::mma_commit(&bar_f);
+            }
+            // each tile waits NBLK times on each MMA barrier: both are back at
+            // phase 0 when the next tile starts
+            static_assert(NBLK % 2 == 0, "MMA barrier phases repeat per tile");
+            uint32_t phase_f = 0, phase_a = 0;
+
+            // epilogue 2 of block pb: horizontal col2im of S (TMEM) into the H ring
+            auto epi2 = [&](int pb) {
+                const int row = 4 * pb + lg;
+                const int slot = row % HRING;
+                const int a_lo = wg == 0 ? 0 : 4;
+                float s8[4][8];
+                // warpgroup 1 has 3 window rows; it loads a 4th (columns 64 + 49
+                // .. 64 + 56: the zero taps of the padded bank, S = 0 there) so
+                // that both warpgroups run the same unconditional pair loop
+    #pragma unroll
+                for (int j = 0; j < 4; ++j) tc::tmem_ld8(taddr + lane_base + (uint32_t)(64 + KS * (a_lo + j)), s8[j]);
+                tc::tmem_ld_wait();
+                // two window rows at a time: the 7 shuffled values of rows j and
+                // j + 1 are summed as packed pairs (the sum order per row is that
+                // of a scalar loop)
+                uint64_t h2[2] = {0ull, 0ull};
+                if (edge_x) {
+                    // border tile: a source lane outside the warp contributes 0
+    #pragma unroll
+                    for (int j = 0; j < 4; j += 2)
+    #pragma unroll
+                        for (int bb = 0; bb < KS; ++bb) {
+                            const int src = lane - 3 + bb;
+                            const bool ok = src >= 0 && src < 32;
+                            const float v0 = __shfl_sync(0xffffffffu, s8[j][bb], src & 31);
+                            const float v1 = __shfl_sync(0xffffffffu, s8[j + 1][bb], src & 31);
+                            h2[j >> 1] = f2_add(h2[j >> 1], f2_pack(ok ? v0 : 0.0f, ok ? v1 : 0.0f));
+                        }
+                } else {
+                    // interior tile: lanes 3..28 (the only ones used) have all sources in the warp
+    #pragma unroll
+                    for (int j = 0; j < 4; j += 2)
+    #pragma unroll
+                        for (int bb = 0; bb < KS; ++bb)
+                            h2[j >> 1] = f2_add(h2[j >> 1], f2_pack(__shfl_sync(0xffffffffu, s8[j][bb], (lane - 3 + bb) & 31),
+                                                                    __shfl_sync(0xffffffffu, s8[j + 1][bb], (lane - 3 + bb) & 31)));
+                }
+                float h[4];
+                f2_unpack(h2[0], h[0], h[1]);
+                f2_unpack(h2[1], h[2], h[3]);
+                float *hrow = sH + (slot * KS + a_lo) * 32 + lane;
+                hrow[0] = h[0];
+                hrow[32] = h[1];
+                hrow[64] = h[2];
+                if (wg == 0) hrow[96] = h[3];
+            };
+            // vertical col2im of the ext rows whose 7 source rows are complete
+            // (one warp per row, lane = column).  BF16: the row goes to sG.  TF32:
+            // a row that the vertical fold needs is kept in sG; any other owned
+            // pixel is written at once, after the horizontal fold: the frame
+            // value of its mirror column comes from that column's lane.
+            float *gout = MODE == MODE_GRAD_EXT ? p.g_ext : (MODE == MODE_INIT ? im.g[0] : im.g[gcur_out]);
+            auto emit = [&](int ty) {
+                if (ty < -3 || ty >= TY + 3) return;
+                float g = 0.f;
+                int s = (ty + HRING) % HRING;  // ty >= -3
+                if (ty >= 0 && ty + KS <= R3Y) {  // all 7 source rows in the region (warp-uniform)
+    #pragma unroll
+                    for (int aa = 0; aa < KS; ++aa) {
+                        g += sH[(s * KS + aa) * 32 + lane];
+                        s = s + 1 == HRING ? 0 : s + 1;
+                    }
+                } else {
+    #pragma unroll
+                    for (int aa = 0; aa < KS; ++aa) {
+                        const int srow = ty + aa;
+                        if (srow >= 0 && srow < R3Y) g += sH[(s * KS + aa) * 32 + lane];
+                        s = s + 1 == HRING ? 0 : s + 1;
+                    }
+                }
+                if constexpr (C::FULL_G) {
+                    sG[(ty + 3) * 32 + lane] = g;
+                    return;
+                }
+                const int y = y0 + ty, slot = fold_slot(y, H);  // uniform over the warp
+                if (slot >= 0) {
+                    sG[slot * 32 + lane] = g;
+                    return;
+                }
+                if (MODE == MODE_ENERGY_EXT) return;
+                const int x = x0 + lane - 3;
+                const int qx = x < 3 ? (-x - 1) - x0 + 3 : (x >= W - 3 ? (2 * W - 1 - x) - x0 + 3 : -1);
+                const float gm = __shfl_sync(0xffffffffu, g, qx & 31);
+                if (ty >= sy && ty < sy + oh && lane - 3 >= sx && lane - 3 < sx + ow) {
+                    float gv = g;
+                    if (qx >= 0) gv += gm;
+                    // combined model: grad_w F = e^w (.) K^T r, e^w as the prologue formed it
+                    if (MODEL == 1) gv *= expf(xg[(size_t)y * W + x]);
+                    gout[(size_t)y * W + x] = gv;
+                }
+            };
+
+            for (int blk = 0; blk < NBLK; ++blk) {
+                // (a) horizontal col2im of the previous block (its MMA_adj completed
+                // before the im2col of this block), overlapping MMA_fwd(blk)
+                if (blk > 0) epi2(blk - 1);
+                // (b) epilogue 1 of this block: rho' -> R (hi | lo), energy terms
+                if (!tc::mbar_wait(&bar_f, phase_f)) tc_ok = false;
+                phase_f ^= 1u;
+                tc::fence_after_sync();
+                {
+                    const int row = 4 * blk + lg, col = lane;
+                    const bool inimg = all_in || ((unsigned)(y0 - 3 + row) < (unsigned)H && (unsigned)(x0 - 3 + col) < (unsigned)W);
+                    const bool owned = row >= 3 + sy && row < 3 + sy + oh && col >= 3 + sx && col < 3 + sx + ow;
+                    float z[24];
+    #pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        float t8[8];
+                        tc::tmem_ld8(taddr + lane_base + (uint32_t)(24 * wg + 8 * j), t8);
+    #pragma unroll
+                        for (int k = 0; k < 8; ++k) z[8 * j + k] = t8[k];
+                    }
+                    tc::tmem_ld_wait();
+                    // pairs of filters in packed FP32 (one instruction per pair for
+                    // q = 1 + z^2, 2 theta z, r = 2 theta z / q and the F sum; the
+                    // reciprocal and log2 stay scalar on the special-function unit)
+                    const float4 *th4 = reinterpret_cast<const float4 *>(sTh + 24 * wg);
+                    const float4 *tw4 = reinterpret_cast<const float4 *>(sTh + NF + 24 * wg);
+                    const uint64_t one2 = f2_pack(1.0f, 1.0f);
+                    uint64_t r2[12], ps2 = 0ull;  // ps2 = (0, 0)
+    #pragma unroll
+                    for (int j = 0; j < 6; ++j) {
+                        const float4 t1 = th4[j], t2 = tw4[j];
+                        const uint64_t thp[2] = {f2_pack(t1.x, t1.y), f2_pack(t1.z, t1.w)};
+                        const uint64_t twp[2] = {f2_pack(t2.x, t2.y), f2_pack(t2.z, t2.w)};
+    #pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            const uint64_t zp = f2_pack(z[4 * j + 2 * k], z[4 * j + 2 * k + 1]);
+                            const uint64_t qp = f2_fma(zp, zp, one2);
+                            float q0, q1;
+                            f2_unpack(qp, q0, q1);
+                            r2[2 * j + k] = f2_mul(f2_mul(twp[k], zp), f2_pack(rcp_ftz(q0), rcp_ftz(q1)));
+                            ps2 = f2_fma(thp[k], f2_pack(lg2_ftz(q0), lg2_ftz(q1)), ps2);
+                        }
+                    }
+                    if (!all_in) {  // tile-uniform: only border tiles have halo pixels off the image
+                        if (!inimg) {
+    #pragma unroll
+                            for (int i = 0; i < 12; ++i) r2[i] = 0ull;
+                        }
+                    }
+                    float pa, pb;
+                    f2_unpack(ps2, pa, pb);
+                    if (owned) sum2_add(accF, (pa + pb) * LN2);
+                    unsigned char *rowp = sR + tc::kmajor_offset((lg << 5) + lane, 0, C::KADJ, C::EB);
+    #pragma unroll
+                    for (int j = 0; j < 24 / C::E; ++j) {
+                        uint4 hi, lo;
+                        if constexpr (C::RLO) {
+                            hilo_chunk2<C::OPF>(r2 + j * (C::E / 2), hi, lo);
+                            *reinterpret_cast<uint4 *>(rowp + ((NF + 24 * wg) / C::E + j) * 128) = lo;
+                        } else {  // r rounded once to BF16
+                            uint32_t h[4];
+    #pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                float x0, x1;
+                                f2_unpack(r2[j * (C::E / 2) + q], x0, x1);
+                                h[q] = bf16x2_rn(x0, x1);
+                            }
+                            hi = make_uint4(h[0], h[1], h[2], h[3]);
+                        }
+                        *reinterpret_cast<uint4 *>(rowp + ((24 * wg) / C::E + j) * 128) = hi;
+                    }
+                }
+                // one barrier publishes both the H rows of block blk - 1 and the R
+                // operand of block blk (and orders epi2's reads of S before MMA_adj)
                 tc::fence_before_sync();
+                tc::fence_proxy_async();
                 __syncthreads();
                 if (tid == 0) {
                     tc::fence_after_sync();
-#pragma unroll
-                    for (int ks = 0; ks < C::KFWD / C::KSTEP; ++ks)
-                        tc::mma<C::OPF>(taddr, tc::make_smem_desc(sAF_u32 + ks * 256, 128, SBO_F),
-                                     tc::make_smem_desc(sBf_u32 + (ks % KS_F) * 256, 128, SBO_BF), IDESC_F,
+    #pragma unroll
+                    for (int ks = 0; ks < C::KADJ / C::KSTEP; ++ks)
+                        tc::mma<C::OPF>(taddr + 64, tc::make_smem_desc(sR_u32 + ks * 256, 128, SBO_A),
+                                     tc::make_smem_desc(sBa_u32 + (ks % KS_A) * 256, 128, SBO_BA), IDESC_A,
                                      ks > 0 ? 1u : 0u);
-                    tc::mma_commit(&bar_f);
+                    tc::mma_commit(&bar_a);
                 }
-            }
-        }
-        // last block's col2im, then the ext rows whose missing sources lie off the tile
-        __syncthreads();  // the emits of block NBLK - 2 are done with the ring slots epi2 rewrites
-        if (!tc::mbar_wait(&bar_a, phase_a)) tc_ok = false;
-        phase_a ^= 1u;
-        tc::fence_after_sync();
-        epi2(NBLK - 1);
-        tc::fence_before_sync();
-        __syncthreads();
-        if (tid < 128) emit(4 * (NBLK - 1) - 6 + (tid >> 5));
-        if (tid >= 128 && tid < 224) emit(4 * (NBLK - 1) - 2 + ((tid - 128) >> 5));  // 58, 59, 60
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        if (warp == 0) tc::tmem_dealloc(taddr, TMEM_COLS);
-
-        // ---- fold the frame, write the owned gradient ------------------------
-        // (frame columns first, then the frame row, then the corner)
-        // one warp per owned row, lane = owned column (no index division)
-        if (MODE != MODE_ENERGY_EXT && C::FULL_G && lane < ow) {
-            for (int r = warp; r < oh; r += NT / 32) {
-                const int ty = sy + r, tx = sx + lane;
-                const int y = y0 + ty, x = x0 + tx;
-                float gv = sG[(ty + 3) * 32 + tx + 3];
-                if (y < 3 || y >= H - 3 || x < 3 || x >= W - 3) {
-                    // ext positions the symmetric extension maps onto (y, x): at
-                    // most one per axis (H, W >= 8); scalars, so that nothing is
-                    // indexed dynamically (local memory)
-                    const int oy = ty + 3, ox = tx + 3;
-                    const int qy = y < 3 ? (-y - 1) - y0 + 3 : (y >= H - 3 ? (2 * H - 1 - y) - y0 + 3 : -1);
-                    const int qx = x < 3 ? (-x - 1) - x0 + 3 : (x >= W - 3 ? (2 * W - 1 - x) - x0 + 3 : -1);
-                    if (qx >= 0) gv += sG[oy * 32 + qx];
-                    if (qy >= 0) {
-                        gv += sG[qy * 32 + ox];
-                        if (qx >= 0) gv += sG[qy * 32 + qx];
+                // vertical col2im of the rows whose sources block blk - 1 completed
+                // (the ring slots it reads are rewritten only after the next
+                // barrier); one row per warp: warps 0, 5, 2, 7, i.e. one per SM
+                // sub-partition and two per warpgroup
+                if (blk > 0 && (warp & 1) == (warp >> 2)) emit(4 * (blk - 1) - 6 + (warp & 3));
+                // (c) im2col of the next block into the operand buffer, once
+                // MMA_adj(blk) has read R from it
+                if (blk + 1 < NBLK) {
+                    if (!tc::mbar_wait(&bar_a, phase_a)) tc_ok = false;
+                    phase_a ^= 1u;
+                    tc::fence_after_sync();
+                    im2col<FMT>(sP, sAF, blk + 1, m, part);
+                    tc::fence_proxy_async();
+                    tc::fence_before_sync();
+                    __syncthreads();
+                    if (tid == 0) {
+                        tc::fence_after_sync();
+    #pragma unroll
+                        for (int ks = 0; ks < C::KFWD / C::KSTEP; ++ks)
+                            tc::mma<C::OPF>(taddr, tc::make_smem_desc(sAF_u32 + ks * 256, 128, SBO_F),
+                                         tc::make_smem_desc(sBf_u32 + (ks % KS_F) * 256, 128, SBO_BF), IDESC_F,
+                                         ks > 0 ? 1u : 0u);
+                        tc::mma_commit(&bar_f);
                     }
                 }
-                // combined model: grad_w F = e^w (.) K^T r, e^w as the prologue formed it
-                if (MODEL == 1) gv *= expf(xg[(size_t)y * W + x]);
-                gout[(size_t)y * W + x] = gv;
             }
-        }
-        // TF32: the rows kept for the vertical fold (the others were written
-        // by the vertical col2im)
-        if (MODE != MODE_ENERGY_EXT && !C::FULL_G) {
-            for (int idx = tid; idx < NFOLD * 32; idx += NT) {
-                const int sl = idx >> 5, ln = idx & 31;
-                const int y = sl < 6 ? sl - 3 : H - 9 + sl;  // inverse of fold_slot
-                const int ty = y - y0, tx = ln - 3, x = x0 + tx;
-                if (ty < sy || ty >= sy + oh || tx < sx || tx >= sx + ow) continue;  // owned pixels only
-                float gv = sG[sl * 32 + ln];
-                // ext positions the symmetric extension maps onto (y, x): at
-                // most one per axis (H, W >= 8)
-                const int qx = x < 3 ? (-x - 1) - x0 + 3 : (x >= W - 3 ? (2 * W - 1 - x) - x0 + 3 : -1);
-                const int qs = y < 3 ? fold_slot(-y - 1, H) : (y >= H - 3 ? fold_slot(2 * H - 1 - y, H) : -1);
-                if (qx >= 0) gv += sG[sl * 32 + qx];
-                if (qs >= 0) {
-                    gv += sG[qs * 32 + ln];
-                    if (qx >= 0) gv += sG[qs * 32 + qx];
+            // last block's col2im, then the ext rows whose missing sources lie off the tile
+            __syncthreads();  // the emits of block NBLK - 2 are done with the ring slots epi2 rewrites
+            if (!tc::mbar_wait(&bar_a, phase_a)) tc_ok = false;
+            phase_a ^= 1u;
+            tc::fence_after_sync();
+            epi2(NBLK - 1);
+            tc::fence_before_sync();
+            __syncthreads();
+            if (tid < 128) emit(4 * (NBLK - 1) - 6 + (tid >> 5));
+            if (tid >= 128 && tid < 224) emit(4 * (NBLK - 1) - 2 + ((tid - 128) >> 5));  // 58, 59, 60
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+
+            // ---- fold the frame, write the owned gradient ------------------------
+            // (frame columns first, then the frame row, then the corner)
+            // one warp per owned row, lane = owned column (no index division)
+            if (MODE != MODE_ENERGY_EXT && C::FULL_G && lane < ow) {
+                for (int r = warp; r < oh; r += NT / 32) {
+                    const int ty = sy + r, tx = sx + lane;
+                    const int y = y0 + ty, x = x0 + tx;
+                    float gv = sG[(ty + 3) * 32 + tx + 3];
+                    if (y < 3 || y >= H - 3 || x < 3 || x >= W - 3) {
+                        // ext positions the symmetric extension maps onto (y, x): at
+                        // most one per axis (H, W >= 8); scalars, so that nothing is
+                        // indexed dynamically (local memory)
+                        const int oy = ty + 3, ox = tx + 3;
+                        const int qy = y < 3 ? (-y - 1) - y0 + 3 : (y >= H - 3 ? (2 * H - 1 - y) - y0 + 3 : -1);
+                        const int qx = x < 3 ? (-x - 1) - x0 + 3 : (x >= W - 3 ? (2 * W - 1 - x) - x0 + 3 : -1);
+                        if (qx >= 0) gv += sG[oy * 32 + qx];
+                        if (qy >= 0) {
+                            gv += sG[qy * 32 + ox];
+                            if (qx >= 0) gv += sG[qy * 32 + qx];
+                        }
+                    }
+                    // combined model: grad_w F = e^w (.) K^T r, e^w as the prologue formed it
+                    if (MODEL == 1) gv *= expf(xg[(size_t)y * W + x]);
+                    gout[(size_t)y * W + x] = gv;
                 }
-                if (MODEL == 1) gv *= expf(xg[(size_t)y * W + x]);
-                gout[(size_t)y * W + x] = gv;
+            }
+            // TF32: the rows kept for the vertical fold (the others were written
+            // by the vertical col2im)
+            if (MODE != MODE_ENERGY_EXT && !C::FULL_G) {
+                for (int idx = tid; idx < NFOLD * 32; idx += NT) {
+                    const int sl = idx >> 5, ln = idx & 31;
+                    const int y = sl < 6 ? sl - 3 : H - 9 + sl;  // inverse of fold_slot
+                    const int ty = y - y0, tx = ln - 3, x = x0 + tx;
+                    if (ty < sy || ty >= sy + oh || tx < sx || tx >= sx + ow) continue;  // owned pixels only
+                    float gv = sG[sl * 32 + ln];
+                    // ext positions the symmetric extension maps onto (y, x): at
+                    // most one per axis (H, W >= 8)
+                    const int qx = x < 3 ? (-x - 1) - x0 + 3 : (x >= W - 3 ? (2 * W - 1 - x) - x0 + 3 : -1);
+                    const int qs = y < 3 ? fold_slot(-y - 1, H) : (y >= H - 3 ? fold_slot(2 * H - 1 - y, H) : -1);
+                    if (qx >= 0) gv += sG[sl * 32 + qx];
+                    if (qs >= 0) {
+                        gv += sG[qs * 32 + ln];
+                        if (qx >= 0) gv += sG[qs * 32 + qx];
+                    }
+                    if (MODEL == 1) gv *= expf(xg[(size_t)y * W + x]);
+                    gout[(size_t)y * W + x] = gv;
+                }
+            }
+            if (!tc_ok) {
+                accGD = __int_as_float(0x7fc00000);  // NaN step sum: the image stops (FE_ENONFINITE)
+                if (tid == 0) atomicExch(p.tc_error, 1);
+            }
+            const Sum2 vals[NRED] = {accF, accG, {accGD, 0.f}, {accDD, 0.f}, {accDP, 0.f}};
+            tile_finish<NT>(p, MODE, gtile, img, im, st, vals, sRed, &sLast);
+            // a wait that ran out leaves the barriers' phases unknown: the CTA
+            // takes no further tile, and the persistent launch stops
+            if (PERSIST && __syncthreads_or(!tc_ok)) {
+                if (tid == 0) atomicExch(&p.loop->abort, 1);
+                break;
             }
         }
-        if (!tc_ok) {
-            accGD = __int_as_float(0x7fc00000);  // NaN step sum: the image stops (FE_ENONFINITE)
-            if (tid == 0) atomicExch(p.tc_error, 1);
-        }
-        const Sum2 vals[NRED] = {accF, accG, {accGD, 0.f}, {accDD, 0.f}, {accDP, 0.f}};
-        tile_finish<NT>(p, MODE, gtile, img, im, st, vals, sRed, &sLast);
+        if constexpr (!PERSIST) break;
     }
+    // tensor memory is released once every MMA and load of it has completed
+    if (setup) {
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (warp == 0) tc::tmem_dealloc(tbase, TMEM_COLS);
+    }
+    if constexpr (PERSIST) persist_exit(p, gridDim.x);
     if (MODE == MODE_TRIAL) loop_control(p, gridDim.x);
 }
 
@@ -755,7 +810,8 @@ cudaError_t prepare_fmt() {
     // the dynamic shared memory of the form, and the largest shared-memory
     // carveout (BF16 runs three CTAs per SM)
     const int b = (int)Cfg<FMT>::BYTES;
-    const void *fns[4] = {reinterpret_cast<const void *>(&tc_tile_kernel<MODE_TRIAL, FMT, MODEL>),
+    const void *fns[5] = {reinterpret_cast<const void *>(&tc_tile_kernel<MODE_TRIAL, FMT, MODEL>),
+                          reinterpret_cast<const void *>(&tc_tile_kernel<MODE_PTRIAL, FMT, MODEL>),
                           reinterpret_cast<const void *>(&tc_tile_kernel<MODE_INIT, FMT, MODEL>),
                           reinterpret_cast<const void *>(&tc_tile_kernel<MODE_GRAD_EXT, FMT, MODEL>),
                           reinterpret_cast<const void *>(&tc_tile_kernel<MODE_ENERGY_EXT, FMT, MODEL>)};
@@ -786,6 +842,13 @@ const void *trial_entry(int fmt) {
     return fmt == 1   ? reinterpret_cast<const void *>(&tc_tile_kernel<MODE_TRIAL, 1, MODEL>)
            : fmt == 3 ? reinterpret_cast<const void *>(&tc_tile_kernel<MODE_TRIAL, 3, MODEL>)
                       : reinterpret_cast<const void *>(&tc_tile_kernel<MODE_TRIAL, 2, MODEL>);
+}
+
+template <int MODEL>
+const void *ptrial_entry(int fmt) {
+    return fmt == 1   ? reinterpret_cast<const void *>(&tc_tile_kernel<MODE_PTRIAL, 1, MODEL>)
+           : fmt == 3 ? reinterpret_cast<const void *>(&tc_tile_kernel<MODE_PTRIAL, 3, MODEL>)
+                      : reinterpret_cast<const void *>(&tc_tile_kernel<MODE_PTRIAL, 2, MODEL>);
 }
 
 }  // namespace

@@ -239,6 +239,108 @@ __device__ void decide(const KParams &p, ImgState *st, const double *t, int mode
     }
 }
 
+// ---- persistent trial launches ---------------------------------------------
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// The next tile of a persistent launch (warp 0 of the CTA, all 32 lanes):
+// the lanes look at 32 images at a time, starting with the image the CTA
+// took its last tile from (pref), and the first image with tiles left is
+// claimed by one atomic increment of its counter.  Returns the global tile
+// index, or -1 when every image has stopped or the launch aborts.
+__device__ int persist_grab(const KParams &p, int &pref) {
+    const int lane = threadIdx.x & 31;
+    LoopCtl *lc = p.loop;
+    unsigned long long seen = ~0ull, t0 = 0;
+    for (;;) {
+        // lane 0 reads the shared words and broadcasts them: every lane takes
+        // the same branches (the ballots below need the whole warp)
+        int stop = 0;
+        if (lane == 0) stop = *(volatile int *)&lc->abort != 0 || *(volatile int *)&lc->active <= 0;
+        if (__shfl_sync(0xffffffffu, stop, 0)) return -1;
+        for (int base = 0; base < p.nimg; base += 32) {
+            const int k = base + lane;
+            int j = pref + k;
+            if (j >= p.nimg) j -= p.nimg;
+            const int nt = k < p.nimg ? __ldg(&p.imgs[j].ntiles) : 0;
+            const bool avail = k < p.nimg && *(volatile int *)(p.sched + j) < nt;
+            unsigned m = __ballot_sync(0xffffffffu, avail);
+            while (m) {
+                const int l = __ffs(m) - 1;
+                m &= m - 1u;
+                int t = 0;
+                if (lane == l) t = atomicAdd(p.sched + j, 1);
+                t = __shfl_sync(0xffffffffu, t, l);
+                const int jl = __shfl_sync(0xffffffffu, j, l), ntl = __shfl_sync(0xffffffffu, nt, l);
+                if (t < ntl) {
+                    pref = jl;
+                    return __ldg(p.porder + __ldg(&p.imgs[jl].tile_begin) + t);
+                }
+            }
+        }
+        // nothing to take now: tiles come back when a trial is decided
+        int stalled = 0;
+        if (lane == 0) {
+            const unsigned long long d = *(volatile unsigned long long *)&lc->decisions, now = global_ns();
+            if (d != seen) {
+                seen = d;
+                t0 = now;
+            } else if (now - t0 > PERSIST_STALL_NS) {
+                atomicExch(&lc->abort, 1);
+                stalled = 1;
+            }
+        }
+        if (__shfl_sync(0xffffffffu, stalled, 0)) return -1;
+        __nanosleep(200);
+    }
+}
+
+// After the decision of image img's trial (thread 0 of the deciding CTA):
+// the image's next trial is released (its tile counter back to 0), or the
+// image leaves the launch.  The trial budget of the per-trial launches
+// (FE_ETIMEOUT once it is spent) applies per image.
+__device__ void persist_next(const KParams &p, ImgState *st, int img) {
+    if (st->done == 0 && st->n < st->target && st->trials >= st->trial_limit) {
+        st->status = FE_ETIMEOUT;
+        st->done = 1;
+    }
+    const bool more = st->done == 0 && st->n < st->target;
+    __threadfence();  // the state, the planes and the reset arrival count first
+    if (more)
+        atomicExch(p.sched + img, 0);
+    else
+        atomicSub(&p.loop->active, 1);
+    atomicAdd(&p.loop->decisions, 1ull);
+}
+
+// End of a persistent launch (thread 0 of every CTA): the last CTA to leave
+// marks images that a stalled launch left unfinished (FE_ETIMEOUT), and ends
+// the graph's while loop.
+__device__ void persist_exit(const KParams &p, unsigned participants) {
+    if (threadIdx.x != 0) return;
+    __threadfence();
+    const unsigned prev = atomicAdd(&p.loop->grid_arrivals, 1u);
+    if (prev != participants - 1u) return;
+    __threadfence();
+    LoopCtl *lc = p.loop;
+    lc->grid_arrivals = 0u;
+    for (int j = 0; j < p.nimg; ++j) {
+        volatile ImgState *s = p.st + j;
+        if (s->done == 0 && s->n < s->target) {
+            s->status = FE_ETIMEOUT;
+            s->done = 1;
+        }
+    }
+    lc->active = 0;
+    lc->launches += 1;
+    __threadfence();
+    if (p.use_cond) cudaGraphSetConditional(p.cond, 0u);
+}
+
 // Per-tile partial sums -> partials[gtile] (FP64): each thread's compensated
 // FP32 sums are reduced per warp, the warps' results in FP64.  The last CTA
 // of the image reduces the image's partials in FP64 in a fixed order (so the
@@ -250,6 +352,9 @@ __device__ void tile_finish(const KParams &p, int mode, int gtile, int img, cons
                             const Sum2 (&vals)[NRED], double *sRed, int *sLast) {
     constexpr int NWARP = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // persistent launches: this thread's plane and gradient writes are
+    // visible GPU-wide before the arrival below releases them to the next trial
+    if (mode == MODE_PTRIAL) __threadfence();
 #pragma unroll
     for (int k = 0; k < NRED; ++k) {
         const Sum2 v = warp_sum2(vals[k]);
@@ -294,14 +399,15 @@ __device__ void tile_finish(const KParams &p, int mode, int gtile, int img, cons
                 tot[k] = s;
             }
             tot[1] *= im.gscale;  // variant: G = (lambda/2) sum_p (u^2 - 2 f^2 log u)
-            if (mode == MODE_TRIAL || mode == MODE_INIT) {
-                decide(p, st, tot, mode);
+            if (mode == MODE_TRIAL || mode == MODE_PTRIAL || mode == MODE_INIT) {
+                decide(p, st, tot, mode == MODE_PTRIAL ? MODE_TRIAL : mode);
             } else {
                 p.results[2 * img] = tot[0];
                 p.results[2 * img + 1] = tot[1];
             }
             p.img_arrivals[img] = 0u;
             __threadfence();
+            if (mode == MODE_PTRIAL) persist_next(p, st, img);
         }
     }
 }

@@ -56,6 +56,11 @@ __host__ __device__ constexpr uint32_t kmajor_offset(int r, int k, int K, int el
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+// generic-proxy accesses of global memory (other CTAs' plane writes, made
+// visible to this thread) before this thread's TMA loads of it
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
 __device__ __forceinline__ void fence_before_sync() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }

@@ -191,16 +191,18 @@ def test_trajectory_64x64_100_iterations(fe, orc, bank, tile):
 @pytest.mark.parametrize("tile", [0, 32 | 0x100])
 def test_loop_modes_bit_identical(fe, bank, tile):
     """The CUDA-graph loop (one while node; for clusters the kernel node carries
-    the cluster dimension) and the host loop give the same bits."""
+    the cluster dimension), the persistent launch (the cluster tile runs as the
+    graph loop) and the host loop give the same bits."""
     k, th = bank
     _, f = _problem(100, 90, seed=5)
     outs = []
-    for mode in (0, 1):
+    for mode in (0, 1, 2):
         with fe.Solver([f], k, th, L0=1e-2, loop_mode=mode, tile=tile) as s:
             assert s.step(25) == fe.FE_OK
             outs.append((s.get_u(0), s.info(0)))
-    assert np.array_equal(outs[0][0], outs[1][0])
-    assert outs[0][1]["L"] == outs[1][1]["L"] and outs[0][1]["H"] == outs[1][1]["H"]
+    for m in (1, 2):  # the graph loop and the persistent launch
+        assert np.array_equal(outs[0][0], outs[m][0])
+        assert outs[0][1]["L"] == outs[m][1]["L"] and outs[0][1]["H"] == outs[m][1]["H"]
 
 
 def test_checkpoint_resume_bit_exact(fe, bank):

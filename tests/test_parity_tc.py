@@ -141,17 +141,19 @@ def test_tc_trajectory_64x64_100_iterations(fe, orc, bank, prec):
 @pytest.mark.parametrize("prec", ["bf16", "tf32"])
 def test_tc_batch_and_loop_modes(fe, bank, prec):
     """Uneven batch in one context equals single-image contexts bit for bit;
-    the CUDA-graph loop equals the host loop bit for bit."""
+    the CUDA-graph loop and the persistent launch equal the host loop bit for
+    bit."""
     k, th = bank
     shapes = [(64, 64), (131, 77), (9, 300), (200, 150)]
     fs = [_problem(H, W, seed=30 + i)[1] for i, (H, W) in enumerate(shapes)]
     outs = {}
-    for mode in (0, 1):
+    for mode in (0, 1, 2):
         with fe.Solver(fs, k, th, L0=1e-2, prec=prec, loop_mode=mode) as s:
             assert s.step(6) == fe.FE_OK
             outs[mode] = [s.get_u(i) for i in range(len(fs))]
     for i in range(len(fs)):
         assert np.array_equal(outs[0][i], outs[1][i])
+        assert np.array_equal(outs[0][i], outs[2][i])
         with fe.Solver([fs[i]], k, th, L0=1e-2, prec=prec) as s1:
             s1.step(6)
             assert np.array_equal(s1.get_u(0), outs[1][i])
