@@ -323,9 +323,9 @@ FE_API long long fe_launch_count(const fe_ctx *ctx);
  * ONE persistent launch that runs every trial of every image: its CTAs take
  * tiles from per-image counters, and the block that decides an image's
  * trial releases the tiles of that image's next trial at once, so images
- * advance independently instead of in lockstep.  Mode 2 applies to the FP32
- * tiles that run on one CTA (not the thread-block cluster tiles) and runs
- * as mode 1 otherwise; modes 1 and 2 run as
+ * advance independently instead of in lockstep.  Mode 2 applies where a tile
+ * runs on one CTA (every tensor-core form; the FP32 tiles without a
+ * thread-block cluster) and runs as mode 1 otherwise; modes 1 and 2 run as
  * mode 0 on a driver without conditional graph nodes.  All modes compute
  * the same iterates, energies and decisions bit for bit (each image's trials
  * and each trial's reduction order are the same).  A persistent launch in

@@ -447,11 +447,9 @@ fe_status load_inputs(fe_ctx *c, const float *const *f, const float *const *u0) 
     return FE_OK;
 }
 
-// Whether this context's trial kernel runs as one persistent launch: the
-// FP32 tiles that one CTA works on alone (not the thread-block cluster
-// tiles).  The tensor-core forms keep per-trial launches: their persistent
-// kernel is correct (bit for bit) but measured slower.
-bool persist_supported(const fe_ctx *c) { return c->prm.prec == FE_FP32 && c->cluster == 1; }
+// Whether this context's trial kernel can run as one persistent launch: the
+// tiles that one CTA works on alone (not the thread-block cluster tiles).
+bool persist_supported(const fe_ctx *c) { return c->prm.prec != FE_FP32 || c->cluster == 1; }
 
 // CUDA graph of the device loop: a while node whose body is one trial kernel
 // node.  Per-trial launches (persist false): one launch per trial of every
@@ -470,10 +468,15 @@ fe_status build_graph(fe_ctx *c, bool persist) {
     const size_t smem = tc ? tc_smem_bytes(fmt) : fp32_smem_bytes(c->tile_y);
     int grid = c->ntiles * (tc ? 1 : c->cluster);
     if (persist) {
+        // CTAs per SM: the residency the kernel is built for (its launch
+        // bounds and shared memory; the occupancy calculator was measured to
+        // report 1 for the tensor-core kernel, which runs 3 per SM), or the
+        // calculator's figure if higher.  A CTA that finds no room waits to
+        // be scheduled; it holds no tile meanwhile, so no other CTA waits on it.
         int per_sm = 0, sms = 0;
         FE_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
         FE_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
-        if (per_sm < 1) return set_err(c, FE_EUNSUPPORTED, "persistent launch: no CTA fits on an SM");
+        per_sm = std::max(per_sm, tc ? tc_ctas_per_sm(fmt) : fp32_ctas_per_sm(c->tile_y));
         grid = std::max(1, std::min(c->ntiles, per_sm * sms));
     }
     cudaGraph_t g = nullptr;

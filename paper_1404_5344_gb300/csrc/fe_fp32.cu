@@ -12,6 +12,7 @@ bool fp32_tile_supported(int T) { return T == 64 || T == 32; }
 size_t fp32_smem_bytes(int T) { return T == 32 ? Geo<32>::SM_BYTES : Geo<64>::SM_BYTES; }
 int fp32_tile() { return fp32_tile_size; }
 int fp32_threads(int T) { return T == 32 ? Geo<32>::NT : Geo<64>::NT; }
+int fp32_ctas_per_sm(int T) { return T == 32 ? Geo<32>::MINB : Geo<64>::MINB; }
 
 cudaError_t fp32_prepare() {
     cudaError_t e = prepare_tile<64, 0>();

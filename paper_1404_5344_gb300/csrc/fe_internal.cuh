@@ -141,6 +141,7 @@ bool fp32_tile_supported(int T);     // T = 64 or 32
 size_t fp32_smem_bytes(int T = fp32_tile_size);
 int fp32_tile();                                    // the default tile, fp32_tile_size
 int fp32_threads(int T = fp32_tile_size);           // block size of the tile kernel
+int fp32_ctas_per_sm(int T);  // CTAs per SM the tile kernel is built for (launch bounds, shared memory)
 cudaError_t fp32_prepare();  // opt in to the large shared-memory carve-out (every tile and model)
 // model: 0 = Eq. variant (iterate u), 1 = combined model (iterate w = log u);
 // cl: CTAs per tile (1, or 4 = a thread-block cluster per 32 x 32 tile);
@@ -164,6 +165,7 @@ constexpr int tc_tile_y = 58, tc_tile_x = 26;  // output tile; tile + 3-pixel ha
 constexpr int tc_box_x = 44, tc_box_y = 70;
 size_t tc_smem_bytes(int fmt);
 int tc_threads();
+int tc_ctas_per_sm(int fmt);  // CTAs per SM the kernel is built for (launch bounds, shared memory)
 cudaError_t tc_prepare();  // every format and model
 // model: 0 = Eq. variant (iterate u), 1 = combined model (iterate w = log u)
 cudaError_t tc_launch(int mode, int fmt, const KParams &p, int grid, cudaStream_t s, int model = 0);

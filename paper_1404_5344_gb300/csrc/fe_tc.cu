@@ -63,6 +63,7 @@ void tc_build_weights(int fmt, const float *filters, int nf, std::vector<unsigne
 
 size_t tc_smem_bytes(int fmt) { return fmt == 1 ? Cfg<1>::BYTES : (fmt == 3 ? Cfg<3>::BYTES : Cfg<2>::BYTES); }
 int tc_threads() { return NT; }
+int tc_ctas_per_sm(int fmt) { return fmt != 2 ? 3 : 2; }
 
 cudaError_t tc_prepare() {
     cudaError_t e = prepare_fmt<1, 0>();
