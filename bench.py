@@ -50,10 +50,15 @@ FLOP_PER_PIXEL_TRIAL = 2 * 48 * 49 * 2  # forward + adjoint bank, 2 flop per MAC
 # launch with every image active, per pixel, from one ncu capture of the
 # current kernels on 24 x 512^2 (profiles/*_trial_24x512.md); None where no
 # capture of the current kernel exists
-TRAFFIC_PER_PIXEL = {("fp32", "variant"): 137.891584e6 / 6291456,
-                     ("bf16", "variant"): 129.373440e6 / 6291456,
-                     ("tf32", "variant"): 127.864576e6 / 6291456,
-                     ("fp32", "combined"): 137.784832e6 / 6291456}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per pixel-trial
+# of the persistent trial kernel: one ncu capture of one persistent launch
+# (one step: 300 iterations of 24 x 512^2 + 24 x 256^2), divided by the
+# step's pixel-trials (profiles/persistent_trial_kernels_24x512.md)
+TRAFFIC_PER_PIXEL_TRIAL = {("fp32", "variant"): 5.701457e+10 / 2431909888,
+                           ("bf16", "variant"): 6.096201e+10 / 2450784256,
+                           ("bf16r", "variant"): 6.096867e+10 / 2450325504,
+                           ("tf32", "variant"): 5.993003e+10 / 2428305408,
+                           ("fp32", "combined"): 5.802384e+10 / 2471952384}
 METRIC = "Mpixel*iter/s of fused iPiano step"
 
 
@@ -72,7 +77,7 @@ def parse():
                          "(lambda1 = 160, lambda2 = 0.004, FP32 form)")
     ap.add_argument("--loop-mode", type=int, default=2,
                     help="0 host chunks of per-trial launches, 1 graph while node of per-trial launches, "
-                         "2 one persistent launch per step (default)")
+                         "2 one persistent launch per step (default), 3 the same without a graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the other forms (TF32, BF16, combined model, batch of 64) in the default line")
@@ -747,7 +752,8 @@ def measure_peaks(fe, local):
 
 LOOP_NAMES = {0: "host chunks of per-trial launches",
               1: "cuda-graph while node of per-trial launches",
-              2: "one persistent launch per step (cuda graph)"}
+              2: "one persistent launch per step (cuda graph)",
+              3: "one persistent launch per step (no graph)"}
 
 
 def measure_throughput(fe, torch, args, f_dev, k, th, shapes, prec, model, steps, warmup, stream, flush,
@@ -804,7 +810,7 @@ def measure_throughput(fe, torch, args, f_dev, k, th, shapes, prec, model, steps
             "cluster": cluster, "clocks": clk, "steps": steps}
 
 
-def roofline_of(prec, model, r, npix, peaks, sm_mhz_max):
+def roofline_of(prec, model, r, npix, peaks, sm_mhz_max, loop_mode=2):
     """Roofline object of the trial kernel: algorithmic work (9408 flop per
     pixel per trial, every image-trial that ran) over the device time of the
     iteration loop, against the measured peak of the unit that bounds it."""
@@ -815,10 +821,14 @@ def roofline_of(prec, model, r, npix, peaks, sm_mhz_max):
     # cover only the images still iterating, so a plain average per launch
     # would not be a full-batch time
     full_ms = r["loop_ms"] / (r["pix_trials"] / npix)
+    # loop modes 2 and 3 run one persistent launch per step (one-CTA tiles)
+    persistent = loop_mode in (2, 3) and r["cluster"] == 1
+    mode_name = "MODE_PTRIAL" if persistent else "MODE_TRIAL"
+    bpt = TRAFFIC_PER_PIXEL_TRIAL.get((prec, model)) if persistent else None
     if prec == "fp32":
         derived = sms * 128 * 2 * sm_mhz_max * 1e6 / 1e12
         peak = peaks.get("ffma") or derived
-        rl = {"bound": "alu", "kernel": "fp32_tile_kernel<MODE_TRIAL>",
+        rl = {"bound": "alu", "kernel": "fp32_tile_kernel<%s>" % mode_name,
               "peak_basis": ("measured FP32 FMA rate (fe_peak ffma, %d SMs at full occupancy)" % sms
                              if peaks.get("ffma") else "FP32 FMA from unit counts"),
               "peak_derived": round(derived, 3),
@@ -828,7 +838,7 @@ def roofline_of(prec, model, r, npix, peaks, sm_mhz_max):
         bf16_sust, src = measured_bf16_sustained()
         ratio = 1.0 if prec in ("bf16", "bf16r") else 1.1 / 2.25
         peak = bf16_sust * ratio
-        rl = {"bound": "tensor", "kernel": "tc_tile_kernel<MODE_TRIAL, %s>" % prec.upper(),
+        rl = {"bound": "tensor", "kernel": "tc_tile_kernel<%s, %s>" % (mode_name, prec.upper()),
               "peak_basis": "dense %s tensor peak = %.1f TFLOP/s sustained BF16 (%s) x %.3f" % (
                   prec.upper(), bf16_sust, src, ratio),
               "peak_measured_tcgen05": peaks.get("tc_" + prec[:4]),
@@ -836,10 +846,12 @@ def roofline_of(prec, model, r, npix, peaks, sm_mhz_max):
                                              "burst" % prec}
     rl.update({"achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
                "frac": round(achieved / peak, 4),
-               "traffic": (round(TRAFFIC_PER_PIXEL[(prec, model)] * npix) if (prec, model) in TRAFFIC_PER_PIXEL
-                           else None),
-               "traffic_basis": "ncu DRAM bytes of one trial launch of 24x512^2 with all images active, scaled "
-                                "to this workload's full-batch launch by pixels",
+               "traffic": round(bpt * r["pix_trials"] / r["steps"]) if bpt else None,
+               "traffic_per_full_batch_trial": round(bpt * npix) if bpt else None,
+               "traffic_basis": ("ncu DRAM bytes of one persistent launch (one step of 24x512^2 + 24x256^2, 300 "
+                                 "iterations) = %.2f bytes per pixel-trial, times this run's pixel-trials per launch "
+                                 "(one launch per step); per full-batch trial: times the batch's pixels" % bpt
+                                 if bpt else None),
                "work": "9408 flop (2 x 48 x 49 MAC) per pixel per trial, every image-trial",
                "ms_per_full_batch_trial": round(full_ms, 4)})
     if prec == "fp32":
@@ -923,7 +935,7 @@ def main():
     # measured peaks (outside the timed region) and the roofline against them
     peaks = measure_peaks(fe, local) if not args.no_peaks else {"sms": fe.device_sms()}
     sm_mhz_max = (clk or {}).get("sm_max_mhz") or 2070.0
-    rl = roofline_of(args.prec, args.model, r, npix, peaks, sm_mhz_max)
+    rl = roofline_of(args.prec, args.model, r, npix, peaks, sm_mhz_max, args.loop_mode)
 
     # the other forms on the same workload (and the batching form), so that
     # one run carries every form's number under the same clock record
@@ -949,7 +961,7 @@ def main():
                 "e2e": {"value": round(e2e_value, 2), "unit": "Mpixel*iter/s",
                         "h2d_bytes_per_step": int(npix * 4), "d2h_bytes_per_step": int(npix * 4)},
                 "gpu_launches": int(launches), "trial_kernel_launches": int(trial_launches),
-                "trials": int(r["trials"]), "statuses": r["statuses"],
+                "trials": int(r["trials"]), "pixel_trials": int(r["pix_trials"]), "statuses": r["statuses"],
                 "roofline": rl, "clocks": clk, "peaks": peaks}
         if clk and clk.get("sm_mhz") and args.prec == "fp32" and peaks.get("sms"):
             line["roofline"]["frac_of_derived_at_observed_clock"] = round(
@@ -983,7 +995,7 @@ def measure_forms(fe, torch, args, f_dev, k, th, shapes, npix, stream, flush, pe
         out[name] = {"value": round(r["pix_iters"] / (r["total_ms"] / 1e3) / 1e6, 2), "unit": "Mpixel*iter/s",
                      "precision": prec, "model": model, "steps": steps, "warmup": warmup,
                      "ms_per_step": round(r["total_ms"] / steps, 3), "statuses": r["statuses"],
-                     "tile": "%dx%d" % r["tile"], "roofline": roofline_of(prec, model, r, npix, peaks, sm_mhz_max),
+                     "tile": "%dx%d" % r["tile"], "roofline": roofline_of(prec, model, r, npix, peaks, sm_mhz_max, args.loop_mode),
                      "clocks": r["clocks"]}
     # batching form: time to tolerance of 64 uneven images
     sizes, bfs, bk, bth = batch64_inputs()

@@ -325,8 +325,11 @@ FE_API long long fe_launch_count(const fe_ctx *ctx);
  * trial releases the tiles of that image's next trial at once, so images
  * advance independently instead of in lockstep.  Mode 2 applies where a tile
  * runs on one CTA (every tensor-core form; the FP32 tiles without a
- * thread-block cluster) and runs as mode 1 otherwise; modes 1 and 2 run as
- * mode 0 on a driver without conditional graph nodes.  All modes compute
+ * thread-block cluster) and runs as mode 1 otherwise; 3 = the persistent
+ * launch of mode 2 issued directly, without a graph (for profilers that do
+ * not follow kernels into conditional graph nodes; runs as mode 0 where
+ * mode 2 runs as mode 1); modes 1 and 2 run as mode 0 on a driver without
+ * conditional graph nodes.  All modes compute
  * the same iterates, energies and decisions bit for bit (each image's trials
  * and each trial's reduction order are the same).  A persistent launch in
  * which no trial is decided for 4 s stops; the images it left unfinished get

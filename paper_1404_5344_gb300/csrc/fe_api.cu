@@ -456,9 +456,10 @@ bool persist_supported(const fe_ctx *c) { return c->prm.prec != FE_FP32 || c->cl
 // image, the last CTA sets the while condition.  Persistent (persist true):
 // the body is one launch of as many CTAs as fit on the GPU at once (at most
 // one per tile), which runs every trial of every image and ends the loop.
-fe_status build_graph(fe_ctx *c, bool persist) {
-    const int gi = persist ? 1 : 0;
-    if (c->graph_built[gi]) return FE_OK;
+// Kernel, block size, shared memory and grid of a trial launch: per-trial
+// (every tile, times the cluster size) or persistent.
+fe_status trial_config(fe_ctx *c, bool persist, const void **fn_out, int *threads_out, size_t *smem_out,
+                       int *grid_out) {
     const int fmt = tc_format(c->prm.prec);
     const bool tc = c->prm.prec != FE_FP32;
     const void *fn = persist ? (tc ? tc_ptrial_entry(fmt, c->prm.model) : fp32_ptrial_entry(c->tile_y, c->prm.model))
@@ -479,6 +480,22 @@ fe_status build_graph(fe_ctx *c, bool persist) {
         per_sm = std::max(per_sm, tc ? tc_ctas_per_sm(fmt) : fp32_ctas_per_sm(c->tile_y));
         grid = std::max(1, std::min(c->ntiles, per_sm * sms));
     }
+    *fn_out = fn;
+    *threads_out = threads;
+    *smem_out = smem;
+    *grid_out = grid;
+    return FE_OK;
+}
+
+fe_status build_graph(fe_ctx *c, bool persist) {
+    const int gi = persist ? 1 : 0;
+    if (c->graph_built[gi]) return FE_OK;
+    const bool tc = c->prm.prec != FE_FP32;
+    const void *fn = nullptr;
+    int threads = 0, grid = 0;
+    size_t smem = 0;
+    fe_status cst = trial_config(c, persist, &fn, &threads, &smem, &grid);
+    if (cst != FE_OK) return cst;
     cudaGraph_t g = nullptr;
     FE_CUDA(c, cudaGraphCreate(&g, 0));
     cudaGraphConditionalHandle h;
@@ -545,25 +562,48 @@ fe_status build_graph(fe_ctx *c, bool persist) {
     return FE_OK;
 }
 
+// After a persistent launch (synchronised): a launch that stopped because no
+// trial was decided for PERSIST_STALL_NS is reported.
+fe_status check_persist(fe_ctx *c) {
+    LoopCtl lc;
+    FE_CUDA(c, cudaMemcpy(&lc, c->d_loop, sizeof lc, cudaMemcpyDeviceToHost));
+    if (lc.abort)
+        set_err(c, FE_ETIMEOUT, "persistent launch stopped: no trial was decided for %.0f s",
+                1e-9 * (double)PERSIST_STALL_NS);
+    return FE_OK;
+}
+
 // Run trial launches until no image is active (or the budget is spent).
-// Loop mode 2 runs the persistent launch where the tile allows it (else as
-// mode 1), mode 1 the graph of per-trial launches, mode 0 (or a driver
+// Loop mode 2 runs the persistent launch in a CUDA graph where the tile
+// allows it (else as mode 1), mode 3 the same launch without a graph (else
+// as mode 0), mode 1 the graph of per-trial launches, mode 0 (or a driver
 // without conditional graph nodes) host-side chunks of per-trial launches.
 fe_status run_loop(fe_ctx *c, long long n_hint, long long budget, bool sync) {
-    if (c->loop_mode >= 1) {
+    if (c->loop_mode == 3 && persist_supported(c)) {
+        const void *fn = nullptr;
+        int threads = 0, grid = 0;
+        size_t smem = 0;
+        fe_status st = trial_config(c, true, &fn, &threads, &smem, &grid);
+        if (st != FE_OK) return st;
+        KParams kp = c->kp;
+        kp.tile0 = 0;
+        kp.use_cond = 0;
+        void *args[] = {&kp};
+        FE_CUDA(c, cudaLaunchKernel(fn, dim3((unsigned)grid), dim3((unsigned)threads), args, smem, c->s));
+        if (sync) {
+            FE_CUDA(c, cudaStreamSynchronize(c->s));
+            return check_persist(c);
+        }
+        return FE_OK;
+    }
+    if (c->loop_mode == 1 || c->loop_mode == 2) {
         const bool persist = c->loop_mode == 2 && persist_supported(c);
         fe_status st = build_graph(c, persist);
         if (st == FE_OK) {
             FE_CUDA(c, cudaGraphLaunch(c->gexec[persist ? 1 : 0], c->s));
             if (sync) {
                 FE_CUDA(c, cudaStreamSynchronize(c->s));
-                if (persist) {
-                    LoopCtl lc;
-                    FE_CUDA(c, cudaMemcpy(&lc, c->d_loop, sizeof lc, cudaMemcpyDeviceToHost));
-                    if (lc.abort)
-                        set_err(c, FE_ETIMEOUT, "persistent launch stopped: no trial was decided for %.0f s",
-                                1e-9 * (double)PERSIST_STALL_NS);
-                }
+                if (persist) return check_persist(c);
             }
             return FE_OK;
         }
@@ -901,7 +941,7 @@ fe_status fe_reset(fe_ctx *c, const float *const *f, const float *const *u0) {
 }
 
 fe_status fe_set_loop_mode(fe_ctx *c, int mode) {
-    if (!c || mode < 0 || mode > 2) return FE_EINVAL;
+    if (!c || mode < 0 || mode > 3) return FE_EINVAL;
     c->loop_mode = mode;
     return FE_OK;
 }

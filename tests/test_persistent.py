@@ -68,12 +68,14 @@ def _same(a, b):
 def test_persistent_solve_equals_per_trial_launches(fe, bank48, prec, tile, model):
     """fe_solve to a relative tolerance: images stop after different numbers
     of iterations, and the small L0 makes the first trials fail the descent
-    test; the persistent launch reproduces the per-trial launches."""
+    test; the persistent launch (in a graph, mode 2, or issued directly,
+    mode 3) reproduces the per-trial launches."""
     fs = _fs(SHAPES, seed=3)
     run = lambda s: s.solve(60, 1e-4)
     a = _run(fe, fs, bank48, 0, prec, tile, model, run, L0=1e-4)
     b = _run(fe, fs, bank48, 2, prec, tile, model, run, L0=1e-4)
     _same(a, b)
+    _same(a, _run(fe, fs, bank48, 3, prec, tile, model, run, L0=1e-4))  # the same launch without a graph
     assert any(x["backtracks"] > 0 for x in b[2]), "the case exercises rejected trials"
     assert len({x["n"] for x in b[2]}) > 1, "images stop at different iterations"
 
