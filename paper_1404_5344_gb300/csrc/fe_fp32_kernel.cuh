@@ -299,10 +299,8 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
                 if (tid == 0) sTask = t;
             }
             __syncthreads();
-            gtile = sTask;
+            gtile = sTask;  // claimed with an acquire fence (persist_grab)
             if (gtile < 0) break;
-            // acquire: the decision and the planes of the image's previous trial
-            __threadfence();
         } else {
             const int bt = p.tile0 + (int)blockIdx.x / CL;
             gtile = p.order ? p.order[bt] : bt;

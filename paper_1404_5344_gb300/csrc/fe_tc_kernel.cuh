@@ -291,10 +291,8 @@ __global__ void __launch_bounds__(NT, FMT != 2 ? 3 : 2) tc_tile_kernel(const KPa
                 if (lane == 0) sTask = t;
             }
             __syncthreads();
-            gtile = sTask;
+            gtile = sTask;  // claimed with an acquire fence (persist_grab)
             if (gtile < 0) break;
-            // acquire: the decision and the planes of the image's previous trial
-            __threadfence();
         } else {
             gtile = p.order ? p.order[p.tile0 + (int)blockIdx.x] : p.tile0 + (int)blockIdx.x;
         }

@@ -278,6 +278,9 @@ __device__ int persist_grab(const KParams &p, int &pref) {
                 const int jl = __shfl_sync(0xffffffffu, j, l), ntl = __shfl_sync(0xffffffffu, nt, l);
                 if (t < ntl) {
                     pref = jl;
+                    // acquire: the image's decision and the planes of its
+                    // previous trial (the CTA's barrier passes them on)
+                    __threadfence();
                     return __ldg(p.porder + __ldg(&p.imgs[jl].tile_begin) + t);
                 }
             }
@@ -352,9 +355,9 @@ __device__ void tile_finish(const KParams &p, int mode, int gtile, int img, cons
                             const Sum2 (&vals)[NRED], double *sRed, int *sLast) {
     constexpr int NWARP = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // persistent launches: this thread's plane and gradient writes are
-    // visible GPU-wide before the arrival below releases them to the next trial
-    if (mode == MODE_PTRIAL) __threadfence();
+    // (the CTA's plane and gradient writes are released to the deciding CTA,
+    // and through it to the image's next trial, by the barriers below and
+    // thread 0's fence before its arrival: the pattern of a grid barrier)
 #pragma unroll
     for (int k = 0; k < NRED; ++k) {
         const Sum2 v = warp_sum2(vals[k]);
