@@ -421,6 +421,17 @@ FE_API fe_status fe_tc_gemm_selftest(int prec, int N, int K, const float *A, con
  * trial kernels' MMA waits take the same bounded path. */
 FE_API fe_status fe_tc_wait_selftest(unsigned max_iter, int *timed_out);
 
+/* Bounded-wait self-test of the persistent trial launch (loop mode 2; no
+ * counterpart in the paper): one warp runs the launch's tile claim against
+ * one image whose only tile is taken, with the image still counted active
+ * and no trial ever decided, and a wait limit of stall_s seconds (0 <
+ * stall_s <= 5; the solver uses 4 s).  *aborted = 1 if the claim gave up
+ * and raised the launch's abort flag (0 otherwise), *waited_s = the
+ * kernel's duration.  Returns FE_ETIMEOUT when it gave up (the expected
+ * outcome), FE_EINVAL, FE_ENOMEM, FE_ECUDA.  Allocates and frees its own
+ * device buffer; synchronises the device. */
+FE_API fe_status fe_persist_wait_selftest(double stall_s, int *aborted, double *waited_s);
+
 /* ---- Peak-rate microbenchmarks ---------------------------------------------
  * Measured roofline denominators (no counterpart in the paper): the rate of
  * the units the solver's kernels are bound by, on the current device, each

@@ -133,6 +133,7 @@ struct KParams {
     // and each image's tiles in the order they are taken (global indices)
     int *sched;
     const int *porder;
+    unsigned long long persist_stall_ns;  // wait limit of the claim (0: PERSIST_STALL_NS)
 };
 
 // FP32 fused tile kernel (fe_fp32.cu)

@@ -255,6 +255,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ int persist_grab(const KParams &p, int &pref) {
     const int lane = threadIdx.x & 31;
     LoopCtl *lc = p.loop;
+    const unsigned long long limit = p.persist_stall_ns ? p.persist_stall_ns : PERSIST_STALL_NS;
     unsigned long long seen = ~0ull, t0 = 0;
     for (;;) {
         // lane 0 reads the shared words and broadcasts them: every lane takes
@@ -292,7 +293,7 @@ __device__ int persist_grab(const KParams &p, int &pref) {
             if (d != seen) {
                 seen = d;
                 t0 = now;
-            } else if (now - t0 > PERSIST_STALL_NS) {
+            } else if (now - t0 > limit) {
                 atomicExch(&lc->abort, 1);
                 stalled = 1;
             }

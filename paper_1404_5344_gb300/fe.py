@@ -30,7 +30,7 @@ EXPORTS = (
     "fe_default_params", "fe_init_batch", "fe_init", "fe_reset", "fe_destroy", "fe_step",
     "fe_solve", "fe_get_info", "fe_get_u", "fe_energy", "fe_gradient", "fe_get_state",
     "fe_set_state", "fe_num_images", "fe_image_size", "fe_launch_count", "fe_set_loop_mode", "fe_tile_size",
-    "fe_ssim", "fe_psnr", "fe_tc_wait_selftest", "fe_tile_cluster",
+    "fe_ssim", "fe_psnr", "fe_tc_wait_selftest", "fe_persist_wait_selftest", "fe_tile_cluster",
     "fe_last_error", "fe_status_string", "fe_abi_version", "fe_gradient_noalloc",
     "fe_tc_gemm_selftest", "fe_cnn_create", "fe_cnn_destroy", "fe_cnn_num_params",
     "fe_cnn_last_error", "fe_cnn_set_params", "fe_cnn_get_params", "fe_cnn_forward",
@@ -87,6 +87,7 @@ def _load(path: str = LIB_PATH) -> C.CDLL:
     L.fe_tile_cluster.argtypes = [VP]
     L.fe_ssim.argtypes = [VP, VP, I, I, D, P(D), VP]
     L.fe_tc_wait_selftest.argtypes = [C.c_uint, P(I)]
+    L.fe_persist_wait_selftest.argtypes = [D, P(I), P(D)]
     L.fe_psnr.argtypes = [VP, VP, C.c_longlong, D, P(D), VP]
     L.fe_launch_count.argtypes = [VP]
     L.fe_launch_count.restype = C.c_longlong
@@ -117,7 +118,7 @@ def _load(path: str = LIB_PATH) -> C.CDLL:
     for name in ("fe_tc_gemm_selftest", "fe_gradient_noalloc", "fe_init_batch","fe_init", "fe_reset", "fe_step", "fe_solve", "fe_get_info",
                  "fe_get_u", "fe_energy", "fe_gradient", "fe_get_state", "fe_set_state",
                  "fe_image_size", "fe_set_loop_mode", "fe_num_images", "fe_abi_version", "fe_tile_size",
-                 "fe_ssim", "fe_psnr", "fe_tc_wait_selftest", "fe_tile_cluster", "fe_peak",
+                 "fe_ssim", "fe_psnr", "fe_tc_wait_selftest", "fe_persist_wait_selftest", "fe_tile_cluster", "fe_peak",
                  "fe_device_sms", "fe_solve_to_energy"):
         getattr(L, name).restype = C.c_int
     return L

@@ -165,3 +165,17 @@ def test_persistent_one_trial_launch_per_call(fe, bank48):
         c0 = s.launch_count()
         s.step(20)
         assert s.launch_count() - c0 == 1 + max(s.info(j)["trials"] for j in range(len(fs)))
+
+
+def test_persistent_claim_wait_is_bounded(fe):
+    """The persistent launch's tile claim waits for a trial decision with a
+    time limit: with one image counted active, its only tile taken and no
+    decision ever coming, the claim gives up after the limit, returns no
+    tile and raises the launch's abort flag (the solver's limit is 4 s; the
+    self-test runs it at 0.2 s).  Nothing here faults or hangs the GPU."""
+    import ctypes as C
+    aborted, waited = C.c_int(-1), C.c_double(0.0)
+    st = fe.lib.fe_persist_wait_selftest(0.2, C.byref(aborted), C.byref(waited))
+    assert st == fe.FE_ETIMEOUT and aborted.value == 1
+    assert 0.2 <= waited.value < 3.0, waited.value
+    assert fe.lib.fe_persist_wait_selftest(0.0, C.byref(aborted), C.byref(waited)) == fe.FE_EINVAL
