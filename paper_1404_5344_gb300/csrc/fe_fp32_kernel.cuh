@@ -341,35 +341,61 @@ __global__ void __launch_bounds__(Geo<T>::NT, Geo<T>::MINB) fp32_tile_kernel(con
                 const float *gc = im.g[gcur];
                 float *un = im.u[(cur + 1) % 3];
                 const float *f2p = im.f2;
-                for (int idx = tid; idx < R6Y * R6X; idx += NT) {
-                    const int ry = idx / R6X, rx = idx - ry * R6X;
-                    const int y = y0 - 6 + ry, x = x0 - 6 + rx;
-                    const size_t off = (size_t)reflect(y, H) * W + reflect(x, W);
-                    const bool inner = ry >= 6 && ry < 6 + TY && rx >= 6 && rx < 6 + TX && y < H && x < W;
-                    float v;
-                    if (TRIAL) {
-                        // L2 loads: a persistent launch rewrites these planes while it runs
-                        const float u0 = __ldcg(uc + off), u_1 = __ldcg(upv + off), g0 = __ldcg(gc + off);
-                        const float f2 = __ldg(f2p + off);
-                        const float dprev = u0 - u_1;
-                        const float uhat = fmaf(-a, g0, fmaf(b, dprev, u0));
-                        v = MODEL == 0 ? prox_g(uhat, f2, tl) : prox_w(uhat, f2, a, l1, l2);
-                        if (inner && rank == 0) {
-                            un[off] = v;
-                            const float d = v - u0;
-                            accGD = fmaf(g0, d, accGD);
-                            accDD = fmaf(d, d, accDD);
-                            accDP = fmaf(d, dprev, accDP);
-                            sum2_add(accG, MODEL == 0 ? v * v - 2.0f * f2 * logf(v) : data_w(v, f2, l1, l2));
-                        }
-                    } else {
-                        v = __ldg(uc + off);
-                        if (inner && rank == 0) {
-                            const float f2 = __ldg(f2p + off);
-                            sum2_add(accG, MODEL == 0 ? v * v - 2.0f * f2 * logf(v) : data_w(v, f2, l1, l2));
+                // UNR positions per thread at a time: their loads are issued
+                // together before the arithmetic (positions past the region
+                // load the last one's values and are skipped); the 32 x 32
+                // tile takes one (its register budget is smaller)
+                constexpr int UNR = T == 64 ? 4 : 1, NPIX = R6Y * R6X;
+                for (int base = 0; base < NPIX; base += UNR * NT) {
+                    size_t offk[UNR];
+                    float u0k[UNR], u1k[UNR], g0k[UNR], f2k[UNR];
+#pragma unroll
+                    for (int k = 0; k < UNR; ++k) {
+                        const int idx = base + k * NT + tid;
+                        const int idc = idx < NPIX ? idx : NPIX - 1;
+                        const int ry = idc / R6X, rx = idc - ry * R6X;
+                        offk[k] = (size_t)reflect(y0 - 6 + ry, H) * W + reflect(x0 - 6 + rx, W);
+                        f2k[k] = __ldg(f2p + offk[k]);
+                        if (TRIAL) {
+                            // L2 loads: a persistent launch rewrites these planes while it runs
+                            u0k[k] = __ldcg(uc + offk[k]);
+                            u1k[k] = __ldcg(upv + offk[k]);
+                            g0k[k] = __ldcg(gc + offk[k]);
+                        } else {
+                            u0k[k] = __ldg(uc + offk[k]);
+                            u1k[k] = g0k[k] = 0.f;
                         }
                     }
-                    sU[ry * SU_LD + rx] = MODEL == 0 ? v : expf(v);  // the bank sees u
+#pragma unroll
+                    for (int k = 0; k < UNR; ++k) {
+                        const int idx = base + k * NT + tid;
+                        if (idx >= NPIX) continue;
+                        const int ry = idx / R6X, rx = idx - ry * R6X;
+                        const int y = y0 - 6 + ry, x = x0 - 6 + rx;
+                        const size_t off = offk[k];
+                        const bool inner = ry >= 6 && ry < 6 + TY && rx >= 6 && rx < 6 + TX && y < H && x < W;
+                        const float u0 = u0k[k], f2 = f2k[k];
+                        float v;
+                        if (TRIAL) {
+                            const float u_1 = u1k[k], g0 = g0k[k];
+                            const float dprev = u0 - u_1;
+                            const float uhat = fmaf(-a, g0, fmaf(b, dprev, u0));
+                            v = MODEL == 0 ? prox_g(uhat, f2, tl) : prox_w(uhat, f2, a, l1, l2);
+                            if (inner && rank == 0) {
+                                un[off] = v;
+                                const float d = v - u0;
+                                accGD = fmaf(g0, d, accGD);
+                                accDD = fmaf(d, d, accDD);
+                                accDP = fmaf(d, dprev, accDP);
+                                sum2_add(accG, MODEL == 0 ? v * v - 2.0f * f2 * logf(v) : data_w(v, f2, l1, l2));
+                            }
+                        } else {
+                            v = u0;
+                            if (inner && rank == 0)
+                                sum2_add(accG, MODEL == 0 ? v * v - 2.0f * f2 * logf(v) : data_w(v, f2, l1, l2));
+                        }
+                        sU[ry * SU_LD + rx] = MODEL == 0 ? v : expf(v);  // the bank sees u
+                    }
                 }
             }
 
