@@ -82,6 +82,17 @@ struct Cfg {
     static constexpr int OPF = BF ? 1 : 2;                 // operand format of the instruction descriptor
     static constexpr bool RLO = FMT != 3;                  // r carried as hi + lo
     static constexpr int KADJ = RLO ? 2 * NF : NF;         // adjoint K: r hi | r lo, or r
+    // XRING (FMT 3): the forward A operand is read in place from a ring of
+    // u^{n+1} rows whose entry (row, column) holds that column's 8 window
+    // values (one 16-byte core-matrix row; hi plane, then lo plane): window
+    // row dy of a block is the ring at a descriptor start dy rows further, so
+    // no per-block im2col.  XSLOTS rows plus XMIRROR copies of the first ones,
+    // so that the 4 rows of a block's window row are always contiguous.
+    static constexpr bool XRING = FMT == 3;
+    static constexpr int XSLOTS = 10, XMIRROR = 3;
+    static constexpr int XROW_BYTES = R3X * 16;                            // 32 entries of 16 bytes
+    static constexpr int XPLANE = (XSLOTS + XMIRROR) * XROW_BYTES;         // hi plane, then lo plane
+    static constexpr int BF_DY = 2 * NF * 16;                              // forward B of one window row
     static constexpr int EB = BF ? 2 : 4;                  // operand bytes
     static constexpr int KSTEP = BF ? 16 : 8;              // K per MMA
     static constexpr int KPASS = BF ? 64 : 56;             // 7 rows x 8 taps, padded to KSTEP
@@ -92,16 +103,19 @@ struct Cfg {
     static constexpr int NPL = 2;                          // planes: hi, lo
     static constexpr int PL_WORDS = R6Y * PP * EB / 4;     // plane stride in 4-byte words
     static_assert(PL_WORDS * 4 >= R6Y * PP * EB, "plane holds the u region");
-    static constexpr size_t AF_BYTES = (size_t)128 * KFWD * EB;
+    static constexpr size_t AF_BYTES = XRING ? (size_t)2 * XPLANE : (size_t)128 * KFWD * EB;  // XRING: the ring
     static constexpr size_t R_BYTES = (size_t)128 * KADJ * EB;
-    static constexpr size_t BF_BYTES = (size_t)NF * KPASS * EB;   // one pass: hi and lo MMAs share it
+    // forward B: one pass (hi and lo MMAs share it); XRING: per window row
+    // dy, N = 48 x K = 16 (the row's 8 taps twice: for the hi and lo planes)
+    static constexpr size_t BF_BYTES = XRING ? (size_t)KS * BF_DY : (size_t)NF * KPASS * EB;
     static constexpr size_t BA_BYTES = (size_t)NTAP * NF * EB;    // likewise for r hi and r lo
     // one buffer holds the A operand of the forward GEMM (im2col of block b + 1)
     // and the R operand of the adjoint GEMM (block b) in turn: R is written
-    // after MMA_fwd(b) completed, the im2col after MMA_adj(b) completed
-    static constexpr size_t OFF_AF = 0;
-    static constexpr size_t OFF_R = OFF_AF;
-    static constexpr size_t OFF_H = OFF_AF + (AF_BYTES > R_BYTES ? AF_BYTES : R_BYTES);
+    // after MMA_fwd(b) completed, the im2col after MMA_adj(b) completed.
+    // XRING: R, then the ring (both live throughout the block loop)
+    static constexpr size_t OFF_R = 0;
+    static constexpr size_t OFF_AF = XRING ? R_BYTES : 0;
+    static constexpr size_t OFF_H = XRING ? OFF_AF + AF_BYTES : OFF_AF + (AF_BYTES > R_BYTES ? AF_BYTES : R_BYTES);
     // gradient rows: BF16 keeps every row of the region (three CTAs per SM
     // fit either way; the final pass then folds and writes with all warps),
     // TF32 only the rows of the vertical fold (image rows -3..2, H-3..H+2),
@@ -120,7 +134,9 @@ struct Cfg {
     // gradient rows, none of which is live before the first im2col
     static constexpr size_t STAGE_PLANE = ((size_t)tc_box_y * tc_box_x * 4 + 127) / 128 * 128;
     static constexpr size_t OFF_STAGE = 0;
-    static_assert(OFF_STAGE + 4 * STAGE_PLANE <= OFF_BF, "the staging planes end before the B operands");
+    static_assert(XRING || OFF_STAGE + 4 * STAGE_PLANE <= OFF_BF, "the staging planes end before the B operands");
+    static_assert(!XRING || (OFF_AF % 16 == 0 && XPLANE % 16 == 0 && 4 + KS - 1 <= XSLOTS && XMIRROR == 3),
+                  "ring: 16-byte rows; the 10 rows of a block's windows fit; 4 consecutive rows contiguous");
     static_assert(OFF_H % 16 == 0 && OFF_BF % 128 == 0 && OFF_BA % 128 == 0 && OFF_U % 128 == 0,
                   "operand alignment");
     static_assert(OFF_U % 16 == 0 && OFF_TH % 16 == 0 && OFF_RED % 8 == 0 && OFF_G % 16 == 0, "alignment");
@@ -251,6 +267,45 @@ __device__ __forceinline__ void im2col(const uint32_t *__restrict__ sP, unsigned
     }
 }
 
+// One entry of the window-row ring (XRING): R6 row r of u^{n+1}, column c
+// (0..31): the 8 values u(r, c .. c + 7) of plane pl (hi, lo), read as the
+// im2col reads a window row (five words, funnel shifts), into slot
+// r % XSLOTS and, for the first XMIRROR slots, into their copies after the
+// last slot.
+template <int FMT>
+__device__ __forceinline__ void xring_entry(const uint32_t *__restrict__ sP, unsigned char *__restrict__ sX, int r,
+                                            int c, int pl) {
+    using C = Cfg<FMT>;
+    static_assert(C::BF, "BF16 ring entries");
+    constexpr int ROW_WORDS = PP * C::EB / 4;
+    const uint32_t *w = sP + pl * C::PL_WORDS + r * ROW_WORDS + (c >> 1);  // words c/2 .. c/2 + 4: in the row
+    const uint32_t sh = (uint32_t)(c & 1) * 16u;
+    const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3], w4 = w[4];
+    const uint4 v = make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh), __funnelshift_r(w2, w3, sh),
+                               __funnelshift_r(w3, w4, sh));
+    const int slot = r % C::XSLOTS;
+    unsigned char *d = sX + pl * C::XPLANE + slot * C::XROW_BYTES + c * 16;
+    *reinterpret_cast<uint4 *>(d) = v;
+    if (slot < C::XMIRROR) *reinterpret_cast<uint4 *>(d + C::XSLOTS * C::XROW_BYTES) = v;
+}
+
+// Forward GEMM of block blk from the ring (XRING; one thread): window row dy
+// is one MMA of K = 16 (the 8 taps on the hi plane, then on the lo plane)
+// whose A operand starts at the ring slot of R6 row 4 blk + dy (the block's
+// 4 rows are 4 consecutive slots, 512 bytes each: SBO 128, the lo plane
+// XPLANE bytes further) and whose B operand is window row dy's taps.
+template <int FMT>
+__device__ __forceinline__ void mma_fwd_xring(uint32_t taddr, uint32_t sX_u32, uint32_t sBf_u32, int blk,
+                                              uint32_t idesc) {
+    using C = Cfg<FMT>;
+#pragma unroll
+    for (int dy = 0; dy < KS; ++dy) {
+        const uint32_t slot = (uint32_t)((4 * blk + dy) % C::XSLOTS);
+        tc::mma<C::OPF>(taddr, tc::make_smem_desc(sX_u32 + slot * C::XROW_BYTES, C::XPLANE, 128),
+                        tc::make_smem_desc(sBf_u32 + dy * C::BF_DY, C::BF_DY / 2, 128), idesc, dy > 0 ? 1u : 0u);
+    }
+}
+
 // MODEL 0: Eq. variant, iterate u.  MODEL 1: the combined model (Eq. newmodel)
 // in w = log u: the prox is prox_w, the planes hold u = e^w, and the
 // gradient is e^w (.) K^T r.
@@ -321,7 +376,8 @@ __global__ void __launch_bounds__(NT, FMT != 2 ? 3 : 2) tc_tile_kernel(const KPa
             // The symmetric extension is applied afterwards, by indexing the
             // staged box at reflected coordinates (all of which lie in the box).
             constexpr int SP = (int)(C::STAGE_PLANE / 4);  // staging plane stride (floats)
-            const bool use_tma = TRIAL && im.tmap != nullptr;
+            // (XRING: plain loads; the ring and R leave no room for the staging box)
+            const bool use_tma = TRIAL && im.tmap != nullptr && !C::XRING;
             const int ys = y0 - 6, xs = ((x0 - 6) >> 2) << 2;  // arithmetic shift: floor
             const float *stg = reinterpret_cast<const float *>(smem + C::OFF_STAGE);
             // the copies' barrier is initialised with the CTA's first tile,
@@ -490,8 +546,15 @@ __global__ void __launch_bounds__(NT, FMT != 2 ? 3 : 2) tc_tile_kernel(const KPa
             // before the im2col of block 0 reads the planes and overwrites the
             // staging area
             __syncthreads();
-            // block 0: im2col and forward MMA
-            im2col<FMT>(sP, sAF, 0, m, part);
+            // block 0: im2col (XRING: the ring's first 10 rows) and forward MMA
+            if constexpr (C::XRING) {
+                for (int e = tid; e < 2 * C::XSLOTS * R3X; e += NT) {
+                    const int pl = e / (C::XSLOTS * R3X), rem = e - pl * (C::XSLOTS * R3X);
+                    xring_entry<FMT>(sP, sAF, rem / R3X, rem % R3X, pl);
+                }
+            } else {
+                im2col<FMT>(sP, sAF, 0, m, part);
+            }
             tc::fence_proxy_async();
             tc::fence_before_sync();
             __syncthreads();
@@ -499,11 +562,15 @@ __global__ void __launch_bounds__(NT, FMT != 2 ? 3 : 2) tc_tile_kernel(const KPa
             const uint32_t taddr = tbase;
             const uint32_t lane_base = (uint32_t)(lg * 32) << 16;
             if (tid == 0) {
-    #pragma unroll
-                for (int ks = 0; ks < C::KFWD / C::KSTEP; ++ks)
-                    tc::mma<C::OPF>(taddr, tc::make_smem_desc(sAF_u32 + ks * 256, 128, SBO_F),
-                                 tc::make_smem_desc(sBf_u32 + (ks % KS_F) * 256, 128, SBO_BF), IDESC_F,
-                                 ks > 0 ? 1u : 0u);
+                if constexpr (C::XRING) {
+                    mma_fwd_xring<FMT>(taddr, sAF_u32, sBf_u32, 0, IDESC_F);
+                } else {
+#pragma unroll
+                    for (int ks = 0; ks < C::KFWD / C::KSTEP; ++ks)
+                        tc::mma<C::OPF>(taddr, tc::make_smem_desc(sAF_u32 + ks * 256, 128, SBO_F),
+                                     tc::make_smem_desc(sBf_u32 + (ks % KS_F) * 256, 128, SBO_BF), IDESC_F,
+                                     ks > 0 ? 1u : 0u);
+                }
                 tc::mma_commit(&bar_f);
             }
             // each tile waits NBLK times on each MMA barrier: both are back at
@@ -606,7 +673,15 @@ __global__ void __launch_bounds__(NT, FMT != 2 ? 3 : 2) tc_tile_kernel(const KPa
             for (int blk = 0; blk < NBLK; ++blk) {
                 // (a) horizontal col2im of the previous block (its MMA_adj completed
                 // before the im2col of this block), overlapping MMA_fwd(blk)
-                if (blk > 0) epi2(blk - 1);
+                if (blk > 0) {
+                    if constexpr (C::XRING) {
+                        // (XRING: no im2col waited for MMA_adj(blk - 1))
+                        if (!tc::mbar_wait(&bar_a, phase_a)) tc_ok = false;
+                        phase_a ^= 1u;
+                        tc::fence_after_sync();
+                    }
+                    epi2(blk - 1);
+                }
                 // (b) epilogue 1 of this block: rho' -> R (hi | lo), energy terms
                 if (!tc::mbar_wait(&bar_f, phase_f)) tc_ok = false;
                 phase_f ^= 1u;
@@ -697,20 +772,32 @@ __global__ void __launch_bounds__(NT, FMT != 2 ? 3 : 2) tc_tile_kernel(const KPa
                 // (c) im2col of the next block into the operand buffer, once
                 // MMA_adj(blk) has read R from it
                 if (blk + 1 < NBLK) {
-                    if (!tc::mbar_wait(&bar_a, phase_a)) tc_ok = false;
-                    phase_a ^= 1u;
-                    tc::fence_after_sync();
-                    im2col<FMT>(sP, sAF, blk + 1, m, part);
+                    if constexpr (C::XRING) {
+                        // the 4 new rows of block blk + 1's windows (R6 rows
+                        // 4 blk + 10 .. + 13), into the slots of the rows only
+                        // block blk read (MMA_fwd(blk) completed before
+                        // epilogue 1); MMA_adj(blk) may still run
+                        xring_entry<FMT>(sP, sAF, 4 * blk + 10 + ((tid >> 5) & 3), tid & 31, tid >> 7);
+                    } else {
+                        if (!tc::mbar_wait(&bar_a, phase_a)) tc_ok = false;
+                        phase_a ^= 1u;
+                        tc::fence_after_sync();
+                        im2col<FMT>(sP, sAF, blk + 1, m, part);
+                    }
                     tc::fence_proxy_async();
                     tc::fence_before_sync();
                     __syncthreads();
                     if (tid == 0) {
                         tc::fence_after_sync();
-    #pragma unroll
-                        for (int ks = 0; ks < C::KFWD / C::KSTEP; ++ks)
-                            tc::mma<C::OPF>(taddr, tc::make_smem_desc(sAF_u32 + ks * 256, 128, SBO_F),
-                                         tc::make_smem_desc(sBf_u32 + (ks % KS_F) * 256, 128, SBO_BF), IDESC_F,
-                                         ks > 0 ? 1u : 0u);
+                        if constexpr (C::XRING) {
+                            mma_fwd_xring<FMT>(taddr, sAF_u32, sBf_u32, blk + 1, IDESC_F);
+                        } else {
+#pragma unroll
+                            for (int ks = 0; ks < C::KFWD / C::KSTEP; ++ks)
+                                tc::mma<C::OPF>(taddr, tc::make_smem_desc(sAF_u32 + ks * 256, 128, SBO_F),
+                                             tc::make_smem_desc(sBf_u32 + (ks % KS_F) * 256, 128, SBO_BF), IDESC_F,
+                                             ks > 0 ? 1u : 0u);
+                        }
                         tc::mma_commit(&bar_f);
                     }
                 }
