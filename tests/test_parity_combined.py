@@ -237,6 +237,35 @@ def test_tc_gradient_parity_combined(fe, orc, bank, shape, prec):
     assert Fg == pytest.approx(F_ref, rel=10 * EF_TOL if prec == "bf16" else 2 * EF_TOL)
 
 
+@pytest.mark.parametrize("shape", [(64, 64), (131, 77), (59, 27)])
+def test_bf16r_gradient_parity_combined(fe, orc, bank, shape):
+    """FE_BF16R on the combined model: grad_w F = e^w (.) K^T r with r rounded
+    once to BF16, so the BF16 form's bound gains e^w 2^-9 sum_i |K_i|^T |r_i|
+    per pixel (round-to-nearest BF16 of each response)."""
+    from rounding import ROUND
+    k, th = bank
+    kq = ROUND["bf16"](k)
+    H, W = shape
+    _, f = _problem(H, W, seed=H + 2 * W)
+    w = np.log(f).astype(np.float32)
+    with _solver(fe, f, k, th, prec="bf16r") as s:
+        g, Fg = s.gradient(0, w)
+    g_ref, F_ref = orc.gradFw(w, kq, th)
+    u = np.exp(w.astype(np.float64))
+    v_ref = g_ref / u
+    eps = 2.0 ** -24
+    A, Rb = np.zeros_like(u), np.zeros_like(u)
+    for i in range(kq.shape[0]):
+        ka = np.abs(kq[i]).astype(np.float64)
+        z = orc.K(u, kq[i])
+        A += th[i] * orc.KT(np.abs(2.0 * (1.0 - z * z) / (1.0 + z * z) ** 2) * orc.K(u, ka), ka)
+        Rb += orc.KT(np.abs(th[i] * 2.0 * z / (1.0 + z * z)), ka)
+    bound = u * (TC_GRAD_TOL["bf16"] * np.max(np.abs(v_ref)) + 4 * eps * A + 2.0 ** -9 * Rb) + 2 * eps * np.abs(g_ref)
+    err = np.abs(g.astype(np.float64) - g_ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    assert Fg == pytest.approx(F_ref, rel=10 * EF_TOL)
+
+
 @pytest.mark.parametrize("prec", ["bf16", "tf32"])
 def test_tc_single_step_parity_combined(fe, orc, bank, prec):
     from rounding import ROUND

@@ -20,7 +20,8 @@ KEYS = ("n", "trials", "backtracks", "L", "alpha", "F", "G", "H", "H_prev", "rel
 SHAPES = [(64, 64), (131, 77), (9, 300), (200, 150), (8, 8), (517, 33), (256, 260)]
 
 FORMS = [("fp32", 64, "variant"), ("fp32", 32, "variant"), ("fp32", 64, "combined"),
-         ("bf16", 0, "variant"), ("tf32", 0, "variant"), ("bf16r", 0, "variant"), ("bf16", 0, "combined")]
+         ("bf16", 0, "variant"), ("tf32", 0, "variant"), ("bf16r", 0, "variant"), ("bf16", 0, "combined"),
+         ("bf16r", 0, "combined")]
 
 
 @pytest.fixture(scope="module")
