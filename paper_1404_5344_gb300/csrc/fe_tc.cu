@@ -38,7 +38,7 @@ float tc_round(int fmt, float x) {
 void tc_build_weights(int fmt, const float *filters, int nf, std::vector<unsigned char> &fwd,
                       std::vector<unsigned char> &adj) {
     const int eb = fmt != 2 ? 2 : 4, kpass = fmt != 2 ? 64 : 56;
-    fwd.assign(fmt == 1 ? Cfg<1>::BF_BYTES : (fmt == 3 ? Cfg<3>::BF_BYTES : Cfg<2>::BF_BYTES), 0);
+    fwd.assign((size_t)NF * kpass * eb, 0);
     adj.assign((size_t)NTAP * NF * eb, 0);
     auto put = [&](std::vector<unsigned char> &buf, int r, int k, int K, float v) {
         const uint32_t off = tc::kmajor_offset(r, k, K, eb);
@@ -55,20 +55,7 @@ void tc_build_weights(int fmt, const float *filters, int nf, std::vector<unsigne
             // forward: K index 8a + b reads u(p + (a, b)) of the window, i.e.
             // correlation with the flipped filter (index 8a + 7 stays 0)
             const int a = t / KS, b = t % KS;
-            if (fmt == 3) {
-                // window row a's B (N = 48 x K = 16: the 8 taps of the row for
-                // the hi plane, then again for the lo plane), K-major with
-                // the two K chunks BF_DY / 2 bytes apart
-                const uint32_t bits = f2u(tc_round(fmt, filters[(size_t)i * KT + (KT - 1 - t)]));
-                const uint16_t h = (uint16_t)(bits >> 16);
-                for (int kc = 0; kc < 2; ++kc) {
-                    const size_t off = (size_t)a * Cfg<3>::BF_DY + (size_t)kc * (Cfg<3>::BF_DY / 2) +
-                                       (size_t)(i / 8) * 128 + (size_t)(i % 8) * 16 + (size_t)b * 2;
-                    std::memcpy(&fwd[off], &h, 2);
-                }
-            } else {
-                put(fwd, i, 8 * a + b, kpass, filters[(size_t)i * KT + (KT - 1 - t)]);
-            }
+            put(fwd, i, 8 * a + b, kpass, filters[(size_t)i * KT + (KT - 1 - t)]);
             // adjoint: S[q, t] = sum_i k_i[t] r_i(q)
             put(adj, t, i, NF, filters[(size_t)i * KT + t]);
         }

@@ -82,17 +82,17 @@ struct Cfg {
     static constexpr int OPF = BF ? 1 : 2;                 // operand format of the instruction descriptor
     static constexpr bool RLO = FMT != 3;                  // r carried as hi + lo
     static constexpr int KADJ = RLO ? 2 * NF : NF;         // adjoint K: r hi | r lo, or r
-    // XRING (FMT 3): the forward A operand is read in place from a ring of
-    // u^{n+1} rows whose entry (row, column) holds that column's 8 window
-    // values (one 16-byte core-matrix row; hi plane, then lo plane): window
-    // row dy of a block is the ring at a descriptor start dy rows further, so
-    // no per-block im2col.  XSLOTS rows plus XMIRROR copies of the first ones,
-    // so that the 4 rows of a block's window row are always contiguous.
-    static constexpr bool XRING = FMT == 3;
-    static constexpr int XSLOTS = 10, XMIRROR = 3;
+    // XRING (BF16 forms): the forward A operand is read in place from a ring
+    // of u^{n+1} rows whose entry (row, column) holds that column's 8 window
+    // values (one 16-byte core-matrix row; a ring per plane, hi and lo):
+    // window rows dy and dy + 1 of a block are the ring at a descriptor start
+    // dy rows further, the second K chunk one ring row (LBO) later, so there
+    // is no per-block im2col.  XSLOTS rows plus XMIRROR copies of the first
+    // ones, so that the 5 rows an MMA spans are always contiguous.
+    static constexpr bool XRING = FMT != 2;
+    static constexpr int XSLOTS = 10, XMIRROR = 4;
     static constexpr int XROW_BYTES = R3X * 16;                            // 32 entries of 16 bytes
     static constexpr int XPLANE = (XSLOTS + XMIRROR) * XROW_BYTES;         // hi plane, then lo plane
-    static constexpr int BF_DY = 2 * NF * 16;                              // forward B of one window row
     static constexpr int EB = BF ? 2 : 4;                  // operand bytes
     static constexpr int KSTEP = BF ? 16 : 8;              // K per MMA
     static constexpr int KPASS = BF ? 64 : 56;             // 7 rows x 8 taps, padded to KSTEP
@@ -105,9 +105,7 @@ struct Cfg {
     static_assert(PL_WORDS * 4 >= R6Y * PP * EB, "plane holds the u region");
     static constexpr size_t AF_BYTES = XRING ? (size_t)2 * XPLANE : (size_t)128 * KFWD * EB;  // XRING: the ring
     static constexpr size_t R_BYTES = (size_t)128 * KADJ * EB;
-    // forward B: one pass (hi and lo MMAs share it); XRING: per window row
-    // dy, N = 48 x K = 16 (the row's 8 taps twice: for the hi and lo planes)
-    static constexpr size_t BF_BYTES = XRING ? (size_t)KS * BF_DY : (size_t)NF * KPASS * EB;
+    static constexpr size_t BF_BYTES = (size_t)NF * KPASS * EB;   // one pass: hi and lo MMAs share it
     static constexpr size_t BA_BYTES = (size_t)NTAP * NF * EB;    // likewise for r hi and r lo
     // one buffer holds the A operand of the forward GEMM (im2col of block b + 1)
     // and the R operand of the adjoint GEMM (block b) in turn: R is written
@@ -116,27 +114,30 @@ struct Cfg {
     static constexpr size_t OFF_R = 0;
     static constexpr size_t OFF_AF = XRING ? R_BYTES : 0;
     static constexpr size_t OFF_H = XRING ? OFF_AF + AF_BYTES : OFF_AF + (AF_BYTES > R_BYTES ? AF_BYTES : R_BYTES);
-    // gradient rows: BF16 keeps every row of the region (three CTAs per SM
-    // fit either way; the final pass then folds and writes with all warps),
-    // TF32 only the rows of the vertical fold (image rows -3..2, H-3..H+2),
-    // writing the others as they are formed, so that two CTAs fit per SM
-    static constexpr bool FULL_G = BF;
+    // gradient rows: FE_BF16R keeps every row of the region (three CTAs per
+    // SM fit either way; the final pass then folds and writes with all
+    // warps), FE_BF16 and TF32 only the rows of the vertical fold (image rows
+    // -3..2, H-3..H+2), writing the others as they are formed, so that three
+    // (FE_BF16: r hi | lo beside the ring) or two (TF32) CTAs fit per SM
+    static constexpr bool FULL_G = FMT == 3;
     static constexpr int GROWS = FULL_G ? R3Y : NFOLD;
     static constexpr size_t OFF_G = OFF_H + (size_t)HRING * 7 * 32 * 4;
-    static constexpr size_t OFF_BF = (OFF_G + (size_t)GROWS * R3X * 4 + 127) / 128 * 128;
+    // TMA staging of the trial's four input planes (u^n, u^{n-1}, g^n, f^2 on
+    // the tile + 6 box): overlays the operand buffers, the H ring and the
+    // gradient rows, none of which is live before the first im2col (or ring
+    // rows); the B operands start after whichever ends last
+    static constexpr size_t STAGE_PLANE = ((size_t)tc_box_y * tc_box_x * 4 + 127) / 128 * 128;
+    static constexpr size_t OFF_STAGE = 0;
+    static constexpr size_t END_G = (OFF_G + (size_t)GROWS * R3X * 4 + 127) / 128 * 128;
+    static constexpr size_t OFF_BF = END_G > OFF_STAGE + 4 * STAGE_PLANE ? END_G : OFF_STAGE + 4 * STAGE_PLANE;
     static constexpr size_t OFF_BA = OFF_BF + BF_BYTES;
     static constexpr size_t OFF_U = OFF_BA + BA_BYTES;       // NPL planes of u^{n+1}
     static constexpr size_t OFF_TH = OFF_U + (size_t)NPL * PL_WORDS * 4;
     static constexpr size_t OFF_RED = OFF_TH + (size_t)2 * NF * 4;
     static constexpr size_t BYTES = OFF_RED + (size_t)(NT / 32) * NRED * 8;
-    // TMA staging of the trial's four input planes (u^n, u^{n-1}, g^n, f^2 on
-    // the tile + 6 box): overlays the operand buffer, the H ring and the
-    // gradient rows, none of which is live before the first im2col
-    static constexpr size_t STAGE_PLANE = ((size_t)tc_box_y * tc_box_x * 4 + 127) / 128 * 128;
-    static constexpr size_t OFF_STAGE = 0;
-    static_assert(XRING || OFF_STAGE + 4 * STAGE_PLANE <= OFF_BF, "the staging planes end before the B operands");
-    static_assert(!XRING || (OFF_AF % 16 == 0 && XPLANE % 16 == 0 && 4 + KS - 1 <= XSLOTS && XMIRROR == 3),
-                  "ring: 16-byte rows; the 10 rows of a block's windows fit; 4 consecutive rows contiguous");
+    static_assert(OFF_STAGE + 4 * STAGE_PLANE <= OFF_BF, "the staging planes end before the B operands");
+    static_assert(!XRING || (OFF_AF % 16 == 0 && XPLANE % 16 == 0 && 4 + KS - 1 <= XSLOTS && XMIRROR == 4),
+                  "ring: 16-byte rows; the 10 rows of a block's windows fit; 5 consecutive rows contiguous");
     static_assert(OFF_H % 16 == 0 && OFF_BF % 128 == 0 && OFF_BA % 128 == 0 && OFF_U % 128 == 0,
                   "operand alignment");
     static_assert(OFF_U % 16 == 0 && OFF_TH % 16 == 0 && OFF_RED % 8 == 0 && OFF_G % 16 == 0, "alignment");
@@ -289,21 +290,26 @@ __device__ __forceinline__ void xring_entry(const uint32_t *__restrict__ sP, uns
     if (slot < C::XMIRROR) *reinterpret_cast<uint4 *>(d + C::XSLOTS * C::XROW_BYTES) = v;
 }
 
-// Forward GEMM of block blk from the ring (XRING; one thread): window row dy
-// is one MMA of K = 16 (the 8 taps on the hi plane, then on the lo plane)
-// whose A operand starts at the ring slot of R6 row 4 blk + dy (the block's
-// 4 rows are 4 consecutive slots, 512 bytes each: SBO 128, the lo plane
-// XPLANE bytes further) and whose B operand is window row dy's taps.
+// Forward GEMM of block blk from the ring (XRING; one thread): for each
+// plane (hi, lo) and pair of window rows (2j, 2j + 1), one MMA of K = 16
+// whose A operand starts at the ring slot of R6 row 4 blk + 2j (the block's
+// 4 rows are 4 consecutive slots, 512 bytes each: SBO 128) with its second
+// K chunk, window row 2j + 1, one slot further (LBO 512), and whose B
+// operand is the same pass of the bank as the im2col form's (window rows 2j,
+// 2j + 1; row 7 is the zero-weight padding row, whose A chunk reads a ring
+// row that holds finite values).  8 MMAs, as the im2col form.
 template <int FMT>
 __device__ __forceinline__ void mma_fwd_xring(uint32_t taddr, uint32_t sX_u32, uint32_t sBf_u32, int blk,
-                                              uint32_t idesc) {
+                                              uint32_t idesc, uint32_t sbo_bf) {
     using C = Cfg<FMT>;
 #pragma unroll
-    for (int dy = 0; dy < KS; ++dy) {
-        const uint32_t slot = (uint32_t)((4 * blk + dy) % C::XSLOTS);
-        tc::mma<C::OPF>(taddr, tc::make_smem_desc(sX_u32 + slot * C::XROW_BYTES, C::XPLANE, 128),
-                        tc::make_smem_desc(sBf_u32 + dy * C::BF_DY, C::BF_DY / 2, 128), idesc, dy > 0 ? 1u : 0u);
-    }
+    for (int pl = 0; pl < 2; ++pl)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t slot = (uint32_t)((4 * blk + 2 * j) % C::XSLOTS);
+            tc::mma<C::OPF>(taddr, tc::make_smem_desc(sX_u32 + pl * C::XPLANE + slot * C::XROW_BYTES, C::XROW_BYTES, 128),
+                            tc::make_smem_desc(sBf_u32 + j * 256, 128, sbo_bf), idesc, (pl | j) ? 1u : 0u);
+        }
 }
 
 // MODEL 0: Eq. variant, iterate u.  MODEL 1: the combined model (Eq. newmodel)
@@ -376,8 +382,7 @@ __global__ void __launch_bounds__(NT, FMT != 2 ? 3 : 2) tc_tile_kernel(const KPa
             // The symmetric extension is applied afterwards, by indexing the
             // staged box at reflected coordinates (all of which lie in the box).
             constexpr int SP = (int)(C::STAGE_PLANE / 4);  // staging plane stride (floats)
-            // (XRING: plain loads; the ring and R leave no room for the staging box)
-            const bool use_tma = TRIAL && im.tmap != nullptr && !C::XRING;
+            const bool use_tma = TRIAL && im.tmap != nullptr;
             const int ys = y0 - 6, xs = ((x0 - 6) >> 2) << 2;  // arithmetic shift: floor
             const float *stg = reinterpret_cast<const float *>(smem + C::OFF_STAGE);
             // the copies' barrier is initialised with the CTA's first tile,
@@ -563,7 +568,7 @@ __global__ void __launch_bounds__(NT, FMT != 2 ? 3 : 2) tc_tile_kernel(const KPa
             const uint32_t lane_base = (uint32_t)(lg * 32) << 16;
             if (tid == 0) {
                 if constexpr (C::XRING) {
-                    mma_fwd_xring<FMT>(taddr, sAF_u32, sBf_u32, 0, IDESC_F);
+                    mma_fwd_xring<FMT>(taddr, sAF_u32, sBf_u32, 0, IDESC_F, SBO_BF);
                 } else {
 #pragma unroll
                     for (int ks = 0; ks < C::KFWD / C::KSTEP; ++ks)
@@ -790,7 +795,7 @@ __global__ void __launch_bounds__(NT, FMT != 2 ? 3 : 2) tc_tile_kernel(const KPa
                     if (tid == 0) {
                         tc::fence_after_sync();
                         if constexpr (C::XRING) {
-                            mma_fwd_xring<FMT>(taddr, sAF_u32, sBf_u32, blk + 1, IDESC_F);
+                            mma_fwd_xring<FMT>(taddr, sAF_u32, sBf_u32, blk + 1, IDESC_F, SBO_BF);
                         } else {
 #pragma unroll
                             for (int ks = 0; ks < C::KFWD / C::KSTEP; ++ks)
