@@ -308,79 +308,178 @@ __global__ void __launch_bounds__(NT) wgrad_kernel(const float *__restrict__ x, 
     }
 }
 
-// The same partial sums for CIN = COUT = 32, register-blocked: 288 threads,
-// each accumulating 2 blocks of 4 output x 4 input channels of one tap over
-// the tile's 256 pixels (8 shared loads per 16 FMAs instead of 2 per FMA);
-// the input planes are padded to 325 floats so that the 8 input-channel
-// blocks a warp reads fall on different banks.  Output layout as above.
-constexpr int WG32_NT = 288, WG32_PL = (TS + 2) * (TS + 2) + 1;
+// ---- tensor-core weight gradient of the 32 -> 32 layers -----------------------
+// dW[o][c][tap] = sum_p g[o][p] x[c][p + off(tap)] as GEMMs with the pixels as
+// K.  Per 16 x 8 tile (K = 128 pixels: 8 MMA steps of two pixel rows) and tap
+// column dx, D[(dy, c), o] (M = 128 = dy 0..3 x 32 input channels, the dy = 3
+// rows unused; N = 32 output channels) accumulates in tensor memory over
+// every tile the CTA takes (persistent CTAs; three tap columns = 96 TMEM
+// columns), and the CTA writes its sums once.  A operand: a table of 16-byte
+// entries X[dx][iy][c] = x[c][iy][dx .. dx + 7] (8 pixels of one halo row), so
+// that row (dy, c) of step s is entry X[dx][2s + dy][c] (rows 16 bytes apart:
+// SBO 128) and its second pixel row one halo row further (LBO 512).  B
+// operand: G[py][o] = g[o][py][0 .. 7].  Both are carried as BF16 hi + lo
+// (products hi*hi + lo*hi + hi*lo: about 16 bits), summed in FP32.
+constexpr int WG_IY = TC_OY + 3;              // 19 halo rows: the last is read only by the unused dy = 3 rows
+constexpr int WG_ROW = CW * 16;               // one halo row of the table: 32 channels x 16 bytes
+constexpr int WG_DX = WG_IY * WG_ROW;         // one tap column of the table
+constexpr int WG_XPL = 3 * WG_DX;             // the hi (or lo) table
+constexpr int WG_GPL = TC_OY * WG_ROW;        // the hi (or lo) G: 16 pixel rows x 32 channels x 16 bytes
+constexpr int WG_XF_LD = TC_NPX + 1;          // FP32 staging of the halo tile: channel stride (odd: banks)
+constexpr int WG_SMEM = 2 * WG_XPL + 2 * WG_GPL + (CW * WG_XF_LD + 4 * CW) * 4;
+static_assert(WG_XPL % 128 == 0 && WG_GPL % 128 == 0, "operand alignment");
+
+__device__ __forceinline__ void split8(const float *v, uint4 &hi, uint4 &lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        h[j] = bf16x2_rn(v[2 * j], v[2 * j + 1]);
+        l[j] = bf16x2_rn(v[2 * j] - __uint_as_float(h[j] << 16), v[2 * j + 1] - __uint_as_float(h[j] & 0xffff0000u));
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// part[blockIdx.x][COUT*CIN*9 + COUT] (as wgrad_kernel's), the grid = the
+// persistent CTAs (each takes at least one tile).  128 threads.  A
+// completion wait that runs out sets *err and the CTA stops.
 template <bool RELU>
-__global__ void __launch_bounds__(WG32_NT) wgrad32_kernel(const float *__restrict__ x, const float *__restrict__ dy,
-                                                          const float *__restrict__ yout, float *__restrict__ part,
-                                                          int H, int W) {
-    extern __shared__ __align__(16) float wsm[];
-    float *sg = wsm;                    // [32][256]
-    float *sx = wsm + CW * TS * TS;     // [32][WG32_PL]
-    const int b = blockIdx.z, tx0 = blockIdx.x * TS, ty0 = blockIdx.y * TS;
-    const int tid = threadIdx.x;
+__global__ void __launch_bounds__(128) wgrad32_tc_kernel(const float *__restrict__ x, const float *__restrict__ dy,
+                                                         const float *__restrict__ yout, float *__restrict__ part,
+                                                         int B, int H, int W, int *err) {
+    extern __shared__ __align__(1024) unsigned char gsm[];
+    unsigned char *sX = gsm;                                       // [hi | lo][dx][iy][c][8 pixels]
+    unsigned char *sG = gsm + 2 * WG_XPL;                          // [hi | lo][py][o][8 pixels]
+    float *sXf = reinterpret_cast<float *>(gsm + 2 * WG_XPL + 2 * WG_GPL);  // [c][iy][ix]
+    float *sBias = sXf + CW * WG_XF_LD;                            // [warp][o]
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tbase;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const size_t plane = (size_t)H * W;
-    for (int j = tid; j < CW * (TS + 2) * (TS + 2); j += WG32_NT) {
-        const int c = j / ((TS + 2) * (TS + 2)), r = j % ((TS + 2) * (TS + 2));
-        const int yy = ty0 - 1 + r / (TS + 2), xx = tx0 - 1 + r % (TS + 2);
-        sx[c * WG32_PL + r] =
-            (yy >= 0 && yy < H && xx >= 0 && xx < W) ? x[((size_t)b * CW + c) * plane + (size_t)yy * W + xx] : 0.f;
+    const int tiles_x = (W + TC_OX - 1) / TC_OX, tiles_img = tiles_x * ((H + TC_OY - 1) / TC_OY);
+    const int ntiles = tiles_img * B;
+    if (tid == 0) tc::mbar_init(&bar, 1);
+    if (warp == 0) tc::tmem_alloc(&tbase, 128);
+    // the table's last halo row (read only by the unused dy = 3 rows) holds zeros
+    for (int j = tid; j < 2 * 3 * CW; j += 128) {
+        const int pl = j / (3 * CW), dx = (j / CW) % 3, c = j % CW;
+        *reinterpret_cast<uint4 *>(sX + pl * WG_XPL + dx * WG_DX + (WG_IY - 1) * WG_ROW + c * 16) =
+            make_uint4(0u, 0u, 0u, 0u);
     }
-    for (int j = tid; j < CW * TS * TS; j += WG32_NT) {
-        const int o = j / (TS * TS), r = j % (TS * TS);
-        const int yy = ty0 + r / TS, xx = tx0 + r % TS;
-        float g = 0.f;
-        if (yy < H && xx < W) {
-            const size_t idx = ((size_t)b * CW + o) * plane + (size_t)yy * W + xx;
-            g = dy[idx];
-            if (RELU && !(yout[idx] > 0.f)) g = 0.f;
-        }
-        sg[j] = g;
-    }
+    tc::fence_before_sync();
     __syncthreads();
-    constexpr int nw = CW * CW * 9;
-    float *out = part + (size_t)((blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (nw + CW);
-#pragma unroll 1
-    for (int task = tid; task < 9 * 64; task += WG32_NT) {
-        const int t = task >> 6, ob = (task >> 3) & 7, cb = task & 7;
-        const int dy0 = t / 3, dx0 = t % 3;
-        float acc[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-        const float *gp = sg + (ob * 4) * (TS * TS);
-        const float *xp = sx + (cb * 4) * WG32_PL + dy0 * (TS + 2) + dx0;
-#pragma unroll 1
-        for (int ry = 0; ry < TS; ++ry) {
-#pragma unroll 4
-            for (int rx = 0; rx < TS; ++rx) {
-                const int r = ry * TS + rx, q = ry * (TS + 2) + rx;
-                float gv[4], xv[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) gv[i] = gp[i * (TS * TS) + r];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) xv[j] = xp[j * WG32_PL + q];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(gv[i], xv[j], acc[i][j]);
-            }
+    tc::fence_after_sync();
+    const uint32_t taddr = tbase;
+    float bsum = 0.f;  // this thread's share of dB[o], o = lane
+    uint32_t phase = 0;
+    bool first = true, ok = true;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int b = tile / tiles_img, tr = tile - b * tiles_img;
+        const int ty0 = (tr / tiles_x) * TC_OY, tx0 = (tr % tiles_x) * TC_OX;
+        // FP32 halo tile of x (zero padding)
+        for (int j = tid; j < CW * TC_NPX; j += 128) {
+            const int c = j / TC_NPX, px = j - c * TC_NPX, iy = px / TC_IX, ix = px - iy * TC_IX;
+            const int yy = ty0 - 1 + iy, xx = tx0 - 1 + ix;
+            sXf[c * WG_XF_LD + px] =
+                (yy >= 0 && yy < H && xx >= 0 && xx < W) ? __ldg(x + ((size_t)b * CW + c) * plane + (size_t)yy * W + xx)
+                                                         : 0.f;
         }
+        // G: entry (py, o) = (warp + 4 k, lane), 8 pixels, hi and lo; g = dY,
+        // masked by Y > 0 after a ReLU
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int k = 0; k < TC_OY / 4; ++k) {
+            const int py = warp + 4 * k, yy = ty0 + py;
+            float g[8];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) out[(ob * 4 + i) * CW * 9 + (cb * 4 + j) * 9 + t] = acc[i][j];
+            for (int j = 0; j < 8; ++j) {
+                const int xx = tx0 + j;
+                float v = 0.f;
+                if (yy < H && xx < W) {
+                    const size_t idx = ((size_t)b * CW + lane) * plane + (size_t)yy * W + xx;
+                    v = __ldg(dy + idx);
+                    if (RELU && !(__ldg(yout + idx) > 0.f)) v = 0.f;
+                }
+                g[j] = v;
+                bsum += v;
+            }
+            uint4 hi, lo;
+            split8(g, hi, lo);
+            unsigned char *d = sG + py * WG_ROW + lane * 16;
+            *reinterpret_cast<uint4 *>(d) = hi;
+            *reinterpret_cast<uint4 *>(d + WG_GPL) = lo;
+        }
+        __syncthreads();  // the staged halo tile is complete
+        // table entries (dx, iy, c), iy = 0..17, hi and lo
+        for (int j = tid; j < 3 * TC_IY * CW; j += 128) {
+            const int c = j % CW, r = j / CW, dx = r % 3, iy = r / 3;
+            const float *src = sXf + c * WG_XF_LD + iy * TC_IX + dx;
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = src[q];
+            uint4 hi, lo;
+            split8(v, hi, lo);
+            unsigned char *d = sX + dx * WG_DX + iy * WG_ROW + c * 16;
+            *reinterpret_cast<uint4 *>(d) = hi;
+            *reinterpret_cast<uint4 *>(d + WG_XPL) = lo;
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {
+            constexpr uint32_t idesc = tc::make_idesc(1, 128, CW);
+            const uint32_t a0 = tc::smem_u32(sX), g0 = tc::smem_u32(sG);
+#pragma unroll 1
+            for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                for (int st = 0; st < TC_OY / 2; ++st)
+#pragma unroll
+                    for (int ps = 0; ps < 3; ++ps) {  // x hi * g hi, x lo * g hi, x hi * g lo
+                        const int xp = ps == 1, gp = ps == 2;
+                        const uint64_t ad = tc::make_smem_desc(a0 + xp * WG_XPL + dx * WG_DX + 2 * st * WG_ROW, WG_ROW, 128);
+                        const uint64_t bd = tc::make_smem_desc(g0 + gp * WG_GPL + 2 * st * WG_ROW, WG_ROW, 128);
+                        tc::mma<1>(taddr + (uint32_t)(dx * CW), ad, bd, idesc, (first && st == 0 && ps == 0) ? 0u : 1u);
+                    }
+            tc::mma_commit(&bar);
+        }
+        first = false;
+        ok = tc::mbar_wait(&bar, phase);
+        if (!ok) {
+            if (tid == 0) atomicExch(err, 1);
+            ok = tc::mbar_wait(&bar, phase);  // a second bounded chance for MMAs in flight
+        }
+        phase ^= 1u;
+        // the next tile rewrites the operands
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (!__syncthreads_and(ok)) break;
     }
-    if (tid < CW) {
-        float sb = 0.f;
-        for (int r = 0; r < TS * TS; ++r) sb += sg[tid * (TS * TS) + r];
-        out[nw + tid] = sb;
+    // the CTA's partial sums: lane (dy, c) = tid of warps 0..2, columns dx*32 + o
+    const size_t nw = (size_t)CW * CW * 9;
+    float *out = part + (size_t)blockIdx.x * (nw + CW);
+    if (!first && ok) {
+#pragma unroll 1
+        for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+            for (int j = 0; j < CW / 8; ++j) {
+                float t8[8];
+                tc::tmem_ld8(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(dx * CW + 8 * j), t8);
+                tc::tmem_ld_wait();
+                if (warp < 3) {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) out[(size_t)(8 * j + k) * CW * 9 + lane * 9 + warp * 3 + dx] = t8[k];
+                }
+            }
+    } else if (first) {
+        for (size_t e = tid; e < nw; e += 128) out[e] = 0.f;
     }
+    sBias[warp * CW + lane] = bsum;
+    __syncthreads();
+    if (tid < CW) out[nw + tid] = (sBias[tid] + sBias[CW + tid]) + (sBias[2 * CW + tid] + sBias[3 * CW + tid]);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, 128);
 }
 
 // Fixed-order reduction of per-block partials: out[e] = sum_k part[k][e].
@@ -546,7 +645,18 @@ constexpr size_t conv_smem() { return sizeof(float) * ((size_t)CIN * 9 * COUT + 
 template <int CIN, int COUT>
 constexpr size_t wgrad_smem() { return sizeof(float) * ((size_t)COUT * TS * TS + (size_t)CIN * (TS + 2) * (TS + 2)); }
 
-constexpr size_t wgrad32_smem() { return sizeof(float) * ((size_t)CW * TS * TS + (size_t)CW * WG32_PL); }
+// CTAs of the tensor-core weight gradient: two per SM (98 KB of shared
+// memory each), at most one per 16 x 8 tile
+int wgrad32_ctas(const fe_cnn *n, int B, int H, int W) {
+    const long long tiles = (long long)((W + TC_OX - 1) / TC_OX) * ((H + TC_OY - 1) / TC_OY) * B;
+    return (int)std::max<long long>(1, std::min<long long>(tiles, 2LL * n->sms));
+}
+
+// blocks of partial weight-gradient sums a loss_grad needs room for
+size_t grad_parts(const fe_cnn *n, int B, int H, int W) {
+    const size_t nb16 = (size_t)((W + TS - 1) / TS) * ((H + TS - 1) / TS) * B;
+    return std::max(nb16, (size_t)wgrad32_ctas(n, B, H, W));
+}
 
 template <int CIN, int COUT, bool RELU>
 void conv(const fe_cnn *n, const float *x, const float *mask, const float *w, const float *bias, float *y, int B, int H,
@@ -568,7 +678,7 @@ cudaError_t cnn_prepare() {
     FE_SMEM((wgrad_kernel<CW, CW, true>), (wgrad_smem<CW, CW>()));
     FE_SMEM((wgrad_kernel<1, CW, true>), (wgrad_smem<1, CW>()));
     FE_SMEM((conv32_tc_kernel<true>), TC_SMEM);
-    FE_SMEM((wgrad32_kernel<true>), wgrad32_smem());
+    FE_SMEM((wgrad32_tc_kernel<true>), WG_SMEM);
     FE_SMEM((conv32_tc_kernel<false>), TC_SMEM);
 #undef FE_SMEM
     return e;
@@ -595,11 +705,14 @@ fe_status forward(fe_cnn *n, const float *f_dev, int B, int H, int W) {
 template <int CIN, int COUT, bool RELU>
 fe_status wgrad(fe_cnn *n, const float *x, const float *dy, const float *y, int B, int H, int W, int layer) {
     const dim3 grid((W + TS - 1) / TS, (H + TS - 1) / TS, B);
-    const int nb = grid.x * grid.y * grid.z, ne = COUT * CIN * 9 + COUT;
-    if constexpr (CIN == CW && COUT == CW)
-        wgrad32_kernel<RELU><<<grid, WG32_NT, wgrad32_smem(), n->s>>>(x, dy, y, n->part, H, W);
-    else
+    int nb = grid.x * grid.y * grid.z;
+    const int ne = COUT * CIN * 9 + COUT;
+    if constexpr (CIN == CW && COUT == CW) {
+        nb = wgrad32_ctas(n, B, H, W);
+        wgrad32_tc_kernel<RELU><<<nb, 128, WG_SMEM, n->s>>>(x, dy, y, n->part, B, H, W, n->tc_err);
+    } else {
         wgrad_kernel<CIN, COUT, RELU><<<grid, NT, wgrad_smem<CIN, COUT>(), n->s>>>(x, dy, y, n->part, H, W);
+    }
     // weights then bias of this layer are contiguous in the parameter vector
     reduce_parts_kernel<<<(ne + 255) / 256, 256, 0, n->s>>>(n->part, nb, ne, n->g + n->woff[layer]);
     CNN_CUDA(n, cudaGetLastError());
@@ -609,8 +722,7 @@ fe_status wgrad(fe_cnn *n, const float *x, const float *dy, const float *y, int 
 // loss and gradients of all parameters into n->g (device); *loss host
 fe_status loss_grad(fe_cnn *n, const float *f_dev, const float *ut_dev, int B, int H, int W, double *loss) {
     const size_t pix = (size_t)B * H * W;
-    const int nb = (W + TS - 1) / TS * ((H + TS - 1) / TS) * B;
-    fe_status st = ensure_capacity(n, pix, (size_t)nb * (CW * CW * 9 + CW));
+    fe_status st = ensure_capacity(n, pix, grad_parts(n, B, H, W) * (CW * CW * 9 + CW));
     if (st != FE_OK) return st;
     if ((st = forward(n, f_dev, B, H, W)) != FE_OK) return st;
     const int lb = 256;
@@ -796,8 +908,7 @@ fe_status fe_cnn_loss_grad(fe_cnn *n, const float *f, const float *u_target, int
                            float *grad) {
     if (!n || !f || !u_target || B < 1 || H < 1 || W < 1) return FE_EINVAL;
     const size_t pix = (size_t)B * H * W;
-    const int nb = (W + TS - 1) / TS * ((H + TS - 1) / TS) * B;
-    fe_status st = ensure_capacity(n, pix, (size_t)nb * (CW * CW * 9 + CW));
+    fe_status st = ensure_capacity(n, pix, grad_parts(n, B, H, W) * (CW * CW * 9 + CW));
     if (st != FE_OK) return st;
     const float *fd = stage(n, f, pix, 0, &st);
     if (!fd) return st;
