@@ -12,7 +12,7 @@
 //
 // Kernels: conv3x3 forward (bias + ReLU fused; with an optional ReLU mask on
 // the input it also serves as the data gradient, given transposed and
-// flipped weights), weight/bias gradient with per-block partial sums and a
+// flipped weights), weight/bias gradient with per-CTA partial sums and a
 // fixed-order reduction (deterministic), loss + output gradient, Adam.
 //
 // The 32 -> 32 convolutions (three in the forward pass, three data
@@ -27,8 +27,10 @@
 // dx) is the same tile read from a descriptor start shifted by (dy x 10 +
 // dx) pixels, its 8-pixel core-matrix groups (one output row each) 160
 // bytes apart and its two channel chunks of one MMA 2880 bytes apart.  The
-// 1 -> 32 and 32 -> 1 layers (K = 9 or N = 1) stay on the CUDA cores, as
-// do the weight gradients.
+// 1 -> 32 and 32 -> 1 layers (K = 9 or N = 1) stay on the CUDA cores.  The
+// weight gradients of the 32 -> 32 layers run on the tensor cores as well
+// (wgrad32_tc_kernel: the pixels as K); those of the other two layers on the
+// CUDA cores.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -261,51 +263,119 @@ __global__ void __launch_bounds__(128) conv32_tc_kernel(const float *__restrict_
     if (warp == 0) tc::tmem_dealloc(taddr, 32);
 }
 
-// Per-block partial sums of the weight and bias gradients of one layer:
+// Per-CTA partial sums of the weight and bias gradients of one layer (the
+// 1 -> 32 and 32 -> 1 layers):
 //   dW[o][c][tap] += sum_p g[b][o][p] x[b][c][p + off(tap)],  dB[o] += sum_p g[b][o][p]
-// with g = dY * (Y > 0) for a ReLU layer (Y = the layer's output) or dY.
-// part[block][COUT*CIN*9 + COUT].
+// with g = dY * (Y > 0) for a ReLU layer (Y = the layer's output) or dY.  The
+// CTAs are persistent over the 16 x 16 tiles (blockIdx.x, + gridDim.x, ...);
+// a thread owns the parameters tid and tid + NT, sums a tile's 256 pixels in
+// FP32 and the tiles in FP64.  part[blockIdx.x][COUT*CIN*9 + COUT].
 template <int CIN, int COUT, bool RELU>
-__global__ void __launch_bounds__(NT) wgrad_kernel(const float *__restrict__ x, const float *__restrict__ dy,
-                                                   const float *__restrict__ yout, float *__restrict__ part, int H,
-                                                   int W) {
+__global__ void __launch_bounds__(NT, CIN == 1 ? 1 : 2) wgrad_kernel(const float *__restrict__ x, const float *__restrict__ dy,
+                                                   const float *__restrict__ yout, float *__restrict__ part, int B,
+                                                   int H, int W) {
+    constexpr int NW = COUT * CIN * 9, NE = NW + COUT;
+    static_assert(NE <= 2 * NT, "two parameters per thread");
     extern __shared__ __align__(16) float wsm[];
-    float(*sg)[TS * TS] = reinterpret_cast<float(*)[TS * TS]>(wsm);  // [COUT][TS*TS]
-    float(*sx)[TS + 2][TS + 2] = reinterpret_cast<float(*)[TS + 2][TS + 2]>(wsm + COUT * TS * TS);
-    const int b = blockIdx.z, tx0 = blockIdx.x * TS, ty0 = blockIdx.y * TS;
+    // [COUT][TS*TS + 1]: the odd channel stride puts the channels a warp reads at once in distinct banks
+    float(*sg)[TS * TS + 1] = reinterpret_cast<float(*)[TS * TS + 1]>(wsm);
+    float(*sx)[TS + 2][TS + 2] = reinterpret_cast<float(*)[TS + 2][TS + 2]>(wsm + COUT * (TS * TS + 1));
     const int tid = threadIdx.x;
     const size_t plane = (size_t)H * W;
-    for (int j = tid; j < CIN * (TS + 2) * (TS + 2); j += NT) {
-        const int c = j / ((TS + 2) * (TS + 2)), r = j % ((TS + 2) * (TS + 2));
-        const int yy = ty0 - 1 + r / (TS + 2), xx = tx0 - 1 + r % (TS + 2);
-        sx[c][r / (TS + 2)][r % (TS + 2)] =
-            (yy >= 0 && yy < H && xx >= 0 && xx < W) ? x[((size_t)b * CIN + c) * plane + (size_t)yy * W + xx] : 0.f;
-    }
-    for (int j = tid; j < COUT * TS * TS; j += NT) {
-        const int o = j / (TS * TS), r = j % (TS * TS);
-        const int yy = ty0 + r / TS, xx = tx0 + r % TS;
-        float g = 0.f;
-        if (yy < H && xx < W) {
-            const size_t idx = ((size_t)b * COUT + o) * plane + (size_t)yy * W + xx;
-            g = dy[idx];
-            if (RELU && !(yout[idx] > 0.f)) g = 0.f;
+    const int tiles_x = (W + TS - 1) / TS, tiles_img = tiles_x * ((H + TS - 1) / TS), ntiles = tiles_img * B;
+    // 32 -> 1 layer: the next tile's inputs are loaded into registers while
+    // the current one is summed (halo pixel r = tid + NT k, all CIN channels of
+    // it; G element tid + NT i).  1 -> 32 layer (32 G values per thread): each
+    // tile is staged directly, more CTAs per SM hiding the loads.  Zero
+    // padding; g masked by the ReLU.
+    constexpr bool PRE = CIN > 1;
+    constexpr int RX = (TS + 2) * (TS + 2), NR = (RX + NT - 1) / NT, NGL = COUT * TS * TS / NT;
+    static_assert(COUT * TS * TS % NT == 0, "whole G rounds");
+    float xr[NR][CIN], gr[NGL];
+    auto load = [&](int tile) {
+        const int b = tile / tiles_img, tr = tile - b * tiles_img;
+        const int ty0 = (tr / tiles_x) * TS, tx0 = (tr % tiles_x) * TS;
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            const int r = tid + k * NT;
+            const int yy = ty0 - 1 + r / (TS + 2), xx = tx0 - 1 + r % (TS + 2);
+            const bool in = r < RX && yy >= 0 && yy < H && xx >= 0 && xx < W;
+            const float *src = x + (size_t)b * CIN * plane + (in ? (size_t)yy * W + xx : 0);
+#pragma unroll
+            for (int c = 0; c < CIN; ++c) xr[k][c] = in ? __ldg(src + (size_t)c * plane) : 0.f;
         }
-        sg[o][r] = g;
-    }
-    __syncthreads();
-    const size_t nw = (size_t)COUT * CIN * 9;
-    float *out = part + (size_t)((blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (nw + COUT);
-    for (size_t e = tid; e < nw + COUT; e += NT) {
-        float s = 0.f;
-        if (e < nw) {
-            const int o = (int)(e / (CIN * 9)), c = (int)((e / 9) % CIN), t = (int)(e % 9);
-            for (int r = 0; r < TS * TS; ++r) s = fmaf(sg[o][r], sx[c][r / TS + t / 3][r % TS + t % 3], s);
+#pragma unroll
+        for (int i = 0; i < NGL; ++i) {
+            const int j = tid + i * NT;
+            const int o = j / (TS * TS), r = j % (TS * TS);
+            const int yy = ty0 + r / TS, xx = tx0 + r % TS;
+            float g = 0.f;
+            if (yy < H && xx < W) {
+                const size_t idx = ((size_t)b * COUT + o) * plane + (size_t)yy * W + xx;
+                g = __ldg(dy + idx);
+                if (RELU && !(__ldg(yout + idx) > 0.f)) g = 0.f;
+            }
+            gr[i] = g;
+        }
+    };
+    double acc[2] = {0.0, 0.0};
+    if (PRE && (int)blockIdx.x < ntiles) load(blockIdx.x);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        __syncthreads();  // the previous tile's reads of sg and sx are done
+        if constexpr (PRE) {
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                const int r = tid + k * NT;
+                if (r < RX)
+#pragma unroll
+                    for (int c = 0; c < CIN; ++c) (&sx[c][0][0])[r] = xr[k][c];
+            }
+#pragma unroll
+            for (int i = 0; i < NGL; ++i) {
+                const int j = tid + i * NT;
+                sg[j / (TS * TS)][j % (TS * TS)] = gr[i];
+            }
         } else {
-            const int o = (int)(e - nw);
-            for (int r = 0; r < TS * TS; ++r) s += sg[o][r];
+            const int b = tile / tiles_img, tr = tile - b * tiles_img;
+            const int ty0 = (tr / tiles_x) * TS, tx0 = (tr % tiles_x) * TS;
+            for (int j = tid; j < CIN * RX; j += NT) {
+                const int c = j / RX, r = j % RX;
+                const int yy = ty0 - 1 + r / (TS + 2), xx = tx0 - 1 + r % (TS + 2);
+                sx[c][r / (TS + 2)][r % (TS + 2)] =
+                    (yy >= 0 && yy < H && xx >= 0 && xx < W) ? x[((size_t)b * CIN + c) * plane + (size_t)yy * W + xx] : 0.f;
+            }
+            for (int j = tid; j < COUT * TS * TS; j += NT) {
+                const int o = j / (TS * TS), r = j % (TS * TS);
+                const int yy = ty0 + r / TS, xx = tx0 + r % TS;
+                float g = 0.f;
+                if (yy < H && xx < W) {
+                    const size_t idx = ((size_t)b * COUT + o) * plane + (size_t)yy * W + xx;
+                    g = dy[idx];
+                    if (RELU && !(yout[idx] > 0.f)) g = 0.f;
+                }
+                sg[o][r] = g;
+            }
         }
-        out[e] = s;
+        __syncthreads();
+        if (PRE && tile + (int)gridDim.x < ntiles) load(tile + gridDim.x);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int e = tid + k * NT;
+            if (e >= NE) continue;
+            float s = 0.f;
+            if (e < NW) {
+                const int o = e / (CIN * 9), c = (e / 9) % CIN, t = e % 9;
+                for (int r = 0; r < TS * TS; ++r) s = fmaf(sg[o][r], sx[c][r / TS + t / 3][r % TS + t % 3], s);
+            } else {
+                for (int r = 0; r < TS * TS; ++r) s += sg[e - NW][r];
+            }
+            acc[k] += (double)s;
+        }
     }
+    float *out = part + (size_t)blockIdx.x * NE;
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+        if (tid + k * NT < NE) out[tid + k * NT] = (float)acc[k];
 }
 
 // ---- tensor-core weight gradient of the 32 -> 32 layers -----------------------
@@ -320,38 +390,37 @@ __global__ void __launch_bounds__(NT) wgrad_kernel(const float *__restrict__ x, 
 // SBO 128) and its second pixel row one halo row further (LBO 512).  B
 // operand: G[py][o] = g[o][py][0 .. 7].  Both are carried as BF16 hi + lo
 // (products hi*hi + lo*hi + hi*lo: about 16 bits), summed in FP32.
+// Loads are spread over the lanes so that a warp instruction touches few
+// cache lines: five lanes per halo row (iy, c), lane q holding the pixels 2q
+// and 2q + 1 of the row's 10, which give the words of its three entries
+// (dx = 0 and 2: the pair (2q, 2q + 1); dx = 1: (2q + 1, 2q + 2), the second
+// value from lane q + 1); two lanes per G row (py, o), lane h holding the
+// pixels 4h .. 4h + 3 (one 16-byte load when W % 4 == 0).  Each value is
+// rounded to BF16 hi + lo once per word it enters.  The loads of the next tile are issued while the MMAs of the
+// current one run.
 constexpr int WG_IY = TC_OY + 3;              // 19 halo rows: the last is read only by the unused dy = 3 rows
 constexpr int WG_ROW = CW * 16;               // one halo row of the table: 32 channels x 16 bytes
 constexpr int WG_DX = WG_IY * WG_ROW;         // one tap column of the table
 constexpr int WG_XPL = 3 * WG_DX;             // the hi (or lo) table
 constexpr int WG_GPL = TC_OY * WG_ROW;        // the hi (or lo) G: 16 pixel rows x 32 channels x 16 bytes
-constexpr int WG_XF_LD = TC_NPX + 1;          // FP32 staging of the halo tile: channel stride (odd: banks)
-constexpr int WG_SMEM = 2 * WG_XPL + 2 * WG_GPL + (CW * WG_XF_LD + 4 * CW) * 4;
+constexpr int WG_XT = TC_IY * CW / 6 / 4;     // halo-row tasks (6 rows x 5 lanes) per warp: 24
+constexpr int WG_GT = TC_OY / 2;              // G tasks (16 channels x 2 pixel quads) per warp: 8
+constexpr int WG_SMEM = 2 * WG_XPL + 2 * WG_GPL;
 static_assert(WG_XPL % 128 == 0 && WG_GPL % 128 == 0, "operand alignment");
-
-__device__ __forceinline__ void split8(const float *v, uint4 &hi, uint4 &lo) {
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        h[j] = bf16x2_rn(v[2 * j], v[2 * j + 1]);
-        l[j] = bf16x2_rn(v[2 * j] - __uint_as_float(h[j] << 16), v[2 * j + 1] - __uint_as_float(h[j] & 0xffff0000u));
-    }
-    hi = make_uint4(h[0], h[1], h[2], h[3]);
-    lo = make_uint4(l[0], l[1], l[2], l[3]);
-}
+static_assert(TC_IX == 10 && TC_OX == 8, "a halo row is 10 values, an entry 8");
+static_assert(TC_IY * CW == 4 * 6 * WG_XT, "the halo rows split into 6-row tasks over 4 warps");
+static_assert(3 * (WG_SMEM + 2048) <= 228 * 1024, "three CTAs per SM (1 KB static, 1 KB reserved each)");
 
 // part[blockIdx.x][COUT*CIN*9 + COUT] (as wgrad_kernel's), the grid = the
-// persistent CTAs (each takes at least one tile).  128 threads.  A
-// completion wait that runs out sets *err and the CTA stops.
+// persistent CTAs (each takes at least one tile).  128 threads, three CTAs
+// per SM.  A completion wait that runs out sets *err and the CTA stops.
 template <bool RELU>
-__global__ void __launch_bounds__(128) wgrad32_tc_kernel(const float *__restrict__ x, const float *__restrict__ dy,
-                                                         const float *__restrict__ yout, float *__restrict__ part,
-                                                         int B, int H, int W, int *err) {
+__global__ void __launch_bounds__(128, 3) wgrad32_tc_kernel(const float *__restrict__ x, const float *__restrict__ dy,
+                                                            const float *__restrict__ yout, float *__restrict__ part,
+                                                            int B, int H, int W, int *err) {
     extern __shared__ __align__(1024) unsigned char gsm[];
-    unsigned char *sX = gsm;                                       // [hi | lo][dx][iy][c][8 pixels]
-    unsigned char *sG = gsm + 2 * WG_XPL;                          // [hi | lo][py][o][8 pixels]
-    float *sXf = reinterpret_cast<float *>(gsm + 2 * WG_XPL + 2 * WG_GPL);  // [c][iy][ix]
-    float *sBias = sXf + CW * WG_XF_LD;                            // [warp][o]
+    unsigned char *sX = gsm;                                      // [hi | lo][dx][iy][c][8 pixels]
+    unsigned char *sG = gsm + 2 * WG_XPL;                         // [hi | lo][py][o][8 pixels]
     __shared__ uint64_t bar;
     __shared__ uint32_t tbase;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -370,57 +439,98 @@ __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const float *__restrict
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t taddr = tbase;
-    float bsum = 0.f;  // this thread's share of dB[o], o = lane
-    uint32_t phase = 0;
-    bool first = true, ok = true;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+
+    // registers of one tile.  Halo rows: task t of this warp = rows
+    // 6 (warp + 4 t) + r6, r6 = lane / 5 (lanes 30, 31 idle), row R -> (iy, c) =
+    // (R / 32, R % 32); lane q = lane % 5 holds pixels 2q, 2q + 1.  G rows: task
+    // t = row py = (warp >> 1) + 2 t, channel o = 16 (warp & 1) + lane / 2, lane
+    // h = lane % 2 holds pixels 4h .. 4h + 3.  Zero outside the image.
+    const int q = lane % 5, r6 = lane / 5;
+    const int o_g = 16 * (warp & 1) + (lane >> 1), h_g = lane & 1;
+    const bool vec = (W & 3) == 0;  // 16-byte G loads (every row start is then 16-byte aligned)
+    float xa[WG_XT], xb[WG_XT], dv[WG_GT][4], yv[WG_GT][4];
+    auto load = [&](int tile) {
         const int b = tile / tiles_img, tr = tile - b * tiles_img;
         const int ty0 = (tr / tiles_x) * TC_OY, tx0 = (tr % tiles_x) * TC_OX;
-        // FP32 halo tile of x (zero padding)
-        for (int j = tid; j < CW * TC_NPX; j += 128) {
-            const int c = j / TC_NPX, px = j - c * TC_NPX, iy = px / TC_IX, ix = px - iy * TC_IX;
-            const int yy = ty0 - 1 + iy, xx = tx0 - 1 + ix;
-            sXf[c * WG_XF_LD + px] =
-                (yy >= 0 && yy < H && xx >= 0 && xx < W) ? __ldg(x + ((size_t)b * CW + c) * plane + (size_t)yy * W + xx)
-                                                         : 0.f;
+        const int xx = tx0 - 1 + 2 * q;
+#pragma unroll
+        for (int t = 0; t < WG_XT; ++t) {
+            const int R = 6 * (warp + 4 * t) + r6, iy = R >> 5, c = R & 31;
+            const int yy = ty0 - 1 + iy;
+            const bool rowok = lane < 30 && yy >= 0 && yy < H;
+            const float *src = x + ((size_t)b * CW + c) * plane + (size_t)(rowok ? yy : 0) * W;
+            xa[t] = (rowok && xx >= 0 && xx < W) ? __ldg(src + xx) : 0.f;
+            xb[t] = (rowok && xx + 1 < W) ? __ldg(src + xx + 1) : 0.f;  // xx + 1 >= 0
         }
-        // G: entry (py, o) = (warp + 4 k, lane), 8 pixels, hi and lo; g = dY,
-        // masked by Y > 0 after a ReLU
+        const int gx = tx0 + 4 * h_g;
 #pragma unroll
-        for (int k = 0; k < TC_OY / 4; ++k) {
-            const int py = warp + 4 * k, yy = ty0 + py;
-            float g[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int xx = tx0 + j;
-                float v = 0.f;
-                if (yy < H && xx < W) {
-                    const size_t idx = ((size_t)b * CW + lane) * plane + (size_t)yy * W + xx;
-                    v = __ldg(dy + idx);
-                    if (RELU && !(__ldg(yout + idx) > 0.f)) v = 0.f;
+        for (int t = 0; t < WG_GT; ++t) {
+            const int yy = ty0 + (warp >> 1) + 2 * t;
+            const size_t base = ((size_t)b * CW + o_g) * plane + (size_t)(yy < H ? yy : 0) * W + gx;
+            if (vec && yy < H && gx < W) {  // W % 4 == 0: the quad lies in the row
+                const float4 d = __ldg(reinterpret_cast<const float4 *>(dy + base));
+                dv[t][0] = d.x, dv[t][1] = d.y, dv[t][2] = d.z, dv[t][3] = d.w;
+                if (RELU) {
+                    const float4 y = __ldg(reinterpret_cast<const float4 *>(yout + base));
+                    yv[t][0] = y.x, yv[t][1] = y.y, yv[t][2] = y.z, yv[t][3] = y.w;
                 }
-                g[j] = v;
-                bsum += v;
-            }
-            uint4 hi, lo;
-            split8(g, hi, lo);
-            unsigned char *d = sG + py * WG_ROW + lane * 16;
-            *reinterpret_cast<uint4 *>(d) = hi;
-            *reinterpret_cast<uint4 *>(d + WG_GPL) = lo;
-        }
-        __syncthreads();  // the staged halo tile is complete
-        // table entries (dx, iy, c), iy = 0..17, hi and lo
-        for (int j = tid; j < 3 * TC_IY * CW; j += 128) {
-            const int c = j % CW, r = j / CW, dx = r % 3, iy = r / 3;
-            const float *src = sXf + c * WG_XF_LD + iy * TC_IX + dx;
-            float v[8];
+            } else {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = src[q];
-            uint4 hi, lo;
-            split8(v, hi, lo);
-            unsigned char *d = sX + dx * WG_DX + iy * WG_ROW + c * 16;
-            *reinterpret_cast<uint4 *>(d) = hi;
-            *reinterpret_cast<uint4 *>(d + WG_XPL) = lo;
+                for (int j = 0; j < 4; ++j) {
+                    const bool in = yy < H && gx + j < W;
+                    dv[t][j] = in ? __ldg(dy + base + j) : 0.f;
+                    if (RELU) yv[t][j] = in ? __ldg(yout + base + j) : 1.f;
+                }
+            }
+        }
+    };
+
+    __shared__ float sBias[2][CW];
+    float bsum = 0.f;  // this thread's share of dB[o_g]
+    uint32_t phase = 0;
+    bool first = true, ok = true;
+    if ((int)blockIdx.x < ntiles) load(blockIdx.x);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        // (the MMAs of the previous tile have completed: the operands are free)
+#pragma unroll
+        for (int t = 0; t < WG_XT; ++t) {
+            const float a = xa[t], bv = xb[t];
+            const float nx = __shfl_down_sync(0xffffffffu, a, 1);  // pixel 2q + 2 (lane q + 1 of the row)
+            const uint32_t he = bf16x2_rn(a, bv);
+            const uint32_t le = bf16x2_rn(a - __uint_as_float(he << 16), bv - __uint_as_float(he & 0xffff0000u));
+            const uint32_t ho = bf16x2_rn(bv, nx);
+            const uint32_t lo = bf16x2_rn(bv - __uint_as_float(ho << 16), nx - __uint_as_float(ho & 0xffff0000u));
+            const int R = 6 * (warp + 4 * t) + r6;
+            unsigned char *e = sX + (R >> 5) * WG_ROW + (R & 31) * 16;
+            if (lane < 30) {
+                if (q < 4) {  // dx = 0 and dx = 1, word q
+                    *reinterpret_cast<uint32_t *>(e + 4 * q) = he;
+                    *reinterpret_cast<uint32_t *>(e + WG_XPL + 4 * q) = le;
+                    *reinterpret_cast<uint32_t *>(e + WG_DX + 4 * q) = ho;
+                    *reinterpret_cast<uint32_t *>(e + WG_DX + WG_XPL + 4 * q) = lo;
+                }
+                if (q > 0) {  // dx = 2, word q - 1
+                    *reinterpret_cast<uint32_t *>(e + 2 * WG_DX + 4 * (q - 1)) = he;
+                    *reinterpret_cast<uint32_t *>(e + 2 * WG_DX + WG_XPL + 4 * (q - 1)) = le;
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < WG_GT; ++t) {
+            uint32_t hw[2], lw[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                // g = dY, masked by Y > 0 after a ReLU
+                const float g0 = (RELU && !(yv[t][2 * k] > 0.f)) ? 0.f : dv[t][2 * k];
+                const float g1 = (RELU && !(yv[t][2 * k + 1] > 0.f)) ? 0.f : dv[t][2 * k + 1];
+                bsum += g0;
+                bsum += g1;
+                hw[k] = bf16x2_rn(g0, g1);
+                lw[k] = bf16x2_rn(g0 - __uint_as_float(hw[k] << 16), g1 - __uint_as_float(hw[k] & 0xffff0000u));
+            }
+            unsigned char *e = sG + ((warp >> 1) + 2 * t) * WG_ROW + o_g * 16 + 8 * h_g;
+            *reinterpret_cast<uint2 *>(e) = make_uint2(hw[0], hw[1]);
+            *reinterpret_cast<uint2 *>(e + WG_GPL) = make_uint2(lw[0], lw[1]);
         }
         tc::fence_proxy_async();
         tc::fence_before_sync();
@@ -443,6 +553,8 @@ __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const float *__restrict
             tc::mma_commit(&bar);
         }
         first = false;
+        // the next tile's loads (registers only) overlap the MMAs
+        if (tile + (int)gridDim.x < ntiles) load(tile + gridDim.x);
         ok = tc::mbar_wait(&bar, phase);
         if (!ok) {
             if (tid == 0) atomicExch(err, 1);
@@ -474,21 +586,40 @@ __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const float *__restrict
     } else if (first) {
         for (size_t e = tid; e < nw; e += 128) out[e] = 0.f;
     }
-    sBias[warp * CW + lane] = bsum;
+    // dB[o]: the two lanes of channel o in each of its two warps, added as
+    // (h0 + h1) of warp o / 16, then + (h0 + h1) of warp o / 16 + 2
+    bsum += __shfl_xor_sync(0xffffffffu, bsum, 1);
+    if (h_g == 0) sBias[warp >> 1][o_g] = bsum;
     __syncthreads();
-    if (tid < CW) out[nw + tid] = (sBias[tid] + sBias[CW + tid]) + (sBias[2 * CW + tid] + sBias[3 * CW + tid]);
+    if (tid < CW) out[nw + tid] = sBias[0][tid] + sBias[1][tid];
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(taddr, 128);
 }
 
-// Fixed-order reduction of per-block partials: out[e] = sum_k part[k][e].
-__global__ void reduce_parts_kernel(const float *__restrict__ part, int nblocks, int n, float *__restrict__ out) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
+
+// Fixed-order reduction of per-CTA partials: out[e] = sum_k part[k][e] in
+// FP64.  A block (1024 threads) takes 32 parameters (one per lane); its warp
+// w adds the partials k = w, w + 32, ... in order, and the 32 warp sums are
+// added in warp order (the result depends only on nblocks, not on
+// scheduling).
+__global__ void __launch_bounds__(1024) reduce_parts_kernel(const float *__restrict__ part, int nblocks, int n,
+                                                            float *__restrict__ out) {
+    __shared__ double red[32][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, e = blockIdx.x * 32 + lane;
     double s = 0.0;
-    for (int k = 0; k < nblocks; ++k) s += part[(size_t)k * n + e];
-    out[e] = (float)s;
+    if (e < n) {
+#pragma unroll 4
+        for (int k = w; k < nblocks; k += 32) s += part[(size_t)k * n + e];
+    }
+    red[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && e < n) {
+        double t = 0.0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) t += red[j][lane];
+        out[e] = (float)t;
+    }
 }
 
 __global__ void prep_input_kernel(const float *__restrict__ f, float *__restrict__ x, size_t n) {
@@ -643,19 +774,32 @@ fe_status ensure_capacity(fe_cnn *n, size_t pix, size_t parts) {
 template <int CIN, int COUT>
 constexpr size_t conv_smem() { return sizeof(float) * ((size_t)CIN * 9 * COUT + (size_t)CIN * (TS + 2) * (TS + 2)); }
 template <int CIN, int COUT>
-constexpr size_t wgrad_smem() { return sizeof(float) * ((size_t)COUT * TS * TS + (size_t)CIN * (TS + 2) * (TS + 2)); }
+constexpr size_t wgrad_smem() { return sizeof(float) * ((size_t)COUT * (TS * TS + 1) + (size_t)CIN * (TS + 2) * (TS + 2)); }
 
-// CTAs of the tensor-core weight gradient: two per SM (98 KB of shared
+// CTAs of the tensor-core weight gradient: three per SM (73.5 KB of shared
 // memory each), at most one per 16 x 8 tile
 int wgrad32_ctas(const fe_cnn *n, int B, int H, int W) {
     const long long tiles = (long long)((W + TC_OX - 1) / TC_OX) * ((H + TC_OY - 1) / TC_OY) * B;
-    return (int)std::max<long long>(1, std::min<long long>(tiles, 2LL * n->sms));
+    return (int)std::max<long long>(1, std::min<long long>(tiles, 3LL * n->sms));
 }
 
-// blocks of partial weight-gradient sums a loss_grad needs room for
+// CTAs of the CUDA-core weight gradient (1 -> 32 and 32 -> 1 layers): as
+// many as are resident at once, at most one per 16 x 16 tile
+template <int CIN, int COUT, bool RELU>
+int wgrad_ctas(const fe_cnn *n, int B, int H, int W) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, wgrad_kernel<CIN, COUT, RELU>, NT, wgrad_smem<CIN, COUT>()) !=
+            cudaSuccess ||
+        occ < 1)
+        occ = 1;
+    const long long tiles = (long long)((W + TS - 1) / TS) * ((H + TS - 1) / TS) * B;
+    return (int)std::max<long long>(1, std::min<long long>(tiles, (long long)occ * n->sms));
+}
+
+// CTAs of partial weight-gradient sums a loss_grad needs room for
 size_t grad_parts(const fe_cnn *n, int B, int H, int W) {
-    const size_t nb16 = (size_t)((W + TS - 1) / TS) * ((H + TS - 1) / TS) * B;
-    return std::max(nb16, (size_t)wgrad32_ctas(n, B, H, W));
+    return (size_t)std::max({wgrad_ctas<1, CW, true>(n, B, H, W), wgrad_ctas<CW, 1, false>(n, B, H, W),
+                             wgrad32_ctas(n, B, H, W)});
 }
 
 template <int CIN, int COUT, bool RELU>
@@ -675,7 +819,6 @@ cudaError_t cnn_prepare() {
     FE_SMEM((conv3x3_kernel<1, CW, false>), (conv_smem<1, CW>()));
     FE_SMEM((conv3x3_kernel<CW, CW, false>), (conv_smem<CW, CW>()));
     FE_SMEM((wgrad_kernel<CW, 1, false>), (wgrad_smem<CW, 1>()));
-    FE_SMEM((wgrad_kernel<CW, CW, true>), (wgrad_smem<CW, CW>()));
     FE_SMEM((wgrad_kernel<1, CW, true>), (wgrad_smem<1, CW>()));
     FE_SMEM((conv32_tc_kernel<true>), TC_SMEM);
     FE_SMEM((wgrad32_tc_kernel<true>), WG_SMEM);
@@ -704,17 +847,17 @@ fe_status forward(fe_cnn *n, const float *f_dev, int B, int H, int W) {
 
 template <int CIN, int COUT, bool RELU>
 fe_status wgrad(fe_cnn *n, const float *x, const float *dy, const float *y, int B, int H, int W, int layer) {
-    const dim3 grid((W + TS - 1) / TS, (H + TS - 1) / TS, B);
-    int nb = grid.x * grid.y * grid.z;
+    int nb;
     const int ne = COUT * CIN * 9 + COUT;
     if constexpr (CIN == CW && COUT == CW) {
         nb = wgrad32_ctas(n, B, H, W);
         wgrad32_tc_kernel<RELU><<<nb, 128, WG_SMEM, n->s>>>(x, dy, y, n->part, B, H, W, n->tc_err);
     } else {
-        wgrad_kernel<CIN, COUT, RELU><<<grid, NT, wgrad_smem<CIN, COUT>(), n->s>>>(x, dy, y, n->part, H, W);
+        nb = wgrad_ctas<CIN, COUT, RELU>(n, B, H, W);
+        wgrad_kernel<CIN, COUT, RELU><<<nb, NT, wgrad_smem<CIN, COUT>(), n->s>>>(x, dy, y, n->part, B, H, W);
     }
     // weights then bias of this layer are contiguous in the parameter vector
-    reduce_parts_kernel<<<(ne + 255) / 256, 256, 0, n->s>>>(n->part, nb, ne, n->g + n->woff[layer]);
+    reduce_parts_kernel<<<(ne + 31) / 32, 1024, 0, n->s>>>(n->part, nb, ne, n->g + n->woff[layer]);
     CNN_CUDA(n, cudaGetLastError());
     return FE_OK;
 }
