@@ -760,7 +760,8 @@ __global__ void __launch_bounds__(NT, FMT != 2 ? 3 : 2) tc_tile_kernel(const KPa
                 tc::fence_before_sync();
                 tc::fence_proxy_async();
                 __syncthreads();
-                if (tid == 0) {
+                // issued by warp 1, which has no vertical col2im row below
+                if (tid == 32) {
                     tc::fence_after_sync();
     #pragma unroll
                     for (int ks = 0; ks < C::KADJ / C::KSTEP; ++ks)
