@@ -8,8 +8,8 @@ each activation carried as a BF16 hi + lo pair (about 2^-17 relative), so
 the network output differs from the FP64 reference by ~1e-5 relative per
 layer; 1e-4 of max|d| covers five layers, and u0 = f e^d inherits that
 absolute error of d as a relative error.
-Gradients are FP32 sums over all pixels of the batch (per-block partials
-reduced in FP64): 1e-3 of max|grad| covers the accumulation-order
+Gradients are FP32 sums over all pixels of the batch (per-CTA partials
+reduced in FP64 in a fixed order): 1e-3 of max|grad| covers the accumulation-order
 differences of sums of ~1e3 terms of both signs.
 """
 import numpy as np
@@ -103,6 +103,28 @@ def test_loss_and_gradient_parity_128(fe):
         gl, grl = g[off:off + n], gr[off:off + n]
         assert np.max(np.abs(gl - grl)) <= 2e-3 * np.max(np.abs(grl)), (co, ci)
         off += n
+
+
+def test_gradients_repeat_bit_for_bit(fe):
+    """The weight gradients are per-CTA partial sums (persistent CTAs, each
+    taking several tiles) reduced in FP64 in a fixed order, so the same batch
+    gives the same loss and gradient bit for bit: twice on one network and
+    once on a second network with the same parameters.  Two shapes: crops of
+    128 x 128 (more tiles than CTAs; 16-byte loads of the gradient planes)
+    and an odd width with ragged 16 x 8 and 16 x 16 edge tiles."""
+    import torch
+    for (B, H, W), seed in (((8, 128, 128), 21), ((3, 50, 71), 22)):
+        f, u = _batch(B, H, W, seed)
+        fd, ud = torch.from_numpy(f).cuda(), torch.from_numpy(u).cuda()
+        net = fe.CNN(seed=5)
+        l0, g0 = net.loss_grad(fd, ud)
+        l1, g1 = net.loss_grad(fd, ud)
+        other = fe.CNN(seed=9)
+        other.set_params(net.get_params())
+        l2, g2 = other.loss_grad(fd, ud)
+        assert l0 == l1 == l2
+        assert np.array_equal(g0, g1) and np.array_equal(g0, g2)
+        assert np.all(np.isfinite(g0)) and np.max(np.abs(g0)) > 0
 
 
 def test_params_roundtrip_and_training_reduces_loss(fe):
