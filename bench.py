@@ -55,9 +55,9 @@ FLOP_PER_PIXEL_TRIAL = 2 * 48 * 49 * 2  # forward + adjoint bank, 2 flop per MAC
 # (one step: 300 iterations of 24 x 512^2 + 24 x 256^2), divided by the
 # step's pixel-trials (profiles/persistent_trial_kernels_24x512.md)
 TRAFFIC_PER_PIXEL_TRIAL = {("fp32", "variant"): 5.741133e+10 / 2431909888,
-                           ("bf16", "variant"): 6.095041e+10 / 2450784256,
-                           ("bf16r", "variant"): 6.096919e+10 / 2450325504,
-                           ("tf32", "variant"): 5.993423e+10 / 2428305408,
+                           ("bf16", "variant"): 6.098123e+10 / 2450784256,
+                           ("bf16r", "variant"): 6.099123e+10 / 2450325504,
+                           ("tf32", "variant"): 5.992256e+10 / 2428305408,
                            ("fp32", "combined"): 5.818879e+10 / 2471952384}
 METRIC = "Mpixel*iter/s of fused iPiano step"
 
