@@ -381,7 +381,14 @@ FE_API fe_status fe_gradient_noalloc(const float *u, float *g, double *F, int H,
  * accumulation are FP32; training uses Adam (beta1 0.9, beta2 0.999, eps 1e-8).
  * Parameter vector: for each layer, W[cout][cin][3][3] then b[cout].
  * Batches are B images of H x W, row-major, consecutive ("any" pointers).
- * All calls synchronise the stream given at creation. */
+ * All calls synchronise the stream given at creation.  Gradients are sums of
+ * per-CTA partials added in FP64 in a fixed order, so the same inputs and
+ * parameters give the same loss and gradient bit for bit on a given device.
+ * Errors: FE_EINVAL (NULL net or required pointer, B, H or W < 1), FE_ENOMEM
+ * (an allocation at creation), FE_ECUDA (a CUDA call failed, including
+ * growing the activation buffers), FE_ETIMEOUT (a tensor-core completion
+ * wait ran out: the results of that call are not valid); the message is in
+ * fe_cnn_last_error(net). */
 typedef struct fe_cnn fe_cnn;
 
 /* Create with seeded He-normal weights (last layer scaled by 0.1). */
