@@ -17,7 +17,7 @@ buffers and cuts crops):
    first accepted iterate with H <= H* = H_plain + eps (H(f) - H_plain)
    (fe_solve_to_energy).  The energy H(u0) is checked first: if it is not
    below H(f), the solve starts from f (plain iPiano stays the fallback and
-   the judge).  Runs that stop on the relative-change rule alone are also
+   the measure of the CNN's error).  Runs that stop on the relative-change rule alone are also
    reported (their energies can differ).
 """
 from __future__ import annotations
